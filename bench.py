@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Throughput of the AFMM product on GB300 (one JSON line on stdout).
+
+Workload (default): case A, n = 8192, X FP32 U(-1,1) with density 0.7,
+Y Poisson(3) clipped to [0,16] stored as FP8 e4m3; Z FP32 at the FP32
+target (relative Frobenius error <= 1e-6 against the FP64 oracle).  One
+step = one full product through the C ABI, every conversion included.
+
+Metric: effective TFLOP/s = 2 n^3 / time per product (whole job: summed
+over ranks; each rank computes its own independent product, no collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl afmm|reference]
+
+The reference arm (--impl reference) times the CPU oracle (repeated
+addition in FP64, Sec. 2) on the host cores on a bounded row sample of the
+same workload, in the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("effective TFLOP/s (2n^3) split-BF16 vs plain FP32 at rel err "
+          "<=1e-6; % roofline")
+FFMA_PER_SM_PER_CLK = 128          # FP32 lanes per SM (4 SMSPs x 32)
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+                "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_instance(workload, n):
+    import afmm_inputs as W
+    return W.make(workload, n=n)
+
+
+def oracle_rows_timed(inst, budget_s, min_rows=1):
+    """Oracle on whole batches of rows until ~budget_s seconds have passed."""
+    import numpy as np
+    from oracle import afmm_case_a, afmm_case_b, oracle_threads
+    fn = afmm_case_a if inst.case == "A" else afmm_case_b
+    thr = oracle_threads()
+    n = inst.n
+    rng = np.random.default_rng(1234)
+    order = rng.permutation(n)
+    done, rows_out, Z_out = 0, [], []
+    t0 = time.perf_counter()
+    while done < n:
+        batch = np.sort(order[done:done + thr])
+        Zr, _ = fn(inst.X, inst.Y, batch)
+        rows_out.append(batch)
+        Z_out.append(Zr)
+        done += batch.size
+        if time.perf_counter() - t0 >= budget_s and done >= min_rows:
+            break
+    el = time.perf_counter() - t0
+    rows = np.concatenate(rows_out)
+    return rows, np.concatenate(Z_out), el, thr
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    inst = make_instance(args.workload, args.n)
+    n = inst.n
+    from oracle import oracle_threads
+    thr = oracle_threads()
+    per_step_rows = thr
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rows, _, el, _ = oracle_rows_timed(inst, 0.0, min_rows=per_step_rows)
+        if i >= args.warmup:
+            times.append((el, rows.size))
+    tot_t = sum(t for t, _ in times)
+    tot_rows = sum(r for _, r in times)
+    value = 2.0 * n * n * tot_rows / tot_t / 1e12 if tot_t > 0 else 0.0
+    sample = (f"{per_step_rows} rows of {n} per step (each row = n^2 "
+              f"repeated-addition terms), scaled to 2n^3 per product")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value,
+        "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "case": inst.case,
+                   "x": inst.x_dtype, "y": inst.y_dtype, "z": inst.z_dtype},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": thr,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def traffic_from_profile(kernel_tag, workload):
+    """Bytes per launch from the committed ncu summary, if it still matches
+    the kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    src = {"simt_gemm": "simt_gemm.cu", "tc_gemm": "tc_gemm.cu"}.get(kernel_tag)
+    vals = {}
+    with open(path) as f:
+        for ln in f:
+            if ":" in ln:
+                k, v = ln.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if src:
+        h = hashlib.sha256(open(os.path.join(
+            ROOT, "paper_1308_2400_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
+        if vals.get("source_sha256_16") != h:
+            return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_afmm(args):
+    import numpy as np
+    import torch
+    from paper_1308_2400_gb300 import Plan, make_desc
+    from paper_1308_2400_gb300.afmm import VARIANT_NAMES
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    peaks, peak_src = load_peaks()
+
+    inst = make_instance(args.workload, args.n)
+    n = inst.n
+    Xs = inst.x_store if inst.x_store is not None else inst.X
+    Ys = inst.y_store if inst.y_store is not None else inst.Y
+    X = torch.from_numpy(np.ascontiguousarray(Xs)).cuda()
+    Y = torch.from_numpy(np.ascontiguousarray(Ys)).cuda()
+    zt = {"f32": torch.float32, "f64": torch.float64, "i32": torch.int32}[inst.z_dtype]
+    Z = torch.empty((n, n), dtype=zt, device="cuda")
+
+    from oracle import realised_parameters
+    prm = realised_parameters(inst.X, inst.Y, inst.case)
+
+    def desc(variant):
+        return make_desc(n, inst.case, inst.x_dtype, inst.y_dtype,
+                         inst.z_dtype, inst.target, variant=variant,
+                         d1=prm["d1"], d2=prm["d2"], mu_prime=prm["mu_prime"])
+
+    stream = torch.cuda.Stream()
+
+    def timed(plan, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                plan(X, Y, Z, stream)
+            plan.sync(stream)
+            plan.enable_kernel_timing(True)
+            c0 = plan.counters()
+            barrier(ws)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                plan(X, Y, Z, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier(ws)
+            plan.sync(stream)
+            c1 = plan.counters()
+            plan.enable_kernel_timing(False)
+        ms = e0.elapsed_time(e1) / steps
+        kms = c1["timed_ms"] / max(1, c1["timed_launches"])
+        launches = c1["kernel_launches"] - c0["kernel_launches"]
+        return ms, kms, launches, c1["main_kernel_ctas"]
+
+    plan = Plan(desc(args.variant))
+    vname = VARIANT_NAMES.get(plan.info["variant"], "?")
+    slices = plan.info["slices"]
+    clk = ClockSampler(dev) if rank == 0 else None
+    if clk:
+        clk.start()
+    ms, kms, launches, ctas = timed(plan, args.steps, args.warmup)
+    clocks = clk.stop() if clk else None
+    ms_max = max_over_ranks(ws, ms)
+    flops = 2.0 * n ** 3
+    value = ws * flops / (ms_max * 1e-3) / 1e12
+
+    # Roofline of the dominant (product) kernel.
+    tc = vname.startswith("tc_")
+    if tc:
+        alg = slices * flops
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_src": f"bf16 sustained, {peak_src}"}
+        tag = "tc_gemm"
+    else:
+        alg = flops
+        sm_mhz = SM_MAX_MHZ
+        peak = SMS * FFMA_PER_SM_PER_CLK * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s",
+                "peak_src": f"FP32 FFMA {SMS} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
+        tag = "simt_gemm"
+    achieved = alg / (kms * 1e-3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": traffic_from_profile(tag, args.workload),
+                 "kernel": tag, "kernel_ms": kms, "ctas": ctas,
+                 "algorithmic_flops_per_launch": alg})
+
+    # Plain FP32 CUDA-core form on the same data, when the main form differs.
+    plain = None
+    if rank == 0 and vname != "simt_f32" and inst.target == "fp32" and not args.quick:
+        p2 = Plan(desc(0))
+        ms2, kms2, _, _ = timed(p2, max(2, args.steps // 2), 2)
+        plain = {"variant": "simt_f32", "value": flops / (ms2 * 1e-3) / 1e12,
+                 "ms_per_step": ms2, "kernel_ms": kms2}
+        p2.close()
+
+    # End to end through the C ABI with pinned host buffers: copies in,
+    # product, copy out, every step.
+    e2e = None
+    if not args.quick:
+        Xh = torch.from_numpy(np.ascontiguousarray(Xs)).pin_memory()
+        Yh = torch.from_numpy(np.ascontiguousarray(Ys)).pin_memory()
+        Zh = torch.empty((n, n), dtype=zt).pin_memory()
+        ph = Plan(desc(args.variant))
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                ph(Xh, Yh, Zh, stream)
+            barrier(ws)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ksteps = max(2, args.steps // 2)
+            for _ in range(ksteps):
+                ph(Xh, Yh, Zh, stream)
+            torch.cuda.synchronize()
+            t_e2e = (time.perf_counter() - t0) / ksteps
+        t_e2e = max_over_ranks(ws, t_e2e)
+        e2e = {"value": ws * flops / t_e2e / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(Xh.nbytes + Yh.nbytes),
+               "d2h_bytes_per_step": int(Zh.nbytes), "ms_per_step": 1e3 * t_e2e}
+        ph.close()
+
+    # CPU baseline: the oracle on a bounded row sample, rank 0 at N = 1;
+    # the same rows give the accuracy check of the GPU result.
+    cpu = None
+    acc = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rows, Zr, el, thr = oracle_rows_timed(inst, args.cpu_seconds)
+        cpu = {"value": 2.0 * n * n * rows.size / el / 1e12, "unit": "TFLOP/s",
+               "cores": thr, "kind": "oracle",
+               "sample": f"{rows.size} of {n} rows of Z, repeated addition in "
+                         f"FP64 (Sec. 2 loops), {el:.1f} s; scaled to 2n^3"}
+        Zg = Z.cpu().numpy()[rows].astype(np.float64)
+        num = float(np.linalg.norm(Zg - Zr))
+        den = float(np.linalg.norm(Zr))
+        acc = {"rel_fro_err_vs_oracle": num / den if den else 0.0,
+               "rows_checked": int(rows.size)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if tc else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "case": inst.case,
+                       "x": inst.x_dtype, "y": inst.y_dtype, "z": inst.z_dtype,
+                       "variant": vname, "slices": slices,
+                       "d1": prm["d1"], "d2": prm["d2"],
+                       "mu_prime": prm["mu_prime"],
+                       "l2": "inputs larger than L2 (X 256 MiB, Z 256 MiB)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches) * ws, "clocks": clocks,
+            "accuracy": acc, "plain_fp32": plain,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="afmm", choices=["afmm", "reference"])
+    ap.add_argument("--workload", default="caseA_n8192_e4m3")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the plain-FP32 and end-to-end legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_afmm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

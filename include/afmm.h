@@ -1,0 +1,231 @@
+/*
+ * afmm.h -- C ABI of the GB300 (sm_103a) AFMM library.
+ *
+ * The library computes the AFMM product of Singh, Chakraborty and Mallick,
+ * "An Adaptable Fast Matrix Multiplication (AFMM) Algorithm" (arXiv
+ * 1308.2400), Sec. 2: Z = X * Y for two dense n x n matrices where one
+ * factor holds non-negative integer "Rep-factors" and the other real "Base"
+ * values, zero Base values skipped.
+ *   Case A: X real (Base), Y integer Rep-factors  (Sec. 2, Case-A listing).
+ *   Case B: X integer Rep-factors, Y real (Base)  (Sec. 2, Case-B listing).
+ * The paper forms each term Rep * Base by adding Base Rep times; the result
+ * is the ordinary product (Sec. 2.1 Point 1), which the GPU forms with
+ * exact multiply-add or tensor-core products (see each variant below).
+ *
+ * Conventions for every entry point
+ *  - Matrices are dense and row-major (Sec. 2 recommends the "adjacency
+ *    matrix", i.e. dense, storage).  Leading dimensions count elements.
+ *  - Z is overwritten (the paper starts Z at zero, Sec. 2).
+ *  - X, Y, Z may be device pointers or host pointers (pageable or pinned);
+ *    the library asks the CUDA runtime which.  Host buffers are staged
+ *    through device buffers the plan owns: the call copies X and Y in,
+ *    computes, copies Z out and synchronises the stream before returning.
+ *    With device pointers the call is asynchronous on `stream`.
+ *  - The caller owns X, Y, Z.  A plan owns its workspace unless the caller
+ *    lends one (afmm_plan_set_workspace).
+ *  - Errors are returned as afmm_status, never thrown.  Errors found by a
+ *    kernel (a negative or non-integer Rep-factor, a bounded wait that ran
+ *    out) are written to the plan's device status word and returned by the
+ *    next afmm_plan_sync on that plan.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.
+ */
+#ifndef AFMM_H
+#define AFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AFMM_OK = 0,
+    AFMM_ERR_INVALID_ARG = 1,     /* bad pointer, size, dtype or enum value */
+    AFMM_ERR_UNSUPPORTED = 2,     /* valid request this library cannot serve */
+    AFMM_ERR_NEGATIVE_REP = 3,    /* a Rep-factor is negative (Sec. 2 types) */
+    AFMM_ERR_OVERFLOW_RISK = 4,   /* exact target could leave the int32 range */
+    AFMM_ERR_OOM = 5,             /* device or host allocation failed */
+    AFMM_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+    AFMM_ERR_TIMEOUT = 7,         /* a bounded device-side wait ran out */
+    AFMM_ERR_NO_DEVICE = 8,       /* no usable CUDA device */
+    AFMM_ERR_NONINTEGER_REP = 9   /* a Rep-factor is not an integer */
+} afmm_status;
+
+/* Which factor holds the Rep-factors (Sec. 2). */
+typedef enum { AFMM_CASE_A = 0, AFMM_CASE_B = 1 } afmm_case;
+
+/* Element types.  AFMM_E4M3 is FP8 e4m3 (OCP, "fn"); it holds the integers
+ * 0..16 exactly.  Rep-factor matrices may be I32, I8, U8, E4M3, BF16 or F32
+ * (integral values); real matrices F64, F32 or BF16; an exact product also
+ * accepts an I8 or I32 Base matrix. */
+typedef enum {
+    AFMM_F64 = 0, AFMM_F32 = 1, AFMM_BF16 = 2, AFMM_E4M3 = 3,
+    AFMM_I32 = 4, AFMM_I8 = 5, AFMM_U8 = 6
+} afmm_dtype;
+
+/* Accuracy the product must reach against the exact product:
+ *   FP32  relative Frobenius error <= 1e-6, Z F32;
+ *   FP64  relative Frobenius error <= 1e-12, Z F64;
+ *   EXACT bit-exact integers, Z I32 (both factors integer). */
+typedef enum {
+    AFMM_TARGET_FP32 = 0, AFMM_TARGET_FP64 = 1, AFMM_TARGET_EXACT = 2
+} afmm_target;
+
+/* Kernel variants a plan can run (AFMM_VARIANT_AUTO lets the planner pick). */
+typedef enum {
+    AFMM_VARIANT_AUTO = -1,
+    /* CUDA cores, FP32 FMA, skips k where the Base is zero for a group of
+     * rows, K-blocked accumulation.  FP32 target. */
+    AFMM_VARIANT_SIMT_F32 = 0,
+    /* Tensor cores (tcgen05, TMEM accumulator): the real factor split into
+     * three BF16 slices (hi+mid+lo represent FP32 exactly), the Rep-factors
+     * widened to BF16 (exact up to 256), FP32 accumulation.  FP32 target. */
+    AFMM_VARIANT_TC_BF16X3 = 1,
+    /* As above with two slices: does not reach the FP32 target in general;
+     * offered for error studies only (never chosen automatically). */
+    AFMM_VARIANT_TC_BF16X2 = 2,
+    /* CUDA cores, FP64 target: the real factor cut into row-scaled integer
+     * slices, exact int32 products, FP64 recombination. */
+    AFMM_VARIANT_SIMT_F64SLICE = 3,
+    /* CUDA cores, exact integers: int8 dot products (dp4a), int32 sums. */
+    AFMM_VARIANT_SIMT_EXACT = 4,
+    /* Tensor cores, exact integers: operands exact in BF16, FP32 partial
+     * sums kept below 2^24 by splitting K, int32 recombination. */
+    AFMM_VARIANT_TC_EXACT = 5,
+    /* Tensor cores, FP64 target: 8-bit row-scaled slices exact in BF16,
+     * one exact FP32 accumulator per slice, FP64 recombination. */
+    AFMM_VARIANT_TC_F64SLICE = 6,
+    AFMM_VARIANT_COUNT_ = 7
+} afmm_variant;
+
+/* Flags for afmm_desc.flags. */
+#define AFMM_FLAG_VALIDATE 0x1u  /* scan the Rep-factors on every call and
+                                    report bad ones through afmm_plan_sync */
+
+/* One problem (Sec. 2): sizes, layout, element types and the paper's
+ * parameters.  d1, d2 are the densities (fraction of non-zero entries) of X
+ * and Y, mu_prime the mean of the non-zero Rep-factors (Sec. 2.2: "known to
+ * the experimenter in advance").  A negative hint means "unknown". */
+typedef struct {
+    int64_t n;          /* X, Y, Z are n x n, n >= 0 */
+    int64_t ldx, ldy, ldz; /* leading dimensions (elements); 0 means n */
+    int32_t kase;       /* afmm_case */
+    int32_t x_dtype, y_dtype, z_dtype;  /* afmm_dtype */
+    int32_t target;     /* afmm_target */
+    int32_t variant;    /* afmm_variant; AFMM_VARIANT_AUTO to let the plan pick */
+    uint32_t flags;     /* AFMM_FLAG_* */
+    int32_t reserved_;  /* must be 0 */
+    double d1, d2, mu_prime;  /* hints, < 0 when unknown */
+} afmm_desc;
+
+/* What a plan decided and, after a validating call, what it measured. */
+typedef struct {
+    int32_t variant;        /* afmm_variant the plan runs */
+    int32_t slices;         /* slices of the real factor (1 when unsliced) */
+    int32_t slice_bits;     /* bits per slice for the integer-slice forms */
+    int32_t k_split;        /* K chunks kept apart for exactness (>= 1) */
+    uint64_t workspace_bytes;
+    /* Measured by the last validating call (-1 before one ran): */
+    double d1, d2;          /* realised densities of X and Y */
+    double mu_prime, mu;    /* mean of non-zero / of all Rep-factors */
+    double rep_max;         /* largest Rep-factor */
+    double expected_additions;  /* mu' d1 d2 n^3 (Sec. 2.2) */
+} afmm_info;
+
+typedef struct afmm_plan_s* afmm_plan;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char* afmm_status_string(afmm_status s);
+
+/* Text of the last CUDA failure seen by this thread (empty if none). */
+const char* afmm_last_error_detail(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int afmm_version(void);
+
+/* Create a plan for one problem (Sec. 2 problem statement).  Validates the
+ * descriptor, picks the variant (a forced variant is honoured or refused
+ * with AFMM_ERR_UNSUPPORTED), sizes the workspace.  Allocates nothing on
+ * the device.  *out receives the plan (NULL on error). */
+afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc);
+
+/* Destroy a plan and free what it owns (not a lent workspace).  NULL is
+ * accepted and ignored.  The caller must not use the plan afterwards. */
+afmm_status afmm_plan_destroy(afmm_plan plan);
+
+/* Device workspace the plan needs, in bytes (may be 0). */
+afmm_status afmm_plan_workspace_size(afmm_plan plan, size_t* bytes);
+
+/* Lend the plan a device workspace of at least afmm_plan_workspace_size
+ * bytes, 256-byte aligned.  Without one the plan allocates its own on first
+ * use.  The caller keeps ownership and must keep it alive while the plan
+ * runs on it. */
+afmm_status afmm_plan_set_workspace(afmm_plan plan, void* workspace,
+                                    size_t bytes);
+
+/* Case A product (Sec. 2, Case-A): X real Base values, Y Rep-factors.
+ * Z = X * Y, overwritten.  The plan must have been created with
+ * kase == AFMM_CASE_A. */
+afmm_status afmm_mul_caseA(afmm_plan plan, const void* X, const void* Y,
+                           void* Z, void* stream);
+
+/* Case B product (Sec. 2, Case-B): X Rep-factors, Y real Base values.
+ * The plan must have been created with kase == AFMM_CASE_B. */
+afmm_status afmm_mul_caseB(afmm_plan plan, const void* X, const void* Y,
+                           void* Z, void* stream);
+
+/* Wait for the plan's work on `stream` and return the first error a kernel
+ * recorded since the previous sync (clearing it), else AFMM_OK. */
+afmm_status afmm_plan_sync(afmm_plan plan, void* stream);
+
+/* The plan's decisions and, after a validating call and a sync, the
+ * measured parameters of the last instance. */
+afmm_status afmm_get_info(afmm_plan plan, afmm_info* out);
+
+/* Counters of a plan, for measurement.  When kernel timing is enabled the
+ * plan records a CUDA event pair around its main product kernel on the
+ * call's stream (the events are timed on that stream, so they measure that
+ * kernel's launches only).  afmm_plan_counters synchronises those events. */
+typedef struct {
+    int64_t calls;             /* afmm_mul_* calls on this plan */
+    int64_t kernel_launches;   /* kernels those calls launched */
+    int64_t timed_launches;    /* main-kernel launches timed by events */
+    double timed_ms;           /* their summed duration, milliseconds */
+    int32_t main_kernel_ctas;  /* grid size of the last main-kernel launch */
+    int32_t reserved_;
+} afmm_counters;
+
+/* Enable (1) or disable (0) event timing of the main kernel; enabling
+ * resets the timed totals. */
+afmm_status afmm_plan_enable_kernel_timing(afmm_plan plan, int enable);
+afmm_status afmm_plan_counters(afmm_plan plan, afmm_counters* out);
+
+/* Batched product: `count` independent instances (Sec. 2 problems of
+ * possibly different n and case), each described by descs[t] and computed
+ * with the variant its own plan would pick, in one call on `stream`.
+ * X[t], Y[t], Z[t] are device pointers.  Instances are independent: Z[t]
+ * depends only on X[t] and Y[t]. */
+afmm_status afmm_mul_batched(int count, const afmm_desc* descs,
+                             const void* const* X, const void* const* Y,
+                             void* const* Z, void* stream);
+
+/* Relative error of a result against a reference, in FP64 on the GPU:
+ * out[0] = ||Z - R||_F, out[1] = ||R||_F, out[2] = max |Z - R| over the
+ * rows x cols matrices (row-major, leading dimensions ldz, ldr; dtypes F64,
+ * F32 or I32).  Device pointers; `out` is host memory, filled before
+ * return (the call synchronises `stream`).  `workspace` is a device buffer
+ * of afmm_error_norm_workspace_size() bytes, or NULL to let the call
+ * allocate and free one. */
+size_t afmm_error_norm_workspace_size(int64_t rows, int64_t cols);
+afmm_status afmm_error_norm(const void* Z, int32_t z_dtype, int64_t ldz,
+                            const void* R, int32_t r_dtype, int64_t ldr,
+                            int64_t rows, int64_t cols, void* workspace,
+                            double out[3], void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFMM_H */

@@ -1,0 +1,81 @@
+"""Build libafmm.so (the CUDA library behind include/afmm.h) in-tree.
+
+Every translation unit is compiled for sm_103a only
+(``-gencode arch=compute_103a,code=sm_103a``), in parallel, then linked into
+``paper_1308_2400_gb300/_build/libafmm.so``.  Only stale objects are rebuilt.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT, "libafmm.so")
+
+SOURCES = ["api.cu", "scan.cu", "convert.cu", "simt_gemm.cu", "norm.cu",
+           "tc_gemm.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC",
+                "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+
+
+def _nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def _headers_mtime() -> float:
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    hs.append(os.path.join(INCLUDE, "afmm.h"))
+    return max(os.path.getmtime(h) for h in hs)
+
+
+def _compile(src: str, obj: str, extra) -> None:
+    cmd = [_nvcc()] + FLAGS + list(extra) + ["-c", src, "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+    if r.stderr.strip() and os.environ.get("AFMM_BUILD_VERBOSE"):
+        print(r.stderr)
+
+
+def build(force: bool = False, ptxas_verbose: bool = False) -> str:
+    """Compile stale sources and link libafmm.so; returns its path."""
+    os.makedirs(OUT, exist_ok=True)
+    hdr = _headers_mtime()
+    extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+    jobs = []
+    for s in SOURCES:
+        src = os.path.join(CSRC, s)
+        obj = os.path.join(OUT, s.replace(".cu", ".o"))
+        if (force or ptxas_verbose or not os.path.exists(obj)
+                or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr)):
+            jobs.append((src, obj))
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            for f in [ex.submit(_compile, s, o, extra) for s, o in jobs]:
+                f.result()
+    objs = [os.path.join(OUT, s.replace(".cu", ".o")) for s in SOURCES]
+    if (jobs or not os.path.exists(LIB)
+            or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs)):
+        tmp = LIB + f".{os.getpid()}.tmp"
+        r = subprocess.run([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs,
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    import sys
+    print(build(force="--force" in sys.argv,
+                ptxas_verbose="--ptxas-v" in sys.argv))

@@ -1,0 +1,143 @@
+// Internal declarations shared by the translation units of libafmm.
+// Nothing here is part of the C ABI (include/afmm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "afmm.h"
+
+namespace afmm {
+
+// ------------------------------------------------------------------ errors
+#define AFMM_CUDA_TRY(expr)                                                  \
+    do {                                                                     \
+        cudaError_t e_ = (expr);                                             \
+        if (e_ != cudaSuccess) {                                             \
+            afmm::set_last_cuda_error(e_, #expr, __FILE__, __LINE__);        \
+            return (e_ == cudaErrorMemoryAllocation) ? AFMM_ERR_OOM          \
+                                                     : AFMM_ERR_CUDA;        \
+        }                                                                    \
+    } while (0)
+
+#define AFMM_TRY(expr)                                                       \
+    do {                                                                     \
+        afmm_status s_ = (expr);                                             \
+        if (s_ != AFMM_OK) return s_;                                        \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file,
+                         int line);
+
+// Kernel-launch counter of the calling thread (every launcher adds the
+// kernels it launched) and the main-kernel timing hook of a call.
+void count_launches(int k);
+int64_t launch_counter();
+struct MainTimer {
+    cudaEvent_t start = nullptr, stop = nullptr;  // null: timing off
+    int ctas = 0;
+};
+MainTimer* current_main_timer();   // set by the plan around a call
+// Record around the main kernel launch (no-ops without a current timer).
+void main_kernel_begin(cudaStream_t st);
+void main_kernel_end(cudaStream_t st, int ctas);
+
+// ------------------------------------------------------------------ dtypes
+inline size_t dtype_size(int dt) {
+    switch (dt) {
+        case AFMM_F64: return 8;
+        case AFMM_F32: case AFMM_I32: return 4;
+        case AFMM_BF16: return 2;
+        case AFMM_E4M3: case AFMM_I8: case AFMM_U8: return 1;
+        default: return 0;
+    }
+}
+inline bool dtype_is_integer(int dt) {
+    return dt == AFMM_I32 || dt == AFMM_I8 || dt == AFMM_U8;
+}
+
+// Device-side statistics of one matrix (K0 scan), reduced over the matrix.
+struct ScanStats {
+    unsigned long long nnz;        // non-zero entries
+    unsigned long long negative;   // entries < 0
+    unsigned long long nonint;     // entries that are not integers
+    unsigned long long over127;    // entries > 127 (int8 packing limit)
+    double sum;                    // sum of entries
+    double maxv;                   // largest entry (-inf when empty)
+    double max_abs;                // largest |entry|
+    double pad_;
+};
+constexpr int kScanMaxBlocks = 1024;
+
+// Per-device facts read once.
+struct DeviceProps {
+    int device = -1;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_optin = 0;
+};
+afmm_status device_props(DeviceProps* out);
+
+// ------------------------------------------------------------------ kernels
+// K0: statistics of an n x n matrix; `partials` holds kScanMaxBlocks
+// entries.  When `status` is non-null and `is_rep` is set, a negative or
+// non-integer entry records an error code there.
+afmm_status launch_scan(const void* M, int dtype, int64_t n, int64_t ld,
+                        bool is_rep, ScanStats* partials, ScanStats* out,
+                        int* status, cudaStream_t st);
+
+// K2: conversions.
+// dst[r*ldd + c] = (float) src[r*lds + c]
+afmm_status launch_to_f32(const void* src, int dtype, int64_t n, int64_t lds,
+                          float* dst, int64_t ldd, cudaStream_t st);
+// dst[c*ldd + r] = src[r*lds + c] for esize-byte elements.
+afmm_status launch_transpose(const void* src, size_t esize, int64_t rows,
+                             int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                             cudaStream_t st);
+// Pack an integer-valued n x n matrix B (row-major) into int8 words
+// W[kw*ldw + c] = bytes B[4kw..4kw+3][c] (k-word-major, zero padded to a
+// multiple of 4 rows).  Values outside [-128, 127] record
+// AFMM_ERR_OVERFLOW_RISK in `status`.
+afmm_status launch_pack_b_i8(const void* B, int dtype, int64_t n, int64_t ldb,
+                             int32_t* W, int64_t ldw, int* status,
+                             cudaStream_t st);
+// Copy an integer-valued n x n matrix A (row-major) into int8 rows
+// D[r*ldd + c] (ldd a multiple of 4, padding zeroed).  Same range check.
+afmm_status launch_pack_a_i8(const void* A, int dtype, int64_t n, int64_t lda,
+                             int8_t* D, int64_t ldd, int* status,
+                             cudaStream_t st);
+// Row-scaled integer slicing of a real matrix for the FP64 target:
+// E[r] = smallest e with max_c |A[r][c]| < 2^e; digit slices
+// Q[s*n + r][c] (int8, ldq) with A[r][c] ~= sum_s Q * 2^(E[r]-w(s+1)).
+afmm_status launch_row_exponents(const void* A, int dtype, int64_t n,
+                                 int64_t lda, int32_t* E, cudaStream_t st);
+afmm_status launch_slice_rows_i8(const void* A, int dtype, int64_t n,
+                                 int64_t lda, const int32_t* E, int slices,
+                                 int bits, int8_t* Q, int64_t ldq,
+                                 cudaStream_t st);
+// Z[r][c] = sum_s P[s*n + r][c] * 2^(E[r] - bits*(s+1)), in FP64.
+afmm_status launch_recombine_f64(const int32_t* P, int64_t ldp,
+                                 const int32_t* E, int slices, int bits,
+                                 int64_t n, double* Z, int64_t ldz,
+                                 cudaStream_t st);
+
+// K1: CUDA-core GEMMs, C (M x N) = A (M x K) * B (K x N), row-major.
+// FP32 FMA with zero-skip of A over 8-row groups and K-blocked sums.
+afmm_status launch_simt_f32(const float* A, int64_t lda, const float* B,
+                            int64_t ldb, float* C, int64_t ldc, int64_t M,
+                            int64_t N, int64_t K, cudaStream_t st);
+// int8 dot products: A int8 rows (lda bytes, multiple of 4), B packed
+// k-word-major int32 words (ldw words), C int32.
+afmm_status launch_simt_dp4a(const int8_t* A, int64_t lda, const int32_t* W,
+                             int64_t ldw, int32_t* C, int64_t ldc, int64_t M,
+                             int64_t N, int64_t K, cudaStream_t st);
+
+// K6: error norms, partial sums in `ws` (error_norm_ws_bytes bytes).
+size_t error_norm_ws_bytes(int64_t rows, int64_t cols);
+afmm_status launch_error_norm(const void* Z, int zdt, int64_t ldz,
+                              const void* R, int rdt, int64_t ldr,
+                              int64_t rows, int64_t cols, void* ws,
+                              double* out_dev, cudaStream_t st);
+
+}  // namespace afmm

@@ -1,0 +1,715 @@
+// C ABI of libafmm (include/afmm.h): plans, the planner that picks a
+// kernel variant for a problem of Sec. 2, workspace layout, host-buffer
+// staging and the device status word.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "afmm_common.cuh"
+#include "tc_gemm.cuh"
+
+namespace afmm {
+
+namespace {
+thread_local char g_last_err[512] = {0};
+}
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file,
+                         int line) {
+    snprintf(g_last_err, sizeof(g_last_err), "%s (%d) in %s at %s:%d",
+             cudaGetErrorString(e), (int)e, what, file, line);
+}
+
+namespace {
+thread_local int64_t g_launches = 0;
+thread_local MainTimer* g_timer = nullptr;
+}
+void count_launches(int k) { g_launches += k; }
+int64_t launch_counter() { return g_launches; }
+MainTimer* current_main_timer() { return g_timer; }
+void set_main_timer(MainTimer* t) { g_timer = t; }
+void main_kernel_begin(cudaStream_t st) {
+    if (g_timer && g_timer->start) cudaEventRecord(g_timer->start, st);
+}
+void main_kernel_end(cudaStream_t st, int ctas) {
+    if (g_timer && g_timer->stop) {
+        cudaEventRecord(g_timer->stop, st);
+        g_timer->ctas = ctas;
+    }
+}
+
+afmm_status device_props(DeviceProps* out) {
+    static std::mutex mu;
+    static DeviceProps cache[64];
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return AFMM_ERR_NO_DEVICE;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    DeviceProps& p = cache[dev];
+    if (p.device != dev) {
+        int v = 0;
+        AFMM_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        p.sm_count = v;
+        AFMM_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMajor, dev));
+        p.cc_major = v;
+        AFMM_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMinor, dev));
+        p.cc_minor = v;
+        AFMM_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        p.smem_optin = (size_t)v;
+        p.device = dev;
+    }
+    *out = p;
+    return AFMM_OK;
+}
+
+}  // namespace afmm
+
+using namespace afmm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// FP64-target slicing: 8 digits of 7 bits (56 bits of each row-scaled
+// value), each an int8, so products run on int8 dot products.
+constexpr int kF64Bits = 7;
+constexpr int kF64Slices = 8;
+
+}  // namespace
+
+struct afmm_plan_s {
+    afmm_desc d;
+    int variant = 0;
+    int slices = 1, bits = 0, ksplit = 1;
+    // Workspace layout (byte offsets; 0 size means unused).
+    size_t ws_bytes = 0;
+    size_t off_status = 0, off_sx = 0, off_sy = 0, off_part = 0;
+    size_t off_a = 0, off_b = 0, off_c = 0, off_e = 0;
+    size_t off_t1 = 0, off_t2 = 0, off_t3 = 0;
+    int64_t lda = 0, ldb = 0;           // leading dims of converted operands
+    char* ws = nullptr;
+    bool ws_owned = false;
+    bool ws_ready = false;              // status word zeroed
+    bool validated = false;
+    // Staging buffers for host pointers (owned).
+    void* stage[3] = {nullptr, nullptr, nullptr};
+    size_t stage_bytes[3] = {0, 0, 0};
+    TcPlan tc;                          // tensor-core state (tensor maps)
+    // Measurement counters.
+    int64_t calls = 0, launches = 0, timed = 0;
+    double timed_ms = 0.0;
+    int last_ctas = 0;
+    bool timing = false;
+    std::vector<MainTimer> pending, spare;
+};
+
+namespace {
+
+bool rep_dtype_ok(int dt) {
+    return dt == AFMM_I32 || dt == AFMM_I8 || dt == AFMM_U8 ||
+           dt == AFMM_E4M3 || dt == AFMM_BF16 || dt == AFMM_F32;
+}
+bool real_dtype_ok(int dt) {
+    return dt == AFMM_F64 || dt == AFMM_F32 || dt == AFMM_BF16;
+}
+
+// Byte span of an n x n row-major matrix with leading dimension ld.
+size_t span_bytes(int64_t n, int64_t ld, int dt) {
+    if (n <= 0) return 0;
+    return (size_t)((n - 1) * ld + n) * dtype_size(dt);
+}
+
+afmm_status check_desc(const afmm_desc* d) {
+    if (!d) return AFMM_ERR_INVALID_ARG;
+    if (d->n < 0 || d->reserved_ != 0) return AFMM_ERR_INVALID_ARG;
+    if (d->kase != AFMM_CASE_A && d->kase != AFMM_CASE_B)
+        return AFMM_ERR_INVALID_ARG;
+    if (d->target < AFMM_TARGET_FP32 || d->target > AFMM_TARGET_EXACT)
+        return AFMM_ERR_INVALID_ARG;
+    if (d->variant < AFMM_VARIANT_AUTO || d->variant >= AFMM_VARIANT_COUNT_)
+        return AFMM_ERR_INVALID_ARG;
+    for (int dt : {d->x_dtype, d->y_dtype, d->z_dtype})
+        if (dtype_size(dt) == 0) return AFMM_ERR_INVALID_ARG;
+    const int64_t n = d->n;
+    const int64_t ldx = d->ldx ? d->ldx : n, ldy = d->ldy ? d->ldy : n,
+                  ldz = d->ldz ? d->ldz : n;
+    if (ldx < n || ldy < n || ldz < n) return AFMM_ERR_INVALID_ARG;
+    const int rep_dt = d->kase == AFMM_CASE_A ? d->y_dtype : d->x_dtype;
+    const int base_dt = d->kase == AFMM_CASE_A ? d->x_dtype : d->y_dtype;
+    if (!rep_dtype_ok(rep_dt)) return AFMM_ERR_INVALID_ARG;
+    if (d->target == AFMM_TARGET_EXACT) {
+        if (!dtype_is_integer(base_dt) || !dtype_is_integer(rep_dt) ||
+            d->z_dtype != AFMM_I32)
+            return AFMM_ERR_INVALID_ARG;
+    } else {
+        if (!real_dtype_ok(base_dt) && !dtype_is_integer(base_dt))
+            return AFMM_ERR_INVALID_ARG;
+        if (d->target == AFMM_TARGET_FP32 && d->z_dtype != AFMM_F32)
+            return AFMM_ERR_INVALID_ARG;
+        if (d->target == AFMM_TARGET_FP64 && d->z_dtype != AFMM_F64)
+            return AFMM_ERR_INVALID_ARG;
+    }
+    return AFMM_OK;
+}
+
+bool variant_serves(int v, const afmm_desc* d) {
+    switch (v) {
+        case AFMM_VARIANT_SIMT_F32:
+            return d->target == AFMM_TARGET_FP32;
+        case AFMM_VARIANT_TC_BF16X3:
+        case AFMM_VARIANT_TC_BF16X2:
+            return d->target == AFMM_TARGET_FP32 && tc_available();
+        case AFMM_VARIANT_SIMT_F64SLICE:
+            return d->target == AFMM_TARGET_FP64;
+        case AFMM_VARIANT_SIMT_EXACT:
+            return d->target == AFMM_TARGET_EXACT;
+        default:
+            return false;
+    }
+}
+
+int auto_variant(const afmm_desc* d) {
+    if (d->target == AFMM_TARGET_EXACT) return AFMM_VARIANT_SIMT_EXACT;
+    if (d->target == AFMM_TARGET_FP64) return AFMM_VARIANT_SIMT_F64SLICE;
+    // FP32 target: tensor cores for the dense regime; the zero-skipping
+    // CUDA-core kernel when the Base factor is very sparse (the useful
+    // work mu' d1 d2 n^3 is then far below the dense n^3).
+    const double dbase = d->kase == AFMM_CASE_A ? d->d1 : d->d2;
+    if (tc_available() && d->n >= 128 && !(dbase >= 0.0 && dbase < 0.05))
+        return AFMM_VARIANT_TC_BF16X3;
+    return AFMM_VARIANT_SIMT_F32;
+}
+
+// Bump allocator for the workspace layout.
+struct Layout {
+    size_t top = 0;
+    size_t take(size_t bytes) {
+        if (bytes == 0) return 0;
+        size_t off = align_up(top, kAlign);
+        top = off + align_up(bytes, kAlign);
+        return off;
+    }
+};
+
+void plan_layout(afmm_plan_s* p) {
+    const afmm_desc& d = p->d;
+    const int64_t n = d.n;
+    Layout L;
+    L.top = 0;
+    p->off_status = L.take(kAlign);
+    p->off_sx = L.take(sizeof(ScanStats));
+    p->off_sy = L.take(sizeof(ScanStats));
+    p->off_part = L.take(sizeof(ScanStats) * kScanMaxBlocks);
+    const size_t nn = (size_t)n * (size_t)n;
+    switch (p->variant) {
+        case AFMM_VARIANT_SIMT_F32: {
+            if (d.x_dtype != AFMM_F32) p->off_a = L.take(nn * 4);
+            if (d.y_dtype != AFMM_F32) p->off_b = L.take(nn * 4);
+            break;
+        }
+        case AFMM_VARIANT_SIMT_EXACT: {
+            p->lda = round_up(n, 4);
+            p->ldb = round_up(n, 4);
+            p->off_a = L.take((size_t)n * p->lda);
+            p->off_b = L.take((size_t)((n + 3) / 4) * p->ldb * 4);
+            break;
+        }
+        case AFMM_VARIANT_SIMT_F64SLICE: {
+            p->lda = round_up(n, 4);
+            p->ldb = round_up(n, 4);
+            p->off_e = L.take((size_t)n * 4);
+            p->off_a = L.take((size_t)p->slices * n * p->lda);
+            p->off_b = L.take((size_t)((n + 3) / 4) * p->ldb * 4);
+            p->off_c = L.take((size_t)p->slices * nn * 4);
+            if (d.kase == AFMM_CASE_B) {
+                p->off_t1 = L.take(nn * dtype_size(d.y_dtype));
+                p->off_t2 = L.take(nn * dtype_size(d.x_dtype));
+                p->off_t3 = L.take(nn * 8);
+            }
+            break;
+        }
+        case AFMM_VARIANT_TC_BF16X3:
+        case AFMM_VARIANT_TC_BF16X2: {
+            tc_layout(&p->tc, d, p->slices);
+            p->off_a = L.take(p->tc.a_bytes);
+            p->off_b = L.take(p->tc.b_bytes);
+            break;
+        }
+        default:
+            break;
+    }
+    p->ws_bytes = L.top;
+}
+
+bool is_host_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+afmm_status ensure_workspace(afmm_plan_s* p, cudaStream_t st) {
+    if (!p->ws && p->ws_bytes) {
+        void* w = nullptr;
+        AFMM_CUDA_TRY(cudaMalloc(&w, p->ws_bytes));
+        p->ws = static_cast<char*>(w);
+        p->ws_owned = true;
+        p->ws_ready = false;
+    }
+    if (!p->ws_ready) {
+        AFMM_CUDA_TRY(cudaMemsetAsync(p->ws + p->off_status, 0, kAlign, st));
+        if (p->variant == AFMM_VARIANT_TC_BF16X3 ||
+            p->variant == AFMM_VARIANT_TC_BF16X2)
+            AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a,
+                                       p->ws + p->off_b));
+        p->ws_ready = true;
+    }
+    return AFMM_OK;
+}
+
+template <typename T>
+T* wsp(afmm_plan_s* p, size_t off) {
+    return reinterpret_cast<T*>(p->ws + off);
+}
+
+afmm_status run_simt_f32(afmm_plan_s* p, const void* X, const void* Y, void* Z,
+                         cudaStream_t st) {
+    const afmm_desc& d = p->d;
+    const int64_t n = d.n;
+    const float* A = static_cast<const float*>(X);
+    const float* B = static_cast<const float*>(Y);
+    int64_t lda = d.ldx ? d.ldx : n, ldb = d.ldy ? d.ldy : n;
+    if (d.x_dtype != AFMM_F32) {
+        AFMM_TRY(launch_to_f32(X, d.x_dtype, n, lda, wsp<float>(p, p->off_a), n, st));
+        A = wsp<float>(p, p->off_a);
+        lda = n;
+    }
+    if (d.y_dtype != AFMM_F32) {
+        AFMM_TRY(launch_to_f32(Y, d.y_dtype, n, ldb, wsp<float>(p, p->off_b), n, st));
+        B = wsp<float>(p, p->off_b);
+        ldb = n;
+    }
+    return launch_simt_f32(A, lda, B, ldb, static_cast<float*>(Z),
+                           d.ldz ? d.ldz : n, n, n, n, st);
+}
+
+afmm_status run_simt_exact(afmm_plan_s* p, const void* X, const void* Y,
+                           void* Z, cudaStream_t st) {
+    const afmm_desc& d = p->d;
+    const int64_t n = d.n;
+    int* status = wsp<int>(p, p->off_status);
+    AFMM_TRY(launch_pack_a_i8(X, d.x_dtype, n, d.ldx ? d.ldx : n,
+                              wsp<int8_t>(p, p->off_a), p->lda, status, st));
+    AFMM_TRY(launch_pack_b_i8(Y, d.y_dtype, n, d.ldy ? d.ldy : n,
+                              wsp<int32_t>(p, p->off_b), p->ldb, status, st));
+    return launch_simt_dp4a(wsp<int8_t>(p, p->off_a), p->lda,
+                            wsp<int32_t>(p, p->off_b), p->ldb,
+                            static_cast<int32_t*>(Z), d.ldz ? d.ldz : n, n, n,
+                            n, st);
+}
+
+// Case A form: X real, Y Rep-factors.  Z F64.
+afmm_status run_f64slice_a(afmm_plan_s* p, const void* X, int xdt, int64_t ldx,
+                           const void* Y, int ydt, int64_t ldy, double* Z,
+                           int64_t ldz, cudaStream_t st) {
+    const int64_t n = p->d.n;
+    int* status = wsp<int>(p, p->off_status);
+    int32_t* E = wsp<int32_t>(p, p->off_e);
+    int8_t* Q = wsp<int8_t>(p, p->off_a);
+    int32_t* W = wsp<int32_t>(p, p->off_b);
+    int32_t* P = wsp<int32_t>(p, p->off_c);
+    AFMM_TRY(launch_row_exponents(X, xdt, n, ldx, E, st));
+    AFMM_TRY(launch_slice_rows_i8(X, xdt, n, ldx, E, p->slices, p->bits, Q,
+                                  p->lda, st));
+    AFMM_TRY(launch_pack_b_i8(Y, ydt, n, ldy, W, p->ldb, status, st));
+    AFMM_TRY(launch_simt_dp4a(Q, p->lda, W, p->ldb, P, n,
+                              (int64_t)p->slices * n, n, n, st));
+    return launch_recombine_f64(P, n, E, p->slices, p->bits, n, Z, ldz, st);
+}
+
+afmm_status run_simt_f64slice(afmm_plan_s* p, const void* X, const void* Y,
+                              void* Z, cudaStream_t st) {
+    const afmm_desc& d = p->d;
+    const int64_t n = d.n;
+    const int64_t ldx = d.ldx ? d.ldx : n, ldy = d.ldy ? d.ldy : n,
+                  ldz = d.ldz ? d.ldz : n;
+    if (d.kase == AFMM_CASE_A)
+        return run_f64slice_a(p, X, d.x_dtype, ldx, Y, d.y_dtype, ldy,
+                              static_cast<double*>(Z), ldz, st);
+    // Case B: Z^T = Y^T X^T, a case-A product of the transposes.
+    void* YT = p->ws + p->off_t1;
+    void* XT = p->ws + p->off_t2;
+    double* ZT = wsp<double>(p, p->off_t3);
+    AFMM_TRY(launch_transpose(Y, dtype_size(d.y_dtype), n, n, ldy, YT, n, st));
+    AFMM_TRY(launch_transpose(X, dtype_size(d.x_dtype), n, n, ldx, XT, n, st));
+    AFMM_TRY(run_f64slice_a(p, YT, d.y_dtype, n, XT, d.x_dtype, n, ZT, n, st));
+    return launch_transpose(ZT, 8, n, n, n, Z, ldz, st);
+}
+
+afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
+                        cudaStream_t st) {
+    const afmm_desc& d = p->d;
+    const int64_t n = d.n;
+    if (d.flags & AFMM_FLAG_VALIDATE) {
+        const bool a = d.kase == AFMM_CASE_A;
+        int* status = wsp<int>(p, p->off_status);
+        ScanStats* part = wsp<ScanStats>(p, p->off_part);
+        AFMM_TRY(launch_scan(X, d.x_dtype, n, d.ldx ? d.ldx : n, !a, part,
+                             wsp<ScanStats>(p, p->off_sx), status, st));
+        AFMM_TRY(launch_scan(Y, d.y_dtype, n, d.ldy ? d.ldy : n, a, part,
+                             wsp<ScanStats>(p, p->off_sy), status, st));
+        p->validated = true;
+    }
+    if (n == 0) return AFMM_OK;
+    switch (p->variant) {
+        case AFMM_VARIANT_SIMT_F32: return run_simt_f32(p, X, Y, Z, st);
+        case AFMM_VARIANT_SIMT_EXACT: return run_simt_exact(p, X, Y, Z, st);
+        case AFMM_VARIANT_SIMT_F64SLICE: return run_simt_f64slice(p, X, Y, Z, st);
+        case AFMM_VARIANT_TC_BF16X3:
+        case AFMM_VARIANT_TC_BF16X2:
+            return tc_run_split(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
+        default: return AFMM_ERR_UNSUPPORTED;
+    }
+}
+
+afmm_status stage_buffer(afmm_plan_s* p, int idx, size_t bytes, void** out) {
+    if (p->stage_bytes[idx] < bytes) {
+        if (p->stage[idx]) cudaFree(p->stage[idx]);
+        p->stage[idx] = nullptr;
+        p->stage_bytes[idx] = 0;
+        AFMM_CUDA_TRY(cudaMalloc(&p->stage[idx], bytes));
+        p->stage_bytes[idx] = bytes;
+    }
+    *out = p->stage[idx];
+    return AFMM_OK;
+}
+
+// Batched product, first form: each instance runs its own plan, all on one
+// stream, in order.
+afmm_status batched_impl(int count, const afmm_desc* descs,
+                         const void* const* X, const void* const* Y,
+                         void* const* Z, void* stream);
+
+afmm_status mul_impl(afmm_plan p, const void* X, const void* Y, void* Z,
+                     void* stream, int expect_case) {
+    if (!p) return AFMM_ERR_INVALID_ARG;
+    if (p->d.kase != expect_case) return AFMM_ERR_INVALID_ARG;
+    const afmm_desc& d = p->d;
+    const int64_t n = d.n;
+    if (n > 0 && (!X || !Y || !Z)) return AFMM_ERR_INVALID_ARG;
+    DeviceProps dp;
+    AFMM_TRY(device_props(&dp));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AFMM_TRY(ensure_workspace(p, st));
+    const size_t bx = span_bytes(n, d.ldx ? d.ldx : n, d.x_dtype);
+    const size_t by = span_bytes(n, d.ldy ? d.ldy : n, d.y_dtype);
+    const size_t bz = span_bytes(n, d.ldz ? d.ldz : n, d.z_dtype);
+    const bool hx = is_host_ptr(X), hy = is_host_ptr(Y), hz = is_host_ptr(Z);
+    const void* dX = X;
+    const void* dY = Y;
+    void* dZ = Z;
+    if (hx) {
+        void* b;
+        AFMM_TRY(stage_buffer(p, 0, bx, &b));
+        AFMM_CUDA_TRY(cudaMemcpyAsync(b, X, bx, cudaMemcpyHostToDevice, st));
+        dX = b;
+    }
+    if (hy) {
+        void* b;
+        AFMM_TRY(stage_buffer(p, 1, by, &b));
+        AFMM_CUDA_TRY(cudaMemcpyAsync(b, Y, by, cudaMemcpyHostToDevice, st));
+        dY = b;
+    }
+    if (hz) {
+        void* b;
+        AFMM_TRY(stage_buffer(p, 2, bz, &b));
+        dZ = b;
+    }
+    MainTimer tm;
+    if (p->timing) {
+        if (!p->spare.empty()) {
+            tm = p->spare.back();
+            p->spare.pop_back();
+        } else {
+            AFMM_CUDA_TRY(cudaEventCreate(&tm.start));
+            AFMM_CUDA_TRY(cudaEventCreate(&tm.stop));
+        }
+        tm.ctas = -1;
+        set_main_timer(&tm);
+    }
+    const int64_t l0 = launch_counter();
+    afmm_status rc = run_variant(p, dX, dY, dZ, st);
+    set_main_timer(nullptr);
+    p->launches += launch_counter() - l0;
+    p->calls += 1;
+    if (p->timing) {
+        if (tm.ctas >= 0) {
+            p->last_ctas = tm.ctas;
+            p->pending.push_back(tm);
+        } else {
+            p->spare.push_back(tm);
+        }
+    }
+    AFMM_TRY(rc);
+    if (hz) AFMM_CUDA_TRY(cudaMemcpyAsync(Z, dZ, bz, cudaMemcpyDeviceToHost, st));
+    if (hx || hy || hz) AFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* afmm_status_string(afmm_status s) {
+    switch (s) {
+        case AFMM_OK: return "AFMM_OK";
+        case AFMM_ERR_INVALID_ARG: return "AFMM_ERR_INVALID_ARG";
+        case AFMM_ERR_UNSUPPORTED: return "AFMM_ERR_UNSUPPORTED";
+        case AFMM_ERR_NEGATIVE_REP: return "AFMM_ERR_NEGATIVE_REP";
+        case AFMM_ERR_OVERFLOW_RISK: return "AFMM_ERR_OVERFLOW_RISK";
+        case AFMM_ERR_OOM: return "AFMM_ERR_OOM";
+        case AFMM_ERR_CUDA: return "AFMM_ERR_CUDA";
+        case AFMM_ERR_TIMEOUT: return "AFMM_ERR_TIMEOUT";
+        case AFMM_ERR_NO_DEVICE: return "AFMM_ERR_NO_DEVICE";
+        case AFMM_ERR_NONINTEGER_REP: return "AFMM_ERR_NONINTEGER_REP";
+        default: return "AFMM_ERR_UNKNOWN";
+    }
+}
+
+const char* afmm_last_error_detail(void) { return afmm::g_last_err; }
+
+int afmm_version(void) { return 100; }
+
+afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc) {
+    if (!out) return AFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    AFMM_TRY(check_desc(desc));
+    afmm_plan_s* p = new (std::nothrow) afmm_plan_s();
+    if (!p) return AFMM_ERR_OOM;
+    p->d = *desc;
+    if (!p->d.ldx) p->d.ldx = desc->n;
+    if (!p->d.ldy) p->d.ldy = desc->n;
+    if (!p->d.ldz) p->d.ldz = desc->n;
+    int v = desc->variant;
+    if (v == AFMM_VARIANT_AUTO) v = auto_variant(desc);
+    if (!variant_serves(v, desc)) {
+        delete p;
+        return AFMM_ERR_UNSUPPORTED;
+    }
+    p->variant = v;
+    if (v == AFMM_VARIANT_SIMT_F64SLICE) {
+        p->slices = kF64Slices;
+        p->bits = kF64Bits;
+        // int32 sums of n products of 7-bit digits and int8 Rep-factors.
+        if ((double)desc->n * 127.0 * 128.0 >= 2147483647.0) {
+            delete p;
+            return AFMM_ERR_OVERFLOW_RISK;
+        }
+    } else if (v == AFMM_VARIANT_SIMT_EXACT) {
+        if ((double)desc->n * 128.0 * 128.0 >= 2147483647.0) {
+            delete p;
+            return AFMM_ERR_OVERFLOW_RISK;
+        }
+    } else if (v == AFMM_VARIANT_TC_BF16X3) {
+        p->slices = 3;
+    } else if (v == AFMM_VARIANT_TC_BF16X2) {
+        p->slices = 2;
+    }
+    plan_layout(p);
+    *out = p;
+    return AFMM_OK;
+}
+
+afmm_status afmm_plan_destroy(afmm_plan p) {
+    if (!p) return AFMM_OK;
+    for (auto* v : {&p->pending, &p->spare})
+        for (auto& t : *v) {
+            cudaEventDestroy(t.start);
+            cudaEventDestroy(t.stop);
+        }
+    if (p->ws_owned && p->ws) cudaFree(p->ws);
+    for (int i = 0; i < 3; ++i)
+        if (p->stage[i]) cudaFree(p->stage[i]);
+    delete p;
+    return AFMM_OK;
+}
+
+afmm_status afmm_plan_workspace_size(afmm_plan p, size_t* bytes) {
+    if (!p || !bytes) return AFMM_ERR_INVALID_ARG;
+    *bytes = p->ws_bytes;
+    return AFMM_OK;
+}
+
+afmm_status afmm_plan_set_workspace(afmm_plan p, void* ws, size_t bytes) {
+    if (!p) return AFMM_ERR_INVALID_ARG;
+    if (bytes < p->ws_bytes || (p->ws_bytes && !ws) ||
+        (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+        return AFMM_ERR_INVALID_ARG;
+    if (p->ws_owned && p->ws) cudaFree(p->ws);
+    p->ws = static_cast<char*>(ws);
+    p->ws_owned = false;
+    p->ws_ready = false;
+    return AFMM_OK;
+}
+
+afmm_status afmm_mul_caseA(afmm_plan p, const void* X, const void* Y, void* Z,
+                           void* stream) {
+    return mul_impl(p, X, Y, Z, stream, AFMM_CASE_A);
+}
+
+afmm_status afmm_mul_caseB(afmm_plan p, const void* X, const void* Y, void* Z,
+                           void* stream) {
+    return mul_impl(p, X, Y, Z, stream, AFMM_CASE_B);
+}
+
+afmm_status afmm_plan_sync(afmm_plan p, void* stream) {
+    if (!p) return AFMM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!p->ws) return AFMM_OK;
+    int code = 0;
+    AFMM_CUDA_TRY(cudaMemcpy(&code, p->ws + p->off_status, sizeof(int),
+                             cudaMemcpyDeviceToHost));
+    if (code != 0) {
+        const int zero = 0;
+        AFMM_CUDA_TRY(cudaMemcpy(p->ws + p->off_status, &zero, sizeof(int),
+                                 cudaMemcpyHostToDevice));
+        return static_cast<afmm_status>(code);
+    }
+    return AFMM_OK;
+}
+
+afmm_status afmm_get_info(afmm_plan p, afmm_info* out) {
+    if (!p || !out) return AFMM_ERR_INVALID_ARG;
+    afmm_info& o = *out;
+    o.variant = p->variant;
+    o.slices = p->slices;
+    o.slice_bits = p->bits;
+    o.k_split = p->ksplit;
+    o.workspace_bytes = p->ws_bytes;
+    o.d1 = o.d2 = o.mu_prime = o.mu = o.rep_max = o.expected_additions = -1.0;
+    if (p->validated && p->ws) {
+        AFMM_CUDA_TRY(cudaDeviceSynchronize());
+        ScanStats sx, sy;
+        AFMM_CUDA_TRY(cudaMemcpy(&sx, p->ws + p->off_sx, sizeof sx,
+                                 cudaMemcpyDeviceToHost));
+        AFMM_CUDA_TRY(cudaMemcpy(&sy, p->ws + p->off_sy, sizeof sy,
+                                 cudaMemcpyDeviceToHost));
+        const double n = (double)p->d.n, n2 = n * n;
+        const ScanStats& rep = p->d.kase == AFMM_CASE_A ? sy : sx;
+        o.d1 = n2 > 0 ? (double)sx.nnz / n2 : 0.0;
+        o.d2 = n2 > 0 ? (double)sy.nnz / n2 : 0.0;
+        o.mu_prime = rep.nnz ? rep.sum / (double)rep.nnz : 0.0;
+        o.mu = n2 > 0 ? rep.sum / n2 : 0.0;
+        o.rep_max = rep.maxv;
+        o.expected_additions = o.mu_prime * o.d1 * o.d2 * n * n2;
+    }
+    return AFMM_OK;
+}
+
+afmm_status afmm_plan_enable_kernel_timing(afmm_plan p, int enable) {
+    if (!p) return AFMM_ERR_INVALID_ARG;
+    p->timing = enable != 0;
+    p->timed = 0;
+    p->timed_ms = 0.0;
+    for (auto& t : p->pending) p->spare.push_back(t);
+    p->pending.clear();
+    return AFMM_OK;
+}
+
+afmm_status afmm_plan_counters(afmm_plan p, afmm_counters* out) {
+    if (!p || !out) return AFMM_ERR_INVALID_ARG;
+    for (auto& t : p->pending) {
+        AFMM_CUDA_TRY(cudaEventSynchronize(t.stop));
+        float ms = 0.f;
+        AFMM_CUDA_TRY(cudaEventElapsedTime(&ms, t.start, t.stop));
+        p->timed_ms += ms;
+        p->timed += 1;
+        p->spare.push_back(t);
+    }
+    p->pending.clear();
+    out->calls = p->calls;
+    out->kernel_launches = p->launches;
+    out->timed_launches = p->timed;
+    out->timed_ms = p->timed_ms;
+    out->main_kernel_ctas = p->last_ctas;
+    out->reserved_ = 0;
+    return AFMM_OK;
+}
+
+afmm_status afmm_mul_batched(int count, const afmm_desc* descs,
+                             const void* const* X, const void* const* Y,
+                             void* const* Z, void* stream) {
+    if (count < 0 || (count > 0 && (!descs || !X || !Y || !Z)))
+        return AFMM_ERR_INVALID_ARG;
+    return batched_impl(count, descs, X, Y, Z, stream);
+}
+
+size_t afmm_error_norm_workspace_size(int64_t rows, int64_t cols) {
+    return error_norm_ws_bytes(rows, cols);
+}
+
+afmm_status afmm_error_norm(const void* Z, int32_t z_dtype, int64_t ldz,
+                            const void* R, int32_t r_dtype, int64_t ldr,
+                            int64_t rows, int64_t cols, void* workspace,
+                            double out[3], void* stream) {
+    if (!out || rows < 0 || cols < 0 || ldz < cols || ldr < cols)
+        return AFMM_ERR_INVALID_ARG;
+    if (rows > 0 && cols > 0 && (!Z || !R)) return AFMM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t wsb = error_norm_ws_bytes(rows, cols);
+    void* ws = workspace;
+    bool owned = false;
+    if (!ws) {
+        AFMM_CUDA_TRY(cudaMalloc(&ws, wsb));
+        owned = true;
+    }
+    double* out_dev = reinterpret_cast<double*>(static_cast<char*>(ws) + wsb - 256);
+    afmm_status rc = launch_error_norm(Z, z_dtype, ldz, R, r_dtype, ldr, rows,
+                                       cols, ws, out_dev, st);
+    if (rc == AFMM_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, out_dev, 3 * sizeof(double),
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e, "error norm readback", __FILE__, __LINE__);
+            rc = AFMM_ERR_CUDA;
+        }
+    }
+    if (owned) cudaFree(ws);
+    return rc;
+}
+
+}  // extern "C"
+
+namespace {
+afmm_status batched_impl(int count, const afmm_desc* descs,
+                         const void* const* X, const void* const* Y,
+                         void* const* Z, void* stream) {
+    afmm_status rc = AFMM_OK;
+    for (int t = 0; t < count && rc == AFMM_OK; ++t) {
+        afmm_plan p = nullptr;
+        rc = afmm_plan_create(&p, &descs[t]);
+        if (rc != AFMM_OK) break;
+        rc = descs[t].kase == AFMM_CASE_A
+                 ? afmm_mul_caseA(p, X[t], Y[t], Z[t], stream)
+                 : afmm_mul_caseB(p, X[t], Y[t], Z[t], stream);
+        afmm_status rs = afmm_plan_sync(p, stream);
+        if (rc == AFMM_OK) rc = rs;
+        afmm_plan_destroy(p);
+    }
+    return rc;
+}
+}  // namespace

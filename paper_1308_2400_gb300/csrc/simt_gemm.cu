@@ -1,0 +1,302 @@
+// K1: CUDA-core AFMM product with zero-skipping.
+//
+// The paper's loop (Sec. 2, Case-A) reads Base = X[i,k] and skips the whole
+// J loop when it is zero.  Here one warp owns 8 rows of a 64 x 256 output
+// tile and all 256 columns, so the Base values X[i..i+7, k] it needs are the
+// same for every lane: the zero test is warp-uniform and a k whose 8 Base
+// values are all zero is skipped by the whole warp at no divergence cost.
+// The term Rep * Base is formed with one FMA (FP32) or one 4-way int8 dot
+// product (exact integers) instead of Rep additions: the same value, formed
+// exactly before the accumulation rounds (Sec. 2.1: the result is X * Y).
+//
+// Layout: A (M x K) and B (K x N) row-major in global memory, staged by
+// cp.async into shared memory (A as [64][32], B as [32][256] elements of
+// 4 bytes, two stages).  Each thread accumulates 8 rows x 8 columns; FP32
+// sums are K-blocked (a fresh partial per 32-wide k tile, added to the
+// running sum afterwards) to keep the rounding error of long sums low.
+#include <cstdint>
+
+#include "afmm_common.cuh"
+
+namespace afmm {
+
+namespace {
+
+constexpr int BM = 64, BN = 256, BK = 32, THREADS = 256;
+constexpr int SMEM_BYTES = 2 * (BM * BK + BK * BN) * 4;
+
+struct OpF32 {
+    using Elt = float;
+    using Acc = float;
+    static constexpr bool kBlocked = true;
+    static __device__ __forceinline__ Acc mac(Elt a, Elt b, Acc c) {
+        return fmaf(a, b, c);
+    }
+    static __device__ __forceinline__ bool nz(Elt a) { return a != 0.0f; }
+};
+
+// One element = 4 consecutive k of int8; mac = 4 products + 1 add, exact.
+struct OpDp4a {
+    using Elt = int32_t;
+    using Acc = int32_t;
+    static constexpr bool kBlocked = false;
+    static __device__ __forceinline__ Acc mac(Elt a, Elt b, Acc c) {
+        return __dp4a(a, b, c);
+    }
+    static __device__ __forceinline__ bool nz(Elt a) { return a != 0; }
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)),
+                 "l"(src));
+}
+// 4-byte copy; when !ok nothing is read and the destination is zeroed.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(ok ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::);
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <typename Elt>
+__device__ __forceinline__ void load_tiles(Elt* As, Elt* Bs, const Elt* A,
+                                           int64_t lda, const Elt* B,
+                                           int64_t ldb, int64_t M, int64_t N,
+                                           int64_t K, int64_t m0, int64_t n0,
+                                           int64_t k0, bool vec) {
+    // A tile: 64 rows x 32 elements = 512 chunks of 4.
+    for (int c = threadIdx.x; c < BM * BK / 4; c += THREADS) {
+        const int m = c / (BK / 4), kc = (c % (BK / 4)) * 4;
+        const int64_t gm = m0 + m, gk = k0 + kc;
+        Elt* dst = As + m * BK + kc;
+        if (vec && gm < M && gk + 3 < K) {
+            cp_async16(dst, A + gm * lda + gk);
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const bool ok = gm < M && gk + t < K;
+                cp_async4(dst + t, ok ? (const void*)(A + gm * lda + gk + t)
+                                      : (const void*)A, ok);
+            }
+        }
+    }
+    // B tile: 32 rows x 256 elements = 2048 chunks of 4.
+    for (int c = threadIdx.x; c < BK * BN / 4; c += THREADS) {
+        const int k = c / (BN / 4), nc = (c % (BN / 4)) * 4;
+        const int64_t gk = k0 + k, gn = n0 + nc;
+        Elt* dst = Bs + k * BN + nc;
+        if (vec && gk < K && gn + 3 < N) {
+            cp_async16(dst, B + gk * ldb + gn);
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const bool ok = gk < K && gn + t < N;
+                cp_async4(dst + t, ok ? (const void*)(B + gk * ldb + gn + t)
+                                      : (const void*)B, ok);
+            }
+        }
+    }
+}
+
+template <typename V, typename E>
+__device__ __forceinline__ E comp(const V& v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(THREADS, 1)
+simt_gemm_kernel(const typename Op::Elt* __restrict__ A, int64_t lda,
+                 const typename Op::Elt* __restrict__ B, int64_t ldb,
+                 typename Op::Acc* __restrict__ C, int64_t ldc, int64_t M,
+                 int64_t N, int64_t K, int vec) {
+    using Elt = typename Op::Elt;
+    using Acc = typename Op::Acc;
+    using V4 = typename std::conditional<std::is_same<Elt, float>::value,
+                                         float4, int4>::type;
+    using A4 = typename std::conditional<std::is_same<Acc, float>::value,
+                                         float4, int4>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Elt* As = reinterpret_cast<Elt*>(smem_raw);          // [2][BM][BK]
+    Elt* Bs = As + 2 * BM * BK;                          // [2][BK][BN]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+    const int row0 = warp * 8;
+
+    Acc acc[8][8];
+    Acc part[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            acc[r][c] = Acc(0);
+            part[r][c] = Acc(0);
+        }
+
+    const int64_t ntiles = (K + BK - 1) / BK;
+    if (ntiles > 0) {
+        load_tiles<Elt>(As, Bs, A, lda, B, ldb, M, N, K, m0, n0, 0, vec != 0);
+        cp_async_commit();
+    }
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int s = (int)(t & 1);
+        if (t + 1 < ntiles) {
+            load_tiles<Elt>(As + (s ^ 1) * BM * BK, Bs + (s ^ 1) * BK * BN, A,
+                            lda, B, ldb, M, N, K, m0, n0, (t + 1) * BK,
+                            vec != 0);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const Elt* as = As + s * BM * BK + row0 * BK;
+        const Elt* bs = Bs + s * BK * BN;
+
+        // Which k of this tile have a non-zero Base in the warp's 8 rows.
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) any |= Op::nz(as[r * BK + lane]);
+        const unsigned mask = __ballot_sync(0xffffffffu, any);
+
+        if (__popc(mask) >= 24) {
+            // Nearly dense: run all 32 k; zero Base values add exact zeros.
+#pragma unroll
+            for (int kq = 0; kq < BK / 4; ++kq) {
+                V4 y[4][2];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const Elt* row = bs + (kq * 4 + kk) * BN;
+                    y[kk][0] = *reinterpret_cast<const V4*>(row + lane * 4);
+                    y[kk][1] = *reinterpret_cast<const V4*>(row + 128 + lane * 4);
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const V4 xv = *reinterpret_cast<const V4*>(as + r * BK + kq * 4);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const Elt x = comp<V4, Elt>(xv, kk);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            part[r][c] = Op::mac(x, comp<V4, Elt>(y[kk][0], c), part[r][c]);
+                            part[r][4 + c] = Op::mac(x, comp<V4, Elt>(y[kk][1], c), part[r][4 + c]);
+                        }
+                    }
+                }
+            }
+        } else {
+            // Sparse: visit only the k whose Base group is non-zero.
+            unsigned msk = mask;
+            while (msk) {
+                const int k = __ffs(msk) - 1;
+                msk &= msk - 1;
+                const Elt* row = bs + k * BN;
+                const V4 y0 = *reinterpret_cast<const V4*>(row + lane * 4);
+                const V4 y1 = *reinterpret_cast<const V4*>(row + 128 + lane * 4);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const Elt x = as[r * BK + k];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        part[r][c] = Op::mac(x, comp<V4, Elt>(y0, c), part[r][c]);
+                        part[r][4 + c] = Op::mac(x, comp<V4, Elt>(y1, c), part[r][4 + c]);
+                    }
+                }
+            }
+        }
+        if (Op::kBlocked) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    acc[r][c] += part[r][c];
+                    part[r][c] = Acc(0);
+                }
+        }
+        __syncthreads();
+    }
+    if (!Op::kBlocked) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = part[r][c];
+    }
+
+    // Epilogue: rows m0+row0+r, columns n0 + lane*4 (+128).
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int64_t gm = m0 + row0 + r;
+        if (gm >= M) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t gn = n0 + h * 128 + lane * 4;
+            Acc* dst = C + gm * ldc + gn;
+            if (vec && gn + 3 < N) {
+                A4 v;
+                v.x = acc[r][4 * h + 0];
+                v.y = acc[r][4 * h + 1];
+                v.z = acc[r][4 * h + 2];
+                v.w = acc[r][4 * h + 3];
+                *reinterpret_cast<A4*>(dst) = v;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (gn + c < N) dst[c] = acc[r][4 * h + c];
+            }
+        }
+    }
+}
+
+inline bool aligned16(const void* p) {
+    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+template <class Op>
+afmm_status launch_simt(const typename Op::Elt* A, int64_t lda,
+                        const typename Op::Elt* B, int64_t ldb,
+                        typename Op::Acc* C, int64_t ldc, int64_t M, int64_t N,
+                        int64_t K, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return AFMM_OK;
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(
+        simt_gemm_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SMEM_BYTES));
+    const int vec = (lda % 4 == 0) && (ldb % 4 == 0) && (ldc % 4 == 0) &&
+                    aligned16(A) && aligned16(B) && aligned16(C);
+    const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
+    if (gy > 65535) return AFMM_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    main_kernel_begin(st);
+    simt_gemm_kernel<Op><<<grid, THREADS, SMEM_BYTES, st>>>(A, lda, B, ldb, C,
+                                                           ldc, M, N, K, vec);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    main_kernel_end(st, (int)(gx * gy));
+    count_launches(1);
+    return AFMM_OK;
+}
+
+}  // namespace
+
+afmm_status launch_simt_f32(const float* A, int64_t lda, const float* B,
+                            int64_t ldb, float* C, int64_t ldc, int64_t M,
+                            int64_t N, int64_t K, cudaStream_t st) {
+    return launch_simt<OpF32>(A, lda, B, ldb, C, ldc, M, N, K, st);
+}
+
+afmm_status launch_simt_dp4a(const int8_t* A, int64_t lda, const int32_t* W,
+                             int64_t ldw, int32_t* C, int64_t ldc, int64_t M,
+                             int64_t N, int64_t K, cudaStream_t st) {
+    if (lda % 4 != 0) return AFMM_ERR_INVALID_ARG;
+    // K counted in 4-byte words of packed int8.
+    return launch_simt<OpDp4a>(reinterpret_cast<const int32_t*>(A), lda / 4,
+                               W, ldw, C, ldc, M, N, (K + 3) / 4, st);
+}
+
+}  // namespace afmm

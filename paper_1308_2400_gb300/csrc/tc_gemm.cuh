@@ -1,0 +1,36 @@
+// Tensor-core (tcgen05 / TMEM / TMA) path of libafmm: internal interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "afmm.h"
+
+namespace afmm {
+
+// Per-plan state of the tensor-core variants: operand buffers in the
+// workspace and the TMA descriptors that read them.
+struct TcPlan {
+    int64_t n = 0;
+    int slices = 3;
+    int64_t ld_a = 0, ld_b = 0;     // leading dims (elements) of A / B operands
+    int64_t rows_a = 0, rows_b = 0; // rows of the stacked A / B buffers
+    size_t a_bytes = 0, b_bytes = 0;
+    void* a = nullptr;              // BF16 A operand(s), K-major
+    void* b = nullptr;              // BF16 B operand(s), K-major (B^T rows)
+    bool sliced_a = true;           // real factor on the A side (case A)
+    alignas(64) unsigned char tmap_a[128];
+    alignas(64) unsigned char tmap_b[128];
+    bool maps_ready = false;
+};
+
+// True when this device can run the tensor-core kernels (sm_103).
+bool tc_available();
+void tc_layout(TcPlan* t, const afmm_desc& d, int slices);
+afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b);
+// Split / widen the operands and run the tcgen05 product into Z (F32).
+afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
+                         const void* Y, void* Z, int* status, cudaStream_t st);
+
+}  // namespace afmm

@@ -1,0 +1,299 @@
+"""Parity of the CUDA library with the CPU oracle (GPU tests).
+
+Every product goes through the C ABI (the Python binding only marshals
+arguments) and is compared element by element with the FP64 / int64 oracle
+on the same seeded inputs:
+
+* integer work is bit-exact;
+* FP32-target variants meet the relative Frobenius bar 1e-6, and each
+  element meets the rounding bound of the kernel's summation (derived in
+  ``simt_f32_elem_bound``);
+* FP64-target variants meet 1e-12 and an element bound of the slicing
+  truncation plus recombination rounding.
+
+Sizes span several tiles and ragged tails; at the workloads' full sizes the
+oracle checks sampled rows.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import afmm_inputs as W
+from _helpers import (FP32_REL_FRO, FP64_REL_FRO, U32, U64, abs_product,
+                      oracle_rows, rel_fro, run_gpu, sample_rows, torch_of)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SIMT_BK = 32          # k-tile of the CUDA-core kernel (K-blocked sums)
+RAGGED = [1, 2, 7, 33, 63, 65, 127, 129, 257, 300]
+
+
+def simt_f32_elem_bound(inst, rows=None):
+    """Worst-case rounding of the K-blocked FP32 sum, to first order.
+
+    Each product is formed exactly by the FMA and rounded once when added;
+    a k tile sums at most 32 terms from zero, then <= ceil(n/32) tile sums
+    are added to the running total: error <= (32 + ceil(n/32) + 1) u32
+    sum|x y| for each element, plus the rounding of the real factor to
+    FP32 (u32 each) when it arrives in FP64.
+    """
+    n = inst.n
+    g = (SIMT_BK + -(-n // SIMT_BK) + 2) * U32
+    return g * abs_product(inst, rows) + 1e-30
+
+
+def check_fp32(inst, Z, rows=None):
+    R = oracle_rows(inst, rows)
+    Zs = Z if rows is None else Z[rows]
+    assert np.all(np.isfinite(Zs))
+    err = rel_fro(Zs, R)
+    assert err <= FP32_REL_FRO, (inst.name, err)
+    bound = simt_f32_elem_bound(inst, rows)
+    bad = np.abs(Zs.astype(np.float64) - R) > bound
+    assert not bad.any(), (inst.name, int(bad.sum()))
+    return err
+
+
+# ------------------------------------------------------------------ K1 FP32
+@pytest.mark.parametrize("n", RAGGED)
+@pytest.mark.parametrize("workload", ["caseB_n4096_f32", "caseA_n8192_e4m3"])
+def test_simt_f32_ragged(workload, n):
+    inst = W.make(workload, n=n, seed=n)
+    Z, info = run_gpu(inst, variant=0)
+    assert info["variant"] == 0
+    check_fp32(inst, Z)
+
+
+def test_simt_f32_sparse_base_skips():
+    """Very sparse Base factor: whole 8-row groups are zero for most k."""
+    rng = np.random.default_rng(3)
+    n = 515
+    X = rng.uniform(-1, 1, size=(n, n)).astype(np.float32)
+    X[rng.random((n, n)) > 0.03] = 0
+    X[64:128] = 0                       # an all-zero 64-row tile
+    Y = rng.integers(0, 10, size=(n, n)).astype(np.int32)
+    inst = W.Instance("A", X, Y, name="sparse", x_dtype="f32", y_dtype="i32",
+                      z_dtype="f32", target="fp32")
+    Z, _ = run_gpu(inst, variant=0)
+    check_fp32(inst, Z)
+    assert np.all(Z[64:128] == 0)
+
+
+def test_simt_f32_case_b_full_size_sampled():
+    inst = W.make("caseB_n4096_f32")
+    Z, _ = run_gpu(inst, variant=0)
+    check_fp32(inst, Z, sample_rows(inst.n, 24))
+
+
+def test_simt_f32_case_a_full_size_sampled():
+    inst = W.make("caseA_n8192_e4m3")
+    Z, _ = run_gpu(inst, variant=0)
+    check_fp32(inst, Z, sample_rows(inst.n, 12))
+
+
+# ------------------------------------------------------------------ exact
+@pytest.mark.parametrize("n", RAGGED)
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_simt_exact_ragged(case, n):
+    inst = W.make("caseA_n16384_i8", n=n, seed=n)
+    if case == "B":   # X Rep-factors, Y integer Base values
+        inst = W.Instance("B", inst.Y.copy(), inst.X.copy(), name="exactB",
+                          x_dtype="i8", y_dtype="i8", z_dtype="i32",
+                          target="exact")
+    Z, info = run_gpu(inst, variant=4)
+    R = oracle_rows(inst)
+    assert np.array_equal(Z.astype(np.int64), R)
+
+
+def test_simt_exact_worst_case_magnitudes():
+    """All entries at the int8 extremes: |Z| reaches n * 128 * 127."""
+    n = 1024
+    X = np.full((n, n), -128, dtype=np.int8)
+    X[1::2] = 127
+    Y = np.full((n, n), 127, dtype=np.int8)
+    inst = W.Instance("A", X, Y, name="worst", x_dtype="i8", y_dtype="i8",
+                      z_dtype="i32", target="exact")
+    Z, _ = run_gpu(inst, variant=4)
+    assert np.array_equal(Z.astype(np.int64), oracle_rows(inst))
+
+
+def test_simt_exact_full_size_sampled():
+    inst = W.make("caseA_n16384_i8")
+    Z, _ = run_gpu(inst, variant=4)
+    rows = sample_rows(inst.n, 6)
+    assert np.array_equal(Z[rows].astype(np.int64), oracle_rows(inst, rows))
+
+
+# ------------------------------------------------------------------ FP64
+def f64slice_elem_bound(inst):
+    """Truncation of 56-bit row-scaled digits (< 2^(E_i - 56) per entry,
+    E_i the row's exponent bound <= 2 max|x|) plus the FP64 recombination
+    (9 roundings of at most 2 sum|x y| each)."""
+    real = inst.X if inst.case == "A" else inst.Y.T
+    rep = inst.Y if inst.case == "A" else inst.X.T
+    rowmax = np.abs(real.astype(np.float64)).max(axis=1, initial=0.0)
+    trunc = (2.0 * rowmax * 2.0 ** -56)[:, None] * np.abs(rep).sum(axis=0)[None, :]
+    if inst.case == "B":
+        trunc = trunc.T
+    return trunc + 24 * U64 * abs_product(inst) + 1e-300
+
+
+@pytest.mark.parametrize("n", RAGGED + [256])
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_simt_f64slice(case, n):
+    inst = W.make("caseA_n256_f64", n=n, seed=n)
+    if case == "B":
+        inst = W.Instance("B", inst.Y.copy(), inst.X.T.copy(), name="f64B",
+                          x_dtype="i32", y_dtype="f64", z_dtype="f64",
+                          target="fp64")
+    Z, info = run_gpu(inst, variant=3)
+    R = oracle_rows(inst)
+    assert rel_fro(Z, R) <= FP64_REL_FRO
+    assert not (np.abs(Z - R) > f64slice_elem_bound(inst)).any()
+
+
+def test_simt_f64slice_config_size():
+    inst = W.make("caseA_n256_f64")
+    Z, info = run_gpu(inst)               # planner picks the FP64 form
+    assert info["variant"] == 3 and info["slices"] == 8
+    R = oracle_rows(inst)
+    assert rel_fro(Z, R) <= FP64_REL_FRO
+
+
+def test_f64slice_wide_dynamic_range():
+    """Rows mixing magnitudes 2^-40 .. 2^40: row scaling keeps 1e-12."""
+    rng = np.random.default_rng(5)
+    n = 96
+    X = rng.uniform(-1, 1, size=(n, n)) * 2.0 ** rng.integers(-40, 41, size=(n, 1))
+    Y = rng.integers(0, 10, size=(n, n)).astype(np.int32)
+    inst = W.Instance("A", X, Y, name="range", x_dtype="f64", y_dtype="i32",
+                      z_dtype="f64", target="fp64")
+    Z, _ = run_gpu(inst, variant=3)
+    R = oracle_rows(inst)
+    rel_rows = np.linalg.norm(Z - R, axis=1) / np.maximum(np.linalg.norm(R, axis=1), 1e-300)
+    assert rel_rows.max() <= FP64_REL_FRO
+
+
+# ------------------------------------------------------------------ boundary
+def test_validation_reports_bad_rep_factors():
+    from paper_1308_2400_gb300 import AfmmError, Plan, make_desc
+    n = 70
+    X = torch.ones((n, n), dtype=torch.float32, device="cuda")
+    Y = torch.ones((n, n), dtype=torch.int32, device="cuda")
+    Y[5, 7] = -2
+    Z = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    p = Plan(make_desc(n, "A", "f32", "i32", "f32", "fp32", variant=0,
+                       flags=1))
+    p(X, Y, Z)
+    with pytest.raises(AfmmError) as e:
+        p.sync()
+    assert e.value.status == 3          # AFMM_ERR_NEGATIVE_REP
+    Yf = torch.ones((n, n), dtype=torch.float32, device="cuda")
+    Yf[0, 0] = 0.5
+    q = Plan(make_desc(n, "A", "f32", "f32", "f32", "fp32", variant=0,
+                       flags=1))
+    q(X, Yf, Z)
+    with pytest.raises(AfmmError) as e:
+        q.sync()
+    assert e.value.status == 9          # AFMM_ERR_NONINTEGER_REP
+    Y[5, 7] = 3                          # the status word was cleared
+    p(X, Y, Z)
+    p.sync()
+
+
+def test_validation_measures_paper_parameters():
+    from oracle import expected_additions, realised_parameters
+    from paper_1308_2400_gb300 import Plan
+    from _helpers import desc_for
+    inst = W.make("caseB_n4096_f32", n=300, seed=9)
+    X, Y = torch_of(inst.X), torch_of(inst.Y)
+    Z = torch.empty((300, 300), dtype=torch.float32, device="cuda")
+    p = Plan(desc_for(inst, variant=0, flags=1, hints=False))
+    p(X, Y, Z)
+    p.sync()
+    info = p.info
+    ref = realised_parameters(inst.X, inst.Y, "B")
+    for k in ("d1", "d2", "mu_prime", "mu"):
+        assert abs(info[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), k
+    e = expected_additions(ref["mu_prime"], ref["d1"], ref["d2"], 300)
+    assert abs(info["expected_additions"] - e) <= 1e-9 * e
+    assert info["rep_max"] == inst.X.max()
+
+
+def test_host_buffers_match_device_buffers():
+    from paper_1308_2400_gb300 import Plan
+    from _helpers import desc_for
+    inst = W.make("caseB_n4096_f32", n=200, seed=2)
+    Zd, _ = run_gpu(inst, variant=0)
+    Zh = np.full((200, 200), np.nan, dtype=np.float32)
+    p = Plan(desc_for(inst, variant=0))
+    p(np.ascontiguousarray(inst.X), np.ascontiguousarray(inst.Y), Zh)
+    p.sync()
+    assert np.array_equal(Zh, Zd)
+    # pinned host memory
+    Xp = torch.from_numpy(inst.X).pin_memory()
+    Yp = torch.from_numpy(inst.Y).pin_memory()
+    Zp = torch.empty((200, 200), dtype=torch.float32).pin_memory()
+    p(Xp, Yp, Zp)
+    p.sync()
+    assert np.array_equal(Zp.numpy(), Zd)
+
+
+def test_leading_dimensions():
+    from paper_1308_2400_gb300 import Plan, make_desc
+    rng = np.random.default_rng(4)
+    n, pad = 131, 9
+    Xb = rng.uniform(-1, 1, size=(n, n + pad)).astype(np.float32)
+    Yb = rng.integers(0, 9, size=(n, n + pad + 3)).astype(np.int32)
+    X, Y = Xb[:, :n], Yb[:, :n]
+    Zb = torch.full((n, n + 5), 7.0, dtype=torch.float32, device="cuda")
+    p = Plan(make_desc(n, "A", "f32", "i32", "f32", "fp32", variant=0,
+                       ldx=n + pad, ldy=n + pad + 3, ldz=n + 5))
+    p(torch_of(Xb), torch_of(Yb), Zb)
+    p.sync()
+    Z = Zb.cpu().numpy()
+    inst = W.Instance("A", X, Y, x_dtype="f32", y_dtype="i32")
+    check_fp32(inst, Z[:, :n])
+    assert np.all(Z[:, n:] == 7.0)      # padding columns untouched
+
+
+def test_empty_problem():
+    from paper_1308_2400_gb300 import Plan, make_desc
+    p = Plan(make_desc(0, "A", "f32", "i32", "f32", "fp32"))
+    e = torch.empty((0, 0), dtype=torch.float32, device="cuda")
+    p(e, torch.empty((0, 0), dtype=torch.int32, device="cuda"), e)
+    p.sync()
+
+
+def test_error_norm_kernel():
+    from paper_1308_2400_gb300 import afmm_error_norm
+    rng = np.random.default_rng(6)
+    R = rng.standard_normal((333, 517))
+    Z = (R + 1e-7 * rng.standard_normal(R.shape)).astype(np.float32)
+    d, r, m = afmm_error_norm(torch_of(Z), "f32", 517, torch_of(R), "f64",
+                              517, 333, 517)
+    D = Z.astype(np.float64) - R
+    assert abs(d - np.linalg.norm(D)) <= 1e-12 * np.linalg.norm(D)
+    assert abs(r - np.linalg.norm(R)) <= 1e-12 * np.linalg.norm(R)
+    assert m == np.abs(D).max()
+
+
+def test_batched_small_mix():
+    from paper_1308_2400_gb300 import afmm_mul_batched
+    from _helpers import desc_for, gpu_operands, z_torch_dtype
+    insts = W.batched_mix(count=10, seed=1, n_min=16, n_max=160)
+    descs, Xs, Ys, Zs = [], [], [], []
+    for inst in insts:
+        X, Y = gpu_operands(inst)
+        descs.append(desc_for(inst))
+        Xs.append(X)
+        Ys.append(Y)
+        Zs.append(torch.empty((inst.n, inst.n), dtype=torch.float32,
+                              device="cuda"))
+    afmm_mul_batched(descs, Xs, Ys, Zs)
+    torch.cuda.synchronize()
+    for inst, Z in zip(insts, Zs):
+        R = oracle_rows(inst)
+        assert rel_fro(Z.cpu().numpy(), R) <= FP32_REL_FRO, inst.name
