@@ -202,6 +202,13 @@ typedef struct {
 afmm_status afmm_plan_enable_kernel_timing(afmm_plan plan, int enable);
 afmm_status afmm_plan_counters(afmm_plan plan, afmm_counters* out);
 
+/* Self-test of the bounded waits every tensor-core kernel uses: launches
+ * one CTA that waits on an mbarrier nothing will complete, for at most
+ * `limit_ns` nanoseconds (capped at 2 s), and returns the status the
+ * kernel recorded: AFMM_ERR_TIMEOUT when the wait ran out as designed.
+ * The CUDA context stays usable.  Synchronises `stream`. */
+afmm_status afmm_selftest_bounded_wait(uint64_t limit_ns, void* stream);
+
 /* Batched product: `count` independent instances (Sec. 2 problems of
  * possibly different n and case), each described by descs[t] and computed
  * with the variant its own plan would pick, in one call on `stream`.

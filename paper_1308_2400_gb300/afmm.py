@@ -126,6 +126,7 @@ def _lib():
             "afmm_get_info": ([_VP, ctypes.POINTER(afmm_info)], st),
             "afmm_plan_enable_kernel_timing": ([_VP, ctypes.c_int], st),
             "afmm_plan_counters": ([_VP, ctypes.POINTER(afmm_counters)], st),
+            "afmm_selftest_bounded_wait": ([ctypes.c_uint64, _VP], st),
             "afmm_mul_batched": ([ctypes.c_int, ctypes.POINTER(afmm_desc),
                                   ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                   ctypes.POINTER(_VP), _VP], st),
@@ -264,6 +265,11 @@ def afmm_plan_counters(plan: int) -> dict:
            "afmm_plan_counters")
     return {f: getattr(c, f) for f, _ in afmm_counters._fields_
             if f != "reserved_"}
+
+
+def afmm_selftest_bounded_wait(limit_ns: int, stream=None) -> int:
+    """Status recorded by a kernel whose bounded wait must run out."""
+    return int(_lib().afmm_selftest_bounded_wait(int(limit_ns), _stream(stream)))
 
 
 def afmm_mul_batched(descs: Sequence[afmm_desc], X: Sequence, Y: Sequence,

@@ -649,6 +649,12 @@ afmm_status afmm_plan_counters(afmm_plan p, afmm_counters* out) {
     return AFMM_OK;
 }
 
+afmm_status afmm_selftest_bounded_wait(uint64_t limit_ns, void* stream) {
+    DeviceProps dp;
+    AFMM_TRY(device_props(&dp));
+    return tc_selftest_bounded_wait(limit_ns, static_cast<cudaStream_t>(stream));
+}
+
 afmm_status afmm_mul_batched(int count, const afmm_desc* descs,
                              const void* const* X, const void* const* Y,
                              void* const* Z, void* stream) {

@@ -33,4 +33,8 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b);
 afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st);
 
+// Launch a kernel whose only wait can never complete; returns the status
+// it recorded (AFMM_ERR_TIMEOUT expected).
+afmm_status tc_selftest_bounded_wait(uint64_t limit_ns, cudaStream_t st);
+
 }  // namespace afmm

@@ -44,13 +44,25 @@ def simt_f32_elem_bound(inst, rows=None):
     return g * abs_product(inst, rows) + 1e-30
 
 
-def check_fp32(inst, Z, rows=None):
+def tc_elem_bound(inst, rows=None, slices=3):
+    """Rounding of the tensor-core form, to first order.
+
+    The slices of an FP32 value are exact (hi + mid + lo == x); each MMA
+    adds 16-term products of every slice into the FP32 accumulator, so an
+    element sees at most slices * ceil(n/16) + 16 roundings of at most
+    sum|x y|; the factor 2 allows a truncating accumulator.
+    """
+    g = 2 * (slices * -(-inst.n // 16) + 18) * U32
+    return g * abs_product(inst, rows) + 1e-30
+
+
+def check_fp32(inst, Z, rows=None, bound_fn=None):
     R = oracle_rows(inst, rows)
     Zs = Z if rows is None else Z[rows]
     assert np.all(np.isfinite(Zs))
     err = rel_fro(Zs, R)
     assert err <= FP32_REL_FRO, (inst.name, err)
-    bound = simt_f32_elem_bound(inst, rows)
+    bound = (bound_fn or simt_f32_elem_bound)(inst, rows)
     bad = np.abs(Zs.astype(np.float64) - R) > bound
     assert not bad.any(), (inst.name, int(bad.sum()))
     return err
@@ -91,6 +103,68 @@ def test_simt_f32_case_a_full_size_sampled():
     inst = W.make("caseA_n8192_e4m3")
     Z, _ = run_gpu(inst, variant=0)
     check_fp32(inst, Z, sample_rows(inst.n, 12))
+
+
+# ------------------------------------------------------------------ tcgen05
+TC_RAGGED = [1, 7, 33, 127, 128, 129, 255, 256, 257, 300, 513]
+
+
+@pytest.mark.parametrize("n", TC_RAGGED)
+@pytest.mark.parametrize("workload", ["caseA_n8192_e4m3", "caseB_n4096_f32"])
+def test_tc_bf16x3_ragged(workload, n):
+    inst = W.make(workload, n=n, seed=n + 1)
+    Z, info = run_gpu(inst, variant=1)
+    assert info["variant"] == 1 and info["slices"] == 3
+    check_fp32(inst, Z, bound_fn=tc_elem_bound)
+
+
+def test_tc_bf16x3_case_a_full_size_sampled():
+    inst = W.make("caseA_n8192_e4m3")
+    Z, info = run_gpu(inst)                 # the planner's choice
+    assert info["variant"] == 1
+    check_fp32(inst, Z, sample_rows(inst.n, 12), bound_fn=tc_elem_bound)
+
+
+def test_tc_bf16x3_case_b_full_size_sampled():
+    inst = W.make("caseB_n4096_f32")
+    Z, info = run_gpu(inst, variant=1)
+    check_fp32(inst, Z, sample_rows(inst.n, 24), bound_fn=tc_elem_bound)
+
+
+def test_tc_accumulation_is_exact_for_integers():
+    """Integer operands whose partial sums stay below 2^24 must come out
+    exact from the FP32 tensor-core accumulator (products are exact in
+    FP32 and every partial sum is representable)."""
+    rng = np.random.default_rng(21)
+    n = 2048                            # |partial| <= 2048 * 255 * 16 < 2^24
+    X = rng.integers(-255, 256, size=(n, n)).astype(np.float32)
+    X[0, :] = 255.0
+    Y = rng.integers(0, 17, size=(n, n)).astype(np.int32)
+    Y[:, 0] = 16
+    inst = W.Instance("A", X, Y, name="probe", x_dtype="f32", y_dtype="i32",
+                      z_dtype="f32", target="fp32")
+    Z, _ = run_gpu(inst, variant=1)
+    R = X.astype(np.int64) @ Y.astype(np.int64)
+    assert np.array_equal(Z.astype(np.int64), R)
+
+
+def test_tc_two_slices_fall_short_of_fp32():
+    """hi + lo BF16 keeps ~16 bits of each value: the error is well above
+    the three-slice form and above the FP32 bar on this workload."""
+    inst = W.make("caseA_n8192_e4m3", n=1024, seed=3)
+    Z2, _ = run_gpu(inst, variant=2)
+    Z3, _ = run_gpu(inst, variant=1)
+    R = oracle_rows(inst)
+    e2, e3 = rel_fro(Z2, R), rel_fro(Z3, R)
+    assert 1e-6 < e2 < 1e-4 and e3 < 1e-6 and e2 > 4 * e3
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    from paper_1308_2400_gb300.afmm import afmm_selftest_bounded_wait
+    assert afmm_selftest_bounded_wait(50_000_000) == 7      # AFMM_ERR_TIMEOUT
+    inst = W.make("caseA_n8192_e4m3", n=200, seed=4)
+    Z, _ = run_gpu(inst, variant=1)
+    check_fp32(inst, Z, bound_fn=tc_elem_bound)
 
 
 # ------------------------------------------------------------------ exact
