@@ -130,7 +130,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     const uint32_t tmem = bars->tmem_base;
     volatile int* abort = &bars->abort;
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 0) {
+        if (lane == 0) {
         // ---------------------------------------------------- TMA producer
         int stage = 0;
         uint32_t phase = 0;
@@ -172,7 +173,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                     ptx::mbar_wait_bounded(&bars->full[s], (uint32_t)issued_phase[s],
                                            &never, WAIT_LIMIT_NS);
         }
-    } else if (warp == 1 && lane == 0) {
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
         // ---------------------------------------------------- MMA issuer
         constexpr uint32_t IDESC = ptx::idesc_bf16_f32(TC_BM, TC_BN);
         int stage = 0;
@@ -227,7 +231,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
         ptx::mma_commit(&bars->drain);
         volatile int never = 0;
         ptx::mbar_wait_bounded(&bars->drain, 0u, &never, WAIT_LIMIT_NS);
-    } else if (warp >= 2) {
+        }
+        __syncwarp();
+    } else {
         // ---------------------------------------------------- epilogue
         const int q = warp & 3;                 // TMEM lanes 32q .. 32q+31
         const int row = q * 32 + lane;
@@ -236,8 +242,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
         for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
             int tm, tn;
             tile_coords(tile, tiles_m, tiles_n, tm, tn);
-            if (!ptx::mbar_wait_bounded(&bars->tfull[acc], acc_phase, abort,
-                                        WAIT_LIMIT_NS)) {
+            const bool got = ptx::mbar_wait_bounded(&bars->tfull[acc], acc_phase,
+                                                    abort, WAIT_LIMIT_NS);
+            // TMEM loads below are warp-collective: decide as a warp.
+            if (!__all_sync(0xffffffffu, got)) {
                 if (lane == 0) raise_abort(bars, status);
                 break;
             }
@@ -281,6 +289,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     ptx::tc_fence_before();
     __syncthreads();
     if (warp == 1) {
+        __syncwarp();
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem, TMEM_COLS);
     }
