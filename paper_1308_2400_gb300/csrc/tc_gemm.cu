@@ -40,7 +40,8 @@ namespace afmm {
 namespace {
 
 constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 32;
-constexpr int TC_THREADS = 192;
+constexpr int TC_EPI_THREADS = 256;              // 8 epilogue warps
+constexpr int TC_THREADS = 64 + TC_EPI_THREADS;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int A_TILE_BYTES = TC_BM * TC_BK * 2;   // 8 KiB
 constexpr int B_TILE_BYTES = TC_BN * TC_BK * 2;   // 16 KiB
@@ -88,11 +89,12 @@ __device__ __forceinline__ void raise_abort(TcBars* b, int* status) {
     atomicCAS(status, 0, (int)AFMM_ERR_TIMEOUT);
 }
 
-template <int SA, int SB>
+template <int SA, int SB, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-               const __grid_constant__ CUtensorMap tmB, float* __restrict__ Z,
-               int64_t ldz, int M, int N, int K, int vec, int* status) {
+               const __grid_constant__ CUtensorMap tmB, void* __restrict__ Zv,
+               int64_t ldz, int M, int N, int K, int kb_per_chunk, int vec,
+               int* status) {
     using Cfg = TcCfg<SA, SB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
@@ -103,6 +105,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
     const int num_tiles = tiles_m * tiles_n;
     const int num_kb = (K + TC_BK - 1) / TC_BK;
+    const int kbpc = kb_per_chunk > 0 ? kb_per_chunk : num_kb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -111,7 +114,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
         }
         for (int a = 0; a < 2; ++a) {
             ptx::mbar_init(&bars->tfull[a], 1);
-            ptx::mbar_init(&bars->tempty[a], 128);
+            ptx::mbar_init(&bars->tempty[a], TC_EPI_THREADS);
         }
         ptx::mbar_init(&bars->drain, 1);
         bars->abort = 0;
@@ -131,158 +134,237 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     volatile int* abort = &bars->abort;
 
     if (warp == 0) {
-        if (lane == 0) {
         // ---------------------------------------------------- TMA producer
-        int stage = 0;
-        uint32_t phase = 0;
-        int issued_phase[8];
-        for (int s = 0; s < 8; ++s) issued_phase[s] = -1;
-        bool ok = true;
-        for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-            int tm, tn;
-            tile_coords(tile, tiles_m, tiles_n, tm, tn);
-            for (int kb = 0; kb < num_kb; ++kb) {
-                if (!ptx::mbar_wait_bounded(&bars->empty[stage], phase ^ 1u,
-                                            abort, WAIT_LIMIT_NS)) {
-                    ok = false;
-                    break;
-                }
-                ptx::mbar_arrive_expect_tx(&bars->full[stage], Cfg::STAGE_BYTES);
-                uint8_t* st = tiles + stage * Cfg::STAGE_BYTES;
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued_phase[8];
+            for (int s = 0; s < 8; ++s) issued_phase[s] = -1;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+                int tm, tn;
+                tile_coords(tile, tiles_m, tiles_n, tm, tn);
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!ptx::mbar_wait_bounded(&bars->empty[stage], phase ^ 1u, abort,
+                                                WAIT_LIMIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::mbar_arrive_expect_tx(&bars->full[stage], Cfg::STAGE_BYTES);
+                    uint8_t* st = tiles + stage * Cfg::STAGE_BYTES;
 #pragma unroll
-                for (int s = 0; s < SA; ++s)
-                    ptx::tma_load_3d(st + s * A_TILE_BYTES, &tmA, &bars->full[stage],
-                                     kb * TC_BK, tm * TC_BM, s);
+                    for (int s = 0; s < SA; ++s)
+                        ptx::tma_load_3d(st + s * A_TILE_BYTES, &tmA, &bars->full[stage],
+                                         kb * TC_BK, tm * TC_BM, s);
 #pragma unroll
-                for (int s = 0; s < SB; ++s)
-                    ptx::tma_load_3d(st + SA * A_TILE_BYTES + s * B_TILE_BYTES, &tmB,
-                                     &bars->full[stage], kb * TC_BK, tn * TC_BN, s);
-                issued_phase[stage] = (int)phase;
-                if (++stage == Cfg::STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
+                    for (int s = 0; s < SB; ++s)
+                        ptx::tma_load_3d(st + SA * A_TILE_BYTES + s * B_TILE_BYTES, &tmB,
+                                         &bars->full[stage], kb * TC_BK, tn * TC_BN, s);
+                    issued_phase[stage] = (int)phase;
+                    if (++stage == Cfg::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
                 }
             }
-        }
-        if (!ok) {
-            raise_abort(bars, status);
-            // Let this CTA's copies in flight land before it exits.
-            volatile int never = 0;
-            for (int s = 0; s < Cfg::STAGES; ++s)
-                if (issued_phase[s] >= 0)
-                    ptx::mbar_wait_bounded(&bars->full[s], (uint32_t)issued_phase[s],
-                                           &never, WAIT_LIMIT_NS);
-        }
+            if (!ok) {
+                raise_abort(bars, status);
+                // Let this CTA's copies in flight land before it exits.
+                volatile int never = 0;
+                for (int s = 0; s < Cfg::STAGES; ++s)
+                    if (issued_phase[s] >= 0)
+                        ptx::mbar_wait_bounded(&bars->full[s], (uint32_t)issued_phase[s],
+                                               &never, WAIT_LIMIT_NS);
+            }
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {
         // ---------------------------------------------------- MMA issuer
-        constexpr uint32_t IDESC = ptx::idesc_bf16_f32(TC_BM, TC_BN);
-        int stage = 0;
-        uint32_t phase = 0;
-        int acc = 0;
-        uint32_t acc_phase = 0;
-        bool ok = true;
-        for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-            if (!ptx::mbar_wait_bounded(&bars->tempty[acc], acc_phase ^ 1u, abort,
-                                        WAIT_LIMIT_NS)) {
-                ok = false;
-                break;
-            }
-            ptx::tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(acc * TC_BN);
-            for (int kb = 0; kb < num_kb; ++kb) {
-                if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
-                                            WAIT_LIMIT_NS)) {
-                    ok = false;
-                    break;
-                }
-                ptx::tc_fence_after();
-                const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
-#pragma unroll
-                for (int ks = 0; ks < TC_BK / 16; ++ks) {
-#pragma unroll
-                    for (int p = 0; p < Cfg::P; ++p) {
-                        const uint32_t a_addr =
-                            s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
-                        const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
-                                                (SB > 1 ? p : 0) * B_TILE_BYTES + ks * 32;
-                        ptx::mma_f16(d, ptx::sdesc_kmajor_sw64(a_addr),
-                                     ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                     (kb | ks | p) != 0 ? 1u : 0u);
+        // Each tile's K range is cut into chunks of kbpc k-blocks; chunk c
+        // of the CTA accumulates from zero into TMEM slot c % 2, so the
+        // epilogue folds one chunk while the next is being multiplied.
+        if (lane == 0) {
+            constexpr uint32_t IDESC = ptx::idesc_bf16_f32(TC_BM, TC_BN);
+            // Smallest-slice-first needs the chunk's stages resident at once
+            // and at least two more stages left for the producer.
+            const bool small_first =
+                MODE == 0 && Cfg::P > 1 && kbpc <= Cfg::STAGES - 2 && kbpc <= 8;
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t slot_phase[2] = {0u, 0u};
+            int chunk = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+                for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kbpc) {
+                    const int slot = chunk & 1;
+                    if (!ptx::mbar_wait_bounded(&bars->tempty[slot], slot_phase[slot] ^ 1u,
+                                                abort, WAIT_LIMIT_NS)) {
+                        ok = false;
+                        break;
                     }
-                }
-                ptx::mma_commit(&bars->empty[stage]);
-                if (++stage == Cfg::STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
+                    ptx::tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(slot * TC_BN);
+                    const int kb1 = min(kb0 + kbpc, num_kb);
+                    if (small_first) {
+                        // All stages of the chunk resident, then the slice
+                        // products from the smallest slice to the largest,
+                        // so each MMA adds into a partial sum of its own
+                        // magnitude.
+                        int st_[8];
+                        for (int kb = kb0; kb < kb1; ++kb) {
+                            if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
+                                                        WAIT_LIMIT_NS)) {
+                                ok = false;
+                                break;
+                            }
+                            st_[kb - kb0] = stage;
+                            if (++stage == Cfg::STAGES) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        ptx::tc_fence_after();
+                        bool first = true;
+#pragma unroll
+                        for (int p = Cfg::P - 1; p >= 0; --p) {
+                            for (int kb = kb0; kb < kb1; ++kb) {
+                                const uint32_t s0 = ptx::smem_addr(
+                                    tiles + st_[kb - kb0] * Cfg::STAGE_BYTES);
+#pragma unroll
+                                for (int ks = 0; ks < TC_BK / 16; ++ks) {
+                                    const uint32_t a_addr =
+                                        s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
+                                    const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
+                                                            (SB > 1 ? p : 0) * B_TILE_BYTES +
+                                                            ks * 32;
+                                    ptx::mma_f16(d, ptx::sdesc_kmajor_sw64(a_addr),
+                                                 ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                                 first ? 0u : 1u);
+                                    first = false;
+                                }
+                            }
+                        }
+                        for (int kb = kb0; kb < kb1; ++kb)
+                            ptx::mma_commit(&bars->empty[st_[kb - kb0]]);
+                    } else {
+                        for (int kb = kb0; kb < kb1; ++kb) {
+                            if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
+                                                        WAIT_LIMIT_NS)) {
+                                ok = false;
+                                break;
+                            }
+                            ptx::tc_fence_after();
+                            const uint32_t s0 =
+                                ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
+#pragma unroll
+                            for (int ks = 0; ks < TC_BK / 16; ++ks) {
+#pragma unroll
+                                for (int p = 0; p < Cfg::P; ++p) {
+                                    const uint32_t a_addr =
+                                        s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
+                                    const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
+                                                            (SB > 1 ? p : 0) * B_TILE_BYTES +
+                                                            ks * 32;
+                                    ptx::mma_f16(d, ptx::sdesc_kmajor_sw64(a_addr),
+                                                 ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                                 (kb != kb0 || ks != 0 || p != 0) ? 1u : 0u);
+                                }
+                            }
+                            ptx::mma_commit(&bars->empty[stage]);
+                            if (++stage == Cfg::STAGES) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                    }
+                    if (!ok) break;
+                    ptx::mma_commit(&bars->tfull[slot]);
+                    slot_phase[slot] ^= 1u;
+                    ++chunk;
                 }
             }
-            if (!ok) break;
-            ptx::mma_commit(&bars->tfull[acc]);
-            if (++acc == 2) {
-                acc = 0;
-                acc_phase ^= 1u;
-            }
-        }
-        if (!ok) raise_abort(bars, status);
-        // Every MMA issued above completes before TMEM is released.
-        ptx::mma_commit(&bars->drain);
-        volatile int never = 0;
-        ptx::mbar_wait_bounded(&bars->drain, 0u, &never, WAIT_LIMIT_NS);
+            if (!ok) raise_abort(bars, status);
+            // Every MMA issued above completes before TMEM is released.
+            ptx::mma_commit(&bars->drain);
+            volatile int never = 0;
+            ptx::mbar_wait_bounded(&bars->drain, 0u, &never, WAIT_LIMIT_NS);
         }
         __syncwarp();
     } else {
         // ---------------------------------------------------- epilogue
-        const int q = warp & 3;                 // TMEM lanes 32q .. 32q+31
+        // 8 warps: warp w reads TMEM lanes 32*(w%4).. (its rows) and half
+        // h of the 256 columns.  Each chunk is folded into running sums in
+        // registers with round-to-nearest FP32 adds (MODE 0) or exact int32
+        // adds of the chunk's integer partials (MODE 1).
+        using Acc = typename std::conditional<MODE == 0, float, int32_t>::type;
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
         const int row = q * 32 + lane;
-        int acc = 0;
-        uint32_t acc_phase = 0;
-        for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
+        uint32_t slot_phase[2] = {0u, 0u};
+        int chunk = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
             int tm, tn;
             tile_coords(tile, tiles_m, tiles_n, tm, tn);
-            const bool got = ptx::mbar_wait_bounded(&bars->tfull[acc], acc_phase,
-                                                    abort, WAIT_LIMIT_NS);
-            // TMEM loads below are warp-collective: decide as a warp.
-            if (!__all_sync(0xffffffffu, got)) {
-                if (lane == 0) raise_abort(bars, status);
-                break;
-            }
-            ptx::tc_fence_after();
-            const int64_t m = (int64_t)tm * TC_BM + row;
-            const int n0 = tn * TC_BN;
-#pragma unroll 1
-            for (int c = 0; c < TC_BN / 32; ++c) {
-                uint32_t r[32];
-                ptx::tmem_ld_32cols(tmem + ((uint32_t)(q * 32) << 16) +
-                                        (uint32_t)(acc * TC_BN + c * 32), r);
-                ptx::tmem_ld_wait();
-                if (m < M) {
-                    const int col = n0 + c * 32;
-                    float* zr = Z + m * ldz + col;
-                    if (vec && col + 32 <= N) {
+            Acc sum[128];
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4) {
-                            float4 v;
-                            v.x = __uint_as_float(r[j]);
-                            v.y = __uint_as_float(r[j + 1]);
-                            v.z = __uint_as_float(r[j + 2]);
-                            v.w = __uint_as_float(r[j + 3]);
-                            *reinterpret_cast<float4*>(zr + j) = v;
+            for (int j = 0; j < 128; ++j) sum[j] = Acc(0);
+            for (int kb0 = 0; kb0 < num_kb; kb0 += kbpc) {
+                const int slot = chunk & 1;
+                const bool got = ptx::mbar_wait_bounded(&bars->tfull[slot],
+                                                        slot_phase[slot], abort,
+                                                        WAIT_LIMIT_NS);
+                // TMEM loads below are warp-collective: decide as a warp.
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) raise_abort(bars, status);
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < 4; c += 2) {
+                    uint32_t r0[32], r1[32];
+                    ptx::tmem_ld_32cols(lane_base + (uint32_t)(slot * TC_BN + c * 32), r0);
+                    ptx::tmem_ld_32cols(lane_base + (uint32_t)(slot * TC_BN + c * 32 + 32), r1);
+                    ptx::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        if constexpr (MODE == 0) {
+                            sum[c * 32 + j] += __uint_as_float(r0[j]);
+                            sum[c * 32 + 32 + j] += __uint_as_float(r1[j]);
+                        } else {
+                            sum[c * 32 + j] += __float2int_rn(__uint_as_float(r0[j]));
+                            sum[c * 32 + 32 + j] += __float2int_rn(__uint_as_float(r1[j]));
                         }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (col + j < N) zr[j] = __uint_as_float(r[j]);
                     }
                 }
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&bars->tempty[slot]);
+                slot_phase[slot] ^= 1u;
+                ++chunk;
             }
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars->tempty[acc]);
-            if (++acc == 2) {
-                acc = 0;
-                acc_phase ^= 1u;
+            if (!ok) break;
+            const int64_t m = (int64_t)tm * TC_BM + row;
+            const int col0 = tn * TC_BN + h * 128;
+            if (m < M) {
+                Acc* zr = static_cast<Acc*>(Zv) + m * ldz + col0;
+                if (vec && col0 + 128 <= N) {
+#pragma unroll
+                    for (int j = 0; j < 128; j += 4) {
+                        if constexpr (MODE == 0)
+                            *reinterpret_cast<float4*>(zr + j) =
+                                make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
+                        else
+                            *reinterpret_cast<int4*>(zr + j) =
+                                make_int4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 128; ++j)
+                        if (col0 + j < N) zr[j] = sum[j];
+                }
             }
         }
     }
@@ -296,65 +378,125 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
 }
 
 // --------------------------------------------------------------- operands
+// Whether a dtype's values are exact in FP32 (then the split runs in FP32;
+// FP64 arithmetic is slow on this part and kept off the hot path).
+template <int DT>
+constexpr bool kExactInF32 = DT != AFMM_F64 && DT != AFMM_I32;
+
 // Round-to-nearest BF16 slices of v: out[0] = bf16(v), out[s] = bf16 of the
-// residual left by out[0..s-1].  Residuals are exact in FP64.
-template <int S>
-__device__ __forceinline__ void split_bf16(double v, __nv_bfloat16 (&out)[S]) {
-    double r = v;
+// residual left by out[0..s-1].  Each residual is exact in the arithmetic
+// used (FP32 for FP32-exact inputs, FP64 otherwise).
+template <int S, typename T>
+__device__ __forceinline__ void split_bf16(T v, __nv_bfloat16 (&out)[S]) {
+    T r = v;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        out[s] = __double2bfloat16(r);
-        r -= (double)__bfloat162float(out[s]);
+        if constexpr (sizeof(T) == 8) out[s] = __double2bfloat16(r);
+        else out[s] = __float2bfloat16_rn(r);
+        r -= (T)__bfloat162float(out[s]);
     }
 }
 
-// Rows kept as rows (K-major A operand): dst[(s*n + r)*ldk + c].
-// EXACT: a single slice that must equal the source (Rep-factors).
+template <int DT>
+__device__ __forceinline__ auto load_val(const void* p, int64_t i) {
+    if constexpr (kExactInF32<DT>) return (float)Elem<DT>::get(p, i);
+    else return Elem<DT>::get(p, i);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Rows kept as rows (K-major A operand): dst[(s*n + r)*ldk + c], eight
+// columns per thread (one 16-byte store per slice).  EXACT: one slice that
+// must equal the source (Rep-factors); otherwise OVERFLOW_RISK is recorded.
 template <int DT, int S, bool EXACT>
-__global__ void widen_rows_kernel(const void* __restrict__ src, int64_t n,
-                                  int64_t lds, __nv_bfloat16* __restrict__ dst,
-                                  int64_t ldk, int* status) {
-    const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+__global__ void __launch_bounds__(256)
+widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
+                  __nv_bfloat16* __restrict__ dst, int64_t ldk, int vec_f32,
+                  int* status) {
+    const int64_t c = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 8;
     if (c >= ldk) return;
     for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
-        __nv_bfloat16 o[S];
-        if (c < n) {
-            const double v = Elem<DT>::get(src, r * lds + c);
-            split_bf16<S>(v, o);
-            if (EXACT && (double)__bfloat162float(o[0]) != v)
-                atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
-        } else {
+        uint32_t w[S][4];
+        bool done = false;
+        if constexpr (DT == AFMM_F32) {
+            if (vec_f32 && c + 8 <= n) {
+                const float4* p = reinterpret_cast<const float4*>(
+                    static_cast<const float*>(src) + r * lds + c);
+                const float4 a = p[0], b = p[1];
+                const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int s = 0; s < S; ++s) o[s] = __float2bfloat16(0.0f);
+                for (int j = 0; j < 8; j += 2) {
+                    __nv_bfloat16 o0[S], o1[S];
+                    split_bf16<S>(v[j], o0);
+                    split_bf16<S>(v[j + 1], o1);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o0[s], o1[s]);
+                }
+                done = true;
+            }
         }
 #pragma unroll
-        for (int s = 0; s < S; ++s) dst[((int64_t)s * n + r) * ldk + c] = o[s];
+        for (int j = 0; j < 8 && !done; j += 2) {
+            __nv_bfloat16 o[2][S];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int64_t cc = c + j + t;
+                if (cc < n) {
+                    const auto v = load_val<DT>(src, r * lds + cc);
+                    split_bf16<S>(v, o[t]);
+                    if (EXACT && (decltype(v))__bfloat162float(o[t][0]) != v)
+                        atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) o[t][s] = __float2bfloat16_rn(0.0f);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o[0][s], o[1][s]);
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            *reinterpret_cast<uint4*>(dst + ((int64_t)s * n + r) * ldk + c) =
+                make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
     }
 }
 
 // Rows become columns (K-major B operand from a row-major K x N matrix):
-// dst[(s*n + c)*ldk + r] = slice_s(src[r][c]), 32 x 32 tiles via smem.
+// dst[(s*n + c)*ldk + r] = slice_s(src[r][c]).  64 x 64 tiles through
+// shared memory; each thread stores two adjacent BF16 values (4 bytes).
 template <int DT, int S, bool EXACT>
-__global__ void widen_transpose_kernel(const void* __restrict__ src, int64_t n,
-                                       int64_t lds, __nv_bfloat16* __restrict__ dst,
-                                       int64_t ldk, int* status) {
-    __shared__ double tile[32][33];
-    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int64_t r = r0 + i, c = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (r < n && c < n) ? Elem<DT>::get(src, r * lds + c) : 0.0;
+__global__ void __launch_bounds__(256)
+widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
+                       __nv_bfloat16* __restrict__ dst, int64_t ldk, int* status) {
+    using T = decltype(load_val<DT>(nullptr, 0));
+    __shared__ T tile[64][65];
+    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 64;
+    const int tx = threadIdx.x, ty = threadIdx.y;       // 32 x 8
+    for (int i = ty; i < 64; i += 8) {
+        const int64_t r = r0 + i;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t c = c0 + tx + 32 * h;
+            tile[i][tx + 32 * h] = (r < n && c < n) ? load_val<DT>(src, r * lds + c) : T(0);
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int64_t c = c0 + i, r = r0 + threadIdx.x;   // output row c, col r
+    for (int i = ty; i < 64; i += 8) {
+        const int64_t c = c0 + i;                 // output row
+        const int64_t r = r0 + 2 * tx;            // output columns r, r+1
         if (c < n && r < ldk) {
-            const double v = tile[threadIdx.x][i];
-            __nv_bfloat16 o[S];
-            split_bf16<S>(v, o);
-            if (EXACT && (double)__bfloat162float(o[0]) != v)
+            __nv_bfloat16 o0[S], o1[S];
+            const T v0 = tile[2 * tx][i], v1 = tile[2 * tx + 1][i];
+            split_bf16<S>(v0, o0);
+            split_bf16<S>(v1, o1);
+            if (EXACT && ((T)__bfloat162float(o0[0]) != v0 || (T)__bfloat162float(o1[0]) != v1))
                 atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
 #pragma unroll
-            for (int s = 0; s < S; ++s) dst[((int64_t)s * n + c) * ldk + r] = o[s];
+            for (int s = 0; s < S; ++s)
+                *reinterpret_cast<uint32_t*>(dst + ((int64_t)s * n + c) * ldk + r) =
+                    pack2(o0[s], o1[s]);
         }
     }
 }
@@ -363,9 +505,11 @@ template <int S, bool EXACT>
 afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
                               __nv_bfloat16* dst, int64_t ldk, int* status,
                               cudaStream_t st) {
-    const dim3 grid((unsigned)((ldk + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
+    const int64_t per_row = ldk / 8;
+    const dim3 grid((unsigned)((per_row + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
+    const int vec = (lds % 4 == 0) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
-        widen_rows_kernel<DT, S, EXACT><<<grid, 256, 0, st>>>(src, n, lds, dst, ldk,
+        widen_rows_kernel<DT, S, EXACT><<<grid, 256, 0, st>>>(src, n, lds, dst, ldk, vec,
                                                               status);
         return AFMM_OK;
     });
@@ -379,7 +523,7 @@ template <int S, bool EXACT>
 afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
                                    int64_t lds, __nv_bfloat16* dst, int64_t ldk,
                                    int* status, cudaStream_t st) {
-    const int64_t g = (n + 31) / 32;
+    const int64_t g = (n + 63) / 64;
     if (g > 65535) return AFMM_ERR_UNSUPPORTED;
     const dim3 grid((unsigned)g, (unsigned)g), block(32, 8);
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
@@ -427,16 +571,16 @@ afmm_status encode_map(void* out, void* base, int64_t cols, int64_t rows,
     return r == CUDA_SUCCESS ? AFMM_OK : AFMM_ERR_CUDA;
 }
 
-template <int SA, int SB>
-afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status,
-                      cudaStream_t st) {
+template <int SA, int SB, int MODE>
+afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
+                      int* status, cudaStream_t st) {
     using Cfg = TcCfg<SA, SB>;
     DeviceProps dp;
     AFMM_TRY(device_props(&dp));
     const int n = (int)t->n;
     const int tiles = ((n + TC_BM - 1) / TC_BM) * ((n + TC_BN - 1) / TC_BN);
     const int grid = tiles < dp.sm_count ? tiles : dp.sm_count;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
@@ -444,8 +588,8 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status,
     std::memcpy(&ma, t->tmap_a, sizeof ma);
     std::memcpy(&mb, t->tmap_b, sizeof mb);
     main_kernel_begin(st);
-    tc_gemm_kernel<SA, SB><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ma, mb, Z, ldz, n, n, n,
-                                                               vec, status);
+    tc_gemm_kernel<SA, SB, MODE><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
+        ma, mb, Z, ldz, n, n, n, kb_per_chunk, vec, status);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, grid);
     count_launches(1);
@@ -535,8 +679,9 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                                                   status, st)));
         AFMM_TRY((launch_widen_transpose<1, true>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                   status, st)));
-        return t->slices == 3 ? launch_tc<3, 1>(t, Zf, d.ldz, status, st)
-                              : launch_tc<2, 1>(t, Zf, d.ldz, status, st);
+        return t->slices == 3
+                   ? launch_tc<3, 1, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
+                   : launch_tc<2, 1, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
     }
     // Case B: A = Rep-factors X (rows), B = slices of the real Y transposed.
     AFMM_TRY((launch_widen_rows<1, true>(X, d.x_dtype, n, d.ldx, A, t->ld_a, status,
@@ -547,8 +692,9 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
     else
         AFMM_TRY((launch_widen_transpose<2, false>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                    status, st)));
-    return t->slices == 3 ? launch_tc<1, 3>(t, Zf, d.ldz, status, st)
-                          : launch_tc<1, 2>(t, Zf, d.ldz, status, st);
+    return t->slices == 3
+               ? launch_tc<1, 3, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
+               : launch_tc<1, 2, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
 }
 
 }  // namespace afmm

@@ -20,6 +20,8 @@ struct TcPlan {
     void* a = nullptr;              // BF16 A operand(s), K-major
     void* b = nullptr;              // BF16 B operand(s), K-major (B^T rows)
     bool sliced_a = true;           // real factor on the A side (case A)
+    int kb_per_chunk = 2;           // K chunk (in 32-wide k-blocks) folded
+                                    // into the running sums at a time
     alignas(64) unsigned char tmap_a[128];
     alignas(64) unsigned char tmap_b[128];
     bool maps_ready = false;

@@ -44,15 +44,19 @@ def simt_f32_elem_bound(inst, rows=None):
     return g * abs_product(inst, rows) + 1e-30
 
 
+TC_CHUNK = 64        # k per tensor-core chunk folded into the FP32 sums
+
+
 def tc_elem_bound(inst, rows=None, slices=3):
     """Rounding of the tensor-core form, to first order.
 
-    The slices of an FP32 value are exact (hi + mid + lo == x); each MMA
-    adds 16-term products of every slice into the FP32 accumulator, so an
-    element sees at most slices * ceil(n/16) + 16 roundings of at most
-    sum|x y|; the factor 2 allows a truncating accumulator.
+    The slices of an FP32 value are exact (hi + mid + lo == x).  A chunk of
+    64 k is accumulated in TMEM by slices * 4 MMAs (each one rounding of at
+    most the chunk's sum|x y|), then folded into the running FP32 sum with
+    one round-to-nearest add; ceil(n/64) chunks.  The factor 2 allows a
+    truncating accumulator.
     """
-    g = 2 * (slices * -(-inst.n // 16) + 18) * U32
+    g = 2 * (slices * 4 + -(-inst.n // TC_CHUNK) + 4) * U32
     return g * abs_product(inst, rows) + 1e-30
 
 
