@@ -91,8 +91,9 @@ typedef enum {
     AFMM_VARIANT_SIMT_F64SLICE = 3,
     /* CUDA cores, exact integers: int8 dot products (dp4a), int32 sums. */
     AFMM_VARIANT_SIMT_EXACT = 4,
-    /* Tensor cores, exact integers: operands exact in BF16, FP32 partial
-     * sums kept below 2^24 by splitting K, int32 recombination. */
+    /* Tensor cores, exact integers: operands exact in BF16 (|v| <= 256),
+     * K cut into chunks whose FP32 partial sums stay below 2^24 (so every
+     * partial sum is an exact integer), chunks added in int32. */
     AFMM_VARIANT_TC_EXACT = 5,
     /* Tensor cores, FP64 target: 8-bit row-scaled slices exact in BF16,
      * one exact FP32 accumulator per slice, FP64 recombination. */
@@ -118,6 +119,12 @@ typedef struct {
     uint32_t flags;     /* AFMM_FLAG_* */
     int32_t reserved_;  /* must be 0 */
     double d1, d2, mu_prime;  /* hints, < 0 when unknown */
+    /* Magnitude hints for the exact tensor-core form (< 0 when unknown):
+     * the largest Rep-factor and the largest |Base| value.  They size the
+     * K chunks whose FP32 partial sums must stay exact; every call checks
+     * the data against them on the device (AFMM_ERR_OVERFLOW_RISK at
+     * afmm_plan_sync when a value exceeds its hint). */
+    double rep_max, base_max;
 } afmm_desc;
 
 /* What a plan decided and, after a validating call, what it measured. */

@@ -64,7 +64,8 @@ class afmm_desc(ctypes.Structure):
                 ("target", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("reserved_", ctypes.c_int32),
                 ("d1", ctypes.c_double), ("d2", ctypes.c_double),
-                ("mu_prime", ctypes.c_double)]
+                ("mu_prime", ctypes.c_double), ("rep_max", ctypes.c_double),
+                ("base_max", ctypes.c_double)]
 
 
 class afmm_info(ctypes.Structure):
@@ -197,7 +198,8 @@ def make_desc(n: int, case: str = "A", x_dtype="f32", y_dtype="f32",
               z_dtype="f32", target="fp32", variant: int = AFMM_VARIANT_AUTO,
               flags: int = 0, d1: float = -1.0, d2: float = -1.0,
               mu_prime: float = -1.0, ldx: int = 0, ldy: int = 0,
-              ldz: int = 0) -> afmm_desc:
+              ldz: int = 0, rep_max: float = -1.0,
+              base_max: float = -1.0) -> afmm_desc:
     """Fill an ``afmm_desc`` from readable names ("A"/"B", "f32", "fp32")."""
     def code(v, table):
         return table[v] if isinstance(v, str) else int(v)
@@ -208,7 +210,8 @@ def make_desc(n: int, case: str = "A", x_dtype="f32", y_dtype="f32",
                      z_dtype=code(z_dtype, DTYPE_CODES),
                      target=code(target, TARGET_CODES), variant=int(variant),
                      flags=int(flags), reserved_=0, d1=float(d1),
-                     d2=float(d2), mu_prime=float(mu_prime))
+                     d2=float(d2), mu_prime=float(mu_prime),
+                     rep_max=float(rep_max), base_max=float(base_max))
 
 
 def afmm_plan_create(desc: afmm_desc) -> int:

@@ -172,13 +172,17 @@ bool variant_serves(int v, const afmm_desc* d) {
             return d->target == AFMM_TARGET_FP64;
         case AFMM_VARIANT_SIMT_EXACT:
             return d->target == AFMM_TARGET_EXACT;
+        case AFMM_VARIANT_TC_EXACT:
+            return d->target == AFMM_TARGET_EXACT && tc_available();
         default:
             return false;
     }
 }
 
 int auto_variant(const afmm_desc* d) {
-    if (d->target == AFMM_TARGET_EXACT) return AFMM_VARIANT_SIMT_EXACT;
+    if (d->target == AFMM_TARGET_EXACT)
+        return (tc_available() && d->n >= 128) ? AFMM_VARIANT_TC_EXACT
+                                               : AFMM_VARIANT_SIMT_EXACT;
     if (d->target == AFMM_TARGET_FP64) return AFMM_VARIANT_SIMT_F64SLICE;
     // FP32 target: tensor cores for the dense regime; the zero-skipping
     // CUDA-core kernel when the Base factor is very sparse (the useful
@@ -237,9 +241,14 @@ void plan_layout(afmm_plan_s* p) {
             }
             break;
         }
+        case AFMM_VARIANT_TC_EXACT:
         case AFMM_VARIANT_TC_BF16X3:
         case AFMM_VARIANT_TC_BF16X2: {
-            tc_layout(&p->tc, d, p->slices);
+            tc_layout(&p->tc, d, p->variant == AFMM_VARIANT_TC_EXACT ? 0 : p->slices);
+            p->ksplit = p->variant == AFMM_VARIANT_TC_EXACT
+                            ? (int)((d.n + 32LL * p->tc.kb_per_chunk - 1) /
+                                    (32LL * (p->tc.kb_per_chunk > 0 ? p->tc.kb_per_chunk : 1)))
+                            : 1;
             p->off_a = L.take(p->tc.a_bytes);
             p->off_b = L.take(p->tc.b_bytes);
             break;
@@ -271,7 +280,8 @@ afmm_status ensure_workspace(afmm_plan_s* p, cudaStream_t st) {
     if (!p->ws_ready) {
         AFMM_CUDA_TRY(cudaMemsetAsync(p->ws + p->off_status, 0, kAlign, st));
         if (p->variant == AFMM_VARIANT_TC_BF16X3 ||
-            p->variant == AFMM_VARIANT_TC_BF16X2)
+            p->variant == AFMM_VARIANT_TC_BF16X2 ||
+            p->variant == AFMM_VARIANT_TC_EXACT)
             AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a,
                                        p->ws + p->off_b));
         p->ws_ready = true;
@@ -380,6 +390,8 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
         case AFMM_VARIANT_TC_BF16X3:
         case AFMM_VARIANT_TC_BF16X2:
             return tc_run_split(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
+        case AFMM_VARIANT_TC_EXACT:
+            return tc_run_exact(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         default: return AFMM_ERR_UNSUPPORTED;
     }
 }
@@ -519,6 +531,16 @@ afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc) {
         }
     } else if (v == AFMM_VARIANT_SIMT_EXACT) {
         if ((double)desc->n * 128.0 * 128.0 >= 2147483647.0) {
+            delete p;
+            return AFMM_ERR_OVERFLOW_RISK;
+        }
+    } else if (v == AFMM_VARIANT_TC_EXACT) {
+        // int32 sums of n products of operands exact in BF16 (|v| <= 256,
+        // or the magnitude hints when given).
+        const double rb = desc->rep_max >= 0.0 ? desc->rep_max : 256.0;
+        const double bb = desc->base_max >= 0.0 ? desc->base_max : 256.0;
+        if ((double)desc->n * rb * bb >= 2147483647.0 ||
+            tc_exact_chunk_k(rb, bb) < 32) {
             delete p;
             return AFMM_ERR_OVERFLOW_RISK;
         }

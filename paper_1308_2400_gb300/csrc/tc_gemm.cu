@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -105,7 +106,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
     const int num_tiles = tiles_m * tiles_n;
     const int num_kb = (K + TC_BK - 1) / TC_BK;
-    const int kbpc = kb_per_chunk > 0 ? kb_per_chunk : num_kb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -180,74 +180,81 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
         __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------- MMA issuer
-        // Each tile's K range is cut into chunks of kbpc k-blocks; chunk c
-        // of the CTA accumulates from zero into TMEM slot c % 2, so the
-        // epilogue folds one chunk while the next is being multiplied.
         if (lane == 0) {
             constexpr uint32_t IDESC = ptx::idesc_bf16_f32(TC_BM, TC_BN);
-            // Smallest-slice-first needs the chunk's stages resident at once
-            // and at least two more stages left for the producer.
-            const bool small_first =
-                MODE == 0 && Cfg::P > 1 && kbpc <= Cfg::STAGES - 2 && kbpc <= 8;
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t slot_phase[2] = {0u, 0u};
-            int chunk = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-                for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kbpc) {
-                    const int slot = chunk & 1;
-                    if (!ptx::mbar_wait_bounded(&bars->tempty[slot], slot_phase[slot] ^ 1u,
-                                                abort, WAIT_LIMIT_NS)) {
+            if constexpr (MODE == 0) {
+                // Split form: per tile two 128 x 256 FP32 accumulators in
+                // TMEM, columns [0,256) for the products of the hi slice and
+                // [256,512) for those of the smaller slices, so a small
+                // product is never added into a sum of much larger
+                // magnitude.  The epilogue adds the two.
+                uint32_t tphase = 0;
+                for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+                    if (!ptx::mbar_wait_bounded(&bars->tempty[0], tphase ^ 1u, abort,
+                                                WAIT_LIMIT_NS)) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(slot * TC_BN);
-                    const int kb1 = min(kb0 + kbpc, num_kb);
-                    if (small_first) {
-                        // All stages of the chunk resident, then the slice
-                        // products from the smallest slice to the largest,
-                        // so each MMA adds into a partial sum of its own
-                        // magnitude.
-                        int st_[8];
-                        for (int kb = kb0; kb < kb1; ++kb) {
-                            if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
-                                                        WAIT_LIMIT_NS)) {
-                                ok = false;
-                                break;
-                            }
-                            st_[kb - kb0] = stage;
-                            if (++stage == Cfg::STAGES) {
-                                stage = 0;
-                                phase ^= 1u;
-                            }
+                    for (int kb = 0; kb < num_kb; ++kb) {
+                        if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
+                                                    WAIT_LIMIT_NS)) {
+                            ok = false;
+                            break;
                         }
-                        if (!ok) break;
                         ptx::tc_fence_after();
-                        bool first = true;
+                        const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
 #pragma unroll
-                        for (int p = Cfg::P - 1; p >= 0; --p) {
-                            for (int kb = kb0; kb < kb1; ++kb) {
-                                const uint32_t s0 = ptx::smem_addr(
-                                    tiles + st_[kb - kb0] * Cfg::STAGE_BYTES);
+                        for (int ks = 0; ks < TC_BK / 16; ++ks) {
 #pragma unroll
-                                for (int ks = 0; ks < TC_BK / 16; ++ks) {
-                                    const uint32_t a_addr =
-                                        s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
-                                    const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
-                                                            (SB > 1 ? p : 0) * B_TILE_BYTES +
-                                                            ks * 32;
-                                    ptx::mma_f16(d, ptx::sdesc_kmajor_sw64(a_addr),
-                                                 ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                                 first ? 0u : 1u);
-                                    first = false;
-                                }
+                            for (int p = Cfg::P - 1; p >= 0; --p) {
+                                const uint32_t a_addr =
+                                    s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
+                                const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
+                                                        (SB > 1 ? p : 0) * B_TILE_BYTES +
+                                                        ks * 32;
+                                const bool first = kb == 0 && ks == 0 &&
+                                                   (p == 0 || p == Cfg::P - 1);
+                                ptx::mma_f16(tmem + (p == 0 ? 0u : (uint32_t)TC_BN),
+                                             ptx::sdesc_kmajor_sw64(a_addr),
+                                             ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                             first ? 0u : 1u);
                             }
                         }
-                        for (int kb = kb0; kb < kb1; ++kb)
-                            ptx::mma_commit(&bars->empty[st_[kb - kb0]]);
-                    } else {
+                        ptx::mma_commit(&bars->empty[stage]);
+                        if (++stage == Cfg::STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    ptx::mma_commit(&bars->tfull[0]);
+                    tphase ^= 1u;
+                }
+            } else {
+                // Exact form: each tile's K range is cut into chunks of kbpc
+                // k-blocks short enough that every partial sum stays an
+                // exact integer in FP32; chunk c of the CTA accumulates from
+                // zero into TMEM slot c % 2 while the epilogue converts the
+                // previous one to int32.
+                const int kbpc = kb_per_chunk > 0 ? kb_per_chunk : num_kb;
+                uint32_t slot_phase[2] = {0u, 0u};
+                int chunk = 0;
+                for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+                    for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kbpc) {
+                        const int slot = chunk & 1;
+                        if (!ptx::mbar_wait_bounded(&bars->tempty[slot],
+                                                    slot_phase[slot] ^ 1u, abort,
+                                                    WAIT_LIMIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(slot * TC_BN);
+                        const int kb1 = min(kb0 + kbpc, num_kb);
                         for (int kb = kb0; kb < kb1; ++kb) {
                             if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
                                                         WAIT_LIMIT_NS)) {
@@ -277,11 +284,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                 phase ^= 1u;
                             }
                         }
+                        if (!ok) break;
+                        ptx::mma_commit(&bars->tfull[slot]);
+                        slot_phase[slot] ^= 1u;
+                        ++chunk;
                     }
-                    if (!ok) break;
-                    ptx::mma_commit(&bars->tfull[slot]);
-                    slot_phase[slot] ^= 1u;
-                    ++chunk;
                 }
             }
             if (!ok) raise_abort(bars, status);
@@ -294,9 +301,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     } else {
         // ---------------------------------------------------- epilogue
         // 8 warps: warp w reads TMEM lanes 32*(w%4).. (its rows) and half
-        // h of the 256 columns.  Each chunk is folded into running sums in
-        // registers with round-to-nearest FP32 adds (MODE 0) or exact int32
-        // adds of the chunk's integer partials (MODE 1).
+        // h of the 256 columns, 128 values per thread.
         using Acc = typename std::conditional<MODE == 0, float, int32_t>::type;
         const int q = warp & 3;
         const int h = (warp - 2) >> 2;
@@ -304,6 +309,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
         uint32_t slot_phase[2] = {0u, 0u};
         int chunk = 0;
+        const int kbpc = (MODE == 0 || kb_per_chunk <= 0) ? num_kb : kb_per_chunk;
         bool ok = true;
         for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
             int tm, tn;
@@ -312,7 +318,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
 #pragma unroll
             for (int j = 0; j < 128; ++j) sum[j] = Acc(0);
             for (int kb0 = 0; kb0 < num_kb; kb0 += kbpc) {
-                const int slot = chunk & 1;
+                const int slot = MODE == 0 ? 0 : (chunk & 1);
                 const bool got = ptx::mbar_wait_bounded(&bars->tfull[slot],
                                                         slot_phase[slot], abort,
                                                         WAIT_LIMIT_NS);
@@ -324,22 +330,25 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                 }
                 ptx::tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < 4; c += 2) {
+                for (int c = 0; c < 4; ++c) {
                     uint32_t r0[32], r1[32];
-                    ptx::tmem_ld_32cols(lane_base + (uint32_t)(slot * TC_BN + c * 32), r0);
-                    ptx::tmem_ld_32cols(lane_base + (uint32_t)(slot * TC_BN + c * 32 + 32), r1);
-                    ptx::tmem_ld_wait();
+                    if constexpr (MODE == 0) {
+                        // hi-slice sum + small-slice sum, one rounding.
+                        ptx::tmem_ld_32cols(lane_base + (uint32_t)(c * 32), r0);
+                        ptx::tmem_ld_32cols(lane_base + (uint32_t)(TC_BN + c * 32), r1);
+                        ptx::tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if constexpr (MODE == 0) {
-                            sum[c * 32 + j] += __uint_as_float(r0[j]);
-                            sum[c * 32 + 32 + j] += __uint_as_float(r1[j]);
-                        } else {
+                        for (int j = 0; j < 32; ++j)
+                            sum[c * 32 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    } else {
+                        ptx::tmem_ld_32cols(lane_base + (uint32_t)(slot * TC_BN + c * 32), r0);
+                        ptx::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
                             sum[c * 32 + j] += __float2int_rn(__uint_as_float(r0[j]));
-                            sum[c * 32 + 32 + j] += __float2int_rn(__uint_as_float(r1[j]));
-                        }
                     }
                 }
+                // TMEM is free again before the stores below.
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(&bars->tempty[slot]);
                 slot_phase[slot] ^= 1u;
@@ -414,7 +423,7 @@ template <int DT, int S, bool EXACT>
 __global__ void __launch_bounds__(256)
 widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                   __nv_bfloat16* __restrict__ dst, int64_t ldk, int vec_f32,
-                  int* status) {
+                  float lim, int* status) {
     const int64_t c = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 8;
     if (c >= ldk) return;
     for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
@@ -446,7 +455,8 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                 if (cc < n) {
                     const auto v = load_val<DT>(src, r * lds + cc);
                     split_bf16<S>(v, o[t]);
-                    if (EXACT && (decltype(v))__bfloat162float(o[t][0]) != v)
+                    if (EXACT && ((decltype(v))__bfloat162float(o[t][0]) != v ||
+                                  fabs((double)v) > (double)lim))
                         atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
                 } else {
 #pragma unroll
@@ -469,7 +479,8 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
 template <int DT, int S, bool EXACT>
 __global__ void __launch_bounds__(256)
 widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
-                       __nv_bfloat16* __restrict__ dst, int64_t ldk, int* status) {
+                       __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
+                       int* status) {
     using T = decltype(load_val<DT>(nullptr, 0));
     __shared__ T tile[64][65];
     const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 64;
@@ -491,7 +502,9 @@ widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
             const T v0 = tile[2 * tx][i], v1 = tile[2 * tx + 1][i];
             split_bf16<S>(v0, o0);
             split_bf16<S>(v1, o1);
-            if (EXACT && ((T)__bfloat162float(o0[0]) != v0 || (T)__bfloat162float(o1[0]) != v1))
+            if (EXACT && ((T)__bfloat162float(o0[0]) != v0 ||
+                          (T)__bfloat162float(o1[0]) != v1 ||
+                          fabs((double)v0) > (double)lim || fabs((double)v1) > (double)lim))
                 atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
 #pragma unroll
             for (int s = 0; s < S; ++s)
@@ -503,14 +516,14 @@ widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
 
 template <int S, bool EXACT>
 afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
-                              __nv_bfloat16* dst, int64_t ldk, int* status,
-                              cudaStream_t st) {
+                              __nv_bfloat16* dst, int64_t ldk, float lim,
+                              int* status, cudaStream_t st) {
     const int64_t per_row = ldk / 8;
     const dim3 grid((unsigned)((per_row + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
     const int vec = (lds % 4 == 0) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
         widen_rows_kernel<DT, S, EXACT><<<grid, 256, 0, st>>>(src, n, lds, dst, ldk, vec,
-                                                              status);
+                                                              lim, status);
         return AFMM_OK;
     });
     AFMM_TRY(rc);
@@ -522,13 +535,13 @@ afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
 template <int S, bool EXACT>
 afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
                                    int64_t lds, __nv_bfloat16* dst, int64_t ldk,
-                                   int* status, cudaStream_t st) {
+                                   float lim, int* status, cudaStream_t st) {
     const int64_t g = (n + 63) / 64;
     if (g > 65535) return AFMM_ERR_UNSUPPORTED;
     const dim3 grid((unsigned)g, (unsigned)g), block(32, 8);
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
         widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(src, n, lds, dst,
-                                                                     ldk, status);
+                                                                     ldk, lim, status);
         return AFMM_OK;
     });
     AFMM_TRY(rc);
@@ -638,11 +651,43 @@ bool tc_available() {
     return dp.cc_major == 10 && dp.cc_minor == 3 && dp.smem_optin >= (size_t)SMEM_OPTIN;
 }
 
+int tc_exact_chunk_k(double amax, double bmax) {
+    const double per = (amax < 1.0 ? 1.0 : amax) * (bmax < 1.0 ? 1.0 : bmax);
+    const double k = std::floor(16777215.0 / per);
+    return (int)(std::floor(k / TC_BK) * TC_BK);
+}
+
+namespace {
+double dtype_bound(int dt) {
+    switch (dt) {
+        case AFMM_I8: return 128.0;
+        case AFMM_U8: return 255.0;
+        default: return 256.0;      // BF16-exact integers checked on device
+    }
+}
+}  // namespace
+
 void tc_layout(TcPlan* t, const afmm_desc& d, int slices) {
     t->n = d.n;
     t->slices = slices;
     t->sliced_a = d.kase == AFMM_CASE_A;
     t->ld_a = t->ld_b = (d.n + 7) / 8 * 8;
+    if (slices == 0) {
+        // Exact form: A = X, B = Y^T, one BF16 operand each.
+        const int rep_dt = d.kase == AFMM_CASE_A ? d.y_dtype : d.x_dtype;
+        const int base_dt = d.kase == AFMM_CASE_A ? d.x_dtype : d.y_dtype;
+        double rb = dtype_bound(rep_dt), bb = dtype_bound(base_dt);
+        if (d.rep_max >= 0.0 && d.rep_max < rb) rb = d.rep_max;
+        if (d.base_max >= 0.0 && d.base_max < bb) bb = d.base_max;
+        const double amax = d.kase == AFMM_CASE_A ? bb : rb;
+        const double bmax = d.kase == AFMM_CASE_A ? rb : bb;
+        t->lim_a = (float)amax;
+        t->lim_b = (float)bmax;
+        t->kb_per_chunk = tc_exact_chunk_k(amax, bmax) / TC_BK;
+        t->a_bytes = (size_t)d.n * t->ld_a * 2;
+        t->b_bytes = (size_t)d.n * t->ld_b * 2;
+        return;
+    }
     const int sa = t->sliced_a ? slices : 1, sb = t->sliced_a ? 1 : slices;
     t->rows_a = d.n;
     t->rows_b = d.n;
@@ -655,7 +700,8 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b) {
     t->b = b;
     t->maps_ready = false;
     if (t->n <= 0) return AFMM_OK;
-    const int sa = t->sliced_a ? t->slices : 1, sb = t->sliced_a ? 1 : t->slices;
+    const int sl = t->slices > 0 ? t->slices : 1;
+    const int sa = t->sliced_a ? sl : 1, sb = t->sliced_a ? 1 : sl;
     AFMM_TRY(encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM));
     AFMM_TRY(encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN));
     t->maps_ready = true;
@@ -673,28 +719,42 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
         // A = slices of the real X (rows), B = Rep-factors Y transposed.
         if (t->slices == 3)
             AFMM_TRY((launch_widen_rows<3, false>(X, d.x_dtype, n, d.ldx, A, t->ld_a,
-                                                  status, st)));
+                                                  0.f, status, st)));
         else
             AFMM_TRY((launch_widen_rows<2, false>(X, d.x_dtype, n, d.ldx, A, t->ld_a,
-                                                  status, st)));
+                                                  0.f, status, st)));
         AFMM_TRY((launch_widen_transpose<1, true>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
-                                                  status, st)));
+                                                  256.f, status, st)));
         return t->slices == 3
                    ? launch_tc<3, 1, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
                    : launch_tc<2, 1, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
     }
     // Case B: A = Rep-factors X (rows), B = slices of the real Y transposed.
-    AFMM_TRY((launch_widen_rows<1, true>(X, d.x_dtype, n, d.ldx, A, t->ld_a, status,
-                                         st)));
+    AFMM_TRY((launch_widen_rows<1, true>(X, d.x_dtype, n, d.ldx, A, t->ld_a, 256.f,
+                                         status, st)));
     if (t->slices == 3)
         AFMM_TRY((launch_widen_transpose<3, false>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
-                                                   status, st)));
+                                                   0.f, status, st)));
     else
         AFMM_TRY((launch_widen_transpose<2, false>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
-                                                   status, st)));
+                                                   0.f, status, st)));
     return t->slices == 3
                ? launch_tc<1, 3, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
                : launch_tc<1, 2, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
+}
+
+afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
+                         const void* Y, void* Z, int* status, cudaStream_t st) {
+    if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;
+    if (t->kb_per_chunk < 1) return AFMM_ERR_OVERFLOW_RISK;
+    const int64_t n = d.n;
+    auto* A = static_cast<__nv_bfloat16*>(t->a);
+    auto* B = static_cast<__nv_bfloat16*>(t->b);
+    AFMM_TRY((launch_widen_rows<1, true>(X, d.x_dtype, n, d.ldx, A, t->ld_a, t->lim_a,
+                                         status, st)));
+    AFMM_TRY((launch_widen_transpose<1, true>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
+                                              t->lim_b, status, st)));
+    return launch_tc<1, 1, 1>(t, Z, d.ldz, t->kb_per_chunk, status, st);
 }
 
 }  // namespace afmm

@@ -20,8 +20,8 @@ struct TcPlan {
     void* a = nullptr;              // BF16 A operand(s), K-major
     void* b = nullptr;              // BF16 B operand(s), K-major (B^T rows)
     bool sliced_a = true;           // real factor on the A side (case A)
-    int kb_per_chunk = 2;           // K chunk (in 32-wide k-blocks) folded
-                                    // into the running sums at a time
+    int kb_per_chunk = 0;           // exact form: K chunk in 32-wide k-blocks
+    float lim_a = 256.f, lim_b = 256.f;  // exact form: largest |value| allowed
     alignas(64) unsigned char tmap_a[128];
     alignas(64) unsigned char tmap_b[128];
     bool maps_ready = false;
@@ -29,10 +29,17 @@ struct TcPlan {
 
 // True when this device can run the tensor-core kernels (sm_103).
 bool tc_available();
+// slices = 0 selects the exact-integer form (one BF16 operand each side).
 void tc_layout(TcPlan* t, const afmm_desc& d, int slices);
+// Largest K chunk (multiple of 32) with chunk * amax * bmax < 2^24, or 0
+// when even one 32-wide block could overflow.
+int tc_exact_chunk_k(double amax, double bmax);
 afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b);
 // Split / widen the operands and run the tcgen05 product into Z (F32).
 afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
+                         const void* Y, void* Z, int* status, cudaStream_t st);
+// Exact integer product into Z (I32).
+afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st);
 
 // Launch a kernel whose only wait can never complete; returns the status

@@ -44,19 +44,16 @@ def simt_f32_elem_bound(inst, rows=None):
     return g * abs_product(inst, rows) + 1e-30
 
 
-TC_CHUNK = 64        # k per tensor-core chunk folded into the FP32 sums
-
-
 def tc_elem_bound(inst, rows=None, slices=3):
     """Rounding of the tensor-core form, to first order.
 
-    The slices of an FP32 value are exact (hi + mid + lo == x).  A chunk of
-    64 k is accumulated in TMEM by slices * 4 MMAs (each one rounding of at
-    most the chunk's sum|x y|), then folded into the running FP32 sum with
-    one round-to-nearest add; ceil(n/64) chunks.  The factor 2 allows a
-    truncating accumulator.
+    The slices of an FP32 value are exact (hi + mid + lo == x).  The hi
+    products and the smaller slices' products go to two FP32 accumulators;
+    each of the ceil(n/16) MMAs into either rounds at most once relative to
+    that accumulator's sum|x y|, and the epilogue adds the two with one
+    rounding.  The factor 2 allows a truncating accumulator.
     """
-    g = 2 * (slices * 4 + -(-inst.n // TC_CHUNK) + 4) * U32
+    g = 2 * (2 * -(-inst.n // 16) + 8) * U32
     return g * abs_product(inst, rows) + 1e-30
 
 
@@ -169,6 +166,71 @@ def test_bounded_wait_times_out_and_context_survives():
     inst = W.make("caseA_n8192_e4m3", n=200, seed=4)
     Z, _ = run_gpu(inst, variant=1)
     check_fp32(inst, Z, bound_fn=tc_elem_bound)
+
+
+# ------------------------------------------------------------------ exact, TC
+def exact_case(case, n, seed):
+    inst = W.make("caseA_n16384_i8", n=n, seed=seed)
+    if case == "B":   # X Rep-factors, Y integer Base values
+        inst = W.Instance("B", inst.Y.copy(), inst.X.copy(), name="exactB",
+                          x_dtype="i8", y_dtype="i8", z_dtype="i32",
+                          target="exact")
+    return inst
+
+
+@pytest.mark.parametrize("n", TC_RAGGED)
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_tc_exact_ragged(case, n):
+    """No magnitude hints: K chunks sized from the int8 bounds (992)."""
+    inst = exact_case(case, n, seed=n + 7)
+    Z, info = run_gpu(inst, variant=5)
+    assert info["variant"] == 5 and info["k_split"] == -(-n // 992)
+    assert np.array_equal(Z.astype(np.int64), oracle_rows(inst))
+
+
+def test_tc_exact_worst_case_magnitudes():
+    n = 2048                            # two K chunks at the int8 bounds
+    X = np.full((n, n), -128, dtype=np.int8)
+    X[1::2] = 127
+    Y = np.full((n, n), 127, dtype=np.int8)
+    inst = W.Instance("A", X, Y, name="worst", x_dtype="i8", y_dtype="i8",
+                      z_dtype="i32", target="exact")
+    Z, info = run_gpu(inst, variant=5)
+    assert info["k_split"] == 3
+    assert np.array_equal(Z.astype(np.int64), oracle_rows(inst))
+
+
+def test_tc_exact_full_size_sampled_with_hints():
+    """n = 16384 with the workload's magnitudes as hints: 2 K chunks."""
+    import torch as T
+    from paper_1308_2400_gb300 import Plan, make_desc
+    inst = W.make("caseA_n16384_i8")
+    X, Y = torch_of(inst.X), torch_of(inst.Y)
+    Z = T.empty((inst.n, inst.n), dtype=T.int32, device="cuda")
+    p = Plan(make_desc(inst.n, "A", "i8", "i8", "i32", "exact",
+                       rep_max=15, base_max=127))
+    assert p.info["variant"] == 5 and p.info["k_split"] == 2
+    p(X, Y, Z)
+    p.sync()
+    rows = sample_rows(inst.n, 6)
+    assert np.array_equal(Z.cpu().numpy()[rows].astype(np.int64),
+                          oracle_rows(inst, rows))
+
+
+def test_tc_exact_hint_violation_is_reported():
+    import torch as T
+    from paper_1308_2400_gb300 import AfmmError, Plan, make_desc
+    n = 256
+    X = T.ones((n, n), dtype=T.int8, device="cuda")
+    Y = T.ones((n, n), dtype=T.int8, device="cuda")
+    Y[3, 4] = 100                       # above the rep_max hint of 15
+    Z = T.empty((n, n), dtype=T.int32, device="cuda")
+    p = Plan(make_desc(n, "A", "i8", "i8", "i32", "exact", variant=5,
+                       rep_max=15, base_max=127))
+    p(X, Y, Z)
+    with pytest.raises(AfmmError) as e:
+        p.sync()
+    assert e.value.status == 4          # AFMM_ERR_OVERFLOW_RISK
 
 
 # ------------------------------------------------------------------ exact
