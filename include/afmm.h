@@ -238,6 +238,39 @@ afmm_status afmm_error_norm(const void* Z, int32_t z_dtype, int64_t ldz,
                             int64_t rows, int64_t cols, void* workspace,
                             double out[3], void* stream);
 
+/* FP64-target product that allocates nothing (the paper has no counterpart:
+ * this entry point exists for callers of this library, not for the method).
+ *
+ * Who needs it: callers that cannot call cudaMalloc -- for example code
+ * running while another allocator holds all of the device's memory, loops
+ * that cannot afford the device synchronisation cudaMalloc and cudaFree
+ * imply, or hosts that forbid allocation from the context they call in.
+ *
+ * What it computes: the same product as a plan with target
+ * AFMM_TARGET_FP64 (row-scaled 7-bit digits of the real factor, exact int32
+ * digit products, FP64 recombination), Case A or B as desc->kase says.
+ * X, Y, Z are DEVICE pointers laid out as desc describes (dtypes, leading
+ * dimensions; z_dtype must be AFMM_F64); the caller owns them.  Hints and
+ * desc->variant are ignored.
+ *
+ * Scratch: one fixed device array of about 3.8 MiB inside this library,
+ * enough for n <= 256; n > 256 returns AFMM_ERR_UNSUPPORTED (and
+ * afmm_last_error_detail says so).  Every GPU that loads the library holds
+ * the array until the process exits.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, once per device, with
+ * that device current); make that first call before any stream capture.
+ *
+ * Calls share the array and keep its last contents (the call clears what
+ * must start at zero).  Calls that overlap on the GPU -- issued on several
+ * streams or from several threads without ordering -- race on it.
+ *
+ * Asynchronous on `stream`.  A Rep-factor outside [-128, 127] cannot be
+ * reported through a status word without allocating one per call, so it
+ * turns every element of Z into NaN instead.  Returns AFMM_ERR_INVALID_ARG
+ * for a bad descriptor or a host pointer. */
+afmm_status afmm_mul_noalloc(const afmm_desc* desc, const void* X,
+                             const void* Y, void* Z, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

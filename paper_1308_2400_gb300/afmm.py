@@ -128,6 +128,7 @@ def _lib():
             "afmm_plan_enable_kernel_timing": ([_VP, ctypes.c_int], st),
             "afmm_plan_counters": ([_VP, ctypes.POINTER(afmm_counters)], st),
             "afmm_selftest_bounded_wait": ([ctypes.c_uint64, _VP], st),
+            "afmm_mul_noalloc": ([ctypes.POINTER(afmm_desc), _VP, _VP, _VP, _VP], st),
             "afmm_mul_batched": ([ctypes.c_int, ctypes.POINTER(afmm_desc),
                                   ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                   ctypes.POINTER(_VP), _VP], st),
@@ -273,6 +274,14 @@ def afmm_plan_counters(plan: int) -> dict:
 def afmm_selftest_bounded_wait(limit_ns: int, stream=None) -> int:
     """Status recorded by a kernel whose bounded wait must run out."""
     return int(_lib().afmm_selftest_bounded_wait(int(limit_ns), _stream(stream)))
+
+
+def afmm_mul_noalloc(desc: afmm_desc, X, Y, Z, stream=None) -> None:
+    """FP64-target product without any device allocation (n <= 256);
+    device tensors only.  See include/afmm.h."""
+    _check(_lib().afmm_mul_noalloc(ctypes.byref(desc), _ptr(X), _ptr(Y),
+                                   _ptr(Z), _stream(stream)),
+           "afmm_mul_noalloc")
 
 
 def afmm_mul_batched(descs: Sequence[afmm_desc], X: Sequence, Y: Sequence,

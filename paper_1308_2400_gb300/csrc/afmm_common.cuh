@@ -29,6 +29,8 @@ namespace afmm {
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file,
                          int line);
+// Set the text afmm_last_error_detail returns for this thread.
+void set_last_error_text(const char* text);
 
 // Kernel-launch counter of the calling thread (every launcher adds the
 // kernels it launched) and the main-kernel timing hook of a call.

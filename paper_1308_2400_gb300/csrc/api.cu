@@ -43,6 +43,10 @@ void main_kernel_end(cudaStream_t st, int ctas) {
     }
 }
 
+void set_last_error_text(const char* text) {
+    snprintf(g_last_err, sizeof(g_last_err), "%s", text);
+}
+
 afmm_status device_props(DeviceProps* out) {
     static std::mutex mu;
     static DeviceProps cache[64];
