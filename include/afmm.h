@@ -217,13 +217,29 @@ afmm_status afmm_plan_counters(afmm_plan plan, afmm_counters* out);
 afmm_status afmm_selftest_bounded_wait(uint64_t limit_ns, void* stream);
 
 /* Batched product: `count` independent instances (Sec. 2 problems of
- * possibly different n and case), each described by descs[t] and computed
- * with the variant its own plan would pick, in one call on `stream`.
- * X[t], Y[t], Z[t] are device pointers.  Instances are independent: Z[t]
- * depends only on X[t] and Y[t]. */
+ * different n, Case A or B), each described by descs[t], FP32 target
+ * (z_dtype F32).  Each instance runs either the tcgen05 split-BF16 form or
+ * the CUDA-core zero-skip form: descs[t].variant = AFMM_VARIANT_TC_BF16X3 or
+ * AFMM_VARIANT_SIMT_F32 forces the route, AFMM_VARIANT_AUTO applies the
+ * built-in rule (tensor cores unless the Base density hint is below 0.02
+ * or n < 32).  All tensor-core instances run in one persistent grouped
+ * launch, all CUDA-core instances in another; the first call with a given
+ * descriptor array builds the plan (workspace, TMA descriptors, tile lists)
+ * and a CUDA graph of the launches, later calls with an identical array
+ * only refresh the pointer table and launch the graph (a few plans are
+ * cached).  X[t], Y[t], Z[t] are device pointers; Z[t] depends only on X[t]
+ * and Y[t].  Asynchronous on `stream`; calls with the same descriptor array
+ * must not overlap on different streams.  A Rep-factor that is not an
+ * integer of magnitude <= 256 turns that instance's Z into NaN; a bounded
+ * wait that runs out is reported by afmm_batched_sync. */
 afmm_status afmm_mul_batched(int count, const afmm_desc* descs,
                              const void* const* X, const void* const* Y,
                              void* const* Z, void* stream);
+
+/* Synchronise `stream` and return the status recorded by the kernels of the
+ * cached batch with this descriptor array (AFMM_OK, or AFMM_ERR_TIMEOUT);
+ * AFMM_ERR_INVALID_ARG when no such batch ran. */
+afmm_status afmm_batched_sync(int count, const afmm_desc* descs, void* stream);
 
 /* Relative error of a result against a reference, in FP64 on the GPU:
  * out[0] = ||Z - R||_F, out[1] = ||R||_F, out[2] = max |Z - R| over the

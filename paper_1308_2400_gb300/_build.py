@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libafmm.so")
 
 SOURCES = ["api.cu", "scan.cu", "convert.cu", "simt_gemm.cu", "norm.cu",
-           "tc_gemm.cu", "noalloc.cu"]
+           "tc_gemm.cu", "noalloc.cu", "batched_kernels.cu", "batched.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC",
                 "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -55,7 +55,7 @@ def build(force: bool = False, ptxas_verbose: bool = False) -> str:
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OUT, s.replace(".cu", ".o"))
+        obj = os.path.join(OUT, os.path.splitext(s)[0] + ".o")
         if (force or ptxas_verbose or not os.path.exists(obj)
                 or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr)):
             jobs.append((src, obj))
@@ -63,7 +63,7 @@ def build(force: bool = False, ptxas_verbose: bool = False) -> str:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             for f in [ex.submit(_compile, s, o, extra) for s, o in jobs]:
                 f.result()
-    objs = [os.path.join(OUT, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(OUT, os.path.splitext(s)[0] + ".o") for s in SOURCES]
     if (jobs or not os.path.exists(LIB)
             or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs)):
         tmp = LIB + f".{os.getpid()}.tmp"

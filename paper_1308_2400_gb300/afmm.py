@@ -128,6 +128,7 @@ def _lib():
             "afmm_plan_enable_kernel_timing": ([_VP, ctypes.c_int], st),
             "afmm_plan_counters": ([_VP, ctypes.POINTER(afmm_counters)], st),
             "afmm_selftest_bounded_wait": ([ctypes.c_uint64, _VP], st),
+            "afmm_batched_sync": ([ctypes.c_int, ctypes.POINTER(afmm_desc), _VP], st),
             "afmm_mul_noalloc": ([ctypes.POINTER(afmm_desc), _VP, _VP, _VP, _VP], st),
             "afmm_mul_batched": ([ctypes.c_int, ctypes.POINTER(afmm_desc),
                                   ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -293,6 +294,12 @@ def afmm_mul_batched(descs: Sequence[afmm_desc], X: Sequence, Y: Sequence,
     pz = (_VP * cnt)(*[_ptr(t) for t in Z])
     _check(_lib().afmm_mul_batched(cnt, arr, px, py, pz, _stream(stream)),
            "afmm_mul_batched")
+
+
+def afmm_batched_sync(descs: Sequence[afmm_desc], stream=None) -> None:
+    cnt = len(descs)
+    arr = (afmm_desc * cnt)(*descs)
+    _check(_lib().afmm_batched_sync(cnt, arr, _stream(stream)), "afmm_batched_sync")
 
 
 def afmm_error_norm_workspace_size(rows: int, cols: int) -> int:

@@ -135,6 +135,21 @@ afmm_status launch_simt_dp4a(const int8_t* A, int64_t lda, const int32_t* W,
                              int64_t ldw, int32_t* C, int64_t ldc, int64_t M,
                              int64_t N, int64_t K, cudaStream_t st);
 
+// Grouped K1 (FP32): one launch over the tiles of many independent
+// products.  jobs[] and tile_prefix[] (exclusive prefix of each job's tile
+// count, simt_tiles) are device arrays.
+struct SimtJob {
+    const float* A;
+    const float* B;
+    float* C;
+    int64_t lda, ldb, ldc, M, N, K;
+    int vec, tiles_n;
+};
+int simt_tiles(int64_t M, int64_t N);
+int simt_tiles_n(int64_t N);
+afmm_status launch_simt_f32_grouped(const SimtJob* jobs, const int* tile_prefix,
+                                    int njobs, int total_tiles, cudaStream_t st);
+
 // K6: error norms, partial sums in `ws` (error_norm_ws_bytes bytes).
 size_t error_norm_ws_bytes(int64_t rows, int64_t cols);
 afmm_status launch_error_norm(const void* Z, int zdt, int64_t ldz,

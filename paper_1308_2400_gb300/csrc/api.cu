@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "afmm_common.cuh"
+#include "batched.cuh"
 #include "tc_gemm.cuh"
 
 namespace afmm {
@@ -412,12 +413,6 @@ afmm_status stage_buffer(afmm_plan_s* p, int idx, size_t bytes, void** out) {
     return AFMM_OK;
 }
 
-// Batched product, first form: each instance runs its own plan, all on one
-// stream, in order.
-afmm_status batched_impl(int count, const afmm_desc* descs,
-                         const void* const* X, const void* const* Y,
-                         void* const* Z, void* stream);
-
 afmm_status mul_impl(afmm_plan p, const void* X, const void* Y, void* Z,
                      void* stream, int expect_case) {
     if (!p) return AFMM_ERR_INVALID_ARG;
@@ -675,6 +670,14 @@ afmm_status afmm_plan_counters(afmm_plan p, afmm_counters* out) {
     return AFMM_OK;
 }
 
+afmm_status afmm_batched_sync(int count, const afmm_desc* descs, void* stream) {
+    if (count < 0 || (count > 0 && !descs)) return AFMM_ERR_INVALID_ARG;
+    AFMM_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int code = 0;
+    AFMM_TRY(batched_status(count, descs, &code));
+    return static_cast<afmm_status>(code);
+}
+
 afmm_status afmm_selftest_bounded_wait(uint64_t limit_ns, void* stream) {
     DeviceProps dp;
     AFMM_TRY(device_props(&dp));
@@ -686,7 +689,7 @@ afmm_status afmm_mul_batched(int count, const afmm_desc* descs,
                              void* const* Z, void* stream) {
     if (count < 0 || (count > 0 && (!descs || !X || !Y || !Z)))
         return AFMM_ERR_INVALID_ARG;
-    return batched_impl(count, descs, X, Y, Z, stream);
+    return batched_run(count, descs, X, Y, Z, stream, nullptr);
 }
 
 size_t afmm_error_norm_workspace_size(int64_t rows, int64_t cols) {
@@ -726,22 +729,4 @@ afmm_status afmm_error_norm(const void* Z, int32_t z_dtype, int64_t ldz,
 
 }  // extern "C"
 
-namespace {
-afmm_status batched_impl(int count, const afmm_desc* descs,
-                         const void* const* X, const void* const* Y,
-                         void* const* Z, void* stream) {
-    afmm_status rc = AFMM_OK;
-    for (int t = 0; t < count && rc == AFMM_OK; ++t) {
-        afmm_plan p = nullptr;
-        rc = afmm_plan_create(&p, &descs[t]);
-        if (rc != AFMM_OK) break;
-        rc = descs[t].kase == AFMM_CASE_A
-                 ? afmm_mul_caseA(p, X[t], Y[t], Z[t], stream)
-                 : afmm_mul_caseB(p, X[t], Y[t], Z[t], stream);
-        afmm_status rs = afmm_plan_sync(p, stream);
-        if (rc == AFMM_OK) rc = rs;
-        afmm_plan_destroy(p);
-    }
-    return rc;
-}
-}  // namespace
+

@@ -1,0 +1,63 @@
+// Batched products: shared records of the planner (batched.cpp) and the
+// grouped kernels (batched_kernels.cu).  Plain host/device structs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "afmm.h"
+
+namespace afmm {
+
+// Tile shape of the grouped tensor-core kernel.
+constexpr int GB_BM = 128, GB_BN = 256, GB_BK = 32;
+
+// Device record of one tensor-core instance.
+struct GInst {
+    const void* X;
+    const void* Y;
+    float* Z;
+    void* A;               // BF16, K-major A operand(s): [S][n][ldk]
+    void* B;               // BF16, K-major B operand(s): [S][n][ldk]
+    int64_t n, ldx, ldy, ldz, ldk;
+    int kind;              // 0: X real, sliced on A; 1: Y real, sliced on B
+    int x_dtype, y_dtype;
+    int flag;              // index into the per-instance error flags
+};
+
+// Device record of one operand widened to FP32 for the CUDA-core form.
+struct WJob {
+    const void* src;
+    float* dst;
+    int64_t n, lds;
+    int dtype;
+    int pad;
+};
+
+// One tensor-core tile: instance, tile row, tile column.
+struct TileRec {
+    int inst, tm, tn, pad;
+};
+
+// Grouped launches (device arrays throughout).
+afmm_status launch_batch_convert(const GInst* inst, const int* row_prefix,
+                                 const int* tt_prefix, int ninst, int rows_total,
+                                 int tt_total, int* flags, cudaStream_t st);
+afmm_status launch_batch_tc(const GInst* inst, const void* maps, const int* cta_off,
+                            const int* tiles, int grid, const int* flags, int* status,
+                            cudaStream_t st);
+afmm_status launch_batch_widen(const WJob* jobs, const int* prefix, int njobs,
+                               int rows_total, cudaStream_t st);
+
+// Route of an instance under the built-in rule: 1 tensor cores, 0 CUDA cores.
+int batch_rule_route(const afmm_desc& d);
+// Enqueue `count` independent products on `stream`; `kernels_out` receives
+// the number of kernels one call launches.
+afmm_status batched_run(int count, const afmm_desc* descs, const void* const* X,
+                        const void* const* Y, void* const* Z, void* stream,
+                        int* kernels_out);
+// Status word of the cached batch with these descriptors (after a sync).
+afmm_status batched_status(int count, const afmm_desc* descs, int* out);
+void batched_clear_cache();
+
+}  // namespace afmm

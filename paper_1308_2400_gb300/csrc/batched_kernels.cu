@@ -1,0 +1,387 @@
+// Batched AFMM products: many independent instances (Sec. 2 problems of
+// different n, Case A or B) in one call.
+//
+// Per batch signature (the array of descriptors) the library builds once:
+//  - a route per instance: the tcgen05 split-BF16 form or the CUDA-core
+//    zero-skip form (desc.variant when forced, else the planner's rule);
+//  - operand buffers for all instances in one workspace, with two TMA
+//    descriptors per tensor-core instance kept in device memory;
+//  - per-CTA tile lists for one persistent grouped tensor-core launch,
+//    balanced by longest-processing-time-first over 128 x 256 tiles
+//    (a tile's cost is its number of 32-wide K steps);
+//  - a CUDA graph: grouped conversions -> grouped tensor-core product, and
+//    grouped FP32 widening -> grouped CUDA-core product on a parallel
+//    branch.
+// Every call copies the instances' X, Y, Z pointers into a device table and
+// launches the graph on the caller's stream.  This file holds the kernels
+// and their launchers; batched.cpp holds the planning and the graph.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "afmm_common.cuh"
+#include "batched.cuh"
+#include "bf16_split.cuh"
+#include "ptx_sm100.cuh"
+#include "tc_gemm.cuh"
+
+namespace afmm {
+namespace {
+
+constexpr int GB_EPI = 256;
+constexpr int GB_THREADS = 64 + GB_EPI;
+constexpr uint32_t GB_TMEM_COLS = 512;
+constexpr int GB_A_TILE = GB_BM * GB_BK * 2;      // 8 KiB
+constexpr int GB_B_TILE = GB_BN * GB_BK * 2;      // 16 KiB
+constexpr int GB_STAGE = GB_A_TILE + 3 * GB_B_TILE;   // fits 3A+1B and 1A+3B
+constexpr int GB_STAGES = 4;
+constexpr int GB_SMEM = 1024 + GB_STAGES * GB_STAGE + 256;
+constexpr uint64_t GB_WAIT_NS = 2000000000ull;
+static_assert(GB_SMEM <= 232448, "shared memory");
+
+
+struct GBars {
+    uint64_t full[GB_STAGES];
+    uint64_t empty[GB_STAGES];
+    uint64_t tfull, tempty, drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ int find_job(const int* prefix, int n, int b) {
+    int lo = 0, hi = n - 1;               // last j with prefix[j] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ----------------------------------------------------------- conversions
+// Block b converts one row of the A operand of one instance: Case A slices
+// a row of the real X into 3 BF16 rows; Case B widens a row of the
+// Rep-factors X to BF16 (values must be exact, |v| <= 256, else the
+// instance's flag is set and its Z becomes NaN).
+__global__ void __launch_bounds__(256)
+g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix,
+              int ninst, int* __restrict__ flags) {
+    const int j = find_job(row_prefix, ninst, blockIdx.x);
+    const GInst& g = inst[j];
+    const int64_t r = blockIdx.x - row_prefix[j];
+    const int64_t n = g.n, ldk = g.ldk;
+    for (int64_t c = 2 * threadIdx.x; c < ldk; c += 512) {
+        double v0 = 0.0, v1 = 0.0;
+        if (c < n) v0 = load_any(g.X, r * g.ldx + c, g.x_dtype);
+        if (c + 1 < n) v1 = load_any(g.X, r * g.ldx + c + 1, g.x_dtype);
+        if (g.kind == 0) {
+            __nv_bfloat16 o0[3], o1[3];
+            split_bf16<3>((float)v0, o0);
+            split_bf16<3>((float)v1, o1);
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+                *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.A) + ((int64_t)s * n + r) * ldk + c) =
+                    pack2(o0[s], o1[s]);
+        } else {
+            const __nv_bfloat16 b0 = __double2bfloat16(v0), b1 = __double2bfloat16(v1);
+            if ((double)__bfloat162float(b0) != v0 || (double)__bfloat162float(b1) != v1 ||
+                fabs(v0) > 256.0 || fabs(v1) > 256.0)
+                atomicExch(&flags[g.flag], 1);
+            *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.A) + r * ldk + c) = pack2(b0, b1);
+        }
+    }
+}
+
+// Block b converts one 64 x 64 tile of the B operand (Y transposed to
+// K-major): Case A widens the Rep-factors Y; Case B slices the real Y.
+__global__ void __launch_bounds__(256)
+g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_prefix,
+                   int ninst, int* __restrict__ flags) {
+    __shared__ float tile[64][65];
+    const int j = find_job(tt_prefix, ninst, blockIdx.x);
+    const GInst& g = inst[j];
+    const int64_t n = g.n, ldk = g.ldk;
+    const int64_t tpr = (n + 63) / 64;
+    const int64_t t = blockIdx.x - tt_prefix[j];
+    const int64_t r0 = (t / tpr) * 64, c0 = (t % tpr) * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 64; i += 8) {
+        const int64_t r = r0 + i;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t c = c0 + tx + 32 * h;
+            tile[i][tx + 32 * h] =
+                (r < n && c < n) ? (float)load_any(g.Y, r * g.ldy + c, g.y_dtype) : 0.f;
+        }
+    }
+    __syncthreads();
+    for (int i = ty; i < 64; i += 8) {
+        const int64_t c = c0 + i;            // output row
+        const int64_t r = r0 + 2 * tx;       // output columns r, r+1
+        if (c < n && r < ldk) {
+            const float v0 = tile[2 * tx][i], v1 = tile[2 * tx + 1][i];
+            if (g.kind == 0) {
+                const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
+                if (__bfloat162float(b0) != v0 || __bfloat162float(b1) != v1 ||
+                    fabsf(v0) > 256.f || fabsf(v1) > 256.f)
+                    atomicExch(&flags[g.flag], 1);
+                *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.B) + c * ldk + r) = pack2(b0, b1);
+            } else {
+                __nv_bfloat16 o0[3], o1[3];
+                split_bf16<3>(v0, o0);
+                split_bf16<3>(v1, o1);
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+                    *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.B) + ((int64_t)s * n + c) * ldk + r) =
+                        pack2(o0[s], o1[s]);
+            }
+        }
+    }
+}
+
+// Block b widens one row of one operand to FP32 for the CUDA-core form.
+__global__ void __launch_bounds__(256)
+g_widen_kernel(const WJob* __restrict__ jobs, const int* __restrict__ prefix, int njobs) {
+    const int j = find_job(prefix, njobs, blockIdx.x);
+    const WJob& w = jobs[j];
+    const int64_t r = blockIdx.x - prefix[j];
+    for (int64_t c = threadIdx.x; c < w.n; c += 256)
+        w.dst[r * w.n + c] = (float)load_any(w.src, r * w.lds + c, w.dtype);
+}
+
+// ----------------------------------------------------------- grouped TC
+// Persistent: CTA b runs tiles[cta_off[b] .. cta_off[b+1]) in order; a tile
+// is (instance, tm, tn).  Roles as in the single-product kernel: warp 0 TMA,
+// warp 1 TMEM + MMA, warps 2..9 epilogue; two accumulators per tile (hi
+// slice | smaller slices).  Stage layout: A slices then B slices, 8 KiB per
+// A tile and 16 KiB per B tile (3A+1B for Case A, 1A+3B for Case B).
+__global__ void __launch_bounds__(GB_THREADS, 1)
+g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps,
+            const int* __restrict__ cta_off, const int4* __restrict__ tiles,
+            const int* __restrict__ flags, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = ptx::smem_addr(smem_raw);
+    uint8_t* stg = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    GBars* bars = reinterpret_cast<GBars*>(stg + GB_STAGES * GB_STAGE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = cta_off[blockIdx.x], t1 = cta_off[blockIdx.x + 1];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < GB_STAGES; ++s) {
+            ptx::mbar_init(&bars->full[s], 1);
+            ptx::mbar_init(&bars->empty[s], 1);
+        }
+        ptx::mbar_init(&bars->tfull, 1);
+        ptx::mbar_init(&bars->tempty, GB_EPI);
+        ptx::mbar_init(&bars->drain, 1);
+        bars->abort = 0;
+        ptx::fence_barrier_init();
+        ptx::fence_proxy_async_smem();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(&bars->tmem_base, GB_TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile int* abort = &bars->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[GB_STAGES];
+            for (int s = 0; s < GB_STAGES; ++s) issued[s] = -1;
+            bool ok = true;
+            for (int t = t0; ok && t < t1; ++t) {
+                const int4 tl = tiles[t];
+                const GInst& g = inst[tl.x];
+                const CUtensorMap* ma = &maps[2 * tl.x];
+                const CUtensorMap* mb = &maps[2 * tl.x + 1];
+                const int sa = g.kind == 0 ? 3 : 1, sb = g.kind == 0 ? 1 : 3;
+                const uint32_t bytes = sa * GB_A_TILE + sb * GB_B_TILE;
+                const int nkb = (int)((g.n + GB_BK - 1) / GB_BK);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!ptx::mbar_wait_bounded(&bars->empty[stage], phase ^ 1u, abort,
+                                                GB_WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::mbar_arrive_expect_tx(&bars->full[stage], bytes);
+                    uint8_t* st = stg + stage * GB_STAGE;
+                    for (int s = 0; s < sa; ++s)
+                        ptx::tma_load_3d(st + s * GB_A_TILE, ma, &bars->full[stage],
+                                         kb * GB_BK, tl.y * GB_BM, s);
+                    for (int s = 0; s < sb; ++s)
+                        ptx::tma_load_3d(st + sa * GB_A_TILE + s * GB_B_TILE, mb,
+                                         &bars->full[stage], kb * GB_BK, tl.z * GB_BN, s);
+                    issued[stage] = (int)phase;
+                    if (++stage == GB_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                bars->abort = 1;
+                atomicCAS(status, 0, (int)AFMM_ERR_TIMEOUT);
+                volatile int never = 0;
+                for (int s = 0; s < GB_STAGES; ++s)
+                    if (issued[s] >= 0)
+                        ptx::mbar_wait_bounded(&bars->full[s], (uint32_t)issued[s], &never,
+                                               GB_WAIT_NS);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t IDESC = ptx::idesc_bf16_f32(GB_BM, GB_BN);
+            int stage = 0;
+            uint32_t phase = 0, tphase = 0;
+            bool ok = true;
+            for (int t = t0; ok && t < t1; ++t) {
+                const int4 tl = tiles[t];
+                const GInst& g = inst[tl.x];
+                const int kind = g.kind;
+                const int sa = kind == 0 ? 3 : 1;
+                const int nkb = (int)((g.n + GB_BK - 1) / GB_BK);
+                if (!ptx::mbar_wait_bounded(&bars->tempty, tphase ^ 1u, abort, GB_WAIT_NS)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
+                                                GB_WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t s0 = ptx::smem_addr(stg + stage * GB_STAGE);
+#pragma unroll
+                    for (int ks = 0; ks < GB_BK / 16; ++ks) {
+#pragma unroll
+                        for (int p = 2; p >= 0; --p) {
+                            const uint32_t a_addr =
+                                s0 + (kind == 0 ? p : 0) * GB_A_TILE + ks * 32;
+                            const uint32_t b_addr =
+                                s0 + sa * GB_A_TILE + (kind == 1 ? p : 0) * GB_B_TILE + ks * 32;
+                            const bool first = kb == 0 && ks == 0 && (p == 0 || p == 2);
+                            ptx::mma_f16(tmem + (p == 0 ? 0u : (uint32_t)GB_BN),
+                                         ptx::sdesc_kmajor_sw64(a_addr),
+                                         ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                         first ? 0u : 1u);
+                        }
+                    }
+                    ptx::mma_commit(&bars->empty[stage]);
+                    if (++stage == GB_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                ptx::mma_commit(&bars->tfull);
+                tphase ^= 1u;
+            }
+            if (!ok) {
+                bars->abort = 1;
+                atomicCAS(status, 0, (int)AFMM_ERR_TIMEOUT);
+            }
+            ptx::mma_commit(&bars->drain);
+            volatile int never = 0;
+            ptx::mbar_wait_bounded(&bars->drain, 0u, &never, GB_WAIT_NS);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const int row = q * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
+        uint32_t tphase = 0;
+        for (int t = t0; t < t1; ++t) {
+            const int4 tl = tiles[t];
+            const GInst& g = inst[tl.x];
+            const bool got = ptx::mbar_wait_bounded(&bars->tfull, tphase, abort, GB_WAIT_NS);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) {
+                    bars->abort = 1;
+                    atomicCAS(status, 0, (int)AFMM_ERR_TIMEOUT);
+                }
+                break;
+            }
+            ptx::tc_fence_after();
+            float sum[128];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t r0[32], r1[32];
+                ptx::tmem_ld_32cols(lane_base + (uint32_t)(c * 32), r0);
+                ptx::tmem_ld_32cols(lane_base + (uint32_t)(GB_BN + c * 32), r1);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    sum[c * 32 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars->tempty);
+            tphase ^= 1u;
+            const bool bad = flags[g.flag] != 0;
+            const int64_t m = (int64_t)tl.y * GB_BM + row;
+            const int64_t col0 = (int64_t)tl.z * GB_BN + h * 128;
+            if (m < g.n) {
+                float* zr = g.Z + m * g.ldz + col0;
+#pragma unroll
+                for (int j = 0; j < 128; ++j)
+                    if (col0 + j < g.n) zr[j] = bad ? __int_as_float(0x7fc00000) : sum[j];
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, GB_TMEM_COLS);
+    }
+}
+
+}  // namespace
+
+afmm_status launch_batch_convert(const GInst* inst, const int* row_prefix,
+                                 const int* tt_prefix, int ninst, int rows_total,
+                                 int tt_total, int* flags, cudaStream_t st) {
+    if (ninst <= 0) return AFMM_OK;
+    AFMM_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (ninst + 1), st));
+    g_rows_kernel<<<rows_total, 256, 0, st>>>(inst, row_prefix, ninst, flags);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    g_transpose_kernel<<<tt_total, 256, 0, st>>>(inst, tt_prefix, ninst, flags);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
+    return AFMM_OK;
+}
+
+afmm_status launch_batch_tc(const GInst* inst, const void* maps, const int* cta_off,
+                            const int* tiles, int grid, const int* flags, int* status,
+                            cudaStream_t st) {
+    if (grid <= 0) return AFMM_OK;
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(g_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       GB_SMEM));
+    g_tc_kernel<<<grid, GB_THREADS, GB_SMEM, st>>>(
+        inst, static_cast<const CUtensorMap*>(maps), cta_off,
+        reinterpret_cast<const int4*>(tiles), flags, status);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
+}
+
+afmm_status launch_batch_widen(const WJob* jobs, const int* prefix, int njobs,
+                               int rows_total, cudaStream_t st) {
+    if (njobs <= 0) return AFMM_OK;
+    g_widen_kernel<<<rows_total, 256, 0, st>>>(jobs, prefix, njobs);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
+}
+
+}  // namespace afmm

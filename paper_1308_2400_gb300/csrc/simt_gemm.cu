@@ -111,24 +111,25 @@ __device__ __forceinline__ E comp(const V& v, int i) {
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
+// One 64 x 256 output tile C[m0.., n0..] of C = A * B.
 template <class Op>
-__global__ void __launch_bounds__(THREADS, 1)
-simt_gemm_kernel(const typename Op::Elt* __restrict__ A, int64_t lda,
-                 const typename Op::Elt* __restrict__ B, int64_t ldb,
-                 typename Op::Acc* __restrict__ C, int64_t ldc, int64_t M,
-                 int64_t N, int64_t K, int vec) {
+__device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A,
+                                          int64_t lda,
+                                          const typename Op::Elt* __restrict__ B,
+                                          int64_t ldb, typename Op::Acc* __restrict__ C,
+                                          int64_t ldc, int64_t M, int64_t N, int64_t K,
+                                          int vec, int64_t m0, int64_t n0,
+                                          unsigned char* smem_raw) {
     using Elt = typename Op::Elt;
     using Acc = typename Op::Acc;
     using V4 = typename std::conditional<std::is_same<Elt, float>::value,
                                          float4, int4>::type;
     using A4 = typename std::conditional<std::is_same<Acc, float>::value,
                                          float4, int4>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Elt* As = reinterpret_cast<Elt*>(smem_raw);          // [2][BM][BK]
     Elt* Bs = As + 2 * BM * BK;                          // [2][BK][BN]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
     const int row0 = warp * 8;
 
     Acc acc[8][8];
@@ -255,6 +256,37 @@ simt_gemm_kernel(const typename Op::Elt* __restrict__ A, int64_t lda,
     }
 }
 
+template <class Op>
+__global__ void __launch_bounds__(THREADS, 1)
+simt_gemm_kernel(const typename Op::Elt* __restrict__ A, int64_t lda,
+                 const typename Op::Elt* __restrict__ B, int64_t ldb,
+                 typename Op::Acc* __restrict__ C, int64_t ldc, int64_t M,
+                 int64_t N, int64_t K, int vec) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    simt_tile<Op>(A, lda, B, ldb, C, ldc, M, N, K, vec, (int64_t)blockIdx.y * BM,
+                  (int64_t)blockIdx.x * BN, smem_raw);
+}
+
+// Grouped form: block b runs tile b - tile_prefix[j] of job j, where
+// tile_prefix is the exclusive prefix sum of the jobs' tile counts.
+__global__ void __launch_bounds__(THREADS, 1)
+simt_grouped_kernel(const SimtJob* __restrict__ jobs,
+                    const int* __restrict__ tile_prefix, int njobs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = blockIdx.x;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {                       // last j with tile_prefix[j] <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const SimtJob& j = jobs[lo];
+    const int t = b - tile_prefix[lo];
+    const int tn = t % j.tiles_n, tm = t / j.tiles_n;
+    simt_tile<OpF32>(j.A, j.lda, j.B, j.ldb, j.C, j.ldc, j.M, j.N, j.K, j.vec,
+                     (int64_t)tm * BM, (int64_t)tn * BN, smem_raw);
+}
+
 inline bool aligned16(const void* p) {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
 }
@@ -297,6 +329,24 @@ afmm_status launch_simt_dp4a(const int8_t* A, int64_t lda, const int32_t* W,
     // K counted in 4-byte words of packed int8.
     return launch_simt<OpDp4a>(reinterpret_cast<const int32_t*>(A), lda / 4,
                                W, ldw, C, ldc, M, N, (K + 3) / 4, st);
+}
+
+int simt_tiles(int64_t M, int64_t N) {
+    return (int)(((M + BM - 1) / BM) * ((N + BN - 1) / BN));
+}
+int simt_tiles_n(int64_t N) { return (int)((N + BN - 1) / BN); }
+
+afmm_status launch_simt_f32_grouped(const SimtJob* jobs, const int* tile_prefix,
+                                    int njobs, int total_tiles, cudaStream_t st) {
+    if (njobs <= 0 || total_tiles <= 0) return AFMM_OK;
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(simt_grouped_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_BYTES));
+    simt_grouped_kernel<<<total_tiles, THREADS, SMEM_BYTES, st>>>(jobs, tile_prefix,
+                                                                 njobs);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
 }
 
 }  // namespace afmm

@@ -33,6 +33,7 @@
 
 #include "afmm_common.cuh"
 #include "elem.cuh"
+#include "bf16_split.cuh"
 #include "ptx_sm100.cuh"
 #include "tc_gemm.cuh"
 
@@ -387,35 +388,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
 }
 
 // --------------------------------------------------------------- operands
-// Whether a dtype's values are exact in FP32 (then the split runs in FP32;
-// FP64 arithmetic is slow on this part and kept off the hot path).
-template <int DT>
-constexpr bool kExactInF32 = DT != AFMM_F64 && DT != AFMM_I32;
-
-// Round-to-nearest BF16 slices of v: out[0] = bf16(v), out[s] = bf16 of the
-// residual left by out[0..s-1].  Each residual is exact in the arithmetic
-// used (FP32 for FP32-exact inputs, FP64 otherwise).
-template <int S, typename T>
-__device__ __forceinline__ void split_bf16(T v, __nv_bfloat16 (&out)[S]) {
-    T r = v;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        if constexpr (sizeof(T) == 8) out[s] = __double2bfloat16(r);
-        else out[s] = __float2bfloat16_rn(r);
-        r -= (T)__bfloat162float(out[s]);
-    }
-}
-
-template <int DT>
-__device__ __forceinline__ auto load_val(const void* p, int64_t i) {
-    if constexpr (kExactInF32<DT>) return (float)Elem<DT>::get(p, i);
-    else return Elem<DT>::get(p, i);
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
-
 // Rows kept as rows (K-major A operand): dst[(s*n + r)*ldk + c], eight
 // columns per thread (one 16-byte store per slice).  EXACT: one slice that
 // must equal the source (Rep-factors); otherwise OVERFLOW_RISK is recorded.
@@ -567,9 +539,11 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     return fn;
 }
 
+}  // namespace
+
 // 3-D map over a stack of `slices` BF16 matrices of `rows` x `cols` (K)
 // with leading dimension `ld`; box = 32 (K) x box_rows x 1.
-afmm_status encode_map(void* out, void* base, int64_t cols, int64_t rows,
+afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
                        int64_t ld, int slices, int box_rows) {
     auto fn = get_encode_fn();
     if (!fn) return AFMM_ERR_CUDA;
@@ -583,6 +557,8 @@ afmm_status encode_map(void* out, void* base, int64_t cols, int64_t rows,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? AFMM_OK : AFMM_ERR_CUDA;
 }
+
+namespace {
 
 template <int SA, int SB, int MODE>
 afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
@@ -702,8 +678,8 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b) {
     if (t->n <= 0) return AFMM_OK;
     const int sl = t->slices > 0 ? t->slices : 1;
     const int sa = t->sliced_a ? sl : 1, sb = t->sliced_a ? 1 : sl;
-    AFMM_TRY(encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM));
-    AFMM_TRY(encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN));
+    AFMM_TRY(tc_encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM));
+    AFMM_TRY(tc_encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN));
     t->maps_ready = true;
     return AFMM_OK;
 }

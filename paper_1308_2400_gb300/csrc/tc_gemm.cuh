@@ -27,6 +27,12 @@ struct TcPlan {
     bool maps_ready = false;
 };
 
+// TMA descriptor (written to `out`, 128 bytes, 64-byte aligned) of a stack
+// of `slices` BF16 matrices, `rows` x `cols` with leading dimension `ld`
+// elements; boxes of 32 columns x box_rows rows x 1 slice, 64-byte swizzle.
+afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
+                          int64_t ld, int slices, int box_rows);
+
 // True when this device can run the tensor-core kernels (sm_103).
 bool tc_available();
 // slices = 0 selects the exact-integer form (one BF16 operand each side).

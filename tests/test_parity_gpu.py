@@ -420,20 +420,88 @@ def test_error_norm_kernel():
     assert m == np.abs(D).max()
 
 
-def test_batched_small_mix():
-    from paper_1308_2400_gb300 import afmm_mul_batched
-    from _helpers import desc_for, gpu_operands, z_torch_dtype
-    insts = W.batched_mix(count=10, seed=1, n_min=16, n_max=160)
+def _batch(insts, routes=None):
+    """Device operands, descriptors (forced route when given) and outputs."""
+    from _helpers import desc_for, gpu_operands
     descs, Xs, Ys, Zs = [], [], [], []
-    for inst in insts:
+    for t, inst in enumerate(insts):
         X, Y = gpu_operands(inst)
-        descs.append(desc_for(inst))
+        v = -1 if routes is None else routes[t]
+        descs.append(desc_for(inst, variant=v))
         Xs.append(X)
         Ys.append(Y)
-        Zs.append(torch.empty((inst.n, inst.n), dtype=torch.float32,
-                              device="cuda"))
-    afmm_mul_batched(descs, Xs, Ys, Zs)
-    torch.cuda.synchronize()
+        Zs.append(torch.full((inst.n, inst.n), float("nan"), dtype=torch.float32,
+                             device="cuda"))
+    return descs, Xs, Ys, Zs
+
+
+def _check_batch(insts, Zs):
     for inst, Z in zip(insts, Zs):
         R = oracle_rows(inst)
-        assert rel_fro(Z.cpu().numpy(), R) <= FP32_REL_FRO, inst.name
+        Zn = Z.cpu().numpy()
+        assert np.all(np.isfinite(Zn)), inst.name
+        assert rel_fro(Zn, R) <= FP32_REL_FRO, inst.name
+
+
+@pytest.mark.parametrize("route", ["auto", "tc", "simt", "mixed"])
+def test_batched_grouped_routes(route):
+    from paper_1308_2400_gb300 import afmm_mul_batched
+    from paper_1308_2400_gb300.afmm import afmm_batched_sync
+    insts = W.batched_mix(count=14, seed=5, n_min=16, n_max=400)
+    routes = {"auto": None, "tc": [1] * 14, "simt": [0] * 14,
+              "mixed": [t % 2 for t in range(14)]}[route]
+    descs, Xs, Ys, Zs = _batch(insts, routes)
+    afmm_mul_batched(descs, Xs, Ys, Zs)
+    afmm_batched_sync(descs)
+    _check_batch(insts, Zs)
+
+
+def test_batched_graph_replay_with_new_data():
+    """Same descriptors, new operands: the cached plan and graph must read
+    the new pointers."""
+    from paper_1308_2400_gb300 import afmm_mul_batched
+    from paper_1308_2400_gb300.afmm import afmm_batched_sync
+    first = W.batched_mix(count=9, seed=6, n_min=40, n_max=300)
+    descs, Xs, Ys, Zs = _batch(first, [t % 2 for t in range(9)])
+    afmm_mul_batched(descs, Xs, Ys, Zs)
+    afmm_batched_sync(descs)
+    _check_batch(first, Zs)
+    second = W.batched_mix(count=9, seed=6, n_min=40, n_max=300)
+    rng = np.random.default_rng(7)
+    for inst in second:                 # same shapes and kinds, new values
+        real = inst.X if inst.case == "A" else inst.Y
+        real *= rng.uniform(0.5, 2.0, size=real.shape).astype(real.dtype)
+    _, Xs2, Ys2, Zs2 = _batch(second, [t % 2 for t in range(9)])
+    afmm_mul_batched(descs, Xs2, Ys2, Zs2)
+    afmm_batched_sync(descs)
+    _check_batch(second, Zs2)
+
+
+def test_batched_bad_rep_factor_poisons_only_its_instance():
+    """A Rep-factor not exact in BF16 (300) on the tensor-core route turns
+    that instance's Z into NaN; the other instance is unaffected."""
+    from paper_1308_2400_gb300 import afmm_mul_batched
+    from paper_1308_2400_gb300.afmm import afmm_batched_sync
+    rng = np.random.default_rng(9)
+    insts = []
+    for t in range(2):
+        n = 150 + 20 * t
+        X = rng.standard_normal((n, n)).astype(np.float32)
+        Y = rng.integers(0, 9, size=(n, n)).astype(np.int32)
+        insts.append(W.Instance("A", X, Y, name=f"b{t}", x_dtype="f32",
+                                y_dtype="i32", z_dtype="f32", target="fp32"))
+    insts[0].Y[3, 5] = 300
+    descs, Xs, Ys, Zs = _batch(insts, [1, 1])
+    afmm_mul_batched(descs, Xs, Ys, Zs)
+    afmm_batched_sync(descs)
+    assert np.all(np.isnan(Zs[0].cpu().numpy()))
+    _check_batch(insts[1:], Zs[1:])
+
+
+def test_batched_small_mix():
+    from paper_1308_2400_gb300 import afmm_mul_batched
+    insts = W.batched_mix(count=10, seed=1, n_min=16, n_max=160)
+    descs, Xs, Ys, Zs = _batch(insts)
+    afmm_mul_batched(descs, Xs, Ys, Zs)
+    torch.cuda.synchronize()
+    _check_batch(insts, Zs)
