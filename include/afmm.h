@@ -254,6 +254,59 @@ afmm_status afmm_error_norm(const void* Z, int32_t z_dtype, int64_t ldz,
                             int64_t rows, int64_t cols, void* workspace,
                             double out[3], void* stream);
 
+/* ------------------------------------------------------------------
+ * Learned dispatch of batched instances (the paper has no counterpart:
+ * Sec. 2.2's addition count mu' d1 d2 n^3 is one of the model's inputs).
+ * A small MLP maps AFMM_DISPATCH_FEATURES features of an instance to one
+ * predicted log2-time per kernel variant; the batch planner picks the
+ * variant with the smallest prediction.  Parameters are FP32, flat,
+ * row-major: [W1 (F x H), b1 (H), W2 (H x H), b2 (H), W3 (H x V), b3 (V)];
+ * H1 = relu(x W1 + b1), H2 = relu(H1 W2 + b2), p = H2 W3 + b3.
+ * ------------------------------------------------------------------ */
+#define AFMM_DISPATCH_FEATURES 8
+typedef struct {
+    int32_t features, hidden, outputs, reserved_;
+} afmm_mlp_shape;
+
+/* Features of one instance, from its descriptor (hints used as given):
+ * log2 n, Base density, Rep density, log2(1 + mu'), case (0 A, 1 B),
+ * log2(1 + mu' d1 d2 n^3), log2 n^3, (1 - Base density)^8.  out holds
+ * AFMM_DISPATCH_FEATURES floats (host memory). */
+afmm_status afmm_dispatch_features(const afmm_desc* desc, float* out);
+
+int64_t afmm_mlp_param_count(const afmm_mlp_shape* shape);
+/* Device scratch (floats) the forward / training calls need for `rows`. */
+int64_t afmm_mlp_work_floats(const afmm_mlp_shape* shape, int rows);
+
+/* P (rows x outputs) = MLP(X) (rows x features), device pointers. */
+afmm_status afmm_mlp_forward(const afmm_mlp_shape* shape, const float* params,
+                             const float* X, int rows, float* P, float* work,
+                             void* stream);
+
+/* Mean-squared error over the observed targets (mask M = 1) and its
+ * gradient with respect to every parameter: loss (device float) =
+ * sum M (P - T)^2 / count, grads laid out like params.  Device pointers. */
+afmm_status afmm_mlp_loss_grad(const afmm_mlp_shape* shape, const float* params,
+                               const float* X, const float* T, const float* M,
+                               int rows, float count, float* grads, float* work,
+                               float* loss, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on n parameters, in place. */
+afmm_status afmm_mlp_adam(int64_t n, float* params, const float* grads, float* m,
+                          float* v, float lr, float beta1, float beta2, float eps,
+                          int step, void* stream);
+
+/* Install the dispatch model used for batched instances whose variant is
+ * AFMM_VARIANT_AUTO (host copies are kept; NULL params removes it):
+ * features are normalised as (x - mean) / scale, and output o predicts the
+ * time of variant variant_of_output[o]. */
+afmm_status afmm_set_dispatch_model(const afmm_mlp_shape* shape, const float* params,
+                                    const float* feat_mean, const float* feat_scale,
+                                    const int32_t* variant_of_output);
+
+/* The variant the batch planner would give this instance (host call). */
+int32_t afmm_dispatch_variant(const afmm_desc* desc);
+
 /* FP64-target product that allocates nothing (the paper has no counterpart:
  * this entry point exists for callers of this library, not for the method).
  *

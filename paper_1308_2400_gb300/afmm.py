@@ -84,6 +84,14 @@ class afmm_counters(ctypes.Structure):
                 ("main_kernel_ctas", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
+AFMM_DISPATCH_FEATURES = 8
+
+
+class afmm_mlp_shape(ctypes.Structure):
+    _fields_ = [("features", ctypes.c_int32), ("hidden", ctypes.c_int32),
+                ("outputs", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+
+
 class AfmmError(RuntimeError):
     def __init__(self, status: int, where: str = ""):
         self.status = int(status)
@@ -128,6 +136,21 @@ def _lib():
             "afmm_plan_enable_kernel_timing": ([_VP, ctypes.c_int], st),
             "afmm_plan_counters": ([_VP, ctypes.POINTER(afmm_counters)], st),
             "afmm_selftest_bounded_wait": ([ctypes.c_uint64, _VP], st),
+            "afmm_dispatch_features": ([ctypes.POINTER(afmm_desc),
+                                        ctypes.POINTER(ctypes.c_float)], st),
+            "afmm_mlp_param_count": ([ctypes.POINTER(afmm_mlp_shape)], ctypes.c_int64),
+            "afmm_mlp_work_floats": ([ctypes.POINTER(afmm_mlp_shape), ctypes.c_int],
+                                     ctypes.c_int64),
+            "afmm_mlp_forward": ([ctypes.POINTER(afmm_mlp_shape), _VP, _VP, ctypes.c_int,
+                                  _VP, _VP, _VP], st),
+            "afmm_mlp_loss_grad": ([ctypes.POINTER(afmm_mlp_shape), _VP, _VP, _VP, _VP,
+                                    ctypes.c_int, ctypes.c_float, _VP, _VP, _VP, _VP], st),
+            "afmm_mlp_adam": ([ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_int, _VP], st),
+            "afmm_set_dispatch_model": ([ctypes.POINTER(afmm_mlp_shape), _VP, _VP, _VP,
+                                         _VP], st),
+            "afmm_dispatch_variant": ([ctypes.POINTER(afmm_desc)], ctypes.c_int32),
             "afmm_batched_sync": ([ctypes.c_int, ctypes.POINTER(afmm_desc), _VP], st),
             "afmm_mul_noalloc": ([ctypes.POINTER(afmm_desc), _VP, _VP, _VP, _VP], st),
             "afmm_mul_batched": ([ctypes.c_int, ctypes.POINTER(afmm_desc),
@@ -300,6 +323,67 @@ def afmm_batched_sync(descs: Sequence[afmm_desc], stream=None) -> None:
     cnt = len(descs)
     arr = (afmm_desc * cnt)(*descs)
     _check(_lib().afmm_batched_sync(cnt, arr, _stream(stream)), "afmm_batched_sync")
+
+
+def afmm_dispatch_features(desc: afmm_desc):
+    out = (ctypes.c_float * AFMM_DISPATCH_FEATURES)()
+    _check(_lib().afmm_dispatch_features(ctypes.byref(desc), out),
+           "afmm_dispatch_features")
+    return [float(v) for v in out]
+
+
+def mlp_shape(features: int, hidden: int, outputs: int) -> afmm_mlp_shape:
+    return afmm_mlp_shape(features=features, hidden=hidden, outputs=outputs,
+                          reserved_=0)
+
+
+def afmm_mlp_param_count(shape: afmm_mlp_shape) -> int:
+    return int(_lib().afmm_mlp_param_count(ctypes.byref(shape)))
+
+
+def afmm_mlp_work_floats(shape: afmm_mlp_shape, rows: int) -> int:
+    return int(_lib().afmm_mlp_work_floats(ctypes.byref(shape), int(rows)))
+
+
+def afmm_mlp_forward(shape, params, X, rows, P, work, stream=None) -> None:
+    _check(_lib().afmm_mlp_forward(ctypes.byref(shape), _ptr(params), _ptr(X),
+                                   int(rows), _ptr(P), _ptr(work), _stream(stream)),
+           "afmm_mlp_forward")
+
+
+def afmm_mlp_loss_grad(shape, params, X, T, M, rows, count, grads, work, loss,
+                       stream=None) -> None:
+    _check(_lib().afmm_mlp_loss_grad(ctypes.byref(shape), _ptr(params), _ptr(X),
+                                     _ptr(T), _ptr(M), int(rows), float(count),
+                                     _ptr(grads), _ptr(work), _ptr(loss),
+                                     _stream(stream)), "afmm_mlp_loss_grad")
+
+
+def afmm_mlp_adam(n, params, grads, m, v, lr, beta1, beta2, eps, step,
+                  stream=None) -> None:
+    _check(_lib().afmm_mlp_adam(int(n), _ptr(params), _ptr(grads), _ptr(m), _ptr(v),
+                                float(lr), float(beta1), float(beta2), float(eps),
+                                int(step), _stream(stream)), "afmm_mlp_adam")
+
+
+def afmm_set_dispatch_model(shape, params, mean, scale, variants) -> None:
+    """Host arrays (numpy float32 / int32); params None removes the model."""
+    import numpy as np
+    if params is None:
+        _check(_lib().afmm_set_dispatch_model(None, None, None, None, None),
+               "afmm_set_dispatch_model")
+        return
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    m = np.ascontiguousarray(mean, dtype=np.float32)
+    s = np.ascontiguousarray(scale, dtype=np.float32)
+    v = np.ascontiguousarray(variants, dtype=np.int32)
+    _check(_lib().afmm_set_dispatch_model(ctypes.byref(shape), p.ctypes.data,
+                                          m.ctypes.data, s.ctypes.data,
+                                          v.ctypes.data), "afmm_set_dispatch_model")
+
+
+def afmm_dispatch_variant(desc: afmm_desc) -> int:
+    return int(_lib().afmm_dispatch_variant(ctypes.byref(desc)))
 
 
 def afmm_error_norm_workspace_size(rows: int, cols: int) -> int:

@@ -150,6 +150,17 @@ int simt_tiles_n(int64_t N);
 afmm_status launch_simt_f32_grouped(const SimtJob* jobs, const int* tile_prefix,
                                     int njobs, int total_tiles, cudaStream_t st);
 
+// Dispatch MLP (mlp.cu).
+int64_t mlp_param_count(const afmm_mlp_shape& s);
+int64_t mlp_work_floats(const afmm_mlp_shape& s, int rows);
+afmm_status mlp_forward(const afmm_mlp_shape& s, const float* params, const float* X,
+                        int rows, float* P, float* work, cudaStream_t st);
+afmm_status mlp_loss_grad(const afmm_mlp_shape& s, const float* params, const float* X,
+                          const float* T, const float* M, int rows, float count,
+                          float* grads, float* work, float* loss, cudaStream_t st);
+afmm_status mlp_adam(int64_t n, float* params, const float* grads, float* m, float* v,
+                     float lr, float b1, float b2, float eps, int step, cudaStream_t st);
+
 // K6: error norms, partial sums in `ws` (error_norm_ws_bytes bytes).
 size_t error_norm_ws_bytes(int64_t rows, int64_t cols);
 afmm_status launch_error_norm(const void* Z, int zdt, int64_t ldz,

@@ -670,6 +670,62 @@ afmm_status afmm_plan_counters(afmm_plan p, afmm_counters* out) {
     return AFMM_OK;
 }
 
+int64_t afmm_mlp_param_count(const afmm_mlp_shape* s) {
+    if (!s || s->features <= 0 || s->hidden <= 0 || s->outputs <= 0) return -1;
+    return mlp_param_count(*s);
+}
+
+int64_t afmm_mlp_work_floats(const afmm_mlp_shape* s, int rows) {
+    if (!s || rows < 0 || s->features <= 0 || s->hidden <= 0 || s->outputs <= 0) return -1;
+    return mlp_work_floats(*s, rows);
+}
+
+afmm_status afmm_mlp_forward(const afmm_mlp_shape* s, const float* params, const float* X,
+                             int rows, float* P, float* work, void* stream) {
+    if (afmm_mlp_param_count(s) < 0 || rows < 0 || (rows > 0 && (!params || !X || !P || !work)))
+        return AFMM_ERR_INVALID_ARG;
+    if (rows == 0) return AFMM_OK;
+    return mlp_forward(*s, params, X, rows, P, work, static_cast<cudaStream_t>(stream));
+}
+
+afmm_status afmm_mlp_loss_grad(const afmm_mlp_shape* s, const float* params, const float* X,
+                               const float* T, const float* M, int rows, float count,
+                               float* grads, float* work, float* loss, void* stream) {
+    if (afmm_mlp_param_count(s) < 0 || rows <= 0 || !params || !X || !T || !M || !grads ||
+        !work || !loss)
+        return AFMM_ERR_INVALID_ARG;
+    return mlp_loss_grad(*s, params, X, T, M, rows, count, grads, work, loss,
+                         static_cast<cudaStream_t>(stream));
+}
+
+afmm_status afmm_mlp_adam(int64_t n, float* params, const float* grads, float* m, float* v,
+                          float lr, float beta1, float beta2, float eps, int step,
+                          void* stream) {
+    if (n < 0 || step < 1 || (n > 0 && (!params || !grads || !m || !v)))
+        return AFMM_ERR_INVALID_ARG;
+    if (n == 0) return AFMM_OK;
+    return mlp_adam(n, params, grads, m, v, lr, beta1, beta2, eps, step,
+                    static_cast<cudaStream_t>(stream));
+}
+
+afmm_status afmm_dispatch_features(const afmm_desc* d, float* out) {
+    if (!d || !out) return AFMM_ERR_INVALID_ARG;
+    return dispatch_features(*d, out);
+}
+
+afmm_status afmm_set_dispatch_model(const afmm_mlp_shape* s, const float* params,
+                                    const float* mean, const float* scale,
+                                    const int32_t* variants) {
+    afmm_status rc = set_dispatch_model(s, params, mean, scale, variants);
+    if (rc == AFMM_OK) batched_clear_cache();   // cached routes may change
+    return rc;
+}
+
+int32_t afmm_dispatch_variant(const afmm_desc* d) {
+    if (!d) return -1;
+    return dispatch_route(*d) == 1 ? AFMM_VARIANT_TC_BF16X3 : AFMM_VARIANT_SIMT_F32;
+}
+
 afmm_status afmm_batched_sync(int count, const afmm_desc* descs, void* stream) {
     if (count < 0 || (count > 0 && !descs)) return AFMM_ERR_INVALID_ARG;
     AFMM_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));

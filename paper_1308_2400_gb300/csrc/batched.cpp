@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <list>
 #include <memory>
@@ -85,11 +86,6 @@ bool same_descs(const BatchState& b, int count, const afmm_desc* d, int dev) {
            std::memcmp(b.descs.data(), d, sizeof(afmm_desc) * (size_t)count) == 0;
 }
 
-int route_of(const afmm_desc& d) {
-    if (d.variant == AFMM_VARIANT_SIMT_F32) return 0;
-    if (d.variant == AFMM_VARIANT_TC_BF16X3) return 1;
-    return batch_rule_route(d);
-}
 
 afmm_status check_batch_desc(const afmm_desc& d) {
     if (d.n < 0 || d.reserved_ != 0 || d.target != AFMM_TARGET_FP32 ||
@@ -116,7 +112,7 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
     const bool tc_ok = tc_available();
     for (int i = 0; i < count; ++i) {
         AFMM_TRY(check_batch_desc(descs[i]));
-        int r = route_of(descs[i]);
+        int r = dispatch_route(descs[i]);
         if (r == 1 && !tc_ok) {
             if (descs[i].variant == AFMM_VARIANT_TC_BF16X3) return AFMM_ERR_UNSUPPORTED;
             r = 0;
@@ -341,6 +337,113 @@ afmm_status capture(BatchState* b) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------- dispatch model
+struct DispatchModel {
+    afmm_mlp_shape shape{};
+    std::vector<float> params, mean, scale;
+    std::vector<int> variant_of_output;
+};
+static std::mutex g_model_mu;
+static std::unique_ptr<DispatchModel> g_model;
+
+static void features_of(const afmm_desc& d, float* f) {
+    const double n = (double)(d.n > 0 ? d.n : 1);
+    const bool a = d.kase == AFMM_CASE_A;
+    const double d1 = d.d1 >= 0.0 ? d.d1 : 1.0, d2 = d.d2 >= 0.0 ? d.d2 : 1.0;
+    const double mu = d.mu_prime >= 0.0 ? d.mu_prime : 1.0;
+    const double dbase = a ? d1 : d2, drep = a ? d2 : d1;
+    f[0] = (float)std::log2(n);
+    f[1] = (float)dbase;
+    f[2] = (float)drep;
+    f[3] = (float)std::log2(1.0 + mu);
+    f[4] = a ? 0.f : 1.f;
+    f[5] = (float)std::log2(1.0 + mu * d1 * d2 * n * n * n);
+    f[6] = (float)(3.0 * std::log2(n));
+    f[7] = (float)std::pow(1.0 - dbase, 8.0);
+}
+
+// Variant with the smallest predicted time, or -1 without a model.
+static int model_route(const afmm_desc& d) {
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    if (!g_model) return -1;
+    const DispatchModel& m = *g_model;
+    const int F = m.shape.features, H = m.shape.hidden, V = m.shape.outputs;
+    std::vector<double> x(F), h1(H), h2(H);
+    float f[AFMM_DISPATCH_FEATURES];
+    features_of(d, f);
+    for (int i = 0; i < F; ++i)
+        x[i] = ((i < AFMM_DISPATCH_FEATURES ? f[i] : 0.f) - m.mean[i]) / m.scale[i];
+    const float* W1 = m.params.data();
+    const float* b1 = W1 + (size_t)F * H;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + (size_t)H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + (size_t)H * V;
+    for (int o = 0; o < H; ++o) {
+        double s = b1[o];
+        for (int i = 0; i < F; ++i) s += x[i] * W1[(size_t)i * H + o];
+        h1[o] = s > 0.0 ? s : 0.0;
+    }
+    for (int o = 0; o < H; ++o) {
+        double s = b2[o];
+        for (int i = 0; i < H; ++i) s += h1[i] * W2[(size_t)i * H + o];
+        h2[o] = s > 0.0 ? s : 0.0;
+    }
+    int best = -1;
+    double bestv = 0.0;
+    for (int o = 0; o < V; ++o) {
+        double s = b3[o];
+        for (int i = 0; i < H; ++i) s += h2[i] * W3[(size_t)i * V + o];
+        if (best < 0 || s < bestv) {
+            best = o;
+            bestv = s;
+        }
+    }
+    return m.variant_of_output[best];
+}
+
+
+afmm_status dispatch_features(const afmm_desc& d, float* out) {
+    features_of(d, out);
+    return AFMM_OK;
+}
+
+afmm_status set_dispatch_model(const afmm_mlp_shape* s, const float* params,
+                               const float* mean, const float* scale,
+                               const int32_t* variants) {
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    if (!params) {
+        g_model.reset();
+        return AFMM_OK;
+    }
+    if (!s || !mean || !scale || !variants || s->features <= 0 ||
+        s->features > AFMM_DISPATCH_FEATURES || s->hidden <= 0 || s->outputs <= 0)
+        return AFMM_ERR_INVALID_ARG;
+    auto m = std::make_unique<DispatchModel>();
+    m->shape = *s;
+    const size_t np = (size_t)mlp_param_count(*s);
+    m->params.assign(params, params + np);
+    m->mean.assign(mean, mean + s->features);
+    m->scale.assign(scale, scale + s->features);
+    for (int i = 0; i < s->features; ++i)
+        if (!(m->scale[i] > 0.f)) return AFMM_ERR_INVALID_ARG;
+    for (int o = 0; o < s->outputs; ++o) {
+        if (variants[o] != AFMM_VARIANT_SIMT_F32 && variants[o] != AFMM_VARIANT_TC_BF16X3)
+            return AFMM_ERR_INVALID_ARG;
+        m->variant_of_output.push_back(variants[o] == AFMM_VARIANT_TC_BF16X3 ? 1 : 0);
+    }
+    g_model = std::move(m);
+    return AFMM_OK;
+}
+
+int dispatch_route(const afmm_desc& d) {
+    if (d.variant == AFMM_VARIANT_SIMT_F32) return 0;
+    if (d.variant == AFMM_VARIANT_TC_BF16X3) return 1;
+    const int r = model_route(d);
+    return r >= 0 ? r : batch_rule_route(d);
+}
+
 
 int batch_rule_route(const afmm_desc& d) {
     // Tensor cores unless the Base factor is so sparse that the CUDA-core

@@ -59,5 +59,11 @@ afmm_status batched_run(int count, const afmm_desc* descs, const void* const* X,
 // Status word of the cached batch with these descriptors (after a sync).
 afmm_status batched_status(int count, const afmm_desc* descs, int* out);
 void batched_clear_cache();
+// Learned dispatch (batched.cpp).
+afmm_status dispatch_features(const afmm_desc& d, float* out);
+afmm_status set_dispatch_model(const afmm_mlp_shape* s, const float* params,
+                               const float* mean, const float* scale,
+                               const int32_t* variants);
+int dispatch_route(const afmm_desc& d);   // 1 tensor cores, 0 CUDA cores
 
 }  // namespace afmm
