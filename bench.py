@@ -394,6 +394,92 @@ def run_afmm(args):
     return 0
 
 
+def run_batched(args):
+    """The uneven batched workload: 512 independent instances in one
+    afmm_mul_batched call per step (grouped launches in a CUDA graph), the
+    variant of each instance picked by the learned dispatcher; beside it the
+    autotuner's per-instance best, fixed routes and the paper's count rule."""
+    import numpy as np
+    import torch
+    import afmm_inputs as W
+    from paper_1308_2400_gb300 import afmm as A
+    from paper_1308_2400_gb300 import tune
+    from oracle import afmm_case_a, afmm_case_b
+
+    torch.cuda.set_device(0)
+    peaks, peak_src = load_peaks()
+    insts = W.batched_mix(count=args.count, seed=0)
+    ops = [tune.device_operands(t) for t in insts]
+    Xs, Ys, Zs = [o[0] for o in ops], [o[1] for o in ops], [o[2] for o in ops]
+    flops = float(sum(2.0 * t.n ** 3 for t in insts))
+    model = None
+    if os.path.exists(tune.DEFAULT_MODEL):
+        model = tune.load(tune.DEFAULT_MODEL)
+        tune.install(model)
+    auto = [tune.instance_desc(t) for t in insts]
+    routes_mlp = [1 if A.afmm_dispatch_variant(d) == A.AFMM_VARIANT_TC_BF16X3 else 0
+                  for d in auto]
+
+    def forced(routes):
+        return [tune.instance_desc(t, tune.VARIANTS[r]) for t, r in zip(insts, routes)]
+
+    clk = ClockSampler(0)
+    clk.start()
+    ms = tune.time_batch(auto, Xs, Ys, Zs, reps=args.steps, warmup=args.warmup)
+    clocks = clk.stop()
+    # accuracy of the timed results on a sample of instances
+    errs = []
+    for i in range(0, len(insts), max(1, len(insts) // 12)):
+        t = insts[i]
+        rows = np.arange(0, t.n, max(1, t.n // 16))
+        R = (afmm_case_a if t.case == "A" else afmm_case_b)(t.X, t.Y, rows)[0]
+        Zg = Zs[i].cpu().numpy()[rows].astype(np.float64)
+        errs.append(float(np.linalg.norm(Zg - R) / max(np.linalg.norm(R), 1e-300)))
+    table = tune.autotune(insts, reps=3)
+    best = [int(v) for v in table.argmin(axis=1)]
+    thr = tune.fit_paper_threshold(insts, table)
+    A.afmm_set_dispatch_model(None, None, None, None, None)
+    routes_rule = [1 if A.afmm_dispatch_variant(d) == A.AFMM_VARIANT_TC_BF16X3 else 0
+                   for d in auto]
+    if model is not None:
+        tune.install(model)
+    policies = {"autotune_best": best, "learned": routes_mlp, "rule": routes_rule,
+                "paper_count_rule": tune.paper_count_choice(insts, thr),
+                "all_tc": [1] * len(insts), "all_simt": [0] * len(insts)}
+    times = {}
+    for name, r in policies.items():
+        reps = max(2, min(args.steps, 10)) if name != "all_simt" else 2
+        times[name] = tune.time_batch(forced(r), Xs, Ys, Zs, reps=reps, warmup=1)
+    line = {
+        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "batched_512", "count": len(insts),
+                   "sum_2n3": flops, "tc_instances": int(sum(routes_mlp)),
+                   "dispatch": "learned" if model else "rule"},
+        "roofline": {"bound": "tensor", "unit": "TFLOP/s",
+                     "achieved": 3 * flops / (ms * 1e-3) / 1e12,
+                     "peak": peaks.get("bf16_tflops_sustained", 1700.0),
+                     "frac": 3 * flops / (ms * 1e-3) / 1e12 /
+                             peaks.get("bf16_tflops_sustained", 1700.0),
+                     "note": "whole step (conversions + grouped products), 3 slices"},
+        "dispatch": {
+            "batch_ms": times,
+            "regret_batch": times["learned"] / times["autotune_best"] - 1.0,
+            "regret_table": tune.regret(table, routes_mlp),
+            "gain_vs_paper_count_rule": times["paper_count_rule"] / times["learned"],
+            "gain_vs_rule": times["rule"] / times["learned"],
+            "paper_count_threshold": thr,
+            "autotune_tc_share": float(np.mean(best)),
+        },
+        "accuracy": {"max_rel_fro_err_sampled": max(errs), "instances": len(errs)},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -407,9 +493,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="skip the plain-FP32 and end-to-end legs")
+    ap.add_argument("--count", type=int, default=512,
+                    help="instances of the batched workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched_512":
+        return run_batched(args)
     return run_afmm(args)
 
 
