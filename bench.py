@@ -435,21 +435,32 @@ def run_batched(args):
         R = (afmm_case_a if t.case == "A" else afmm_case_b)(t.X, t.Y, rows)[0]
         Zg = Zs[i].cpu().numpy()[rows].astype(np.float64)
         errs.append(float(np.linalg.norm(Zg - R) / max(np.linalg.norm(R), 1e-300)))
-    table = tune.autotune(insts, reps=3)
-    best = [int(v) for v in table.argmin(axis=1)]
-    thr = tune.fit_paper_threshold(insts, table)
-    A.afmm_set_dispatch_model(None, None, None, None, None)
-    routes_rule = [1 if A.afmm_dispatch_variant(d) == A.AFMM_VARIANT_TC_BF16X3 else 0
-                   for d in auto]
-    if model is not None:
-        tune.install(model)
-    policies = {"autotune_best": best, "learned": routes_mlp, "rule": routes_rule,
-                "paper_count_rule": tune.paper_count_choice(insts, thr),
-                "all_tc": [1] * len(insts), "all_simt": [0] * len(insts)}
-    times = {}
-    for name, r in policies.items():
-        reps = max(2, min(args.steps, 10)) if name != "all_simt" else 2
-        times[name] = tune.time_batch(forced(r), Xs, Ys, Zs, reps=reps, warmup=1)
+    dispatch = None
+    if not args.quick:
+        table = tune.autotune(insts, reps=3)
+        best = [int(v) for v in table.argmin(axis=1)]
+        thr = tune.fit_paper_threshold(insts, table)
+        A.afmm_set_dispatch_model(None, None, None, None, None)
+        routes_rule = [1 if A.afmm_dispatch_variant(d) == A.AFMM_VARIANT_TC_BF16X3 else 0
+                       for d in auto]
+        if model is not None:
+            tune.install(model)
+        policies = {"autotune_best": best, "learned": routes_mlp, "rule": routes_rule,
+                    "paper_count_rule": tune.paper_count_choice(insts, thr),
+                    "all_tc": [1] * len(insts), "all_simt": [0] * len(insts)}
+        times = {}
+        for name, r in policies.items():
+            reps = max(2, min(args.steps, 10)) if name != "all_simt" else 2
+            times[name] = tune.time_batch(forced(r), Xs, Ys, Zs, reps=reps, warmup=1)
+        dispatch = {
+            "batch_ms": times,
+            "regret_batch": times["learned"] / times["autotune_best"] - 1.0,
+            "regret_table": tune.regret(table, routes_mlp),
+            "gain_vs_paper_count_rule": times["paper_count_rule"] / times["learned"],
+            "gain_vs_rule": times["rule"] / times["learned"],
+            "paper_count_threshold": thr,
+            "autotune_tc_share": float(np.mean(best)),
+        }
     line = {
         "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -464,15 +475,7 @@ def run_batched(args):
                      "frac": 3 * flops / (ms * 1e-3) / 1e12 /
                              peaks.get("bf16_tflops_sustained", 1700.0),
                      "note": "whole step (conversions + grouped products), 3 slices"},
-        "dispatch": {
-            "batch_ms": times,
-            "regret_batch": times["learned"] / times["autotune_best"] - 1.0,
-            "regret_table": tune.regret(table, routes_mlp),
-            "gain_vs_paper_count_rule": times["paper_count_rule"] / times["learned"],
-            "gain_vs_rule": times["rule"] / times["learned"],
-            "paper_count_threshold": thr,
-            "autotune_tc_share": float(np.mean(best)),
-        },
+        "dispatch": dispatch,
         "accuracy": {"max_rel_fro_err_sampled": max(errs), "instances": len(errs)},
         "clocks": clocks,
     }

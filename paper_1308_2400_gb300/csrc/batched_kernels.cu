@@ -61,7 +61,8 @@ __device__ __forceinline__ int find_job(const int* prefix, int n, int b) {
 // Block b converts one row of the A operand of one instance: Case A slices
 // a row of the real X into 3 BF16 rows; Case B widens a row of the
 // Rep-factors X to BF16 (values must be exact, |v| <= 256, else the
-// instance's flag is set and its Z becomes NaN).
+// instance's flag is set and its Z becomes NaN).  Eight columns per thread,
+// one 16-byte store per slice; FP32 arithmetic throughout.
 __global__ void __launch_bounds__(256)
 g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix,
               int ninst, int* __restrict__ flags) {
@@ -69,24 +70,50 @@ g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix
     const GInst& g = inst[j];
     const int64_t r = blockIdx.x - row_prefix[j];
     const int64_t n = g.n, ldk = g.ldk;
-    for (int64_t c = 2 * threadIdx.x; c < ldk; c += 512) {
-        double v0 = 0.0, v1 = 0.0;
-        if (c < n) v0 = load_any(g.X, r * g.ldx + c, g.x_dtype);
-        if (c + 1 < n) v1 = load_any(g.X, r * g.ldx + c + 1, g.x_dtype);
+    const bool vec = g.x_dtype == AFMM_F32 && (g.ldx % 4) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(g.X) & 15u) == 0);
+    for (int64_t c = 8 * threadIdx.x; c < ldk; c += 8 * 256) {
+        float v[8];
+        if (vec && c + 8 <= n) {
+            const float4* q = reinterpret_cast<const float4*>(
+                static_cast<const float*>(g.X) + r * g.ldx + c);
+            const float4 a = q[0], b = q[1];
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                v[t] = (c + t < n) ? load_any_f(g.X, r * g.ldx + c + t, g.x_dtype) : 0.f;
+        }
         if (g.kind == 0) {
-            __nv_bfloat16 o0[3], o1[3];
-            split_bf16<3>((float)v0, o0);
-            split_bf16<3>((float)v1, o1);
+            uint32_t w[3][4];
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                __nv_bfloat16 o0[3], o1[3];
+                split_bf16<3>(v[t], o0);
+                split_bf16<3>(v[t + 1], o1);
+#pragma unroll
+                for (int s = 0; s < 3; ++s) w[s][t / 2] = pack2(o0[s], o1[s]);
+            }
 #pragma unroll
             for (int s = 0; s < 3; ++s)
-                *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.A) + ((int64_t)s * n + r) * ldk + c) =
-                    pack2(o0[s], o1[s]);
+                *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(g.A) +
+                                          ((int64_t)s * n + r) * ldk + c) =
+                    make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
         } else {
-            const __nv_bfloat16 b0 = __double2bfloat16(v0), b1 = __double2bfloat16(v1);
-            if ((double)__bfloat162float(b0) != v0 || (double)__bfloat162float(b1) != v1 ||
-                fabs(v0) > 256.0 || fabs(v1) > 256.0)
-                atomicExch(&flags[g.flag], 1);
-            *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.A) + r * ldk + c) = pack2(b0, b1);
+            uint32_t w[4];
+            bool bad = false;
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                const __nv_bfloat16 b0 = __float2bfloat16_rn(v[t]);
+                const __nv_bfloat16 b1 = __float2bfloat16_rn(v[t + 1]);
+                bad |= __bfloat162float(b0) != v[t] || __bfloat162float(b1) != v[t + 1] ||
+                       fabsf(v[t]) > 256.f || fabsf(v[t + 1]) > 256.f;
+                w[t / 2] = pack2(b0, b1);
+            }
+            if (bad) atomicExch(&flags[g.flag], 1);
+            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(g.A) + r * ldk + c) =
+                make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -110,10 +137,11 @@ g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_pr
         for (int h = 0; h < 2; ++h) {
             const int64_t c = c0 + tx + 32 * h;
             tile[i][tx + 32 * h] =
-                (r < n && c < n) ? (float)load_any(g.Y, r * g.ldy + c, g.y_dtype) : 0.f;
+                (r < n && c < n) ? load_any_f(g.Y, r * g.ldy + c, g.y_dtype) : 0.f;
         }
     }
     __syncthreads();
+    bool bad = false;
     for (int i = ty; i < 64; i += 8) {
         const int64_t c = c0 + i;            // output row
         const int64_t r = r0 + 2 * tx;       // output columns r, r+1
@@ -121,21 +149,23 @@ g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_pr
             const float v0 = tile[2 * tx][i], v1 = tile[2 * tx + 1][i];
             if (g.kind == 0) {
                 const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
-                if (__bfloat162float(b0) != v0 || __bfloat162float(b1) != v1 ||
-                    fabsf(v0) > 256.f || fabsf(v1) > 256.f)
-                    atomicExch(&flags[g.flag], 1);
-                *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.B) + c * ldk + r) = pack2(b0, b1);
+                bad |= __bfloat162float(b0) != v0 || __bfloat162float(b1) != v1 ||
+                       fabsf(v0) > 256.f || fabsf(v1) > 256.f;
+                *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.B) + c * ldk + r) =
+                    pack2(b0, b1);
             } else {
                 __nv_bfloat16 o0[3], o1[3];
                 split_bf16<3>(v0, o0);
                 split_bf16<3>(v1, o1);
 #pragma unroll
                 for (int s = 0; s < 3; ++s)
-                    *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.B) + ((int64_t)s * n + c) * ldk + r) =
+                    *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.B) +
+                                                 ((int64_t)s * n + c) * ldk + r) =
                         pack2(o0[s], o1[s]);
             }
         }
     }
+    if (bad) atomicExch(&flags[g.flag], 1);
 }
 
 // Block b widens one row of one operand to FP32 for the CUDA-core form.
@@ -145,7 +175,7 @@ g_widen_kernel(const WJob* __restrict__ jobs, const int* __restrict__ prefix, in
     const WJob& w = jobs[j];
     const int64_t r = blockIdx.x - prefix[j];
     for (int64_t c = threadIdx.x; c < w.n; c += 256)
-        w.dst[r * w.n + c] = (float)load_any(w.src, r * w.lds + c, w.dtype);
+        w.dst[r * w.n + c] = load_any_f(w.src, r * w.lds + c, w.dtype);
 }
 
 // ----------------------------------------------------------- grouped TC

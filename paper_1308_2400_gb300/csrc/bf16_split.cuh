@@ -53,4 +53,23 @@ __device__ __forceinline__ double load_any(const void* p, int64_t i, int dt) {
     }
 }
 
+// Runtime-dtype read as float (FP64 values are rounded to FP32; integers
+// above 2^24 lose their low bits, which the exactness checks then flag).
+__device__ __forceinline__ float load_any_f(const void* p, int64_t i, int dt) {
+    switch (dt) {
+        case AFMM_F64: return (float)static_cast<const double*>(p)[i];
+        case AFMM_F32: return static_cast<const float*>(p)[i];
+        case AFMM_BF16:
+            return __bfloat162float(__ushort_as_bfloat16(static_cast<const uint16_t*>(p)[i]));
+        case AFMM_E4M3: {
+            __nv_fp8_e4m3 v;
+            v.__x = static_cast<const uint8_t*>(p)[i];
+            return static_cast<float>(v);
+        }
+        case AFMM_I32: return (float)static_cast<const int32_t*>(p)[i];
+        case AFMM_I8: return (float)static_cast<const int8_t*>(p)[i];
+        default: return (float)static_cast<const uint8_t*>(p)[i];
+    }
+}
+
 }  // namespace afmm
