@@ -124,13 +124,29 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, v):
+    """Largest value over the ranks (the job's time is its slowest rank's)."""
     if ws <= 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard(count, rank, ws):
+    """Units of rank `rank` when `count` independent units are split over
+    `ws` ranks: contiguous, sizes differing by at most one."""
+    base, extra = divmod(count, ws)
+    lo = rank * base + min(rank, extra)
+    return range(lo, lo + base + (1 if rank < extra else 0))
+
+
+def whole_job_value(units_per_rank, flops_per_unit, max_ms):
+    """Whole-job throughput (TFLOP/s): every rank's units over the slowest
+    rank's time."""
+    return sum(units_per_rank) * flops_per_unit / (max_ms * 1e-3) / 1e12
 
 
 def make_instance(workload, n):
@@ -253,10 +269,20 @@ def run_afmm(args):
     from oracle import realised_parameters
     prm = realised_parameters(inst.X, inst.Y, inst.case)
 
+    # Magnitude hints (the paper's "known in advance" parameters extend to
+    # the largest Rep-factor and Base value); they size the exact form's
+    # K chunks and are checked on the device every call.
+    rep = inst.Y if inst.case == "A" else inst.X
+    real = inst.X if inst.case == "A" else inst.Y
+    rep_max = float(np.max(rep)) if inst.target == "exact" else -1.0
+    base_max = float(np.max(np.abs(real.astype(np.float64)))) \
+        if inst.target == "exact" else -1.0
+
     def desc(variant):
         return make_desc(n, inst.case, inst.x_dtype, inst.y_dtype,
                          inst.z_dtype, inst.target, variant=variant,
-                         d1=prm["d1"], d2=prm["d2"], mu_prime=prm["mu_prime"])
+                         d1=prm["d1"], d2=prm["d2"], mu_prime=prm["mu_prime"],
+                         rep_max=rep_max, base_max=base_max)
 
     stream = torch.cuda.Stream()
 
@@ -296,7 +322,7 @@ def run_afmm(args):
     Z_main = Z.cpu().numpy() if (rank == 0 and ws == 1) else None
     ms_max = max_over_ranks(ws, ms)
     flops = 2.0 * n ** 3
-    value = ws * flops / (ms_max * 1e-3) / 1e12
+    value = whole_job_value([1] * ws, flops, ms_max)
 
     # Roofline of the dominant (product) kernel.
     tc = vname.startswith("tc_")

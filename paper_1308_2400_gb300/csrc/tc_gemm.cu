@@ -486,6 +486,45 @@ widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
     }
 }
 
+// Rep-factors stored in one byte (e4m3, u8, i8) widened to BF16 and
+// transposed to K-major: 64 source rows x 128 source columns per block,
+// 4-byte coalesced reads, 128-byte row writes.  Needs n % 4 == 0 and a
+// 4-byte aligned source with lds % 4 == 0.
+template <int DT>
+__global__ void __launch_bounds__(256)
+widen_transpose_bytes_kernel(const uint8_t* __restrict__ src, int64_t n, int64_t lds,
+                             __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
+                             int* status) {
+    __shared__ float tile[64][129];
+    const int64_t c0 = (int64_t)blockIdx.x * 128, r0 = (int64_t)blockIdx.y * 64;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int i = 0; i < 8; ++i) {
+        const int rr = warp + 8 * i;
+        const int64_t r = r0 + rr, c = c0 + 4 * lane;
+        uint32_t w = 0;
+        if (r < n && c < n) w = *reinterpret_cast<const uint32_t*>(src + r * lds + c);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint8_t byte = (uint8_t)(w >> (8 * b));
+            tile[rr][4 * lane + b] = (float)Elem<DT>::get(&byte, 0);
+        }
+    }
+    __syncthreads();
+    bool bad = false;
+    for (int i = 0; i < 16; ++i) {
+        const int cc = warp * 16 + i;              // output row within the block
+        const int64_t c = c0 + cc, r = r0 + 2 * lane;
+        if (c < n && r < ldk) {
+            const float v0 = tile[2 * lane][cc], v1 = tile[2 * lane + 1][cc];
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
+            bad |= __bfloat162float(b0) != v0 || __bfloat162float(b1) != v1 ||
+                   fabsf(v0) > lim || fabsf(v1) > lim;
+            *reinterpret_cast<uint32_t*>(dst + c * ldk + r) = pack2(b0, b1);
+        }
+    }
+    if (bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+}
+
 template <int S, bool EXACT>
 afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
                               __nv_bfloat16* dst, int64_t ldk, float lim,
@@ -508,6 +547,24 @@ template <int S, bool EXACT>
 afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
                                    int64_t lds, __nv_bfloat16* dst, int64_t ldk,
                                    float lim, int* status, cudaStream_t st) {
+    if constexpr (S == 1 && EXACT) {
+        const bool bytes = dt == AFMM_E4M3 || dt == AFMM_U8 || dt == AFMM_I8;
+        if (bytes && n % 4 == 0 && lds % 4 == 0 &&
+            (reinterpret_cast<uintptr_t>(src) & 3u) == 0 && n > 0) {
+            const dim3 grid((unsigned)((n + 127) / 128), (unsigned)((n + 63) / 64));
+            if (grid.y > 65535) return AFMM_ERR_UNSUPPORTED;
+            const uint8_t* s8 = static_cast<const uint8_t*>(src);
+            if (dt == AFMM_E4M3)
+                widen_transpose_bytes_kernel<AFMM_E4M3><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
+            else if (dt == AFMM_U8)
+                widen_transpose_bytes_kernel<AFMM_U8><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
+            else
+                widen_transpose_bytes_kernel<AFMM_I8><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
+            AFMM_CUDA_TRY(cudaGetLastError());
+            count_launches(1);
+            return AFMM_OK;
+        }
+    }
     const int64_t g = (n + 63) / 64;
     if (g > 65535) return AFMM_ERR_UNSUPPORTED;
     const dim3 grid((unsigned)g, (unsigned)g), block(32, 8);
@@ -691,6 +748,12 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
     auto* A = static_cast<__nv_bfloat16*>(t->a);
     auto* B = static_cast<__nv_bfloat16*>(t->b);
     float* Zf = static_cast<float*>(Z);
+    if (d.kase == AFMM_CASE_A && t->slices == 3 && tc_fused_usable(d, X)) {
+        // B = Rep-factors Y transposed; X is split inside the product kernel.
+        AFMM_TRY((launch_widen_transpose<1, true>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
+                                                  256.f, status, st)));
+        return tc_run_fused_caseA(t, d, X, Z, status, st);
+    }
     if (d.kase == AFMM_CASE_A) {
         // A = slices of the real X (rows), B = Rep-factors Y transposed.
         if (t->slices == 3)

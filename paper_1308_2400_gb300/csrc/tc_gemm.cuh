@@ -44,6 +44,12 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b);
 // Split / widen the operands and run the tcgen05 product into Z (F32).
 afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st);
+// Case A, three slices, X FP32 with 16-byte aligned rows: the fused kernel
+// (tc_fused.cu) reads X directly and splits it in shared memory.
+bool tc_fused_usable(const afmm_desc& d, const void* X);
+afmm_status tc_run_fused_caseA(const TcPlan* t, const afmm_desc& d, const void* X,
+                               void* Z, int* status, cudaStream_t st);
+
 // Exact integer product into Z (I32).
 afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st);
