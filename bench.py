@@ -278,9 +278,9 @@ def run_afmm(args):
     base_max = float(np.max(np.abs(real.astype(np.float64)))) \
         if inst.target == "exact" else -1.0
 
-    def desc(variant):
+    def desc(variant, flags=0):
         return make_desc(n, inst.case, inst.x_dtype, inst.y_dtype,
-                         inst.z_dtype, inst.target, variant=variant,
+                         inst.z_dtype, inst.target, variant=variant, flags=flags,
                          d1=prm["d1"], d2=prm["d2"], mu_prime=prm["mu_prime"],
                          rep_max=rep_max, base_max=base_max)
 
@@ -354,6 +354,17 @@ def run_afmm(args):
                  "ms_per_step": ms2, "kernel_ms": kms2}
         p2.close()
 
+    # The split of the real factor done in a separate pass instead of inside
+    # the product kernel (Case A), for comparison.
+    separate = None
+    if rank == 0 and vname == "tc_bf16x3" and inst.case == "A" and not args.quick:
+        from paper_1308_2400_gb300.afmm import AFMM_FLAG_SEPARATE_SPLIT
+        p3 = Plan(desc(args.variant, AFMM_FLAG_SEPARATE_SPLIT))
+        ms3, kms3, _, _ = timed(p3, max(2, min(args.steps // 4, 100)), 3)
+        separate = {"value": flops / (ms3 * 1e-3) / 1e12, "ms_per_step": ms3,
+                    "kernel_ms": kms3}
+        p3.close()
+
     # End to end through the C ABI with pinned host buffers: copies in,
     # product, copy out, every step.
     e2e = None
@@ -410,7 +421,7 @@ def run_afmm(args):
                        "parallelism": f"replicas x{ws}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches) * ws, "clocks": clocks,
-            "accuracy": acc, "plain_fp32": plain,
+            "accuracy": acc, "plain_fp32": plain, "separate_split": separate,
         }
         print(json.dumps(line), flush=True)
     plan.close()

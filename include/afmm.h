@@ -104,6 +104,10 @@ typedef enum {
 /* Flags for afmm_desc.flags. */
 #define AFMM_FLAG_VALIDATE 0x1u  /* scan the Rep-factors on every call and
                                     report bad ones through afmm_plan_sync */
+#define AFMM_FLAG_SEPARATE_SPLIT 0x2u  /* split the real factor into BF16
+                                    slices in a separate pass even where
+                                    the product kernel could split it
+                                    in shared memory (Case A, FP32 X) */
 
 /* One problem (Sec. 2): sizes, layout, element types and the paper's
  * parameters.  d1, d2 are the densities (fraction of non-zero entries) of X

@@ -41,6 +41,7 @@ AFMM_VARIANT_SIMT_EXACT = 4
 AFMM_VARIANT_TC_EXACT = 5
 AFMM_VARIANT_TC_F64SLICE = 6
 AFMM_FLAG_VALIDATE = 0x1
+AFMM_FLAG_SEPARATE_SPLIT = 0x2
 
 VARIANT_NAMES = {
     AFMM_VARIANT_SIMT_F32: "simt_f32", AFMM_VARIANT_TC_BF16X3: "tc_bf16x3",

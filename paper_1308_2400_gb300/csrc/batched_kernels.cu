@@ -33,8 +33,9 @@ constexpr uint32_t GB_TMEM_COLS = 512;
 constexpr int GB_A_TILE = GB_BM * GB_BK * 2;      // 8 KiB
 constexpr int GB_B_TILE = GB_BN * GB_BK * 2;      // 16 KiB
 constexpr int GB_STAGE = GB_A_TILE + 3 * GB_B_TILE;   // fits 3A+1B and 1A+3B
-constexpr int GB_STAGES = 4;
-constexpr int GB_SMEM = 1024 + GB_STAGES * GB_STAGE + 256;
+constexpr int GB_STAGES = 3;
+constexpr int GB_EPI_SMEM = 8 * 32 * 33 * 4;         // per-warp 32 x 33 floats
+constexpr int GB_SMEM = 1024 + GB_STAGES * GB_STAGE + 256 + GB_EPI_SMEM;
 constexpr uint64_t GB_WAIT_NS = 2000000000ull;
 static_assert(GB_SMEM <= 232448, "shared memory");
 
@@ -192,6 +193,7 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
     const uint32_t raw = ptx::smem_addr(smem_raw);
     uint8_t* stg = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
     GBars* bars = reinterpret_cast<GBars*>(stg + GB_STAGES * GB_STAGE);
+    float* epi = reinterpret_cast<float*>(stg + GB_STAGES * GB_STAGE + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = cta_off[blockIdx.x], t1 = cta_off[blockIdx.x + 1];
 
@@ -355,15 +357,29 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
             ptx::tc_fence_before();
             ptx::mbar_arrive(&bars->tempty);
             tphase ^= 1u;
+            // Coalesced stores: each 32 x 32 block goes through this warp's
+            // shared-memory tile (thread = row on the way in, thread =
+            // column on the way out), one 128-byte row segment per store.
             const bool bad = flags[g.flag] != 0;
-            const int64_t m = (int64_t)tl.y * GB_BM + row;
-            const int64_t col0 = (int64_t)tl.z * GB_BN + h * 128;
-            if (m < g.n) {
-                float* zr = g.Z + m * g.ldz + col0;
+            float* sm = epi + (warp - 2) * 32 * 33;
+            const int64_t mbase = (int64_t)tl.y * GB_BM + q * 32;
 #pragma unroll
-                for (int j = 0; j < 128; ++j)
-                    if (col0 + j < g.n) zr[j] = bad ? __int_as_float(0x7fc00000) : sum[j];
+            for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) sm[lane * 33 + j] = sum[c * 32 + j];
+                __syncwarp();
+                const int64_t col = (int64_t)tl.z * GB_BN + h * 128 + c * 32 + lane;
+                if (col < g.n) {
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int64_t m = mbase + rr;
+                        if (m < g.n)
+                            g.Z[m * g.ldz + col] =
+                                bad ? __int_as_float(0x7fc00000) : sm[rr * 33 + lane];
+                    }
+                }
+                __syncwarp();
             }
+            (void)row;
         }
     }
     ptx::tc_fence_before();

@@ -4,13 +4,14 @@
 // Y Rep-factors; Z = X * Y with X = hi + mid + lo in BF16 and the hi-slice
 // and small-slice products in separate TMEM accumulators), but X is read
 // once, as FP32, straight from the caller's matrix: TMA brings 128 x 32 FP32
-// tiles (128-byte swizzle) into a small ring, and four converter warps cut
+// tiles (128-byte swizzle) into a small ring, and eight converter warps cut
 // each value into its three BF16 slices and write them into the stage in
 // the 64-byte-swizzled K-major layout the MMA reads.  The separate split
 // pass and its 6 bytes per element of slice traffic disappear.
 //
-// Warps: 0 TMA (X tiles and B tiles), 1 TMEM + MMA, 2..5 converters,
-// 6..9 epilogue (row per thread, 32 columns at a time).
+// Warps: 0 TMA (X tiles and B tiles), 1 TMEM + MMA, 2..9 converters (two
+// per SMSP, half a row each), 10..13 epilogue (row per thread, 32 columns
+// at a time).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -26,7 +27,8 @@ namespace afmm {
 namespace {
 
 constexpr int FM = 128, FN = 256, FK = 32;
-constexpr int F_THREADS = 320;
+constexpr int F_CONV = 256;                      // 8 converter warps
+constexpr int F_THREADS = 64 + F_CONV + 128;      // + 4 epilogue warps
 constexpr int F_NX = 3;                          // FP32 X tile ring
 constexpr int F_NS = 4;                          // operand stages
 constexpr int F_X_BYTES = FM * FK * 4;           // 16 KiB
@@ -82,11 +84,11 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmX,
     if (threadIdx.x == 0) {
         for (int i = 0; i < F_NX; ++i) {
             ptx::mbar_init(&bars->x_full[i], 1);
-            ptx::mbar_init(&bars->x_empty[i], 128);
+            ptx::mbar_init(&bars->x_empty[i], F_CONV);
         }
         for (int s = 0; s < F_NS; ++s) {
             ptx::mbar_init(&bars->b_full[s], 1);
-            ptx::mbar_init(&bars->a_full[s], 128);
+            ptx::mbar_init(&bars->a_full[s], F_CONV);
             ptx::mbar_init(&bars->s_empty[s], 1);
         }
         ptx::mbar_init(&bars->tfull, 1);
@@ -196,13 +198,15 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmX,
             ptx::mbar_wait_bounded(&bars->drain, 0u, &never, F_WAIT_NS);
         }
         __syncwarp();
-    } else if (warp < 6) {
+    } else if (warp < 2 + F_CONV / 32) {
         // ------------------------------------------------ converters
-        // Thread = row m of the 128-row tile.  FP32 row m of an X tile sits
-        // at m*128 with its 16-byte chunk j stored at chunk j ^ (m & 7)
-        // (128-byte swizzle); BF16 row m of a slice tile sits at m*64 with
-        // chunk c stored at c ^ ((m >> 1) & 3) (64-byte swizzle).
-        const int m = (warp - 2) * 32 + lane;
+        // Thread = half hh of row m of the 128-row tile (k 16hh .. 16hh+15).
+        // FP32 row m of an X tile sits at m*128 with its 16-byte chunk j
+        // stored at chunk j ^ (m & 7) (128-byte swizzle); BF16 row m of a
+        // slice tile sits at m*64 with chunk c stored at c ^ ((m >> 1) & 3)
+        // (64-byte swizzle).
+        const int t = threadIdx.x - 64;
+        const int m = t & 127, hh = t >> 7;
         int xs = 0, s = 0;
         uint32_t xph = 0, sph = 0;
         bool ok = true;
@@ -216,7 +220,7 @@ tc_fused_kernel(const __grid_constant__ CUtensorMap tmX,
                 const uint8_t* xr = xbuf + xs * F_X_BYTES + m * 128;
                 uint8_t* ar = stg + s * F_STAGE + m * 64;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 2 * hh; c < 2 * hh + 2; ++c) {
                     const float4 f0 = *reinterpret_cast<const float4*>(
                         xr + (((2 * c) ^ (m & 7)) << 4));
                     const float4 f1 = *reinterpret_cast<const float4*>(
@@ -321,7 +325,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 bool tc_fused_usable(const afmm_desc& d, const void* X) {
-    return d.kase == AFMM_CASE_A && d.x_dtype == AFMM_F32 && d.n >= 32 &&
+    return !(d.flags & AFMM_FLAG_SEPARATE_SPLIT) && d.kase == AFMM_CASE_A &&
+           d.x_dtype == AFMM_F32 && d.n >= 32 &&
            (d.ldx ? d.ldx : d.n) % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
 }
 
