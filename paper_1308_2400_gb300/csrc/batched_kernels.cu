@@ -64,7 +64,7 @@ __device__ __forceinline__ int find_job(const int* prefix, int n, int b) {
 // Rep-factors X to BF16 (values must be exact, |v| <= 256, else the
 // instance's flag is set and its Z becomes NaN).  Eight columns per thread,
 // one 16-byte store per slice; FP32 arithmetic throughout.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix,
               int ninst, int* __restrict__ flags) {
     const int j = find_job(row_prefix, ninst, blockIdx.x);
@@ -73,9 +73,20 @@ g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix
     const int64_t n = g.n, ldk = g.ldk;
     const bool vec = g.x_dtype == AFMM_F32 && (g.ldx % 4) == 0 &&
                      ((reinterpret_cast<uintptr_t>(g.X) & 15u) == 0);
-    for (int64_t c = 8 * threadIdx.x; c < ldk; c += 8 * 256) {
+    const bool vec8 = (g.x_dtype == AFMM_U8 || g.x_dtype == AFMM_I8 ||
+                       g.x_dtype == AFMM_E4M3) &&
+                      (g.ldx % 8) == 0 && ((reinterpret_cast<uintptr_t>(g.X) & 7u) == 0);
+    for (int64_t c = 8 * threadIdx.x; c < ldk; c += 8 * 128) {
         float v[8];
-        if (vec && c + 8 <= n) {
+        if (vec8 && c + 8 <= n) {
+            const uint2 w = *reinterpret_cast<const uint2*>(
+                static_cast<const uint8_t*>(g.X) + r * g.ldx + c);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const uint8_t byte = (uint8_t)((t < 4 ? w.x : w.y) >> (8 * (t & 3)));
+                v[t] = load_any_f(&byte, 0, g.x_dtype);
+            }
+        } else if (vec && c + 8 <= n) {
             const float4* q = reinterpret_cast<const float4*>(
                 static_cast<const float*>(g.X) + r * g.ldx + c);
             const float4 a = q[0], b = q[1];
@@ -398,7 +409,7 @@ afmm_status launch_batch_convert(const GInst* inst, const int* row_prefix,
                                  int tt_total, int* flags, cudaStream_t st) {
     if (ninst <= 0) return AFMM_OK;
     AFMM_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (ninst + 1), st));
-    g_rows_kernel<<<rows_total, 256, 0, st>>>(inst, row_prefix, ninst, flags);
+    g_rows_kernel<<<rows_total, 128, 0, st>>>(inst, row_prefix, ninst, flags);
     AFMM_CUDA_TRY(cudaGetLastError());
     g_transpose_kernel<<<tt_total, 256, 0, st>>>(inst, tt_prefix, ninst, flags);
     AFMM_CUDA_TRY(cudaGetLastError());

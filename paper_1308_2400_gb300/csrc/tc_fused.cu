@@ -325,7 +325,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 bool tc_fused_usable(const afmm_desc& d, const void* X) {
-    return !(d.flags & AFMM_FLAG_SEPARATE_SPLIT) && d.kase == AFMM_CASE_A &&
+    return (d.flags & AFMM_FLAG_FUSED_SPLIT) && d.kase == AFMM_CASE_A &&
            d.x_dtype == AFMM_F32 && d.n >= 32 &&
            (d.ldx ? d.ldx : d.n) % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
 }

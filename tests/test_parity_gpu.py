@@ -119,6 +119,16 @@ def test_tc_bf16x3_ragged(workload, n):
     check_fp32(inst, Z, bound_fn=tc_elem_bound)
 
 
+@pytest.mark.parametrize("n", [32, 200, 256, 1000])
+def test_tc_fused_split_kernel(n):
+    """Case A with the split done inside the product kernel
+    (AFMM_FLAG_FUSED_SPLIT): same accuracy bar as the separate pass."""
+    from paper_1308_2400_gb300.afmm import AFMM_FLAG_FUSED_SPLIT
+    inst = W.make("caseA_n8192_e4m3", n=n, seed=n + 3)
+    Z, info = run_gpu(inst, variant=1, flags=AFMM_FLAG_FUSED_SPLIT)
+    check_fp32(inst, Z, bound_fn=tc_elem_bound)
+
+
 def test_tc_bf16x3_case_a_full_size_sampled():
     inst = W.make("caseA_n8192_e4m3")
     Z, info = run_gpu(inst)                 # the planner's choice
