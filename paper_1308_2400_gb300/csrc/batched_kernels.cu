@@ -132,6 +132,9 @@ g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix
 
 // Block b converts one 64 x 64 tile of the B operand (Y transposed to
 // K-major): Case A widens the Rep-factors Y; Case B slices the real Y.
+// Loads: a thread reads 4 consecutive source values (one 16-byte load for
+// FP32, one 4-byte load for one-byte dtypes, when aligned); stores: 4
+// threads write one 128-byte output row segment (16 BF16 values each).
 __global__ void __launch_bounds__(256)
 g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_prefix,
                    int ninst, int* __restrict__ flags) {
@@ -142,38 +145,81 @@ g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_pr
     const int64_t tpr = (n + 63) / 64;
     const int64_t t = blockIdx.x - tt_prefix[j];
     const int64_t r0 = (t / tpr) * 64, c0 = (t % tpr) * 64;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int i = ty; i < 64; i += 8) {
-        const int64_t r = r0 + i;
+    const int tid = threadIdx.x;
+    const int dt = g.y_dtype;
+    const bool f4 = dt == AFMM_F32 && (g.ldy % 4) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(g.Y) & 15u) == 0);
+    const bool b4 = (dt == AFMM_U8 || dt == AFMM_I8 || dt == AFMM_E4M3) &&
+                    (g.ldy % 4) == 0 && ((reinterpret_cast<uintptr_t>(g.Y) & 3u) == 0);
+    // 16 threads per source row (4 values each), 16 rows per pass.
+    const int lc = (tid & 15) * 4;
+    for (int i = tid >> 4; i < 64; i += 16) {
+        const int64_t r = r0 + i, c = c0 + lc;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (r < n) {
+            if (f4 && c + 4 <= n) {
+                const float4 q = *reinterpret_cast<const float4*>(
+                    static_cast<const float*>(g.Y) + r * g.ldy + c);
+                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else if (b4 && c + 4 <= n) {
+                const uint32_t w = *reinterpret_cast<const uint32_t*>(
+                    static_cast<const uint8_t*>(g.Y) + r * g.ldy + c);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t c = c0 + tx + 32 * h;
-            tile[i][tx + 32 * h] =
-                (r < n && c < n) ? load_any_f(g.Y, r * g.ldy + c, g.y_dtype) : 0.f;
+                for (int e = 0; e < 4; ++e) {
+                    const uint8_t byte = (uint8_t)(w >> (8 * e));
+                    v[e] = load_any_f(&byte, 0, dt);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (c + e < n) v[e] = load_any_f(g.Y, r * g.ldy + c + e, dt);
+            }
         }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) tile[i][lc + e] = v[e];
     }
     __syncthreads();
+    // Output row cc (source column), source rows 16*qq .. 16*qq+15.
+    const int cc = tid >> 2, qq = tid & 3;
+    const int64_t c = c0 + cc, r = r0 + 16 * qq;
     bool bad = false;
-    for (int i = ty; i < 64; i += 8) {
-        const int64_t c = c0 + i;            // output row
-        const int64_t r = r0 + 2 * tx;       // output columns r, r+1
-        if (c < n && r < ldk) {
-            const float v0 = tile[2 * tx][i], v1 = tile[2 * tx + 1][i];
-            if (g.kind == 0) {
-                const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
-                bad |= __bfloat162float(b0) != v0 || __bfloat162float(b1) != v1 ||
-                       fabsf(v0) > 256.f || fabsf(v1) > 256.f;
-                *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.B) + c * ldk + r) =
-                    pack2(b0, b1);
-            } else {
-                __nv_bfloat16 o0[3], o1[3];
-                split_bf16<3>(v0, o0);
-                split_bf16<3>(v1, o1);
+    if (c < n && r < ldk) {
+        float v[16];
 #pragma unroll
-                for (int s = 0; s < 3; ++s)
-                    *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(g.B) +
-                                                 ((int64_t)s * n + c) * ldk + r) =
-                        pack2(o0[s], o1[s]);
+        for (int e = 0; e < 16; ++e) v[e] = tile[16 * qq + e][cc];
+        // r + 16 <= ldk unless ldk ends inside this group (ldk % 8 == 0).
+        const int cnt = (int)((ldk - r) < 16 ? (ldk - r) : 16);
+        if (g.kind == 0) {
+            uint32_t w[8];
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                const __nv_bfloat16 b0 = __float2bfloat16_rn(v[e]);
+                const __nv_bfloat16 b1 = __float2bfloat16_rn(v[e + 1]);
+                bad |= __bfloat162float(b0) != v[e] || __bfloat162float(b1) != v[e + 1] ||
+                       fabsf(v[e]) > 256.f || fabsf(v[e + 1]) > 256.f;
+                w[e / 2] = pack2(b0, b1);
+            }
+            __nv_bfloat16* o = static_cast<__nv_bfloat16*>(g.B) + c * ldk + r;
+            *reinterpret_cast<uint4*>(o) = make_uint4(w[0], w[1], w[2], w[3]);
+            if (cnt == 16) *reinterpret_cast<uint4*>(o + 8) = make_uint4(w[4], w[5], w[6], w[7]);
+        } else {
+            uint32_t w[3][8];
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                __nv_bfloat16 o0[3], o1[3];
+                split_bf16<3>(v[e], o0);
+                split_bf16<3>(v[e + 1], o1);
+#pragma unroll
+                for (int sl = 0; sl < 3; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
+            }
+#pragma unroll
+            for (int sl = 0; sl < 3; ++sl) {
+                __nv_bfloat16* o =
+                    static_cast<__nv_bfloat16*>(g.B) + ((int64_t)sl * n + c) * ldk + r;
+                *reinterpret_cast<uint4*>(o) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+                if (cnt == 16)
+                    *reinterpret_cast<uint4*>(o + 8) =
+                        make_uint4(w[sl][4], w[sl][5], w[sl][6], w[sl][7]);
             }
         }
     }
