@@ -15,6 +15,9 @@ mu') with explicit laws:
   caseB_n4096_f32    case B, n=4096: X int32 U{0..15}, d1=0.5; Y FP32 N(0,1).
   caseA_n8192_e4m3   case A, n=8192: X FP32 U(-1,1), d1=0.7; Y Poisson(3)
                      clipped to [0,16], stored as FP8 e4m3 (exact).
+  caseB_n4096_sparse case B, n=4096, the quadratic regime d1 d2 = 1/n of
+                     Sec. 2.2: X int32 U{0..15}, d1 = 1/64; Y FP32 N(0,1),
+                     d2 = 1/64.
   caseA_n16384_i8    case A, n=16384: X int8 U[-127,127], d1=0.8;
                      Y int8 U{0..15}, d2=0.6.
   batched_512        512 instances, n log-uniform in [64,2048], d1, d2
@@ -108,6 +111,18 @@ def _case_b_n4096_f32(n: int, seed: int) -> Instance:
                     z_dtype="f32", target="fp32")
 
 
+def _case_b_n4096_sparse(n: int, seed: int) -> Instance:
+    rx, ry, rm1, rm2 = (rng_for(seed, 1), rng_for(seed, 2), rng_for(seed, 3),
+                        rng_for(seed, 4))
+    d = 1.0 / math.sqrt(max(n, 1))           # d1 = d2 = n^-1/2, d1 d2 = 1/n
+    X = rx.integers(0, 16, size=(n, n), dtype=np.int32)
+    X[~_keep_mask(rm1, (n, n), d, 15.0 / 16.0)] = 0
+    Y = ry.standard_normal(size=(n, n), dtype=np.float32)
+    Y[~_keep_mask(rm2, (n, n), d, 1.0)] = 0.0
+    return Instance("B", X, Y, name="caseB_sparse", x_dtype="i32", y_dtype="f32",
+                    z_dtype="f32", target="fp32")
+
+
 def _case_a_n8192_e4m3(n: int, seed: int) -> Instance:
     rx, ry, rm = rng_for(seed, 1), rng_for(seed, 2), rng_for(seed, 3)
     X = rx.uniform(-1.0, 1.0, size=(n, n)).astype(np.float32)
@@ -133,6 +148,7 @@ def _case_a_n16384_i8(n: int, seed: int) -> Instance:
 _MAKERS = {
     "caseA_n256_f64": (_case_a_n256_f64, 256),
     "caseB_n4096_f32": (_case_b_n4096_f32, 4096),
+    "caseB_n4096_sparse": (_case_b_n4096_sparse, 4096),
     "caseA_n8192_e4m3": (_case_a_n8192_e4m3, 8192),
     "caseA_n16384_i8": (_case_a_n16384_i8, 16384),
 }

@@ -223,7 +223,8 @@ def traffic_from_profile(kernel_tag, workload):
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload}.txt")
     if not os.path.exists(path):
         return None
-    src = {"simt_gemm": "simt_gemm.cu", "tc_gemm": "tc_gemm.cu"}.get(kernel_tag)
+    src = {"simt_gemm": "simt_gemm.cu", "tc_gemm": "tc_gemm.cu",
+           "sparse": "sparse.cu"}.get(kernel_tag)
     vals = {}
     with open(path) as f:
         for ln in f:
@@ -326,7 +327,19 @@ def run_afmm(args):
 
     # Roofline of the dominant (product) kernel.
     tc = vname.startswith("tc_")
-    if tc:
+    if vname == "sparse":
+        # HBM-bound: the product kernel reads the compacted lists (8 bytes per
+        # non-zero of X and Y) and writes Z once (4 n^2 bytes).
+        nnz = float(np.count_nonzero(inst.X) + np.count_nonzero(inst.Y))
+        alg = 8.0 * nnz + 4.0 * n * n
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = alg / (kms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "unit": "GB/s", "peak_src": f"HBM copy, {peak_src}",
+                "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": traffic_from_profile("sparse", args.workload),
+                "kernel": "sp_mul", "kernel_ms": kms, "ctas": ctas,
+                "algorithmic_bytes_per_launch": alg}
+    elif tc:
         alg = slices * flops
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         roof = {"bound": "tensor", "unit": "TFLOP/s",
@@ -339,11 +352,12 @@ def run_afmm(args):
         roof = {"bound": "alu", "unit": "TFLOP/s",
                 "peak_src": f"FP32 FFMA {SMS} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
         tag = "simt_gemm"
-    achieved = alg / (kms * 1e-3) / 1e12
-    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": traffic_from_profile(tag, args.workload),
-                 "kernel": tag, "kernel_ms": kms, "ctas": ctas,
-                 "algorithmic_flops_per_launch": alg})
+    if vname != "sparse":
+        achieved = alg / (kms * 1e-3) / 1e12
+        roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                     "traffic": traffic_from_profile(tag, args.workload),
+                     "kernel": tag, "kernel_ms": kms, "ctas": ctas,
+                     "algorithmic_flops_per_launch": alg})
 
     # Plain FP32 CUDA-core form on the same data, when the main form differs.
     plain = None
@@ -411,7 +425,9 @@ def run_afmm(args):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if tc else "f32", "data": "synthetic",
+            "dtype": "bf16" if tc else ("f64" if inst.target == "fp64" else
+                                        ("i8" if inst.target == "exact" else "f32")),
+            "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "case": inst.case,
                        "x": inst.x_dtype, "y": inst.y_dtype, "z": inst.z_dtype,
                        "variant": vname, "slices": slices,

@@ -95,7 +95,14 @@ typedef enum {
      * K cut into chunks whose FP32 partial sums stay below 2^24 (so every
      * partial sum is an exact integer), chunks added in int32. */
     AFMM_VARIANT_TC_EXACT = 5,
-    AFMM_VARIANT_COUNT_ = 6
+    /* CUDA cores, both factors compacted to per-row (column, value) lists
+     * -- the zero-skip of Sec. 2 on both sides -- for the quadratic regime
+     * of Sec. 2.2 (d1 d2 n small): HBM-bound, FP32 target.  Its workspace
+     * holds the non-zeros planned from the d1, d2 hints (with a margin; all
+     * n^2 without hints); more non-zeros than planned is reported as
+     * AFMM_ERR_OVERFLOW_RISK by afmm_plan_sync and Z is not written. */
+    AFMM_VARIANT_SPARSE = 6,
+    AFMM_VARIANT_COUNT_ = 7
 } afmm_variant;
 
 /* Flags for afmm_desc.flags. */

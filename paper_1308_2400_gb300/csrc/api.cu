@@ -101,6 +101,7 @@ struct afmm_plan_s {
     size_t off_a = 0, off_b = 0, off_c = 0, off_e = 0;
     size_t off_t1 = 0, off_t2 = 0, off_t3 = 0;
     int64_t lda = 0, ldb = 0;           // leading dims of converted operands
+    int64_t cap_x = 0, cap_y = 0;       // sparse form: planned non-zeros
     char* ws = nullptr;
     bool ws_owned = false;
     bool ws_ready = false;              // status word zeroed
@@ -179,6 +180,8 @@ bool variant_serves(int v, const afmm_desc* d) {
             return d->target == AFMM_TARGET_EXACT;
         case AFMM_VARIANT_TC_EXACT:
             return d->target == AFMM_TARGET_EXACT && tc_available();
+        case AFMM_VARIANT_SPARSE:
+            return d->target == AFMM_TARGET_FP32;
         default:
             return false;
     }
@@ -189,9 +192,14 @@ int auto_variant(const afmm_desc* d) {
         return (tc_available() && d->n >= 128) ? AFMM_VARIANT_TC_EXACT
                                                : AFMM_VARIANT_SIMT_EXACT;
     if (d->target == AFMM_TARGET_FP64) return AFMM_VARIANT_SIMT_F64SLICE;
-    // FP32 target: tensor cores for the dense regime; the zero-skipping
-    // CUDA-core kernel when the Base factor is very sparse (the useful
-    // work mu' d1 d2 n^3 is then far below the dense n^3).
+    // FP32 target.  Quadratic regime of Sec. 2.2 (on average at most a few
+    // non-zero terms per element of Z): both factors compacted.
+    if (d->d1 >= 0.0 && d->d2 >= 0.0 && d->d1 * d->d2 * (double)d->n <= 4.0 &&
+        d->n >= 64)
+        return AFMM_VARIANT_SPARSE;
+    // Tensor cores for the dense regime; the zero-skipping CUDA-core kernel
+    // when the Base factor is very sparse (the useful work mu' d1 d2 n^3 is
+    // then far below the dense n^3).
     const double dbase = d->kase == AFMM_CASE_A ? d->d1 : d->d2;
     if (tc_available() && d->n >= 128 && !(dbase >= 0.0 && dbase < 0.05))
         return AFMM_VARIANT_TC_BF16X3;
@@ -244,6 +252,18 @@ void plan_layout(afmm_plan_s* p) {
                 p->off_t2 = L.take(nn * dtype_size(d.x_dtype));
                 p->off_t3 = L.take(nn * 8);
             }
+            break;
+        }
+        case AFMM_VARIANT_SPARSE: {
+            const double n2 = (double)n * (double)n;
+            auto cap = [&](double dens) -> int64_t {
+                if (dens < 0.0) return (int64_t)n2;
+                const double c = 2.0 * dens * n2 + 32.0 * (double)n + 1024.0;
+                return (int64_t)(c < n2 ? c : n2);
+            };
+            p->cap_x = cap(d.d1);
+            p->cap_y = cap(d.d2);
+            p->off_a = L.take(sparse_ws_bytes(n, p->cap_x, p->cap_y));
             break;
         }
         case AFMM_VARIANT_TC_EXACT:
@@ -397,6 +417,11 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
             return tc_run_split(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_TC_EXACT:
             return tc_run_exact(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
+        case AFMM_VARIANT_SPARSE:
+            return launch_sparse(X, d.x_dtype, d.ldx ? d.ldx : n, Y, d.y_dtype,
+                                 d.ldy ? d.ldy : n, static_cast<float*>(Z),
+                                 d.ldz ? d.ldz : n, n, p->cap_x, p->cap_y,
+                                 p->ws + p->off_a, wsp<int>(p, p->off_status), st);
         default: return AFMM_ERR_UNSUPPORTED;
     }
 }

@@ -33,7 +33,6 @@
 
 #include "afmm_common.cuh"
 #include "elem.cuh"
-#include "bf16_split.cuh"
 #include "ptx_sm100.cuh"
 #include "tc_gemm.cuh"
 
@@ -387,198 +386,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     }
 }
 
-// --------------------------------------------------------------- operands
-// Rows kept as rows (K-major A operand): dst[(s*n + r)*ldk + c], eight
-// columns per thread (one 16-byte store per slice).  EXACT: one slice that
-// must equal the source (Rep-factors); otherwise OVERFLOW_RISK is recorded.
-template <int DT, int S, bool EXACT>
-__global__ void __launch_bounds__(256)
-widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
-                  __nv_bfloat16* __restrict__ dst, int64_t ldk, int vec_f32,
-                  float lim, int* status) {
-    const int64_t c = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 8;
-    if (c >= ldk) return;
-    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
-        uint32_t w[S][4];
-        bool done = false;
-        if constexpr (DT == AFMM_F32) {
-            if (vec_f32 && c + 8 <= n) {
-                const float4* p = reinterpret_cast<const float4*>(
-                    static_cast<const float*>(src) + r * lds + c);
-                const float4 a = p[0], b = p[1];
-                const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    __nv_bfloat16 o0[S], o1[S];
-                    split_bf16<S>(v[j], o0);
-                    split_bf16<S>(v[j + 1], o1);
-#pragma unroll
-                    for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o0[s], o1[s]);
-                }
-                done = true;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < 8 && !done; j += 2) {
-            __nv_bfloat16 o[2][S];
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int64_t cc = c + j + t;
-                if (cc < n) {
-                    const auto v = load_val<DT>(src, r * lds + cc);
-                    split_bf16<S>(v, o[t]);
-                    if (EXACT && ((decltype(v))__bfloat162float(o[t][0]) != v ||
-                                  fabs((double)v) > (double)lim))
-                        atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
-                } else {
-#pragma unroll
-                    for (int s = 0; s < S; ++s) o[t][s] = __float2bfloat16_rn(0.0f);
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o[0][s], o[1][s]);
-        }
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-            *reinterpret_cast<uint4*>(dst + ((int64_t)s * n + r) * ldk + c) =
-                make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
-    }
-}
-
-// Rows become columns (K-major B operand from a row-major K x N matrix):
-// dst[(s*n + c)*ldk + r] = slice_s(src[r][c]).  64 x 64 tiles through
-// shared memory; each thread stores two adjacent BF16 values (4 bytes).
-template <int DT, int S, bool EXACT>
-__global__ void __launch_bounds__(256)
-widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
-                       __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
-                       int* status) {
-    using T = decltype(load_val<DT>(nullptr, 0));
-    __shared__ T tile[64][65];
-    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 64;
-    const int tx = threadIdx.x, ty = threadIdx.y;       // 32 x 8
-    for (int i = ty; i < 64; i += 8) {
-        const int64_t r = r0 + i;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t c = c0 + tx + 32 * h;
-            tile[i][tx + 32 * h] = (r < n && c < n) ? load_val<DT>(src, r * lds + c) : T(0);
-        }
-    }
-    __syncthreads();
-    for (int i = ty; i < 64; i += 8) {
-        const int64_t c = c0 + i;                 // output row
-        const int64_t r = r0 + 2 * tx;            // output columns r, r+1
-        if (c < n && r < ldk) {
-            __nv_bfloat16 o0[S], o1[S];
-            const T v0 = tile[2 * tx][i], v1 = tile[2 * tx + 1][i];
-            split_bf16<S>(v0, o0);
-            split_bf16<S>(v1, o1);
-            if (EXACT && ((T)__bfloat162float(o0[0]) != v0 ||
-                          (T)__bfloat162float(o1[0]) != v1 ||
-                          fabs((double)v0) > (double)lim || fabs((double)v1) > (double)lim))
-                atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-                *reinterpret_cast<uint32_t*>(dst + ((int64_t)s * n + c) * ldk + r) =
-                    pack2(o0[s], o1[s]);
-        }
-    }
-}
-
-// Rep-factors stored in one byte (e4m3, u8, i8) widened to BF16 and
-// transposed to K-major: 64 source rows x 128 source columns per block,
-// 4-byte coalesced reads, 128-byte row writes.  Needs n % 4 == 0 and a
-// 4-byte aligned source with lds % 4 == 0.
-template <int DT>
-__global__ void __launch_bounds__(256)
-widen_transpose_bytes_kernel(const uint8_t* __restrict__ src, int64_t n, int64_t lds,
-                             __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
-                             int* status) {
-    __shared__ float tile[64][129];
-    const int64_t c0 = (int64_t)blockIdx.x * 128, r0 = (int64_t)blockIdx.y * 64;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int i = 0; i < 8; ++i) {
-        const int rr = warp + 8 * i;
-        const int64_t r = r0 + rr, c = c0 + 4 * lane;
-        uint32_t w = 0;
-        if (r < n && c < n) w = *reinterpret_cast<const uint32_t*>(src + r * lds + c);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint8_t byte = (uint8_t)(w >> (8 * b));
-            tile[rr][4 * lane + b] = (float)Elem<DT>::get(&byte, 0);
-        }
-    }
-    __syncthreads();
-    bool bad = false;
-    for (int i = 0; i < 16; ++i) {
-        const int cc = warp * 16 + i;              // output row within the block
-        const int64_t c = c0 + cc, r = r0 + 2 * lane;
-        if (c < n && r < ldk) {
-            const float v0 = tile[2 * lane][cc], v1 = tile[2 * lane + 1][cc];
-            const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
-            bad |= __bfloat162float(b0) != v0 || __bfloat162float(b1) != v1 ||
-                   fabsf(v0) > lim || fabsf(v1) > lim;
-            *reinterpret_cast<uint32_t*>(dst + c * ldk + r) = pack2(b0, b1);
-        }
-    }
-    if (bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
-}
-
-template <int S, bool EXACT>
-afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
-                              __nv_bfloat16* dst, int64_t ldk, float lim,
-                              int* status, cudaStream_t st) {
-    const int64_t per_row = ldk / 8;
-    const dim3 grid((unsigned)((per_row + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
-    const int vec = (lds % 4 == 0) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
-    afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
-        widen_rows_kernel<DT, S, EXACT><<<grid, 256, 0, st>>>(src, n, lds, dst, ldk, vec,
-                                                              lim, status);
-        return AFMM_OK;
-    });
-    AFMM_TRY(rc);
-    AFMM_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
-    return AFMM_OK;
-}
-
-template <int S, bool EXACT>
-afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
-                                   int64_t lds, __nv_bfloat16* dst, int64_t ldk,
-                                   float lim, int* status, cudaStream_t st) {
-    if constexpr (S == 1 && EXACT) {
-        const bool bytes = dt == AFMM_E4M3 || dt == AFMM_U8 || dt == AFMM_I8;
-        if (bytes && n % 4 == 0 && lds % 4 == 0 &&
-            (reinterpret_cast<uintptr_t>(src) & 3u) == 0 && n > 0) {
-            const dim3 grid((unsigned)((n + 127) / 128), (unsigned)((n + 63) / 64));
-            if (grid.y > 65535) return AFMM_ERR_UNSUPPORTED;
-            const uint8_t* s8 = static_cast<const uint8_t*>(src);
-            if (dt == AFMM_E4M3)
-                widen_transpose_bytes_kernel<AFMM_E4M3><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
-            else if (dt == AFMM_U8)
-                widen_transpose_bytes_kernel<AFMM_U8><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
-            else
-                widen_transpose_bytes_kernel<AFMM_I8><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
-            AFMM_CUDA_TRY(cudaGetLastError());
-            count_launches(1);
-            return AFMM_OK;
-        }
-    }
-    const int64_t g = (n + 63) / 64;
-    if (g > 65535) return AFMM_ERR_UNSUPPORTED;
-    const dim3 grid((unsigned)g, (unsigned)g), block(32, 8);
-    afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
-        widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(src, n, lds, dst,
-                                                                     ldk, lim, status);
-        return AFMM_OK;
-    });
-    AFMM_TRY(rc);
-    AFMM_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
-    return AFMM_OK;
-}
-
 // --------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     static std::once_flag once;
@@ -750,32 +557,32 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
     float* Zf = static_cast<float*>(Z);
     if (d.kase == AFMM_CASE_A && t->slices == 3 && tc_fused_usable(d, X)) {
         // B = Rep-factors Y transposed; X is split inside the product kernel.
-        AFMM_TRY((launch_widen_transpose<1, true>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
+        AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                   256.f, status, st)));
         return tc_run_fused_caseA(t, d, X, Z, status, st);
     }
     if (d.kase == AFMM_CASE_A) {
         // A = slices of the real X (rows), B = Rep-factors Y transposed.
         if (t->slices == 3)
-            AFMM_TRY((launch_widen_rows<3, false>(X, d.x_dtype, n, d.ldx, A, t->ld_a,
+            AFMM_TRY((tc_widen_rows(3, false, X, d.x_dtype, n, d.ldx, A, t->ld_a,
                                                   0.f, status, st)));
         else
-            AFMM_TRY((launch_widen_rows<2, false>(X, d.x_dtype, n, d.ldx, A, t->ld_a,
+            AFMM_TRY((tc_widen_rows(2, false, X, d.x_dtype, n, d.ldx, A, t->ld_a,
                                                   0.f, status, st)));
-        AFMM_TRY((launch_widen_transpose<1, true>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
+        AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                   256.f, status, st)));
         return t->slices == 3
                    ? launch_tc<3, 1, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
                    : launch_tc<2, 1, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
     }
     // Case B: A = Rep-factors X (rows), B = slices of the real Y transposed.
-    AFMM_TRY((launch_widen_rows<1, true>(X, d.x_dtype, n, d.ldx, A, t->ld_a, 256.f,
+    AFMM_TRY((tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, A, t->ld_a, 256.f,
                                          status, st)));
     if (t->slices == 3)
-        AFMM_TRY((launch_widen_transpose<3, false>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
+        AFMM_TRY((tc_widen_transpose(3, false, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                    0.f, status, st)));
     else
-        AFMM_TRY((launch_widen_transpose<2, false>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
+        AFMM_TRY((tc_widen_transpose(2, false, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                    0.f, status, st)));
     return t->slices == 3
                ? launch_tc<1, 3, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
@@ -789,9 +596,9 @@ afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
     const int64_t n = d.n;
     auto* A = static_cast<__nv_bfloat16*>(t->a);
     auto* B = static_cast<__nv_bfloat16*>(t->b);
-    AFMM_TRY((launch_widen_rows<1, true>(X, d.x_dtype, n, d.ldx, A, t->ld_a, t->lim_a,
+    AFMM_TRY((tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, A, t->ld_a, t->lim_a,
                                          status, st)));
-    AFMM_TRY((launch_widen_transpose<1, true>(Y, d.y_dtype, n, d.ldy, B, t->ld_b,
+    AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                               t->lim_b, status, st)));
     return launch_tc<1, 1, 1>(t, Z, d.ldz, t->kb_per_chunk, status, st);
 }

@@ -33,6 +33,17 @@ struct TcPlan {
 afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
                           int64_t ld, int slices, int box_rows);
 
+// Operand conversions (tc_operands.cu): dst BF16 [slices][n][ldk].  Rows
+// kept (K-major A) or transposed (K-major B, dst row = source column).
+// exact: one slice that must equal the source and stay within |lim|
+// (AFMM_ERR_OVERFLOW_RISK in *status otherwise); else 2 or 3 RN slices.
+afmm_status tc_widen_rows(int slices, bool exact, const void* src, int dt, int64_t n,
+                          int64_t lds, void* dst, int64_t ldk, float lim, int* status,
+                          cudaStream_t st);
+afmm_status tc_widen_transpose(int slices, bool exact, const void* src, int dt, int64_t n,
+                               int64_t lds, void* dst, int64_t ldk, float lim, int* status,
+                               cudaStream_t st);
+
 // True when this device can run the tensor-core kernels (sm_103).
 bool tc_available();
 // slices = 0 selects the exact-integer form (one BF16 operand each side).

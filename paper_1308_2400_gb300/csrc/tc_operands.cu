@@ -1,0 +1,274 @@
+// Operand conversions for the tensor-core products (tc_gemm.cu): exact
+// widening of Rep-factors to BF16 and the hi/mid/lo BF16 split of real
+// values, rows kept (K-major A operand) or transposed (K-major B operand).
+// HBM-bound single passes.
+#include <cuda_bf16.h>
+
+#include "afmm_common.cuh"
+#include "bf16_split.cuh"
+#include "elem.cuh"
+#include "tc_gemm.cuh"
+
+namespace afmm {
+namespace {
+
+// Value of element i as float plus whether it may be represented exactly
+// (for Rep-factors): int32 is range-checked in integer arithmetic so values
+// beyond 2^24 cannot slip through a float rounding.
+template <int DT>
+__device__ __forceinline__ float load_checked(const void* p, int64_t i, float lim,
+                                              bool& bad) {
+    if constexpr (DT == AFMM_I32) {
+        const int32_t v = static_cast<const int32_t*>(p)[i];
+        bad |= (float)(v < 0 ? -(int64_t)v : (int64_t)v) > lim;
+        return (float)v;
+    } else if constexpr (DT == AFMM_F64) {
+        const double v = static_cast<const double*>(p)[i];
+        bad |= (double)(float)v != v;
+        return (float)v;
+    } else {
+        return (float)Elem<DT>::get(p, i);
+    }
+}
+
+// Rows kept as rows (K-major A operand): dst[(s*n + r)*ldk + c], eight
+// columns per thread (one 16-byte store per slice).  EXACT: one slice that
+// must equal the source (Rep-factors); otherwise OVERFLOW_RISK is recorded.
+template <int DT, int S, bool EXACT>
+__global__ void __launch_bounds__(256)
+widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
+                  __nv_bfloat16* __restrict__ dst, int64_t ldk, int vec_f32,
+                  float lim, int* status) {
+    const int64_t c = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 8;
+    if (c >= ldk) return;
+    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
+        uint32_t w[S][4];
+        bool done = false;
+        if constexpr (DT == AFMM_F32) {
+            if (vec_f32 && c + 8 <= n) {
+                const float4* p = reinterpret_cast<const float4*>(
+                    static_cast<const float*>(src) + r * lds + c);
+                const float4 a = p[0], b = p[1];
+                const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    __nv_bfloat16 o0[S], o1[S];
+                    split_bf16<S>(v[j], o0);
+                    split_bf16<S>(v[j + 1], o1);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o0[s], o1[s]);
+                }
+                done = true;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8 && !done; j += 2) {
+            __nv_bfloat16 o[2][S];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int64_t cc = c + j + t;
+                if (cc < n) {
+                    bool bad = false;
+                    const float v = load_checked<DT>(src, r * lds + cc, lim, bad);
+                    split_bf16<S>(v, o[t]);
+                    if (EXACT && (bad || __bfloat162float(o[t][0]) != v || fabsf(v) > lim))
+                        atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) o[t][s] = __float2bfloat16_rn(0.0f);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o[0][s], o[1][s]);
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            *reinterpret_cast<uint4*>(dst + ((int64_t)s * n + r) * ldk + c) =
+                make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    }
+}
+
+// Rows become columns (K-major B operand from a row-major K x N matrix):
+// dst[(s*n + c)*ldk + r] = slice_s(src[r][c]).  64 x 64 tiles through shared
+// memory: a thread reads 4 consecutive source values (one 16-byte load for
+// FP32 when aligned) and writes 16 consecutive outputs of one output row
+// (4 threads per 128-byte row segment).  FP64 real factors are rounded to
+// FP32 first (the FP32 target needs no more).
+template <int DT, int S, bool EXACT>
+__global__ void __launch_bounds__(256)
+widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
+                       __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
+                       int* status) {
+    __shared__ float tile[64][65];
+    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 64;
+    const int tid = threadIdx.x;
+    const bool f4 = DT == AFMM_F32 && (lds % 4) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
+    bool bad = false;
+    const int lc = (tid & 15) * 4;
+    for (int i = tid >> 4; i < 64; i += 16) {
+        const int64_t r = r0 + i, c = c0 + lc;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (r < n) {
+            if (f4 && c + 4 <= n) {
+                const float4 q = *reinterpret_cast<const float4*>(
+                    static_cast<const float*>(src) + r * lds + c);
+                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (c + e < n) v[e] = load_checked<DT>(src, r * lds + c + e, lim, bad);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) tile[i][lc + e] = v[e];
+    }
+    if (!EXACT) bad = false;
+    __syncthreads();
+    const int cc = tid >> 2, qq = tid & 3;
+    const int64_t c = c0 + cc, r = r0 + 16 * qq;
+    if (c < n && r < ldk) {
+        float v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = tile[16 * qq + e][cc];
+        const int cnt = (int)((ldk - r) < 16 ? (ldk - r) : 16);   // 8 or 16
+        uint32_t w[S][8];
+#pragma unroll
+        for (int e = 0; e < 16; e += 2) {
+            __nv_bfloat16 o0[S], o1[S];
+            split_bf16<S>(v[e], o0);
+            split_bf16<S>(v[e + 1], o1);
+            if (EXACT)
+                bad |= __bfloat162float(o0[0]) != v[e] || __bfloat162float(o1[0]) != v[e + 1] ||
+                       fabsf(v[e]) > lim || fabsf(v[e + 1]) > lim;
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
+        }
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+            __nv_bfloat16* o = dst + ((int64_t)sl * n + c) * ldk + r;
+            *reinterpret_cast<uint4*>(o) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+            if (cnt == 16)
+                *reinterpret_cast<uint4*>(o + 8) =
+                    make_uint4(w[sl][4], w[sl][5], w[sl][6], w[sl][7]);
+        }
+    }
+    if (EXACT && bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+}
+
+// Rep-factors stored in one byte (e4m3, u8, i8) widened to BF16 and
+// transposed to K-major: 64 source rows x 128 source columns per block,
+// 4-byte coalesced reads, 128-byte row writes.  Needs n % 4 == 0 and a
+// 4-byte aligned source with lds % 4 == 0.
+template <int DT>
+__global__ void __launch_bounds__(256)
+widen_transpose_bytes_kernel(const uint8_t* __restrict__ src, int64_t n, int64_t lds,
+                             __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
+                             int* status) {
+    __shared__ float tile[64][129];
+    const int64_t c0 = (int64_t)blockIdx.x * 128, r0 = (int64_t)blockIdx.y * 64;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int i = 0; i < 8; ++i) {
+        const int rr = warp + 8 * i;
+        const int64_t r = r0 + rr, c = c0 + 4 * lane;
+        uint32_t w = 0;
+        if (r < n && c < n) w = *reinterpret_cast<const uint32_t*>(src + r * lds + c);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint8_t byte = (uint8_t)(w >> (8 * b));
+            tile[rr][4 * lane + b] = (float)Elem<DT>::get(&byte, 0);
+        }
+    }
+    __syncthreads();
+    bool bad = false;
+    for (int i = 0; i < 16; ++i) {
+        const int cc = warp * 16 + i;              // output row within the block
+        const int64_t c = c0 + cc, r = r0 + 2 * lane;
+        if (c < n && r < ldk) {
+            const float v0 = tile[2 * lane][cc], v1 = tile[2 * lane + 1][cc];
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
+            bad |= __bfloat162float(b0) != v0 || __bfloat162float(b1) != v1 ||
+                   fabsf(v0) > lim || fabsf(v1) > lim;
+            *reinterpret_cast<uint32_t*>(dst + c * ldk + r) = pack2(b0, b1);
+        }
+    }
+    if (bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+}
+
+template <int S, bool EXACT>
+afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
+                              __nv_bfloat16* dst, int64_t ldk, float lim,
+                              int* status, cudaStream_t st) {
+    const int64_t per_row = ldk / 8;
+    const dim3 grid((unsigned)((per_row + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
+    const int vec = (lds % 4 == 0) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
+    afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
+        widen_rows_kernel<DT, S, EXACT><<<grid, 256, 0, st>>>(src, n, lds, dst, ldk, vec,
+                                                              lim, status);
+        return AFMM_OK;
+    });
+    AFMM_TRY(rc);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
+}
+
+template <int S, bool EXACT>
+afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
+                                   int64_t lds, __nv_bfloat16* dst, int64_t ldk,
+                                   float lim, int* status, cudaStream_t st) {
+    if constexpr (S == 1 && EXACT) {
+        const bool bytes = dt == AFMM_E4M3 || dt == AFMM_U8 || dt == AFMM_I8;
+        if (bytes && n % 4 == 0 && lds % 4 == 0 &&
+            (reinterpret_cast<uintptr_t>(src) & 3u) == 0 && n > 0) {
+            const dim3 grid((unsigned)((n + 127) / 128), (unsigned)((n + 63) / 64));
+            if (grid.y > 65535) return AFMM_ERR_UNSUPPORTED;
+            const uint8_t* s8 = static_cast<const uint8_t*>(src);
+            if (dt == AFMM_E4M3)
+                widen_transpose_bytes_kernel<AFMM_E4M3><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
+            else if (dt == AFMM_U8)
+                widen_transpose_bytes_kernel<AFMM_U8><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
+            else
+                widen_transpose_bytes_kernel<AFMM_I8><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
+            AFMM_CUDA_TRY(cudaGetLastError());
+            count_launches(1);
+            return AFMM_OK;
+        }
+    }
+    const int64_t g = (n + 63) / 64;
+    if (g > 65535) return AFMM_ERR_UNSUPPORTED;
+    const dim3 grid((unsigned)g, (unsigned)g), block(256);
+    afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
+        widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(src, n, lds, dst,
+                                                                     ldk, lim, status);
+        return AFMM_OK;
+    });
+    AFMM_TRY(rc);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
+}
+
+}  // namespace
+
+afmm_status tc_widen_rows(int slices, bool exact, const void* src, int dt, int64_t n,
+                          int64_t lds, void* dst, int64_t ldk, float lim, int* status,
+                          cudaStream_t st) {
+    auto* d = static_cast<__nv_bfloat16*>(dst);
+    if (exact && slices == 1) return launch_widen_rows<1, true>(src, dt, n, lds, d, ldk, lim, status, st);
+    if (!exact && slices == 3) return launch_widen_rows<3, false>(src, dt, n, lds, d, ldk, lim, status, st);
+    if (!exact && slices == 2) return launch_widen_rows<2, false>(src, dt, n, lds, d, ldk, lim, status, st);
+    return AFMM_ERR_INVALID_ARG;
+}
+
+afmm_status tc_widen_transpose(int slices, bool exact, const void* src, int dt, int64_t n,
+                               int64_t lds, void* dst, int64_t ldk, float lim, int* status,
+                               cudaStream_t st) {
+    auto* d = static_cast<__nv_bfloat16*>(dst);
+    if (exact && slices == 1) return launch_widen_transpose<1, true>(src, dt, n, lds, d, ldk, lim, status, st);
+    if (!exact && slices == 3) return launch_widen_transpose<3, false>(src, dt, n, lds, d, ldk, lim, status, st);
+    if (!exact && slices == 2) return launch_widen_transpose<2, false>(src, dt, n, lds, d, ldk, lim, status, st);
+    return AFMM_ERR_INVALID_ARG;
+}
+
+}  // namespace afmm

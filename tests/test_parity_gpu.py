@@ -178,6 +178,55 @@ def test_bounded_wait_times_out_and_context_survives():
     check_fp32(inst, Z, bound_fn=tc_elem_bound)
 
 
+# ------------------------------------------------------------------ sparse
+def sparse_elem_bound(inst, rows=None):
+    """Few terms per element: each FMA rounds once in FP32 (summation in a
+    fixed k order), at most nnz(row of X) additions."""
+    return (np.count_nonzero(inst.X, axis=1).max(initial=0) + 2) * U32 * \
+        abs_product(inst, rows) + 1e-30
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 129, 257, 1000])
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_sparse_quadratic_regime(case, n):
+    inst = W.make("caseB_n4096_sparse", n=n, seed=n + 11)
+    if case == "A":                    # real X, Rep-factor Y (roles swapped)
+        inst = W.Instance("A", inst.Y.T.copy(), inst.X.T.copy(), name="spA",
+                          x_dtype="f32", y_dtype="i32", z_dtype="f32",
+                          target="fp32")
+    Z, info = run_gpu(inst, variant=6)
+    assert info["variant"] == 6
+    check_fp32(inst, Z, bound_fn=sparse_elem_bound)
+
+
+def test_sparse_full_size_planner_choice():
+    inst = W.make("caseB_n4096_sparse")
+    Z, info = run_gpu(inst)            # hints d1 d2 n = 1: the sparse form
+    assert info["variant"] == 6
+    check_fp32(inst, Z, sample_rows(inst.n, 40), bound_fn=sparse_elem_bound)
+
+
+def test_sparse_wide_rows_in_column_chunks():
+    inst = W.make("caseB_n4096_sparse", n=7000, seed=3)
+    Z, _ = run_gpu(inst, variant=6)
+    check_fp32(inst, Z, sample_rows(inst.n, 16), bound_fn=sparse_elem_bound)
+
+
+def test_sparse_more_nonzeros_than_planned_is_reported():
+    from paper_1308_2400_gb300 import AfmmError, Plan, make_desc
+    n = 300
+    rng = np.random.default_rng(12)
+    X = torch_of(rng.integers(0, 5, size=(n, n)).astype(np.int32))   # dense
+    Y = torch_of(rng.standard_normal((n, n)).astype(np.float32))
+    Z = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    p = Plan(make_desc(n, "B", "i32", "f32", "f32", "fp32", variant=6,
+                       d1=0.001, d2=0.001))
+    p(X, Y, Z)
+    with pytest.raises(AfmmError) as e:
+        p.sync()
+    assert e.value.status == 4          # AFMM_ERR_OVERFLOW_RISK
+
+
 # ------------------------------------------------------------------ exact, TC
 def exact_case(case, n, seed):
     inst = W.make("caseA_n16384_i8", n=n, seed=seed)
