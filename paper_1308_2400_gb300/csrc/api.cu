@@ -116,6 +116,9 @@ struct afmm_plan_s {
     int last_ctas = 0;
     bool timing = false;
     std::vector<MainTimer> pending, spare;
+    // Transfer pipelining of host buffers (created on first use).
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev[2 * 16 + 2] = {};
 };
 
 namespace {
@@ -438,6 +441,64 @@ afmm_status stage_buffer(afmm_plan_s* p, int idx, size_t bytes, void** out) {
     return AFMM_OK;
 }
 
+// Host X, Y, Z and the split tensor-core form: copy Y in, convert it; then
+// for row blocks of X: copy in (stream s_in), convert and multiply (the
+// call's stream), copy the rows of Z out (stream s_out), so transfers in
+// both directions overlap the products.  Pinned host memory makes the
+// copies asynchronous; pageable memory still gives the right result.
+afmm_status run_pipelined_host(afmm_plan_s* p, const void* X, const void* Y, void* Z,
+                               cudaStream_t st) {
+    const afmm_desc& d = p->d;
+    const int64_t n = d.n, ldx = d.ldx, ldz = d.ldz;
+    const size_t ex = dtype_size(d.x_dtype), ez = dtype_size(d.z_dtype);
+    DeviceProps dp;
+    AFMM_TRY(device_props(&dp));
+    if (!p->s_in) {
+        AFMM_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
+        AFMM_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
+        for (auto& e : p->ev) AFMM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    void *dX, *dY, *dZ;
+    AFMM_TRY(stage_buffer(p, 0, span_bytes(n, ldx, d.x_dtype), &dX));
+    AFMM_TRY(stage_buffer(p, 1, span_bytes(n, d.ldy, d.y_dtype), &dY));
+    AFMM_TRY(stage_buffer(p, 2, span_bytes(n, ldz, d.z_dtype), &dZ));
+    int* status = wsp<int>(p, p->off_status);
+    int64_t bounds[17];
+    const int nb = tc_row_blocks(n, dp.sm_count, bounds, 16);
+    cudaEvent_t ev_y = p->ev[0], ev_done = p->ev[1];
+    // The staging buffers may still be read by the previous call's copies.
+    AFMM_CUDA_TRY(cudaEventRecord(ev_done, st));
+    AFMM_CUDA_TRY(cudaStreamWaitEvent(p->s_in, ev_done, 0));
+    AFMM_CUDA_TRY(cudaMemcpyAsync(dY, Y, span_bytes(n, d.ldy, d.y_dtype),
+                                  cudaMemcpyHostToDevice, p->s_in));
+    AFMM_CUDA_TRY(cudaEventRecord(ev_y, p->s_in));
+    AFMM_CUDA_TRY(cudaStreamWaitEvent(st, ev_y, 0));
+    AFMM_TRY(tc_split_prepare_b(&p->tc, d, dY, status, st));
+    for (int b = 0; b < nb; ++b) {
+        const int64_t r0 = bounds[b], r1 = bounds[b + 1];
+        cudaEvent_t e_in = p->ev[2 + 2 * b], e_c = p->ev[3 + 2 * b];
+        const size_t xoff = (size_t)r0 * ldx * ex;
+        const size_t xbytes = (size_t)((r1 - r0 - 1) * ldx + n) * ex;
+        AFMM_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(dX) + xoff,
+                                      static_cast<const char*>(X) + xoff, xbytes,
+                                      cudaMemcpyHostToDevice, p->s_in));
+        AFMM_CUDA_TRY(cudaEventRecord(e_in, p->s_in));
+        AFMM_CUDA_TRY(cudaStreamWaitEvent(st, e_in, 0));
+        AFMM_TRY(tc_split_rows(&p->tc, d, dX, dZ, r0, r1, status, st));
+        AFMM_CUDA_TRY(cudaEventRecord(e_c, st));
+        AFMM_CUDA_TRY(cudaStreamWaitEvent(p->s_out, e_c, 0));
+        const size_t zoff = (size_t)r0 * ldz * ez;
+        const size_t zbytes = (size_t)((r1 - r0 - 1) * ldz + n) * ez;
+        AFMM_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(Z) + zoff,
+                                      static_cast<const char*>(dZ) + zoff, zbytes,
+                                      cudaMemcpyDeviceToHost, p->s_out));
+    }
+    AFMM_CUDA_TRY(cudaEventRecord(ev_done, p->s_out));
+    AFMM_CUDA_TRY(cudaStreamWaitEvent(st, ev_done, 0));
+    AFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFMM_OK;
+}
+
 afmm_status mul_impl(afmm_plan p, const void* X, const void* Y, void* Z,
                      void* stream, int expect_case) {
     if (!p) return AFMM_ERR_INVALID_ARG;
@@ -453,6 +514,14 @@ afmm_status mul_impl(afmm_plan p, const void* X, const void* Y, void* Z,
     const size_t by = span_bytes(n, d.ldy ? d.ldy : n, d.y_dtype);
     const size_t bz = span_bytes(n, d.ldz ? d.ldz : n, d.z_dtype);
     const bool hx = is_host_ptr(X), hy = is_host_ptr(Y), hz = is_host_ptr(Z);
+    if (hx && hy && hz && n >= 1024 && !(d.flags & (AFMM_FLAG_VALIDATE | AFMM_FLAG_FUSED_SPLIT)) &&
+        (p->variant == AFMM_VARIANT_TC_BF16X3 || p->variant == AFMM_VARIANT_TC_BF16X2)) {
+        const int64_t l0 = launch_counter();
+        afmm_status rc = run_pipelined_host(p, X, Y, Z, st);
+        p->launches += launch_counter() - l0;
+        p->calls += 1;
+        return rc;
+    }
     const void* dX = X;
     const void* dY = Y;
     void* dZ = Z;
@@ -580,6 +649,14 @@ afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc) {
 
 afmm_status afmm_plan_destroy(afmm_plan p) {
     if (!p) return AFMM_OK;
+    if (p->s_in) {
+        cudaStreamSynchronize(p->s_in);
+        cudaStreamSynchronize(p->s_out);
+        for (auto& e : p->ev)
+            if (e) cudaEventDestroy(e);
+        cudaStreamDestroy(p->s_in);
+        cudaStreamDestroy(p->s_out);
+    }
     for (auto* v : {&p->pending, &p->spare})
         for (auto& t : *v) {
             cudaEventDestroy(t.start);

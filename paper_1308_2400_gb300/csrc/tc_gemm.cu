@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -94,7 +95,7 @@ template <int SA, int SB, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB, void* __restrict__ Zv,
-               int64_t ldz, int M, int N, int K, int kb_per_chunk, int vec,
+               int64_t ldz, int m0, int M, int N, int K, int kb_per_chunk, int vec,
                int* status) {
     using Cfg = TcCfg<SA, SB>;
     extern __shared__ uint8_t smem_raw[];
@@ -103,7 +104,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     TcBars* bars = reinterpret_cast<TcBars*>(tiles + Cfg::STAGES * Cfg::STAGE_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
+    // Rows [m0, M) of Z: tile row tm covers rows m0 + tm*BM ..
+    const int tiles_m = (M - m0 + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
     const int num_tiles = tiles_m * tiles_n;
     const int num_kb = (K + TC_BK - 1) / TC_BK;
 
@@ -155,7 +157,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
 #pragma unroll
                     for (int s = 0; s < SA; ++s)
                         ptx::tma_load_3d(st + s * A_TILE_BYTES, &tmA, &bars->full[stage],
-                                         kb * TC_BK, tm * TC_BM, s);
+                                         kb * TC_BK, m0 + tm * TC_BM, s);
 #pragma unroll
                     for (int s = 0; s < SB; ++s)
                         ptx::tma_load_3d(st + SA * A_TILE_BYTES + s * B_TILE_BYTES, &tmB,
@@ -355,7 +357,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                 ++chunk;
             }
             if (!ok) break;
-            const int64_t m = (int64_t)tm * TC_BM + row;
+            const int64_t m = (int64_t)m0 + (int64_t)tm * TC_BM + row;
             const int col0 = tn * TC_BN + h * 128;
             if (m < M) {
                 Acc* zr = static_cast<Acc*>(Zv) + m * ldz + col0;
@@ -426,12 +428,13 @@ namespace {
 
 template <int SA, int SB, int MODE>
 afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
-                      int* status, cudaStream_t st) {
+                      int* status, cudaStream_t st, int m0 = 0, int m1 = -1) {
     using Cfg = TcCfg<SA, SB>;
     DeviceProps dp;
     AFMM_TRY(device_props(&dp));
     const int n = (int)t->n;
-    const int tiles = ((n + TC_BM - 1) / TC_BM) * ((n + TC_BN - 1) / TC_BN);
+    if (m1 < 0) m1 = n;
+    const int tiles = ((m1 - m0 + TC_BM - 1) / TC_BM) * ((n + TC_BN - 1) / TC_BN);
     const int grid = tiles < dp.sm_count ? tiles : dp.sm_count;
     AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -442,7 +445,7 @@ afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
     std::memcpy(&mb, t->tmap_b, sizeof mb);
     main_kernel_begin(st);
     tc_gemm_kernel<SA, SB, MODE><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
-        ma, mb, Z, ldz, n, n, n, kb_per_chunk, vec, status);
+        ma, mb, Z, ldz, m0, m1, n, n, kb_per_chunk, vec, status);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, grid);
     count_launches(1);
@@ -601,6 +604,52 @@ afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
     AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                               t->lim_b, status, st)));
     return launch_tc<1, 1, 1>(t, Z, d.ldz, t->kb_per_chunk, status, st);
+}
+
+afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int* status,
+                               cudaStream_t st) {
+    if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;
+    const int sl = t->slices;
+    if (d.kase == AFMM_CASE_A)        // B = Rep-factors Y transposed
+        return tc_widen_transpose(1, true, Y, d.y_dtype, d.n, d.ldy, t->b, t->ld_b, 256.f,
+                                  status, st);
+    return tc_widen_transpose(sl, false, Y, d.y_dtype, d.n, d.ldy, t->b, t->ld_b, 0.f,
+                              status, st);
+}
+
+afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
+                          int64_t r0, int64_t r1, int* status, cudaStream_t st) {
+    if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;
+    const int64_t n = d.n;
+    const int sl = t->slices;
+    if (d.kase == AFMM_CASE_A)
+        AFMM_TRY(tc_widen_rows(sl, false, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 0.f, status,
+                               st, r0, r1));
+    else
+        AFMM_TRY(tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 256.f, status,
+                               st, r0, r1));
+    const int m0 = (int)r0, m1 = (int)r1;
+    if (d.kase == AFMM_CASE_A)
+        return sl == 3 ? launch_tc<3, 1, 0>(t, Z, d.ldz, 0, status, st, m0, m1)
+                       : launch_tc<2, 1, 0>(t, Z, d.ldz, 0, status, st, m0, m1);
+    return sl == 3 ? launch_tc<1, 3, 0>(t, Z, d.ldz, 0, status, st, m0, m1)
+                   : launch_tc<1, 2, 0>(t, Z, d.ldz, 0, status, st, m0, m1);
+}
+
+int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks) {
+    const int64_t tm = (n + TC_BM - 1) / TC_BM, tn = (n + TC_BN - 1) / TC_BN;
+    // Smallest number of tile rows whose tiles fill whole waves.
+    int64_t g = sms, b = tn;
+    while (b) { const int64_t r = g % b; g = b; b = r; }
+    int64_t unit = sms / g;
+    if (unit < 1) unit = 1;
+    int64_t per = unit * std::max<int64_t>(1, (tm / 4 + unit / 2) / unit);
+    if (per >= tm) per = (tm + 1) / 2;                   // at least two blocks
+    int k = 0;
+    bounds[k++] = 0;
+    for (int64_t r = per; r < tm && k < max_blocks; r += per) bounds[k++] = r * TC_BM;
+    bounds[k] = n;
+    return k;                                            // number of blocks
 }
 
 }  // namespace afmm

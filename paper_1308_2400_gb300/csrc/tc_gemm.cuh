@@ -37,9 +37,10 @@ afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
 // kept (K-major A) or transposed (K-major B, dst row = source column).
 // exact: one slice that must equal the source and stay within |lim|
 // (AFMM_ERR_OVERFLOW_RISK in *status otherwise); else 2 or 3 RN slices.
+// (tc_widen_rows converts rows [r0, r1) only; r1 < 0 means n.)
 afmm_status tc_widen_rows(int slices, bool exact, const void* src, int dt, int64_t n,
                           int64_t lds, void* dst, int64_t ldk, float lim, int* status,
-                          cudaStream_t st);
+                          cudaStream_t st, int64_t r0 = 0, int64_t r1 = -1);
 afmm_status tc_widen_transpose(int slices, bool exact, const void* src, int dt, int64_t n,
                                int64_t lds, void* dst, int64_t ldk, float lim, int* status,
                                cudaStream_t st);
@@ -55,6 +56,17 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b);
 // Split / widen the operands and run the tcgen05 product into Z (F32).
 afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st);
+// The same product in pieces for transfer pipelining: tc_split_prepare_b
+// converts the B operand (all of the factor that is not split by rows);
+// tc_split_rows converts rows [r0, r1) of the A operand and computes rows
+// [r0, r1) of Z.  Case A or B, 2 or 3 slices, the separate-split path.
+afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int* status,
+                               cudaStream_t st);
+afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
+                          int64_t r0, int64_t r1, int* status, cudaStream_t st);
+// Row blocks for pipelining an n x n product: boundaries multiple of 128
+// chosen so each block's tile count fills whole waves of `sms` CTAs.
+int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks);
 // Case A, three slices, X FP32 with 16-byte aligned rows: the fused kernel
 // (tc_fused.cu) reads X directly and splits it in shared memory.
 bool tc_fused_usable(const afmm_desc& d, const void* X);

@@ -38,10 +38,10 @@ template <int DT, int S, bool EXACT>
 __global__ void __launch_bounds__(256)
 widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                   __nv_bfloat16* __restrict__ dst, int64_t ldk, int vec_f32,
-                  float lim, int* status) {
+                  float lim, int* status, int64_t r0, int64_t r1) {
     const int64_t c = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 8;
     if (c >= ldk) return;
-    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
+    for (int64_t r = r0 + blockIdx.y; r < r1; r += gridDim.y) {
         uint32_t w[S][4];
         bool done = false;
         if constexpr (DT == AFMM_F32) {
@@ -198,13 +198,16 @@ widen_transpose_bytes_kernel(const uint8_t* __restrict__ src, int64_t n, int64_t
 template <int S, bool EXACT>
 afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
                               __nv_bfloat16* dst, int64_t ldk, float lim,
-                              int* status, cudaStream_t st) {
+                              int* status, cudaStream_t st, int64_t r0, int64_t r1) {
     const int64_t per_row = ldk / 8;
-    const dim3 grid((unsigned)((per_row + 255) / 256), (unsigned)(n < 65535 ? n : 65535));
+    const int64_t rows = r1 - r0;
+    if (rows <= 0) return AFMM_OK;
+    const dim3 grid((unsigned)((per_row + 255) / 256),
+                    (unsigned)(rows < 65535 ? rows : 65535));
     const int vec = (lds % 4 == 0) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
         widen_rows_kernel<DT, S, EXACT><<<grid, 256, 0, st>>>(src, n, lds, dst, ldk, vec,
-                                                              lim, status);
+                                                              lim, status, r0, r1);
         return AFMM_OK;
     });
     AFMM_TRY(rc);
@@ -253,11 +256,15 @@ afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
 
 afmm_status tc_widen_rows(int slices, bool exact, const void* src, int dt, int64_t n,
                           int64_t lds, void* dst, int64_t ldk, float lim, int* status,
-                          cudaStream_t st) {
+                          cudaStream_t st, int64_t r0, int64_t r1) {
     auto* d = static_cast<__nv_bfloat16*>(dst);
-    if (exact && slices == 1) return launch_widen_rows<1, true>(src, dt, n, lds, d, ldk, lim, status, st);
-    if (!exact && slices == 3) return launch_widen_rows<3, false>(src, dt, n, lds, d, ldk, lim, status, st);
-    if (!exact && slices == 2) return launch_widen_rows<2, false>(src, dt, n, lds, d, ldk, lim, status, st);
+    if (r1 < 0) r1 = n;
+    if (exact && slices == 1)
+        return launch_widen_rows<1, true>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1);
+    if (!exact && slices == 3)
+        return launch_widen_rows<3, false>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1);
+    if (!exact && slices == 2)
+        return launch_widen_rows<2, false>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1);
     return AFMM_ERR_INVALID_ARG;
 }
 
