@@ -162,7 +162,7 @@ afmm_status mlp_adam(int64_t n, float* params, const float* grads, float* m, flo
                      float lr, float b1, float b2, float eps, int step, cudaStream_t st);
 
 // Sparse x sparse product (sparse.cu): workspace for nnz capacities and
-// the launch sequence (count, scan, fill for X and Y; product).
+// the launch sequence (count and fill for X and Y; product).
 size_t sparse_ws_bytes(int64_t n, int64_t cap_x, int64_t cap_y);
 afmm_status launch_sparse(const void* X, int xdt, int64_t ldx, const void* Y, int ydt,
                           int64_t ldy, float* Z, int64_t ldz, int64_t n, int64_t cap_x,

@@ -227,6 +227,89 @@ def test_sparse_more_nonzeros_than_planned_is_reported():
     assert e.value.status == 4          # AFMM_ERR_OVERFLOW_RISK
 
 
+def _sparse_storage(vals, dt):
+    """Device tensor of `vals` stored as dtype `dt`, and the stored values
+    read back in FP64 (what the oracle multiplies)."""
+    tt = {"u8": torch.uint8, "i8": torch.int8, "i32": torch.int32,
+          "f32": torch.float32, "f64": torch.float64}
+    if dt in tt:
+        t = torch.from_numpy(np.ascontiguousarray(vals)).to(tt[dt])
+        back = t.to(torch.float64)
+    elif dt == "bf16":
+        t = torch.from_numpy(np.ascontiguousarray(vals, np.float32)).to(torch.bfloat16)
+        back = t.to(torch.float64)
+    else:                                           # e4m3 bytes
+        f8 = torch.from_numpy(np.ascontiguousarray(vals, np.float32)).to(torch.float8_e4m3fn)
+        back = f8.to(torch.float64)
+        t = f8.view(torch.uint8)
+    return t.cuda(), back.numpy()
+
+
+@pytest.mark.parametrize("n", [512, 333])
+@pytest.mark.parametrize("xd,yd", [("u8", "f32"), ("i8", "bf16"), ("i32", "f64"),
+                                   ("e4m3", "f32")])
+def test_sparse_storage_dtypes(xd, yd, n):
+    """Every element size through the compaction: n = 512 takes the 16-byte
+    load path for all of them, n = 333 the per-element path."""
+    from paper_1308_2400_gb300 import Plan
+    from _helpers import desc_for
+    rng = np.random.default_rng(n + len(xd + yd))
+    d = 3.0 / np.sqrt(n)
+    Xi = rng.integers(1, 16, size=(n, n)) * (rng.random((n, n)) < d)
+    Yr = rng.standard_normal((n, n)) * (rng.random((n, n)) < d)
+    Xt, Xv = _sparse_storage(Xi, xd)
+    Yt, Yv = _sparse_storage(Yr, yd)
+    inst = W.Instance("B", Xv.astype(np.int64), Yv, x_dtype=xd, y_dtype=yd,
+                      z_dtype="f32", target="fp32")
+    Z = torch.full((n, n), float("nan"), device="cuda")
+    p = Plan(desc_for(inst, variant=6))
+    p(Xt, Yt, Z)
+    p.sync()
+    check_fp32(inst, Z.cpu().numpy(), bound_fn=sparse_elem_bound)
+
+
+@pytest.mark.parametrize("ldx,ldy,ldz", [(256 + 16, 256 + 4, 256 + 4),   # aligned rows
+                                         (256 + 3, 256 + 1, 256 + 5)])   # unaligned
+def test_sparse_leading_dimensions(ldx, ldy, ldz):
+    from paper_1308_2400_gb300 import Plan, make_desc
+    rng = np.random.default_rng(ldx)
+    n = 256
+    Xb = (rng.integers(1, 9, size=(n, ldx)) * (rng.random((n, ldx)) < 0.06)).astype(np.uint8)
+    Yb = (rng.standard_normal((n, ldy)) * (rng.random((n, ldy)) < 0.06)).astype(np.float32)
+    Zb = torch.full((n, ldz), 7.0, dtype=torch.float32, device="cuda")
+    p = Plan(make_desc(n, "B", "u8", "f32", "f32", "fp32", variant=6,
+                       ldx=ldx, ldy=ldy, ldz=ldz))
+    p(torch_of(Xb), torch_of(Yb), Zb)
+    p.sync()
+    Z = Zb.cpu().numpy()
+    inst = W.Instance("B", Xb[:, :n].astype(np.int64), Yb[:, :n], x_dtype="u8",
+                      y_dtype="f32")
+    check_fp32(inst, Z[:, :n], bound_fn=sparse_elem_bound)
+    assert np.all(Z[:, n:] == 7.0)      # padding columns untouched
+
+
+def test_sparse_one_dense_factor_and_repeat_calls():
+    """d1 = 1 with d2 = 2/n (d1 d2 n = 2): a dense Rep-factor matrix is
+    compacted too.  A second call gives the same bits (fixed order)."""
+    from paper_1308_2400_gb300 import Plan
+    from _helpers import desc_for
+    rng = np.random.default_rng(77)
+    n = 640
+    X = rng.integers(1, 16, size=(n, n)).astype(np.int32)
+    Y = (rng.standard_normal((n, n)) * (rng.random((n, n)) < 2.0 / n)).astype(np.float32)
+    inst = W.Instance("B", X, Y, x_dtype="i32", y_dtype="f32")
+    p = Plan(desc_for(inst))
+    assert p.info["variant"] == 6
+    Xt, Yt = torch_of(X), torch_of(Y)
+    Z1 = torch.full((n, n), float("nan"), device="cuda")
+    Z2 = torch.full((n, n), float("nan"), device="cuda")
+    p(Xt, Yt, Z1)
+    p(Xt, Yt, Z2)
+    p.sync()
+    check_fp32(inst, Z1.cpu().numpy(), bound_fn=sparse_elem_bound)
+    assert torch.equal(Z1, Z2)
+
+
 # ------------------------------------------------------------------ exact, TC
 def exact_case(case, n, seed):
     inst = W.make("caseA_n16384_i8", n=n, seed=seed)
