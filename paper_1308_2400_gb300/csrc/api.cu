@@ -101,7 +101,6 @@ struct afmm_plan_s {
     size_t off_a = 0, off_b = 0, off_c = 0, off_e = 0;
     size_t off_t1 = 0, off_t2 = 0, off_t3 = 0;
     int64_t lda = 0, ldb = 0;           // leading dims of converted operands
-    int64_t cap_x = 0, cap_y = 0;       // sparse form: planned non-zeros
     char* ws = nullptr;
     bool ws_owned = false;
     bool ws_ready = false;              // status word zeroed
@@ -258,15 +257,7 @@ void plan_layout(afmm_plan_s* p) {
             break;
         }
         case AFMM_VARIANT_SPARSE: {
-            const double n2 = (double)n * (double)n;
-            auto cap = [&](double dens) -> int64_t {
-                if (dens < 0.0) return (int64_t)n2;
-                const double c = 2.0 * dens * n2 + 32.0 * (double)n + 1024.0;
-                return (int64_t)(c < n2 ? c : n2);
-            };
-            p->cap_x = cap(d.d1);
-            p->cap_y = cap(d.d2);
-            p->off_a = L.take(sparse_ws_bytes(n, p->cap_x, p->cap_y));
+            p->off_a = L.take(sparse_ws_bytes(n, d.d1, d.d2));
             break;
         }
         case AFMM_VARIANT_TC_EXACT:
@@ -312,6 +303,7 @@ afmm_status ensure_workspace(afmm_plan_s* p, cudaStream_t st) {
             p->variant == AFMM_VARIANT_TC_EXACT)
             AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a,
                                        p->ws + p->off_b));
+        if (p->variant == AFMM_VARIANT_SPARSE) AFMM_TRY(sparse_reset(p->ws + p->off_a, st));
         p->ws_ready = true;
     }
     return AFMM_OK;
@@ -423,7 +415,7 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
         case AFMM_VARIANT_SPARSE:
             return launch_sparse(X, d.x_dtype, d.ldx ? d.ldx : n, Y, d.y_dtype,
                                  d.ldy ? d.ldy : n, static_cast<float*>(Z),
-                                 d.ldz ? d.ldz : n, n, p->cap_x, p->cap_y,
+                                 d.ldz ? d.ldz : n, n, d.d1, d.d2,
                                  p->ws + p->off_a, wsp<int>(p, p->off_status), st);
         default: return AFMM_ERR_UNSUPPORTED;
     }
@@ -709,6 +701,10 @@ afmm_status afmm_plan_sync(afmm_plan p, void* stream) {
         const int zero = 0;
         AFMM_CUDA_TRY(cudaMemcpy(p->ws + p->off_status, &zero, sizeof(int),
                                  cudaMemcpyHostToDevice));
+        if (p->variant == AFMM_VARIANT_SPARSE) {
+            AFMM_TRY(sparse_reset(p->ws + p->off_a, st));
+            AFMM_CUDA_TRY(cudaStreamSynchronize(st));
+        }
         return static_cast<afmm_status>(code);
     }
     return AFMM_OK;

@@ -3,22 +3,25 @@
 // work is dominated by reading X and Y and writing Z.
 //
 // The zero-skip of Sec. 2 is applied to both factors.  Every row of X and of
-// Y is compacted to (column, value) pairs in column order:
-//   count  one read of the dense factor with 16-byte loads: per row the
-//          non-zero count and a bit mask (one bit per entry, n^2/8 bytes),
-//          per block of rows the block's total;
-//   fill   per row: its offset (the sum of the totals of the blocks before
-//          it, then of the rows before it in its block -- a deterministic
-//          layout with no separate scan pass), then the mask words are
-//          expanded and only the non-zero values are read again.
-// The product takes one warp per row i of Z: it walks the non-zero X[i,k]
-// in k order, G entries at a time (their Y-row pairs loaded together, so
-// that many loads are in flight), and adds X[i,k] * Y[k,j] into a
-// shared-memory row of Z, lanes taking distinct j of one Y row (no atomics;
-// each Z[i,j] sums its terms in increasing k).  The row is written to Z
-// once with 16-byte stores.  Rows wider than the shared-memory row are done
-// in column chunks.
+// Y is compacted to (column, FP32 value) pairs in column order, in one read
+// of the dense factor: one warp per row, 16-byte loads, the non-zeros of
+// each 16-byte piece placed by a warp prefix sum of their counts, and
+// written straight from registers into the row's slot of R pairs (R from
+// the density hint: the expected row count plus six standard deviations).
+// A row with more than R non-zeros -- possible when the density is uneven
+// -- is compacted again by its warp, whole, into an overflow region.  The
+// compaction also records, per row, how many pairs fall before each
+// column-chunk boundary.  X and Y are compacted by one launch.
+//
+// The product takes one warp per (row i, column chunk) of Z: it walks the
+// non-zero X[i,k] in k order, G entries at a time (the chunk's pairs of
+// their Y rows loaded together, so that many loads are in flight), and
+// adds X[i,k] * Y[k,j] into a shared-memory row piece of Z, lanes taking
+// distinct j of one Y row (no atomics; each Z[i,j] sums its terms in
+// increasing k).  The piece is written to Z once with 16-byte stores.
 #include <cuda_runtime.h>
+
+#include <cmath>
 
 #include "afmm_common.cuh"
 #include "elem.cuh"
@@ -26,346 +29,421 @@
 namespace afmm {
 namespace {
 
-constexpr int SP_ROWS = 8;                  // rows (warps) per count/fill block
-constexpr int SP_MAX_CHUNK = 6144;          // floats per warp row buffer
-constexpr int SP_G = 8;                     // X entries whose Y rows load together
-constexpr int SP_PRE = 3;                   // 32-entry pieces of a Y row loaded ahead
-constexpr int SP_MUL_WARPS = 7;             // most warps (rows) per product block
-constexpr int SP_UNROLL = 8;                // 16-byte loads in flight per lane (count)
+constexpr int SP_ROWS = 8;                  // warps (rows) per compaction block
+constexpr int SP_CW = 6144;                 // widest Z row piece a product warp holds
+constexpr int SP_G = 8;                     // X entries whose Y pairs load together
+constexpr int SP_PRE = 2;                   // 16-byte loads (2 pairs) per lane loaded ahead
+constexpr int SP_MUL_WARPS = 7;             // most warps per product block
+constexpr int SP_UNROLL = 8;                // 16-byte loads in flight per lane
+
+// One factor's compaction.  Row r's pairs start at ptr[r] (r * R, or in the
+// overflow region after the n * R slots) and number cnt[r]; spl[r * (C-1) +
+// b - 1] = pairs of row r with column < b * SP_CW (b = 1 .. C-1).
+struct SpMat {
+    const void* M;
+    int64_t ld;
+    int vec;              // rows 16-byte aligned and n a multiple of 16 bytes
+    int R;                // slot size (pairs per row)
+    uint2* ent;           // n * R slots, then ovf_cap overflow pairs
+    int64_t ovf_cap;
+    int* cnt;
+    int64_t* ptr;
+    int* spl;
+};
+struct SpArgs {
+    SpMat m[2];           // X, Y
+    int64_t n;
+    int C;                // column chunks of the product
+    unsigned long long* ovf_used;   // two counters, zero before a compaction
+    int* status;
+};
 
 // Non-zero test of one stored element, in the precision the product uses
-// (FP64 values are rounded to FP32 first, as the fill does).
+// (FP64 values are rounded to FP32 first, like the stored value).
 template <int DT>
 __device__ __forceinline__ bool nz_elem(const typename Elem<DT>::T* v, int e) {
     return (float)Elem<DT>::get(v, e) != 0.f;
 }
 
-// Per row r: cnt[r] = non-zeros, mask[r * W + w] bit b = (entry 32 w + b is
-// non-zero); bsum[block] = the block's total.  Warp per row.  `vec`: rows
-// are 16-byte aligned and n is a multiple of the 16-byte element count.
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Row r of one factor: the first R pairs into its slot, the count, the
+// chunk split counts; a longer row, whole, into the overflow region.
 template <int DT>
-__global__ void __launch_bounds__(SP_ROWS * 32)
-sp_count_kernel(const void* __restrict__ M, int64_t n, int64_t ld, bool vec,
-                uint32_t* __restrict__ mask, int64_t W, int* __restrict__ cnt,
-                int64_t* __restrict__ bsum) {
+__device__ __forceinline__ void compact_row(const SpArgs& a, const SpMat& A, int mi, int64_t r,
+                                            int lane) {
     using T = typename Elem<DT>::T;
-    constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte unit
-    constexpr int G = 32 / V;               // lanes per 32-bit mask word
-    __shared__ int s_cnt[SP_ROWS];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * SP_ROWS + w;
+    constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte piece
+    const int64_t n = a.n;
+    uint2* out = A.ent + r * A.R;
+    const int R = A.R;
+    int* spl = A.spl + r * (a.C - 1);
+    const T* row = static_cast<const T*>(A.M) + r * A.ld;
     int c = 0;
-    if (r < n) {
-        uint32_t* mrow = mask + r * W;
-        if (vec) {
-            const uint4* row = reinterpret_cast<const uint4*>(
-                static_cast<const T*>(M) + r * ld);
-            const int64_t units = n / V;
-            for (int64_t u0 = 0; u0 < units; u0 += 32 * SP_UNROLL) {
-                uint4 q[SP_UNROLL];
+    if (A.vec) {
+        const uint4* row4 = reinterpret_cast<const uint4*>(row);
+        const int64_t units = n / V;
+        for (int64_t u0 = 0; u0 < units; u0 += 32 * SP_UNROLL) {
+            uint4 q[SP_UNROLL];
 #pragma unroll
-                for (int s = 0; s < SP_UNROLL; ++s) {
-                    const int64_t u = u0 + 32 * s + lane;
-                    q[s] = u < units ? row[u] : make_uint4(0, 0, 0, 0);
-                }
-#pragma unroll
-                for (int s = 0; s < SP_UNROLL; ++s) {
-                    const T* e = reinterpret_cast<const T*>(&q[s]);
-                    uint32_t nib = 0;
-#pragma unroll
-                    for (int t = 0; t < V; ++t) nib |= (uint32_t)nz_elem<DT>(e, t) << t;
-                    c += __popc(nib);
-                    // Mask word: the V-bit groups of G neighbouring lanes.
-                    uint32_t word = V == 32 ? nib : nib << ((lane % G) * V);
-#pragma unroll
-                    for (int o = 1; o < G; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
-                    const int64_t widx = ((u0 + 32 * s) * V) / 32 + lane / G;
-                    if (lane % G == 0 && widx < W) mrow[widx] = word;
-                }
-            }
-            for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        } else {
-            const T* row = static_cast<const T*>(M) + r * ld;
-            for (int64_t j0 = 0; j0 < n; j0 += 32) {
-                const int64_t j = j0 + lane;
-                const bool nz = j < n && (float)Elem<DT>::get(row, j) != 0.f;
-                const uint32_t word = __ballot_sync(0xffffffffu, nz);
-                c += __popc(word);
-                if (lane == 0) mrow[j0 / 32] = word;
-            }
-        }
-    }
-    if (lane == 0) s_cnt[w] = c;
-    if (lane == 0 && r < n) cnt[r] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t s = 0;
-        for (int i = 0; i < SP_ROWS; ++i) s += s_cnt[i];
-        bsum[blockIdx.x] = s;
-    }
-}
-
-// Row r's non-zeros as (column, FP32 value bits) pairs at ptr[r] .. in
-// column order; ptr[n] = the total.  Rows past `cap` entries record
-// AFMM_ERR_OVERFLOW_RISK.  Same row-to-block map as the count.
-template <int DT>
-__global__ void __launch_bounds__(SP_ROWS * 32)
-sp_fill_kernel(const void* __restrict__ M, int64_t n, int64_t ld,
-               const uint32_t* __restrict__ mask, int64_t W, const int* __restrict__ cnt,
-               const int64_t* __restrict__ bsum, int64_t* __restrict__ ptr, int64_t cap,
-               uint2* __restrict__ ent, int* status) {
-    using T = typename Elem<DT>::T;
-    __shared__ int64_t s_red[SP_ROWS * 32];
-    __shared__ int s_cnt[SP_ROWS];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = (int64_t)blockIdx.x * SP_ROWS, r = r0 + w;
-    // Offset of this block: the totals of all blocks before it.
-    int64_t part = 0;
-    for (int64_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) part += bsum[b];
-    s_red[threadIdx.x] = part;
-    if (lane == 0) s_cnt[w] = r < n ? cnt[r] : 0;
-    __syncthreads();
-    for (int s = SP_ROWS * 16; s; s >>= 1) {
-        if (threadIdx.x < s) s_red[threadIdx.x] += s_red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (r >= n) return;
-    int64_t off = s_red[0];
-    for (int i = 0; i < w; ++i) off += s_cnt[i];
-    const int c = s_cnt[w];
-    if (lane == 0) {
-        ptr[r] = off;
-        if (r == n - 1) ptr[n] = off + c;
-    }
-    if (off + c > cap) {
-        if (lane == 0) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
-        return;
-    }
-    const T* row = static_cast<const T*>(M) + r * ld;
-    const uint32_t* mrow = mask + r * W;
-    for (int64_t w0 = 0; w0 < W; w0 += 32) {
-        uint32_t word = w0 + lane < W ? mrow[w0 + lane] : 0u;
-        const int pc = __popc(word);
-        int incl = pc;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        int64_t o = off + incl - pc;
-        const int64_t jb = (w0 + lane) * 32;
-        // Up to four set bits per lane per round: their loads issue together.
-        while (__any_sync(0xffffffffu, word != 0)) {
-            int64_t j[4];
-            float v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                j[q] = -1;
-                if (word) {
-                    j[q] = jb + __ffs(word) - 1;
-                    word &= word - 1;
-                }
+            for (int s = 0; s < SP_UNROLL; ++s) {
+                const int64_t u = u0 + 32 * s + lane;
+                q[s] = u < units ? row4[u] : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                v[q] = j[q] >= 0 ? (float)Elem<DT>::get(row, j[q]) : 0.f;
+            for (int s = 0; s < SP_UNROLL; ++s) {
+                const int64_t col0 = (u0 + 32 * s) * V;      // first column of the 32 pieces
+                if (col0 > 0 && col0 < n && col0 % SP_CW == 0 && lane == 0)
+                    spl[col0 / SP_CW - 1] = c;
+                const T* e = reinterpret_cast<const T*>(&q[s]);
+                uint32_t nib = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (j[q] >= 0) ent[o++] = make_uint2((uint32_t)j[q], __float_as_uint(v[q]));
-        }
-        off += __shfl_sync(0xffffffffu, incl, 31);
-    }
-}
-
-// First index in [lo, hi) whose column is >= c (columns increase).
-__device__ __forceinline__ int64_t lower_col(const uint2* __restrict__ e, int64_t lo,
-                                             int64_t hi, int64_t c) {
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)e[mid].x < c) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// Z row i (warp per row), columns [c0, c0 + chunk) per pass.  At most
-// SP_MUL_WARPS warps per block and two blocks per SM (register cap).
-__global__ void __launch_bounds__(SP_MUL_WARPS * 32, 2)
-sp_mul_kernel(const int64_t* __restrict__ px, const uint2* __restrict__ ex,
-              const int64_t* __restrict__ py, const uint2* __restrict__ ey, int64_t n,
-              int chunk, int warps, float* __restrict__ Z, int64_t ldz, bool zvec,
-              const int* status) {
-    extern __shared__ __align__(16) float srow[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * warps + w;
-    if (i >= n || *status != 0) return;
-    float* acc = srow + (int64_t)w * chunk;
-    float4* acc4 = reinterpret_cast<float4*>(acc);
-    const int64_t xb = px[i], xe = px[i + 1];
-    float* zr = Z + i * ldz;
-    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
-        const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
-        const bool narrow = c0 > 0 || c1 < n;
-        for (int j = lane; j < chunk / 4; j += 32) acc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncwarp();
-        for (int64_t e0 = xb; e0 < xe; e0 += 64) {
-            const int m = xe - e0 < 64 ? (int)(xe - e0) : 64;
-            // Lane t holds entries e0 + t and e0 + 32 + t: x, and the span
-            // [yb, yb + yl) of Y row k inside [c0, c1).
-            float xv[2] = {0.f, 0.f};
-            int64_t yb[2] = {0, 0};
-            int yl[2] = {0, 0};
+                for (int t = 0; t < V; ++t) nib |= (uint32_t)nz_elem<DT>(e, t) << t;
+                const unsigned any = __ballot_sync(0xffffffffu, nib != 0);
+                if (any == 0) continue;
+                const int pc = __popc(nib);
+                int excl, tot;
+                if (__ballot_sync(0xffffffffu, pc > 1) == 0) {   // at most one per piece
+                    excl = __popc(any & lanemask_lt());
+                    tot = __popc(any);
+                } else {
+                    int incl = pc;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (lane + 32 * h < m) {
-                    const uint2 e = ex[e0 + lane + 32 * h];
-                    xv[h] = __uint_as_float(e.y);
-                    int64_t b = py[e.x], en = py[e.x + 1];
-                    if (narrow) {
-                        b = lower_col(ey, b, en, c0);
-                        en = lower_col(ey, b, en, c1);
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += t;
                     }
-                    yb[h] = b;
-                    yl[h] = (int)(en - b);
+                    excl = incl - pc;
+                    tot = __shfl_sync(0xffffffffu, incl, 31);
                 }
-            }
-            for (int t = 0; t < m; t += SP_G) {
-                // Entries t .. t+G-1 (all in one half: G divides 32).
-                const int h = t >> 5;
-                const float xh = h ? xv[1] : xv[0];
-                const int64_t bh = h ? yb[1] : yb[0];
-                const int lh = h ? yl[1] : yl[0];
-                uint2 a[SP_G][SP_PRE];
-                float xs[SP_G];
-                const uint2* yp[SP_G];
-                int len[SP_G];
+                if (nib) {
+                    int pos = c + excl;
+                    const int64_t j0 = col0 + (int64_t)lane * V;
 #pragma unroll
-                for (int u = 0; u < SP_G; ++u) {
-                    const int src = (t + u) & 31;
-                    xs[u] = __shfl_sync(0xffffffffu, xh, src);
-                    yp[u] = ey + __shfl_sync(0xffffffffu, bh, src);
-                    len[u] = t + u < m ? __shfl_sync(0xffffffffu, lh, src) : 0;
-#pragma unroll
-                    for (int c = 0; c < SP_PRE; ++c)
-                        a[u][c] = lane + 32 * c < len[u] ? __ldg(yp[u] + lane + 32 * c)
-                                                         : make_uint2(0, 0);
-                }
-#pragma unroll
-                for (int u = 0; u < SP_G; ++u) {
-#pragma unroll
-                    for (int c = 0; c < SP_PRE; ++c) {
-                        if (lane + 32 * c < len[u]) {
-                            float* d = acc + ((int64_t)a[u][c].x - c0);
-                            *d = fmaf(xs[u], __uint_as_float(a[u][c].y), *d);
+                    for (int t = 0; t < V; ++t) {
+                        if ((nib >> t) & 1u) {
+                            if (pos < R)
+                                out[pos] = make_uint2((uint32_t)(j0 + t),
+                                                      __float_as_uint((float)Elem<DT>::get(e, t)));
+                            ++pos;
                         }
                     }
-#pragma unroll 4
-                    for (int f = lane + 32 * SP_PRE; f < len[u]; f += 32) {
-                        const uint2 y = __ldg(yp[u] + f);
-                        float* d = acc + ((int64_t)y.x - c0);
-                        *d = fmaf(xs[u], __uint_as_float(y.y), *d);
-                    }
-                    __syncwarp();          // entry u's terms land before entry u+1's
                 }
+                c += tot;
             }
         }
-        const int64_t cw = c1 - c0;
-        if (zvec) {
-            float4* z4 = reinterpret_cast<float4*>(zr + c0);
-            for (int64_t j = lane; j < cw / 4; j += 32) __stcs(z4 + j, acc4[j]);
-            for (int64_t j = (cw & ~3LL) + lane; j < cw; j += 32) zr[c0 + j] = acc[j];
-        } else {
-            for (int64_t j = lane; j < cw; j += 32) zr[c0 + j] = acc[j];
+    } else {
+        for (int64_t j0 = 0; j0 < n; j0 += 32) {
+            if (j0 > 0 && j0 % SP_CW == 0 && lane == 0) spl[j0 / SP_CW - 1] = c;
+            const int64_t j = j0 + lane;
+            const float v = j < n ? (float)Elem<DT>::get(row, j) : 0.f;
+            const unsigned m = __ballot_sync(0xffffffffu, v != 0.f);
+            if (v != 0.f) {
+                const int pos = c + __popc(m & lanemask_lt());
+                if (pos < R) out[pos] = make_uint2((uint32_t)j, __float_as_uint(v));
+            }
+            c += __popc(m);
         }
-        __syncwarp();
+    }
+    int64_t start = r * (int64_t)R;
+    if (c > R) {
+        // Longer than the slot: the whole row into the overflow region.
+        // Even counts keep every row start 16-byte aligned.
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.ovf_used + mi, (unsigned long long)((c + 1) & ~1));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((int64_t)(base + c) > A.ovf_cap) {
+            if (lane == 0) atomicCAS(a.status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+            return;
+        }
+        start = n * (int64_t)R + (int64_t)base;
+        uint2* o = A.ent + start;
+        int pos = 0;
+        for (int64_t j0 = 0; j0 < n; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const float v = j < n ? (float)Elem<DT>::get(row, j) : 0.f;
+            const unsigned m = __ballot_sync(0xffffffffu, v != 0.f);
+            if (v != 0.f) {
+                const int p = pos + __popc(m & lanemask_lt());
+                if (p < c) o[p] = make_uint2((uint32_t)j, __float_as_uint(v));
+            }
+            pos += __popc(m);
+        }
+    }
+    if (lane == 0) {
+        A.cnt[r] = c;
+        A.ptr[r] = start;
     }
 }
 
-struct SparseWs {
-    uint32_t* mask[2];
-    int* cnt[2];
-    int64_t* bsum[2];
-    int64_t* ptr[2];
-    uint2* ent[2];
+// blockIdx.y = 0: rows of X, 1: rows of Y; one warp per row.
+template <int DTX, int DTY>
+__global__ void __launch_bounds__(SP_ROWS * 32) sp_compact_kernel(SpArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * SP_ROWS + (threadIdx.x >> 5);
+    if (r >= a.n) return;
+    if (blockIdx.y == 0) compact_row<DTX>(a, a.m[0], 0, r, lane);
+    else compact_row<DTY>(a, a.m[1], 1, r, lane);
+}
+
+struct SpMul {
+    const int64_t* px;
+    const int* nx;
+    const uint2* ex;
+    const int64_t* py;
+    const int* ny;
+    const uint2* ey;
+    const int* sy;        // Y split counts, C - 1 per row
+    int64_t n;
+    int C, warps, row_floats;
+    float* Z;
+    int64_t ldz;
+    int zvec;
+    const int* status;
+    unsigned long long* ovf_used;
 };
+
+// Z[i, c0 : c0 + SP_CW) for one warp (the whole row when n <= SP_CW),
+// accumulated in shared memory.  IT indexes the pairs (int when they
+// number fewer than 2^31).  Pairs are read two at a time with 16-byte loads
+// from the even index at or below a span's start; pairs outside the span
+// are masked (every slot and overflow row starts at an even index).
+template <typename IT>
+__global__ void __launch_bounds__(SP_MUL_WARPS * 32, 2)
+sp_mul_kernel(SpMul a) {
+    extern __shared__ __align__(16) float srow[];
+    // The compaction is complete (stream order): its counters are reset here
+    // for the next call, before anything can return.
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ovf_used[0] = 0;
+        a.ovf_used[1] = 0;
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * a.warps + w;
+    const int64_t i = item / a.C;
+    const int cc = (int)(item % a.C);
+    if (i >= a.n || *a.status != 0) return;
+    const int64_t c0 = (int64_t)cc * SP_CW;
+    const int64_t c1 = c0 + SP_CW < a.n ? c0 + SP_CW : a.n;
+    const int cw = (int)(c1 - c0), cw4 = (cw + 3) / 4;
+    float* acc = srow + w * a.row_floats;
+    float4* acc4 = reinterpret_cast<float4*>(acc);
+    for (int j = lane; j < cw4; j += 32) acc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    const uint4* ey4 = reinterpret_cast<const uint4*>(a.ey);
+    const int64_t xb = a.px[i], xe = xb + a.nx[i];
+    const int S = a.C - 1;
+    for (int64_t e0 = xb; e0 < xe; e0 += 32) {
+        const int m = xe - e0 < 32 ? (int)(xe - e0) : 32;
+        // Lane t holds entry e0 + t: x and the span [ys, ye) of Y row k's
+        // pairs inside the column piece.
+        float xv = 0.f;
+        IT ys = 0, ye = 0;
+        if (lane < m) {
+            const uint2 e = a.ex[e0 + lane];
+            xv = __uint_as_float(e.y);
+            const int64_t k = e.x;
+            const IT b = (IT)a.py[k];
+            int lo = 0, hi = a.ny[k];
+            if (S > 0) {
+                if (cc > 0) lo = a.sy[k * S + cc - 1];
+                if (cc < S) hi = a.sy[k * S + cc];
+            }
+            ys = b + lo;
+            ye = b + hi;
+        }
+        for (int t = 0; t < m; t += SP_G) {
+            uint4 p[SP_G][SP_PRE];
+            float xs[SP_G];
+            IT s0[SP_G], s1[SP_G];
+#pragma unroll
+            for (int u = 0; u < SP_G; ++u) {
+                const int src = (t + u) & 31;
+                xs[u] = __shfl_sync(0xffffffffu, xv, src);
+                s0[u] = __shfl_sync(0xffffffffu, ys, src);
+                s1[u] = __shfl_sync(0xffffffffu, ye, src);
+                if (t + u >= m) s1[u] = s0[u];
+                const IT al = s0[u] & ~(IT)1;
+#pragma unroll
+                for (int q = 0; q < SP_PRE; ++q) {
+                    const IT f = al + 2 * (lane + 32 * q);
+                    p[u][q] = f < s1[u] ? __ldg(ey4 + (f >> 1)) : make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SP_G; ++u) {
+                const IT al = s0[u] & ~(IT)1;
+                // This lane's pairs of entry u have distinct columns: read
+                // all the Z values first, then write them.
+                float v[SP_PRE][2];
+                bool ok[SP_PRE][2];
+#pragma unroll
+                for (int q = 0; q < SP_PRE; ++q) {
+                    const IT f = al + 2 * (lane + 32 * q);
+                    ok[q][0] = f >= s0[u] && f < s1[u];
+                    ok[q][1] = f + 1 < s1[u];
+                    v[q][0] = ok[q][0] ? acc[(int)p[u][q].x - (int)c0] : 0.f;
+                    v[q][1] = ok[q][1] ? acc[(int)p[u][q].z - (int)c0] : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < SP_PRE; ++q) {
+                    if (ok[q][0])
+                        acc[(int)p[u][q].x - (int)c0] =
+                            fmaf(xs[u], __uint_as_float(p[u][q].y), v[q][0]);
+                    if (ok[q][1])
+                        acc[(int)p[u][q].z - (int)c0] =
+                            fmaf(xs[u], __uint_as_float(p[u][q].w), v[q][1]);
+                }
+                for (IT f = al + 2 * (lane + 32 * SP_PRE); f < s1[u]; f += 64) {
+                    const uint4 y = __ldg(ey4 + (f >> 1));
+                    const bool ok1 = f + 1 < s1[u];
+                    const float z0 = acc[(int)y.x - (int)c0];
+                    const float z1 = ok1 ? acc[(int)y.z - (int)c0] : 0.f;
+                    acc[(int)y.x - (int)c0] = fmaf(xs[u], __uint_as_float(y.y), z0);
+                    if (ok1) acc[(int)y.z - (int)c0] = fmaf(xs[u], __uint_as_float(y.w), z1);
+                }
+                __syncwarp();          // entry u's terms land before entry u+1's
+            }
+        }
+    }
+    float* zr = a.Z + i * a.ldz + c0;
+    if (a.zvec) {
+        float4* z4 = reinterpret_cast<float4*>(zr);
+        for (int j = lane; j < cw / 4; j += 32) __stcs(z4 + j, acc4[j]);
+        for (int j = (cw & ~3) + lane; j < cw; j += 32) zr[j] = acc[j];
+    } else {
+        for (int j = lane; j < cw; j += 32) zr[j] = acc[j];
+    }
+}
 
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
-size_t sparse_layout(int64_t n, int64_t cap_x, int64_t cap_y, char* base, SparseWs* o) {
-    const int64_t W = (n + 31) / 32, nb = (n + SP_ROWS - 1) / SP_ROWS;
+int chunks_of(int64_t n) { return (int)((n + SP_CW - 1) / SP_CW); }
+
+// Slot size R and overflow capacity of a factor with density hint d (< 0:
+// unknown, R = n and no overflow).
+void sparse_shape(int64_t n, double d, int* R, int64_t* ovf) {
+    *R = (int)n;
+    *ovf = 0;
+    if (!(d >= 0.0)) return;
+    const double mu = d * (double)n;
+    const double want = std::ceil((mu + 6.0 * std::sqrt(mu) + 16.0) / 32.0) * 32.0;
+    if (want >= (double)n) return;
+    *R = (int)want;
+    const double n2 = (double)n * (double)n;
+    const double c = 2.0 * d * n2 + 32.0 * (double)n + 1024.0;
+    *ovf = (int64_t)(c < n2 ? c : n2);
+}
+
+// Workspace: the two overflow counters; per factor the slots and overflow
+// pairs, counts, row starts and chunk split counts.
+size_t sparse_layout(int64_t n, double d1, double d2, char* base, SpArgs* o) {
     size_t top = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + top : nullptr;
         top += up256(bytes);
         return p;
     };
+    unsigned long long* used = reinterpret_cast<unsigned long long*>(take(16));
+    if (o) o->ovf_used = used;
+    const int C = chunks_of(n);
     for (int m = 0; m < 2; ++m) {
-        const int64_t cap = m == 0 ? cap_x : cap_y;
-        SparseWs t;
-        t.mask[m] = reinterpret_cast<uint32_t*>(take((size_t)n * W * 4));
-        t.cnt[m] = reinterpret_cast<int*>(take((size_t)n * 4));
-        t.bsum[m] = reinterpret_cast<int64_t*>(take((size_t)nb * 8));
-        t.ptr[m] = reinterpret_cast<int64_t*>(take((size_t)(n + 1) * 8));
-        t.ent[m] = reinterpret_cast<uint2*>(take((size_t)cap * 8));
-        if (o) {
-            o->mask[m] = t.mask[m];
-            o->cnt[m] = t.cnt[m];
-            o->bsum[m] = t.bsum[m];
-            o->ptr[m] = t.ptr[m];
-            o->ent[m] = t.ent[m];
-        }
+        int R;
+        int64_t ovf;
+        sparse_shape(n, m == 0 ? d1 : d2, &R, &ovf);
+        SpMat t{};
+        t.R = R;
+        t.ovf_cap = ovf;
+        // Two spare pairs: a 16-byte load at a span's last odd index stays inside.
+        t.ent = reinterpret_cast<uint2*>(take(((size_t)n * R + ovf + 2) * 8));
+        t.cnt = reinterpret_cast<int*>(take((size_t)n * 4));
+        t.ptr = reinterpret_cast<int64_t*>(take((size_t)n * 8));
+        t.spl = reinterpret_cast<int*>(take((size_t)n * (C - 1) * 4 + 4));
+        if (o) o->m[m] = t;
     }
     return top;
 }
 
-// Count + fill of one factor into CSR pairs.
-afmm_status compact(const void* M, int dt, int64_t ld, int64_t n, int64_t cap,
-                    const SparseWs& ws, int m, int* status, cudaStream_t st) {
-    const int64_t W = (n + 31) / 32;
-    const unsigned nb = (unsigned)((n + SP_ROWS - 1) / SP_ROWS);
+bool rows_vec(const void* M, int dt, int64_t ld, int64_t n) {
     const size_t es = dtype_size(dt);
-    const int64_t V = 16 / (int64_t)es;
-    const bool vec = (reinterpret_cast<uintptr_t>(M) % 16 == 0) && ((ld * es) % 16 == 0) &&
-                     (n % V == 0);
-    return dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
-        sp_count_kernel<DT><<<nb, SP_ROWS * 32, 0, st>>>(M, n, ld, vec, ws.mask[m], W,
-                                                         ws.cnt[m], ws.bsum[m]);
-        sp_fill_kernel<DT><<<nb, SP_ROWS * 32, 0, st>>>(M, n, ld, ws.mask[m], W, ws.cnt[m],
-                                                        ws.bsum[m], ws.ptr[m], cap,
-                                                        ws.ent[m], status);
-        AFMM_CUDA_TRY(cudaGetLastError());
-        return AFMM_OK;
-    });
+    return reinterpret_cast<uintptr_t>(M) % 16 == 0 && (ld * es) % 16 == 0 &&
+           n % (int64_t)(16 / es) == 0;
 }
 
 }  // namespace
 
-size_t sparse_ws_bytes(int64_t n, int64_t cap_x, int64_t cap_y) {
-    return sparse_layout(n, cap_x, cap_y, nullptr, nullptr);
+size_t sparse_ws_bytes(int64_t n, double d1, double d2) {
+    return sparse_layout(n, d1, d2, nullptr, nullptr);
+}
+
+afmm_status sparse_reset(void* ws, cudaStream_t st) {
+    // The overflow counters sit at the start of the workspace.
+    AFMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 16, st));
+    return AFMM_OK;
 }
 
 afmm_status launch_sparse(const void* X, int xdt, int64_t ldx, const void* Y, int ydt,
-                          int64_t ldy, float* Z, int64_t ldz, int64_t n, int64_t cap_x,
-                          int64_t cap_y, void* ws, int* status, cudaStream_t st) {
+                          int64_t ldy, float* Z, int64_t ldz, int64_t n, double d1,
+                          double d2, void* ws, int* status, cudaStream_t st) {
     if (n <= 0) return AFMM_OK;
-    SparseWs L;
-    sparse_layout(n, cap_x, cap_y, static_cast<char*>(ws), &L);
-    AFMM_TRY(compact(X, xdt, ldx, n, cap_x, L, 0, status, st));
-    AFMM_TRY(compact(Y, ydt, ldy, n, cap_y, L, 1, status, st));
-    const int chunk = (int)(n < SP_MAX_CHUNK ? (n + 31) / 32 * 32 : SP_MAX_CHUNK);
+    SpArgs a{};
+    sparse_layout(n, d1, d2, static_cast<char*>(ws), &a);
+    a.n = n;
+    a.C = chunks_of(n);
+    a.status = status;
+    a.m[0].M = X;
+    a.m[0].ld = ldx;
+    a.m[0].vec = rows_vec(X, xdt, ldx, n);
+    a.m[1].M = Y;
+    a.m[1].ld = ldy;
+    a.m[1].vec = rows_vec(Y, ydt, ldy, n);
+    // Compaction: one warp per row of X (grid.y = 0) and of Y (grid.y = 1).
+    const dim3 grid((unsigned)((n + SP_ROWS - 1) / SP_ROWS), 2);
+    AFMM_TRY(dispatch_dtype(xdt, [&]<int DTX>() -> afmm_status {
+        return dispatch_dtype(ydt, [&]<int DTY>() -> afmm_status {
+            sp_compact_kernel<DTX, DTY><<<grid, SP_ROWS * 32, 0, st>>>(a);
+            return AFMM_OK;
+        });
+    }));
+    AFMM_CUDA_TRY(cudaGetLastError());
+    SpMul mp{};
+    mp.px = a.m[0].ptr;
+    mp.nx = a.m[0].cnt;
+    mp.ex = a.m[0].ent;
+    mp.py = a.m[1].ptr;
+    mp.ny = a.m[1].cnt;
+    mp.ey = a.m[1].ent;
+    mp.sy = a.m[1].spl;
+    mp.n = n;
+    mp.C = a.C;
+    mp.Z = Z;
+    mp.ldz = ldz;
+    mp.zvec = reinterpret_cast<uintptr_t>(Z) % 16 == 0 && ldz % 4 == 0;
+    mp.status = status;
+    mp.ovf_used = a.ovf_used;
+    const int row_floats = a.C > 1 ? SP_CW : (int)((n + 31) / 32 * 32);
     // Warps per block: two blocks fit in one SM's shared memory.
-    int warps = (int)((113 * 1024) / ((size_t)chunk * sizeof(float)));
-    warps = warps < 1 ? 1 : (warps > SP_MUL_WARPS ? SP_MUL_WARPS : warps);
-    const size_t smem = (size_t)warps * chunk * sizeof(float);
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(sp_mul_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+    int warps = (int)((113 * 1024) / ((size_t)row_floats * sizeof(float)));
+    mp.warps = warps < 1 ? 1 : (warps > SP_MUL_WARPS ? SP_MUL_WARPS : warps);
+    mp.row_floats = row_floats;
+    const size_t smem = (size_t)mp.warps * row_floats * sizeof(float);
+    const int64_t pairs_y = n * (int64_t)a.m[1].R + a.m[1].ovf_cap;
+    auto kern = pairs_y < (int64_t)1 << 31 ? sp_mul_kernel<int> : sp_mul_kernel<int64_t>;
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    const bool zvec = reinterpret_cast<uintptr_t>(Z) % 16 == 0 && ldz % 4 == 0;
-    const unsigned blocks = (unsigned)((n + warps - 1) / warps);
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       100));
+    const int64_t items = n * a.C;
+    const unsigned blocks = (unsigned)((items + mp.warps - 1) / mp.warps);
     main_kernel_begin(st);
-    sp_mul_kernel<<<blocks, warps * 32, smem, st>>>(L.ptr[0], L.ent[0], L.ptr[1], L.ent[1], n,
-                                                    chunk, warps, Z, ldz, zvec, status);
+    kern<<<blocks, mp.warps * 32, smem, st>>>(mp);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, (int)blocks);
-    count_launches(5);
+    count_launches(2);
     return AFMM_OK;
 }
 

@@ -310,6 +310,42 @@ def test_sparse_one_dense_factor_and_repeat_calls():
     assert torch.equal(Z1, Z2)
 
 
+def test_sparse_uneven_rows_use_the_overflow_region():
+    """A few dense rows among sparse ones: those rows exceed their slot and
+    are compacted into the overflow region.  Repeat calls agree bit for bit;
+    a call that overflows the region reports it and the next call works."""
+    from paper_1308_2400_gb300 import AfmmError, Plan, make_desc
+    rng = np.random.default_rng(91)
+    n = 512
+    X = (rng.integers(1, 16, size=(n, n)) * (rng.random((n, n)) < 1.0 / 16)).astype(np.int32)
+    X[[3, 100, 257, 400, 511]] = rng.integers(1, 16, size=(5, n))
+    Y = (rng.standard_normal((n, n)) * (rng.random((n, n)) < 1.0 / 16)).astype(np.float32)
+    Y[[0, 7]] = rng.standard_normal((2, n))
+    inst = W.Instance("B", X, Y, x_dtype="i32", y_dtype="f32")
+    d1 = np.count_nonzero(X) / n / n
+    d2 = np.count_nonzero(Y) / n / n
+    p = Plan(make_desc(n, "B", "i32", "f32", "f32", "fp32", variant=6, d1=d1, d2=d2))
+    Xt, Yt = torch_of(X), torch_of(Y)
+    Z1 = torch.full((n, n), float("nan"), device="cuda")
+    Z2 = torch.full((n, n), float("nan"), device="cuda")
+    p(Xt, Yt, Z1)
+    p(Xt, Yt, Z2)
+    p.sync()
+    check_fp32(inst, Z1.cpu().numpy(), bound_fn=sparse_elem_bound)
+    assert torch.equal(Z1, Z2)
+    # Far more dense rows than the overflow region holds: reported.
+    Xd = X.copy()
+    Xd[::2] = rng.integers(1, 16, size=(n // 2, n))
+    p(torch_of(Xd), Yt, Z2)
+    with pytest.raises(AfmmError) as e:
+        p.sync()
+    assert e.value.status == 4          # AFMM_ERR_OVERFLOW_RISK
+    Z3 = torch.full((n, n), float("nan"), device="cuda")
+    p(Xt, Yt, Z3)
+    p.sync()
+    assert torch.equal(Z1, Z3)
+
+
 # ------------------------------------------------------------------ exact, TC
 def exact_case(case, n, seed):
     inst = W.make("caseA_n16384_i8", n=n, seed=seed)
