@@ -34,18 +34,70 @@ __device__ __forceinline__ float load_checked(const void* p, int64_t i, float li
 // Rows kept as rows (K-major A operand): dst[(s*n + r)*ldk + c], eight
 // columns per thread (one 16-byte store per slice).  EXACT: one slice that
 // must equal the source (Rep-factors); otherwise OVERFLOW_RISK is recorded.
+// Eight consecutive elements of one row from aligned vector loads (8 * size
+// bytes: one 8-byte load for 1-byte types, one to four 16-byte loads else).
+template <int DT>
+__device__ __forceinline__ void load8(const void* p, int64_t i,
+                                      typename Elem<DT>::T (&e)[8]) {
+    using T = typename Elem<DT>::T;
+    if constexpr (sizeof(T) == 1) {
+        const uint2 q = *reinterpret_cast<const uint2*>(static_cast<const T*>(p) + i);
+        *reinterpret_cast<uint2*>(e) = q;
+    } else {
+        const uint4* q = reinterpret_cast<const uint4*>(static_cast<const T*>(p) + i);
+#pragma unroll
+        for (int k = 0; k < (int)sizeof(T) / 2; ++k) reinterpret_cast<uint4*>(e)[k] = q[k];
+    }
+}
+
+// Element value as float with the checks of load_checked.
+template <int DT>
+__device__ __forceinline__ float value_checked(typename Elem<DT>::T v, float lim, bool& bad) {
+    if constexpr (DT == AFMM_I32) {
+        bad |= (float)(v < 0 ? -(int64_t)v : (int64_t)v) > lim;
+        return (float)v;
+    } else if constexpr (DT == AFMM_F64) {
+        bad |= (double)(float)v != v;
+        return (float)v;
+    } else {
+        return (float)Elem<DT>::get(&v, 0);
+    }
+}
+
 template <int DT, int S, bool EXACT>
 __global__ void __launch_bounds__(256)
 widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
-                  __nv_bfloat16* __restrict__ dst, int64_t ldk, int vec_f32,
+                  __nv_bfloat16* __restrict__ dst, int64_t ldk, int vec,
                   float lim, int* status, int64_t r0, int64_t r1) {
     const int64_t c = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 8;
     if (c >= ldk) return;
     for (int64_t r = r0 + blockIdx.y; r < r1; r += gridDim.y) {
         uint32_t w[S][4];
         bool done = false;
+        if constexpr (DT != AFMM_F32) {
+            if (vec && c + 8 <= n) {
+                alignas(16) typename Elem<DT>::T e[8];
+                load8<DT>(src, r * lds + c, e);
+                bool bad = false;
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    __nv_bfloat16 o0[S], o1[S];
+                    const float v0 = value_checked<DT>(e[j], lim, bad);
+                    const float v1 = value_checked<DT>(e[j + 1], lim, bad);
+                    split_bf16<S>(v0, o0);
+                    split_bf16<S>(v1, o1);
+                    if (EXACT)
+                        bad |= __bfloat162float(o0[0]) != v0 || fabsf(v0) > lim ||
+                               __bfloat162float(o1[0]) != v1 || fabsf(v1) > lim;
+#pragma unroll
+                    for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o0[s], o1[s]);
+                }
+                if (EXACT && bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+                done = true;
+            }
+        }
         if constexpr (DT == AFMM_F32) {
-            if (vec_f32 && c + 8 <= n) {
+            if (vec && c + 8 <= n) {
                 const float4* p = reinterpret_cast<const float4*>(
                     static_cast<const float*>(src) + r * lds + c);
                 const float4 a = p[0], b = p[1];
@@ -204,7 +256,9 @@ afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
     if (rows <= 0) return AFMM_OK;
     const dim3 grid((unsigned)((per_row + 255) / 256),
                     (unsigned)(rows < 65535 ? rows : 65535));
-    const int vec = (lds % 4 == 0) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
+    // Vector loads of 8 elements need rows aligned to min(16, 8 * size) bytes.
+    const size_t es = dtype_size(dt), va = es * 8 < 16 ? es * 8 : 16;
+    const int vec = (lds * es) % va == 0 && (reinterpret_cast<uintptr_t>(src) % va) == 0;
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
         widen_rows_kernel<DT, S, EXACT><<<grid, 256, 0, st>>>(src, n, lds, dst, ldk, vec,
                                                               lim, status, r0, r1);
