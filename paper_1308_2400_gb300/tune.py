@@ -1,13 +1,14 @@
 """Autotuner and dispatch-model trainer for batched AFMM products.
 
-The autotuner times every candidate kernel variant on each instance alone
-(the batched entry point with a one-instance array and a forced variant,
-CUDA events, median of repeats).  Its table is both the judge of a
-dispatch policy (the per-instance best variant) and the training data of
-the MLP cost model, which maps afmm_dispatch_features() of an instance to
-one predicted log2-time per variant.  The network is trained on the GPU
-with the library's own kernels (afmm_mlp_loss_grad, afmm_mlp_adam) and
-saved as JSON; afmm_set_dispatch_model() installs it.
+The autotuner times every candidate kernel variant on each instance as
+part of a batch (the batched entry point with copies of the instance and a
+forced variant, CUDA events, median of repeats, divided by the copies).
+Its table is both the judge of a dispatch policy (the per-instance best
+variant) and the training data of the MLP cost model, which maps
+afmm_dispatch_features() of an instance to one predicted log2-time per
+variant.  The network is trained on the GPU with the library's own
+kernels (afmm_mlp_loss_grad, afmm_mlp_adam) and saved as JSON;
+afmm_set_dispatch_model() installs it.
 
     python -m paper_1308_2400_gb300.tune --count 300 --out model.json
 """
@@ -72,15 +73,32 @@ def time_batch(descs, Xs, Ys, Zs, reps: int = 5, warmup: int = 2) -> float:
     return statistics.median(ts)
 
 
+def copies_for(n: int, sms: int = 152, waves: int = 4) -> int:
+    """Copies of an n x n instance that give the grouped tensor-core launch
+    about `waves` waves of 128 x 256 tiles (1 .. 64)."""
+    tiles = -(-n // 128) * -(-n // 256)
+    return int(min(64, max(1, -(-waves * sms // tiles))))
+
+
 def autotune(insts, reps: int = 5) -> np.ndarray:
-    """ms[i, v]: instance i alone under VARIANTS[v]."""
+    """ms[i, v]: the cost of instance i under VARIANTS[v] inside a batch.
+
+    A batch runs its instances in grouped launches, so what an instance
+    adds to a batch is its share of a full launch, not the latency of a
+    launch of its own (which, for a small instance, is mostly launch and
+    ramp-up time).  Each entry is therefore the time of one batched call
+    of copies_for(n) copies of the instance (same X and Y, separate Z),
+    divided by the number of copies."""
+    import torch
     table = np.zeros((len(insts), len(VARIANTS)))
     for i, inst in enumerate(insts):
         X, Y, Z = device_operands(inst)
+        r = copies_for(inst.n)
+        Zs = [Z] + [torch.empty_like(Z) for _ in range(r - 1)]
         for v, var in enumerate(VARIANTS):
             d = instance_desc(inst, var)
-            table[i, v] = time_batch([d], [X], [Y], [Z], reps=reps)
-        del X, Y, Z
+            table[i, v] = time_batch([d] * r, [X] * r, [Y] * r, Zs, reps=reps) / r
+        del X, Y, Z, Zs
     return table
 
 

@@ -126,3 +126,18 @@ def test_host_dispatch_uses_the_installed_model():
     finally:
         afmm_set_dispatch_model(None, None, None, None, None)
     assert afmm_dispatch_variant(d) == 0
+
+
+def test_autotuner_copies_fill_the_grouped_launch():
+    """The in-batch cost of an instance is timed on copies of it that give
+    the grouped launch about four waves of 128 x 256 tiles on 152 SMs."""
+    from paper_1308_2400_gb300.tune import copies_for
+    assert copies_for(64) == 64                     # one tile: capped at 64
+    assert copies_for(2048) == 5                    # 128 tiles: ceil(608 / 128)
+    assert copies_for(4096) == 2                    # 512 tiles
+    assert copies_for(8192) == 1
+    for n in (1, 100, 129, 257, 700, 1500, 2047):
+        r = copies_for(n)
+        tiles = -(-n // 128) * -(-n // 256)
+        assert 1 <= r <= 64
+        assert r == 64 or (r * tiles >= 608 and (r - 1) * tiles < 608)
