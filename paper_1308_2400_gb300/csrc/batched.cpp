@@ -55,6 +55,8 @@ struct BatchState {
     SimtJob* d_sjobs = nullptr;
     int* d_row_prefix = nullptr;
     int* d_tt_prefix = nullptr;
+    int* d_row_job = nullptr;            // instance of each A-operand row
+    int* d_tt_job = nullptr;             // instance of each 64 x 64 B tile
     int* d_wprefix = nullptr;
     int* d_sprefix = nullptr;
     int* d_cta_off = nullptr;
@@ -191,6 +193,11 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
     }
     b->rows_total = row_prefix[ntc];
     b->tt_total = tt_prefix[ntc];
+    std::vector<int> row_job(b->rows_total), tt_job(b->tt_total);
+    for (int j = 0; j < ntc; ++j) {
+        std::fill(row_job.begin() + row_prefix[j], row_job.begin() + row_prefix[j + 1], j);
+        std::fill(tt_job.begin() + tt_prefix[j], tt_job.begin() + tt_prefix[j + 1], j);
+    }
     b->wrows_total = wprefix.back();
     b->stiles_total = sprefix.back();
     b->tc_grid = grid;
@@ -207,6 +214,8 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
         b->d_table = bump<char>(base, top, b->table_bytes);
         b->d_row_prefix = bump<int>(base, top, row_prefix.size());
         b->d_tt_prefix = bump<int>(base, top, tt_prefix.size());
+        b->d_row_job = bump<int>(base, top, row_job.size() + 1);
+        b->d_tt_job = bump<int>(base, top, tt_job.size() + 1);
         b->d_wprefix = bump<int>(base, top, wprefix.size());
         b->d_sprefix = bump<int>(base, top, sprefix.size());
         b->d_cta_off = bump<int>(base, top, cta_off.size());
@@ -267,6 +276,8 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
     AFMM_TRY(up(b->d_maps, maps, 2 * (size_t)ntc * 128));
     AFMM_TRY(up(b->d_row_prefix, row_prefix.data(), row_prefix.size() * sizeof(int)));
     AFMM_TRY(up(b->d_tt_prefix, tt_prefix.data(), tt_prefix.size() * sizeof(int)));
+    AFMM_TRY(up(b->d_row_job, row_job.data(), row_job.size() * sizeof(int)));
+    AFMM_TRY(up(b->d_tt_job, tt_job.data(), tt_job.size() * sizeof(int)));
     AFMM_TRY(up(b->d_wprefix, wprefix.data(), wprefix.size() * sizeof(int)));
     AFMM_TRY(up(b->d_sprefix, sprefix.data(), sprefix.size() * sizeof(int)));
     AFMM_TRY(up(b->d_cta_off, cta_off.data(), cta_off.size() * sizeof(int)));
@@ -289,8 +300,9 @@ afmm_status enqueue(BatchState* b, cudaStream_t st, cudaStream_t side,
     AFMM_CUDA_TRY(cudaEventRecord(fork, st));
     AFMM_CUDA_TRY(cudaStreamWaitEvent(side, fork, 0));
     if (ntc > 0) {
-        AFMM_TRY(launch_batch_convert(b->d_ginst, b->d_row_prefix, b->d_tt_prefix, ntc,
-                                      b->rows_total, b->tt_total, b->d_flags, st));
+        AFMM_TRY(launch_batch_convert(b->d_ginst, b->d_row_prefix, b->d_row_job,
+                                      b->d_tt_prefix, b->d_tt_job, ntc, b->rows_total,
+                                      b->tt_total, b->d_flags, st));
         AFMM_TRY(launch_batch_tc(b->d_ginst, b->d_maps, b->d_cta_off,
                                  reinterpret_cast<const int*>(b->d_tiles), b->tc_grid,
                                  b->d_flags, b->d_status, st));

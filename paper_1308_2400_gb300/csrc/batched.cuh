@@ -41,7 +41,8 @@ struct TileRec {
 
 // Grouped launches (device arrays throughout).
 afmm_status launch_batch_convert(const GInst* inst, const int* row_prefix,
-                                 const int* tt_prefix, int ninst, int rows_total,
+                                 const int* row_job, const int* tt_prefix,
+                                 const int* tt_job, int ninst, int rows_total,
                                  int tt_total, int* flags, cudaStream_t st);
 afmm_status launch_batch_tc(const GInst* inst, const void* maps, const int* cta_off,
                             const int* tiles, int grid, const int* flags, int* status,

@@ -23,6 +23,7 @@
 #include "bf16_split.cuh"
 #include "ptx_sm100.cuh"
 #include "tc_gemm.cuh"
+#include "tile_convert.cuh"
 
 namespace afmm {
 namespace {
@@ -59,45 +60,46 @@ __device__ __forceinline__ int find_job(const int* prefix, int n, int b) {
 }
 
 // ----------------------------------------------------------- conversions
-// Block b converts one row of the A operand of one instance: Case A slices
-// a row of the real X into 3 BF16 rows; Case B widens a row of the
-// Rep-factors X to BF16 (values must be exact, |v| <= 256, else the
-// instance's flag is set and its Z becomes NaN).  Eight columns per thread,
-// one 16-byte store per slice; FP32 arithmetic throughout.
-__global__ void __launch_bounds__(128)
-g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix,
-              int ninst, int* __restrict__ flags) {
-    const int j = find_job(row_prefix, ninst, blockIdx.x);
-    const GInst& g = inst[j];
-    const int64_t r = blockIdx.x - row_prefix[j];
+// The instance's dtype is read once per block and selects a specialised
+// body, so the inner loops hold no per-element dtype switch.
+#define G_DTYPE_SWITCH(dt, BODY)                                   \
+    switch (dt) {                                                  \
+        case AFMM_F64: { constexpr int DT = AFMM_F64; BODY; } break;   \
+        case AFMM_F32: { constexpr int DT = AFMM_F32; BODY; } break;   \
+        case AFMM_BF16: { constexpr int DT = AFMM_BF16; BODY; } break; \
+        case AFMM_E4M3: { constexpr int DT = AFMM_E4M3; BODY; } break; \
+        case AFMM_I32: { constexpr int DT = AFMM_I32; BODY; } break;   \
+        case AFMM_I8: { constexpr int DT = AFMM_I8; BODY; } break;     \
+        default: { constexpr int DT = AFMM_U8; BODY; } break;          \
+    }
+
+// One row of the A operand: Case A (KIND 0) slices a row of the real X into
+// 3 BF16 rows; Case B (KIND 1) widens a row of the Rep-factors X to BF16
+// (values must be exact, |v| <= 256, else the instance's flag is set and
+// its Z becomes NaN).  Eight columns per thread and step (vector loads when
+// the rows are aligned), one 16-byte store per slice.
+template <int DT, int KIND>
+__device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags) {
+    using T = typename Elem<DT>::T;
     const int64_t n = g.n, ldk = g.ldk;
-    const bool vec = g.x_dtype == AFMM_F32 && (g.ldx % 4) == 0 &&
-                     ((reinterpret_cast<uintptr_t>(g.X) & 15u) == 0);
-    const bool vec8 = (g.x_dtype == AFMM_U8 || g.x_dtype == AFMM_I8 ||
-                       g.x_dtype == AFMM_E4M3) &&
-                      (g.ldx % 8) == 0 && ((reinterpret_cast<uintptr_t>(g.X) & 7u) == 0);
+    const int64_t va = sizeof(T) * 8 < 16 ? sizeof(T) * 8 : 16;
+    const bool vec = (reinterpret_cast<uintptr_t>(g.X) % va) == 0 &&
+                     (g.ldx * (int64_t)sizeof(T)) % va == 0;
+    const T* x = static_cast<const T*>(g.X) + r * g.ldx;
+    bool bad = false;
     for (int64_t c = 8 * threadIdx.x; c < ldk; c += 8 * 128) {
         float v[8];
-        if (vec8 && c + 8 <= n) {
-            const uint2 w = *reinterpret_cast<const uint2*>(
-                static_cast<const uint8_t*>(g.X) + r * g.ldx + c);
+        if (vec && c + 8 <= n) {
+            alignas(16) T e[8];
+            load8<DT>(x, c, e);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const uint8_t byte = (uint8_t)((t < 4 ? w.x : w.y) >> (8 * (t & 3)));
-                v[t] = load_any_f(&byte, 0, g.x_dtype);
-            }
-        } else if (vec && c + 8 <= n) {
-            const float4* q = reinterpret_cast<const float4*>(
-                static_cast<const float*>(g.X) + r * g.ldx + c);
-            const float4 a = q[0], b = q[1];
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            for (int t = 0; t < 8; ++t) v[t] = value_checked<DT>(e[t], 256.f, bad);
         } else {
 #pragma unroll
             for (int t = 0; t < 8; ++t)
-                v[t] = (c + t < n) ? load_any_f(g.X, r * g.ldx + c + t, g.x_dtype) : 0.f;
+                v[t] = c + t < n ? value_checked<DT>(x[c + t], 256.f, bad) : 0.f;
         }
-        if (g.kind == 0) {
+        if constexpr (KIND == 0) {
             uint32_t w[3][4];
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
@@ -114,7 +116,6 @@ g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix
                     make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
         } else {
             uint32_t w[4];
-            bool bad = false;
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
                 const __nv_bfloat16 b0 = __float2bfloat16_rn(v[t]);
@@ -123,105 +124,53 @@ g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix
                        fabsf(v[t]) > 256.f || fabsf(v[t + 1]) > 256.f;
                 w[t / 2] = pack2(b0, b1);
             }
-            if (bad) atomicExch(&flags[g.flag], 1);
             *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(g.A) + r * ldk + c) =
                 make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
+    if (KIND == 1 && bad) atomicExch(&flags[g.flag], 1);
+}
+
+// Block b converts row b - row_prefix[j] of the A operand of instance
+// j = row_job[b].
+__global__ void __launch_bounds__(128)
+g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix,
+              const int* __restrict__ row_job, int rows_total, int* __restrict__ flags) {
+    const int j = row_job[blockIdx.x];
+    const GInst& g = inst[j];
+    const int64_t r = blockIdx.x - row_prefix[j];
+    if (g.kind == 0) {
+        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 0>(g, r, flags)))
+    } else {
+        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 1>(g, r, flags)))
+    }
 }
 
 // Block b converts one 64 x 64 tile of the B operand (Y transposed to
-// K-major): Case A widens the Rep-factors Y; Case B slices the real Y.
-// Loads: a thread reads 4 consecutive source values (one 16-byte load for
-// FP32, one 4-byte load for one-byte dtypes, when aligned); stores: 4
-// threads write one 128-byte output row segment (16 BF16 values each).
+// K-major) of instance j = tt_job[b]: Case A widens the Rep-factors Y
+// (exact, |v| <= 256); Case B splits the real Y into 3 slices.
 __global__ void __launch_bounds__(256)
 g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_prefix,
-                   int ninst, int* __restrict__ flags) {
+                   const int* __restrict__ tt_job, int* __restrict__ flags) {
     __shared__ float tile[64][65];
-    const int j = find_job(tt_prefix, ninst, blockIdx.x);
+    const int j = tt_job[blockIdx.x];
     const GInst& g = inst[j];
-    const int64_t n = g.n, ldk = g.ldk;
+    const int64_t n = g.n;
     const int64_t tpr = (n + 63) / 64;
     const int64_t t = blockIdx.x - tt_prefix[j];
     const int64_t r0 = (t / tpr) * 64, c0 = (t % tpr) * 64;
-    const int tid = threadIdx.x;
-    const int dt = g.y_dtype;
-    const bool f4 = dt == AFMM_F32 && (g.ldy % 4) == 0 &&
-                    ((reinterpret_cast<uintptr_t>(g.Y) & 15u) == 0);
-    const bool b4 = (dt == AFMM_U8 || dt == AFMM_I8 || dt == AFMM_E4M3) &&
-                    (g.ldy % 4) == 0 && ((reinterpret_cast<uintptr_t>(g.Y) & 3u) == 0);
-    // 16 threads per source row (4 values each), 16 rows per pass.
-    const int lc = (tid & 15) * 4;
-    for (int i = tid >> 4; i < 64; i += 16) {
-        const int64_t r = r0 + i, c = c0 + lc;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (r < n) {
-            if (f4 && c + 4 <= n) {
-                const float4 q = *reinterpret_cast<const float4*>(
-                    static_cast<const float*>(g.Y) + r * g.ldy + c);
-                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-            } else if (b4 && c + 4 <= n) {
-                const uint32_t w = *reinterpret_cast<const uint32_t*>(
-                    static_cast<const uint8_t*>(g.Y) + r * g.ldy + c);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const uint8_t byte = (uint8_t)(w >> (8 * e));
-                    v[e] = load_any_f(&byte, 0, dt);
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (c + e < n) v[e] = load_any_f(g.Y, r * g.ldy + c + e, dt);
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) tile[i][lc + e] = v[e];
-    }
-    __syncthreads();
-    // Output row cc (source column), source rows 16*qq .. 16*qq+15.
-    const int cc = tid >> 2, qq = tid & 3;
-    const int64_t c = c0 + cc, r = r0 + 16 * qq;
+    auto* B = static_cast<__nv_bfloat16*>(g.B);
     bool bad = false;
-    if (c < n && r < ldk) {
-        float v[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) v[e] = tile[16 * qq + e][cc];
-        // r + 16 <= ldk unless ldk ends inside this group (ldk % 8 == 0).
-        const int cnt = (int)((ldk - r) < 16 ? (ldk - r) : 16);
-        if (g.kind == 0) {
-            uint32_t w[8];
-#pragma unroll
-            for (int e = 0; e < 16; e += 2) {
-                const __nv_bfloat16 b0 = __float2bfloat16_rn(v[e]);
-                const __nv_bfloat16 b1 = __float2bfloat16_rn(v[e + 1]);
-                bad |= __bfloat162float(b0) != v[e] || __bfloat162float(b1) != v[e + 1] ||
-                       fabsf(v[e]) > 256.f || fabsf(v[e + 1]) > 256.f;
-                w[e / 2] = pack2(b0, b1);
-            }
-            __nv_bfloat16* o = static_cast<__nv_bfloat16*>(g.B) + c * ldk + r;
-            *reinterpret_cast<uint4*>(o) = make_uint4(w[0], w[1], w[2], w[3]);
-            if (cnt == 16) *reinterpret_cast<uint4*>(o + 8) = make_uint4(w[4], w[5], w[6], w[7]);
-        } else {
-            uint32_t w[3][8];
-#pragma unroll
-            for (int e = 0; e < 16; e += 2) {
-                __nv_bfloat16 o0[3], o1[3];
-                split_bf16<3>(v[e], o0);
-                split_bf16<3>(v[e + 1], o1);
-#pragma unroll
-                for (int sl = 0; sl < 3; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
-            }
-#pragma unroll
-            for (int sl = 0; sl < 3; ++sl) {
-                __nv_bfloat16* o =
-                    static_cast<__nv_bfloat16*>(g.B) + ((int64_t)sl * n + c) * ldk + r;
-                *reinterpret_cast<uint4*>(o) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
-                if (cnt == 16)
-                    *reinterpret_cast<uint4*>(o + 8) =
-                        make_uint4(w[sl][4], w[sl][5], w[sl][6], w[sl][7]);
-            }
-        }
+    if (g.kind == 0) {
+        G_DTYPE_SWITCH(g.y_dtype, (bad = tile_transpose_convert<DT, 1, true>(
+                                       g.Y, n, g.ldy, r0, c0, B, g.ldk, 256.f,
+                                       rows_aligned16(g.Y, g.ldy, sizeof(typename Elem<DT>::T)),
+                                       tile)))
+    } else {
+        G_DTYPE_SWITCH(g.y_dtype, (tile_transpose_convert<DT, 3, false>(
+                                       g.Y, n, g.ldy, r0, c0, B, g.ldk, 0.f,
+                                       rows_aligned16(g.Y, g.ldy, sizeof(typename Elem<DT>::T)),
+                                       tile)))
     }
     if (bad) atomicExch(&flags[g.flag], 1);
 }
@@ -451,13 +400,14 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
 }  // namespace
 
 afmm_status launch_batch_convert(const GInst* inst, const int* row_prefix,
-                                 const int* tt_prefix, int ninst, int rows_total,
+                                 const int* row_job, const int* tt_prefix,
+                                 const int* tt_job, int ninst, int rows_total,
                                  int tt_total, int* flags, cudaStream_t st) {
     if (ninst <= 0) return AFMM_OK;
     AFMM_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (ninst + 1), st));
-    g_rows_kernel<<<rows_total, 128, 0, st>>>(inst, row_prefix, ninst, flags);
+    g_rows_kernel<<<rows_total, 128, 0, st>>>(inst, row_prefix, row_job, rows_total, flags);
     AFMM_CUDA_TRY(cudaGetLastError());
-    g_transpose_kernel<<<tt_total, 256, 0, st>>>(inst, tt_prefix, ninst, flags);
+    g_transpose_kernel<<<tt_total, 256, 0, st>>>(inst, tt_prefix, tt_job, flags);
     AFMM_CUDA_TRY(cudaGetLastError());
     count_launches(2);
     return AFMM_OK;

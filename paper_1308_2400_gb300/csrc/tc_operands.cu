@@ -8,6 +8,7 @@
 #include "bf16_split.cuh"
 #include "elem.cuh"
 #include "tc_gemm.cuh"
+#include "tile_convert.cuh"
 
 namespace afmm {
 namespace {
@@ -34,36 +35,6 @@ __device__ __forceinline__ float load_checked(const void* p, int64_t i, float li
 // Rows kept as rows (K-major A operand): dst[(s*n + r)*ldk + c], eight
 // columns per thread (one 16-byte store per slice).  EXACT: one slice that
 // must equal the source (Rep-factors); otherwise OVERFLOW_RISK is recorded.
-// Eight consecutive elements of one row from aligned vector loads (8 * size
-// bytes: one 8-byte load for 1-byte types, one to four 16-byte loads else).
-template <int DT>
-__device__ __forceinline__ void load8(const void* p, int64_t i,
-                                      typename Elem<DT>::T (&e)[8]) {
-    using T = typename Elem<DT>::T;
-    if constexpr (sizeof(T) == 1) {
-        const uint2 q = *reinterpret_cast<const uint2*>(static_cast<const T*>(p) + i);
-        *reinterpret_cast<uint2*>(e) = q;
-    } else {
-        const uint4* q = reinterpret_cast<const uint4*>(static_cast<const T*>(p) + i);
-#pragma unroll
-        for (int k = 0; k < (int)sizeof(T) / 2; ++k) reinterpret_cast<uint4*>(e)[k] = q[k];
-    }
-}
-
-// Element value as float with the checks of load_checked.
-template <int DT>
-__device__ __forceinline__ float value_checked(typename Elem<DT>::T v, float lim, bool& bad) {
-    if constexpr (DT == AFMM_I32) {
-        bad |= (float)(v < 0 ? -(int64_t)v : (int64_t)v) > lim;
-        return (float)v;
-    } else if constexpr (DT == AFMM_F64) {
-        bad |= (double)(float)v != v;
-        return (float)v;
-    } else {
-        return (float)Elem<DT>::get(&v, 0);
-    }
-}
-
 template <int DT, int S, bool EXACT>
 __global__ void __launch_bounds__(256)
 widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
@@ -141,110 +112,20 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
 }
 
 // Rows become columns (K-major B operand from a row-major K x N matrix):
-// dst[(s*n + c)*ldk + r] = slice_s(src[r][c]).  64 x 64 tiles through shared
-// memory: a thread reads 4 consecutive source values (one 16-byte load for
-// FP32 when aligned) and writes 16 consecutive outputs of one output row
-// (4 threads per 128-byte row segment).  FP64 real factors are rounded to
-// FP32 first (the FP32 target needs no more).
+// dst[(s*n + c)*ldk + r] = slice_s(src[r][c]), one 64 x 64 tile per block
+// (tile_transpose_convert: 16-byte loads, FP32 tile in shared memory,
+// 128-byte output row segments).  FP64 real factors are rounded to FP32
+// first (the FP32 target needs no more).
 template <int DT, int S, bool EXACT>
 __global__ void __launch_bounds__(256)
 widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                        __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
-                       int* status) {
+                       int vec, int* status) {
     __shared__ float tile[64][65];
-    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 64;
-    const int tid = threadIdx.x;
-    const bool f4 = DT == AFMM_F32 && (lds % 4) == 0 &&
-                    ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
-    bool bad = false;
-    const int lc = (tid & 15) * 4;
-    for (int i = tid >> 4; i < 64; i += 16) {
-        const int64_t r = r0 + i, c = c0 + lc;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (r < n) {
-            if (f4 && c + 4 <= n) {
-                const float4 q = *reinterpret_cast<const float4*>(
-                    static_cast<const float*>(src) + r * lds + c);
-                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (c + e < n) v[e] = load_checked<DT>(src, r * lds + c + e, lim, bad);
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) tile[i][lc + e] = v[e];
-    }
-    if (!EXACT) bad = false;
-    __syncthreads();
-    const int cc = tid >> 2, qq = tid & 3;
-    const int64_t c = c0 + cc, r = r0 + 16 * qq;
-    if (c < n && r < ldk) {
-        float v[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) v[e] = tile[16 * qq + e][cc];
-        const int cnt = (int)((ldk - r) < 16 ? (ldk - r) : 16);   // 8 or 16
-        uint32_t w[S][8];
-#pragma unroll
-        for (int e = 0; e < 16; e += 2) {
-            __nv_bfloat16 o0[S], o1[S];
-            split_bf16<S>(v[e], o0);
-            split_bf16<S>(v[e + 1], o1);
-            if (EXACT)
-                bad |= __bfloat162float(o0[0]) != v[e] || __bfloat162float(o1[0]) != v[e + 1] ||
-                       fabsf(v[e]) > lim || fabsf(v[e + 1]) > lim;
-#pragma unroll
-            for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
-        }
-#pragma unroll
-        for (int sl = 0; sl < S; ++sl) {
-            __nv_bfloat16* o = dst + ((int64_t)sl * n + c) * ldk + r;
-            *reinterpret_cast<uint4*>(o) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
-            if (cnt == 16)
-                *reinterpret_cast<uint4*>(o + 8) =
-                    make_uint4(w[sl][4], w[sl][5], w[sl][6], w[sl][7]);
-        }
-    }
+    const bool bad = tile_transpose_convert<DT, S, EXACT>(
+        src, n, lds, (int64_t)blockIdx.y * 64, (int64_t)blockIdx.x * 64, dst, ldk, lim,
+        vec != 0, tile);
     if (EXACT && bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
-}
-
-// Rep-factors stored in one byte (e4m3, u8, i8) widened to BF16 and
-// transposed to K-major: 64 source rows x 128 source columns per block,
-// 4-byte coalesced reads, 128-byte row writes.  Needs n % 4 == 0 and a
-// 4-byte aligned source with lds % 4 == 0.
-template <int DT>
-__global__ void __launch_bounds__(256)
-widen_transpose_bytes_kernel(const uint8_t* __restrict__ src, int64_t n, int64_t lds,
-                             __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
-                             int* status) {
-    __shared__ float tile[64][129];
-    const int64_t c0 = (int64_t)blockIdx.x * 128, r0 = (int64_t)blockIdx.y * 64;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int i = 0; i < 8; ++i) {
-        const int rr = warp + 8 * i;
-        const int64_t r = r0 + rr, c = c0 + 4 * lane;
-        uint32_t w = 0;
-        if (r < n && c < n) w = *reinterpret_cast<const uint32_t*>(src + r * lds + c);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint8_t byte = (uint8_t)(w >> (8 * b));
-            tile[rr][4 * lane + b] = (float)Elem<DT>::get(&byte, 0);
-        }
-    }
-    __syncthreads();
-    bool bad = false;
-    for (int i = 0; i < 16; ++i) {
-        const int cc = warp * 16 + i;              // output row within the block
-        const int64_t c = c0 + cc, r = r0 + 2 * lane;
-        if (c < n && r < ldk) {
-            const float v0 = tile[2 * lane][cc], v1 = tile[2 * lane + 1][cc];
-            const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
-            bad |= __bfloat162float(b0) != v0 || __bfloat162float(b1) != v1 ||
-                   fabsf(v0) > lim || fabsf(v1) > lim;
-            *reinterpret_cast<uint32_t*>(dst + c * ldk + r) = pack2(b0, b1);
-        }
-    }
-    if (bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
 }
 
 template <int S, bool EXACT>
@@ -274,30 +155,13 @@ template <int S, bool EXACT>
 afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
                                    int64_t lds, __nv_bfloat16* dst, int64_t ldk,
                                    float lim, int* status, cudaStream_t st) {
-    if constexpr (S == 1 && EXACT) {
-        const bool bytes = dt == AFMM_E4M3 || dt == AFMM_U8 || dt == AFMM_I8;
-        if (bytes && n % 4 == 0 && lds % 4 == 0 &&
-            (reinterpret_cast<uintptr_t>(src) & 3u) == 0 && n > 0) {
-            const dim3 grid((unsigned)((n + 127) / 128), (unsigned)((n + 63) / 64));
-            if (grid.y > 65535) return AFMM_ERR_UNSUPPORTED;
-            const uint8_t* s8 = static_cast<const uint8_t*>(src);
-            if (dt == AFMM_E4M3)
-                widen_transpose_bytes_kernel<AFMM_E4M3><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
-            else if (dt == AFMM_U8)
-                widen_transpose_bytes_kernel<AFMM_U8><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
-            else
-                widen_transpose_bytes_kernel<AFMM_I8><<<grid, 256, 0, st>>>(s8, n, lds, dst, ldk, lim, status);
-            AFMM_CUDA_TRY(cudaGetLastError());
-            count_launches(1);
-            return AFMM_OK;
-        }
-    }
     const int64_t g = (n + 63) / 64;
     if (g > 65535) return AFMM_ERR_UNSUPPORTED;
     const dim3 grid((unsigned)g, (unsigned)g), block(256);
+    const int vec = rows_aligned16(src, lds, (int64_t)dtype_size(dt));
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
         widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(src, n, lds, dst,
-                                                                     ldk, lim, status);
+                                                                     ldk, lim, vec, status);
         return AFMM_OK;
     });
     AFMM_TRY(rc);

@@ -1,0 +1,137 @@
+// Operand conversion building blocks shared by the single-product
+// conversions (tc_operands.cu) and the grouped ones of a batch
+// (batched_kernels.cu): vector loads of any element type and the 64 x 64
+// tile that widens or splits a row-major factor into a K-major BF16
+// operand.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "bf16_split.cuh"
+#include "elem.cuh"
+
+namespace afmm {
+
+// Eight consecutive elements from element i, by aligned vector loads
+// (8 * size bytes: one 8-byte load for one-byte types, one to four 16-byte
+// loads otherwise).
+template <int DT>
+__device__ __forceinline__ void load8(const void* p, int64_t i,
+                                      typename Elem<DT>::T (&e)[8]) {
+    using T = typename Elem<DT>::T;
+    if constexpr (sizeof(T) == 1) {
+        const uint2 q = *reinterpret_cast<const uint2*>(static_cast<const T*>(p) + i);
+        *reinterpret_cast<uint2*>(e) = q;
+    } else {
+        const uint4* q = reinterpret_cast<const uint4*>(static_cast<const T*>(p) + i);
+#pragma unroll
+        for (int k = 0; k < (int)sizeof(T) / 2; ++k) reinterpret_cast<uint4*>(e)[k] = q[k];
+    }
+}
+
+// Element value as float; `bad` records an int32 beyond lim (checked in
+// integer arithmetic, so values past 2^24 cannot slip through a rounding)
+// or an FP64 value that FP32 does not hold.
+template <int DT>
+__device__ __forceinline__ float value_checked(typename Elem<DT>::T v, float lim, bool& bad) {
+    if constexpr (DT == AFMM_I32) {
+        bad |= (float)(v < 0 ? -(int64_t)v : (int64_t)v) > lim;
+        return (float)v;
+    } else if constexpr (DT == AFMM_F64) {
+        bad |= (double)(float)v != v;
+        return (float)v;
+    } else {
+        return (float)Elem<DT>::get(&v, 0);
+    }
+}
+
+// Rows r0 .. r0+63 and columns c0 .. c0+63 of the row-major n x n source
+// become rows c (K-major) of the destination: dst[(s * n + c) * ldk + r] =
+// slice s of src[r][c], for S BF16 slices (S = 1 and EXACT: the value must
+// be exact in BF16 and |v| <= lim, else the return value is true).
+// Loads: 16 bytes per thread and pass when `vec` (16-byte aligned rows) and
+// the tile is whole in columns, element loads otherwise; the tile goes
+// through shared memory as FP32; stores: four threads write one 128-byte
+// segment of an output row per slice.  256 threads; `tile` is [64][65].
+template <int DT, int S, bool EXACT>
+__device__ __forceinline__ bool tile_transpose_convert(const void* __restrict__ src,
+                                                       int64_t n, int64_t lds, int64_t r0,
+                                                       int64_t c0,
+                                                       __nv_bfloat16* __restrict__ dst,
+                                                       int64_t ldk, float lim, bool vec,
+                                                       float (*tile)[65]) {
+    using T = typename Elem<DT>::T;
+    constexpr int V = 16 / (int)sizeof(T);     // elements per 16-byte load
+    constexpr int TPR = 64 / V;                 // threads per tile row
+    constexpr int RPP = 256 / TPR;              // tile rows per pass
+    constexpr int P = 64 / RPP;                 // passes
+    const int tid = threadIdx.x;
+    const int lc = (tid % TPR) * V, lr = tid / TPR;
+    const T* s = static_cast<const T*>(src);
+    bool bad = false;
+    if (vec && c0 + 64 <= n) {
+        uint4 q[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int64_t r = r0 + lr + RPP * p;
+            q[p] = r < n ? *reinterpret_cast<const uint4*>(s + r * lds + c0 + lc)
+                         : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const T* e = reinterpret_cast<const T*>(&q[p]);
+#pragma unroll
+            for (int t = 0; t < V; ++t) tile[lr + RPP * p][lc + t] = value_checked<DT>(e[t], lim, bad);
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int64_t r = r0 + lr + RPP * p;
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const int64_t c = c0 + lc + t;
+                tile[lr + RPP * p][lc + t] =
+                    (r < n && c < n) ? value_checked<DT>(s[r * lds + c], lim, bad) : 0.f;
+            }
+        }
+    }
+    if (!EXACT) bad = false;
+    __syncthreads();
+    const int cc = tid >> 2, qq = tid & 3;
+    const int64_t c = c0 + cc, r = r0 + 16 * qq;
+    if (c < n && r < ldk) {
+        float v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = tile[16 * qq + e][cc];
+        const int cnt = (int)((ldk - r) < 16 ? (ldk - r) : 16);   // 8 or 16
+        uint32_t w[S][8];
+#pragma unroll
+        for (int e = 0; e < 16; e += 2) {
+            __nv_bfloat16 o0[S], o1[S];
+            split_bf16<S>(v[e], o0);
+            split_bf16<S>(v[e + 1], o1);
+            if (EXACT)
+                bad |= __bfloat162float(o0[0]) != v[e] || __bfloat162float(o1[0]) != v[e + 1] ||
+                       fabsf(v[e]) > lim || fabsf(v[e + 1]) > lim;
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
+        }
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+            __nv_bfloat16* o = dst + ((int64_t)sl * n + c) * ldk + r;
+            *reinterpret_cast<uint4*>(o) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+            if (cnt == 16)
+                *reinterpret_cast<uint4*>(o + 8) =
+                    make_uint4(w[sl][4], w[sl][5], w[sl][6], w[sl][7]);
+        }
+    }
+    return bad;
+}
+
+// Whether rows of a dtype-dt source start 16-byte aligned.
+__host__ __device__ inline bool rows_aligned16(const void* p, int64_t ld, int64_t es) {
+    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && (ld * es) % 16 == 0;
+}
+
+}  // namespace afmm
