@@ -118,6 +118,18 @@ struct afmm_plan_s {
     // Transfer pipelining of host buffers (created on first use).
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev[2 * 16 + 2] = {};
+    // Replay of repeated calls on the same device buffers (small problems,
+    // where the gaps between launches are a large part of a call): the
+    // third call in a row with the same X, Y, Z is captured into a CUDA
+    // graph on a private stream; later ones launch it.
+    const void* g_x = nullptr;
+    const void* g_y = nullptr;
+    void* g_z = nullptr;
+    int g_seen = 0;
+    bool g_off = false;                 // capture failed once: stay eager
+    cudaGraphExec_t g_exec = nullptr;
+    cudaStream_t g_cap = nullptr;
+    int64_t g_launches = 0;
 };
 
 namespace {
@@ -491,6 +503,56 @@ afmm_status run_pipelined_host(afmm_plan_s* p, const void* X, const void* Y, voi
     return AFMM_OK;
 }
 
+constexpr int64_t kGraphMaxN = 2048;
+
+void graph_drop(afmm_plan_s* p) {
+    if (p->g_exec) cudaGraphExecDestroy(p->g_exec);
+    p->g_exec = nullptr;
+}
+
+// Device-buffer call through the replay graph: *done is true when the
+// product was launched here (replayed, or captured and launched).
+afmm_status graph_call(afmm_plan_s* p, const void* X, const void* Y, void* Z,
+                       cudaStream_t st, bool* done) {
+    *done = false;
+    if (X != p->g_x || Y != p->g_y || Z != p->g_z) {
+        graph_drop(p);
+        p->g_x = X;
+        p->g_y = Y;
+        p->g_z = Z;
+        p->g_seen = 1;
+        return AFMM_OK;
+    }
+    if (!p->g_exec) {
+        if (++p->g_seen < 3) return AFMM_OK;
+        if (!p->g_cap)
+            AFMM_CUDA_TRY(cudaStreamCreateWithFlags(&p->g_cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        AFMM_CUDA_TRY(cudaStreamBeginCapture(p->g_cap, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = launch_counter();
+        const afmm_status rc = run_variant(p, X, Y, Z, p->g_cap);
+        const cudaError_t ec = cudaStreamEndCapture(p->g_cap, &g);
+        p->g_launches = launch_counter() - l0;
+        count_launches((int)-p->g_launches);      // nothing ran yet
+        cudaError_t ei = cudaErrorUnknown;
+        if (rc == AFMM_OK && ec == cudaSuccess && g)
+            ei = cudaGraphInstantiate(&p->g_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            (void)cudaGetLastError();               // capture errors are not sticky
+            p->g_exec = nullptr;
+            p->g_off = true;                        // this plan stays eager
+            return AFMM_OK;
+        }
+    }
+    AFMM_CUDA_TRY(cudaGraphLaunch(p->g_exec, st));
+    count_launches((int)p->g_launches);
+    p->launches += p->g_launches;
+    p->calls += 1;
+    *done = true;
+    return AFMM_OK;
+}
+
 afmm_status mul_impl(afmm_plan p, const void* X, const void* Y, void* Z,
                      void* stream, int expect_case) {
     if (!p) return AFMM_ERR_INVALID_ARG;
@@ -533,6 +595,11 @@ afmm_status mul_impl(afmm_plan p, const void* X, const void* Y, void* Z,
         void* b;
         AFMM_TRY(stage_buffer(p, 2, bz, &b));
         dZ = b;
+    }
+    if (!hx && !hy && !hz && !p->timing && !p->g_off && n <= kGraphMaxN) {
+        bool replay = false;
+        AFMM_TRY(graph_call(p, X, Y, Z, st, &replay));
+        if (replay) return AFMM_OK;
     }
     MainTimer tm;
     if (p->timing) {
@@ -641,6 +708,11 @@ afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc) {
 
 afmm_status afmm_plan_destroy(afmm_plan p) {
     if (!p) return AFMM_OK;
+    graph_drop(p);
+    if (p->g_cap) {
+        cudaStreamSynchronize(p->g_cap);
+        cudaStreamDestroy(p->g_cap);
+    }
     if (p->s_in) {
         cudaStreamSynchronize(p->s_in);
         cudaStreamSynchronize(p->s_out);

@@ -601,6 +601,52 @@ def test_leading_dimensions():
     assert np.all(Z[:, n:] == 7.0)      # padding columns untouched
 
 
+@pytest.mark.parametrize("workload,variant", [("caseA_n256_f64", -1), ("caseB_n4096_f32", 1),
+                                              ("caseB_n4096_sparse", 6)])
+def test_repeated_calls_replay_a_graph(workload, variant):
+    """From the third call in a row on the same device buffers the product
+    is replayed from a CUDA graph.  Replays read the buffers' current
+    contents, give the bits of an eager call, and count their launches;
+    new buffers start over."""
+    from paper_1308_2400_gb300 import Plan
+    from _helpers import desc_for, gpu_operands, z_torch_dtype
+    inst = W.make(workload, n=300, seed=5)
+    inst2 = W.make(workload, n=300, seed=6)
+    p = Plan(desc_for(inst, variant=variant))
+    X, Y = gpu_operands(inst)
+    X2, Y2 = gpu_operands(inst2)
+    zt = z_torch_dtype(inst.z_dtype)
+    Z = torch.empty((300, 300), dtype=zt, device="cuda")
+    outs = []
+    for _ in range(5):
+        p(X, Y, Z)
+        p.sync()
+        outs.append(Z.clone())
+    c = p.counters()
+    assert c["calls"] == 5 and c["kernel_launches"] % 5 == 0
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    def check(ins, Zn):
+        if ins.target == "fp64":
+            assert rel_fro(Zn, oracle_rows(ins)) <= FP64_REL_FRO
+        else:
+            check_fp32(ins, Zn, bound_fn=sparse_elem_bound if variant == 6 else tc_elem_bound)
+
+    check(inst, outs[0].cpu().numpy())
+    # New contents in the same buffers: the replay reads them.
+    X.copy_(X2)
+    Y.copy_(Y2)
+    p(X, Y, Z)
+    p.sync()
+    check(inst2, Z.cpu().numpy())
+    # Other buffers: eager again, then a new capture.
+    Z2 = torch.empty_like(Z)
+    for _ in range(4):
+        p(X2, Y2, Z2)
+    p.sync()
+    assert torch.equal(Z2, Z)
+
+
 def test_empty_problem():
     from paper_1308_2400_gb300 import Plan, make_desc
     p = Plan(make_desc(0, "A", "f32", "i32", "f32", "fp32"))
