@@ -372,9 +372,8 @@ afmm_status run_f64slice_a(afmm_plan_s* p, const void* X, int xdt, int64_t ldx,
     int8_t* Q = wsp<int8_t>(p, p->off_a);
     int32_t* W = wsp<int32_t>(p, p->off_b);
     int32_t* P = wsp<int32_t>(p, p->off_c);
-    AFMM_TRY(launch_row_exponents(X, xdt, n, ldx, E, st));
-    AFMM_TRY(launch_slice_rows_i8(X, xdt, n, ldx, E, p->slices, p->bits, Q,
-                                  p->lda, st));
+    AFMM_TRY(launch_exp_slice_rows_i8(X, xdt, n, ldx, E, p->slices, p->bits, Q, p->lda,
+                                      st));
     AFMM_TRY(launch_pack_b_i8(Y, ydt, n, ldy, W, p->ldb, status, st));
     AFMM_TRY(launch_simt_dp4a(Q, p->lda, W, p->ldb, P, n,
                               (int64_t)p->slices * n, n, n, st));
@@ -468,7 +467,7 @@ afmm_status run_pipelined_host(afmm_plan_s* p, const void* X, const void* Y, voi
     AFMM_TRY(stage_buffer(p, 2, span_bytes(n, ldz, d.z_dtype), &dZ));
     int* status = wsp<int>(p, p->off_status);
     int64_t bounds[17];
-    const int nb = tc_row_blocks(n, dp.sm_count, bounds, 16);
+    const int nb = tc_row_blocks(n, dp.sm_count, bounds, 16, d.kase == AFMM_CASE_B);
     cudaEvent_t ev_y = p->ev[0], ev_done = p->ev[1];
     // The staging buffers may still be read by the previous call's copies.
     AFMM_CUDA_TRY(cudaEventRecord(ev_done, st));

@@ -264,10 +264,14 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
     unsigned char* maps = mapbuf.data() +
                           ((64 - (reinterpret_cast<uintptr_t>(mapbuf.data()) & 63)) & 63);
     for (int j = 0; j < ntc; ++j) {
+        // The three slices are always on the A side: Case A reads A = X
+        // slices, B = Y^T; Case B computes Z^T = Y^T X^T, A = the Y^T slices
+        // (buffer B), B = the X rows (buffer A).
         const GInst& g = b->ginst[j];
-        const int sa = g.kind == 0 ? 3 : 1, sb = 4 - sa;
-        AFMM_TRY(tc_encode_map(maps + 2 * j * 128, g.A, g.n, g.n, g.ldk, sa, GB_BM));
-        AFMM_TRY(tc_encode_map(maps + (2 * j + 1) * 128, g.B, g.n, g.n, g.ldk, sb, GB_BN));
+        void* a_side = g.kind == 0 ? g.A : g.B;
+        void* b_side = g.kind == 0 ? g.B : g.A;
+        AFMM_TRY(tc_encode_map(maps + 2 * j * 128, a_side, g.n, g.n, g.ldk, 3, GB_BM));
+        AFMM_TRY(tc_encode_map(maps + (2 * j + 1) * 128, b_side, g.n, g.n, g.ldk, 1, GB_BN));
     }
     auto up = [](void* dst, const void* src, size_t bytes) -> afmm_status {
         if (bytes) AFMM_CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));

@@ -33,8 +33,10 @@ constexpr int GB_THREADS = 64 + GB_EPI;
 constexpr uint32_t GB_TMEM_COLS = 512;
 constexpr int GB_A_TILE = GB_BM * GB_BK * 2;      // 8 KiB
 constexpr int GB_B_TILE = GB_BN * GB_BK * 2;      // 16 KiB
-constexpr int GB_STAGE = GB_A_TILE + 3 * GB_B_TILE;   // fits 3A+1B and 1A+3B
-constexpr int GB_STAGES = 3;
+// Every tile is computed with the three slices on the A side (Case B as
+// Z^T = Y^T X^T), so a stage is 3 A tiles + 1 B tile.
+constexpr int GB_STAGE = 3 * GB_A_TILE + GB_B_TILE;
+constexpr int GB_STAGES = 4;
 constexpr int GB_EPI_SMEM = 8 * 32 * 33 * 4;         // per-warp 32 x 33 floats
 constexpr int GB_SMEM = 1024 + GB_STAGES * GB_STAGE + 256 + GB_EPI_SMEM;
 constexpr uint64_t GB_WAIT_NS = 2000000000ull;
@@ -189,8 +191,9 @@ g_widen_kernel(const WJob* __restrict__ jobs, const int* __restrict__ prefix, in
 // Persistent: CTA b runs tiles[cta_off[b] .. cta_off[b+1]) in order; a tile
 // is (instance, tm, tn).  Roles as in the single-product kernel: warp 0 TMA,
 // warp 1 TMEM + MMA, warps 2..9 epilogue; two accumulators per tile (hi
-// slice | smaller slices).  Stage layout: A slices then B slices, 8 KiB per
-// A tile and 16 KiB per B tile (3A+1B for Case A, 1A+3B for Case B).
+// slice | smaller slices).  Stage layout: the three A slices (8 KiB each)
+// then the B tile (16 KiB); Case B tiles are tiles of Z^T = Y^T X^T and are
+// stored transposed.
 __global__ void __launch_bounds__(GB_THREADS, 1)
 g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps,
             const int* __restrict__ cta_off, const int4* __restrict__ tiles,
@@ -237,8 +240,8 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
                 const GInst& g = inst[tl.x];
                 const CUtensorMap* ma = &maps[2 * tl.x];
                 const CUtensorMap* mb = &maps[2 * tl.x + 1];
-                const int sa = g.kind == 0 ? 3 : 1, sb = g.kind == 0 ? 1 : 3;
-                const uint32_t bytes = sa * GB_A_TILE + sb * GB_B_TILE;
+                constexpr int sa = 3, sb = 1;
+                constexpr uint32_t bytes = sa * GB_A_TILE + sb * GB_B_TILE;
                 const int nkb = (int)((g.n + GB_BK - 1) / GB_BK);
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!ptx::mbar_wait_bounded(&bars->empty[stage], phase ^ 1u, abort,
@@ -281,8 +284,7 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
             for (int t = t0; ok && t < t1; ++t) {
                 const int4 tl = tiles[t];
                 const GInst& g = inst[tl.x];
-                const int kind = g.kind;
-                const int sa = kind == 0 ? 3 : 1;
+                constexpr int sa = 3;
                 const int nkb = (int)((g.n + GB_BK - 1) / GB_BK);
                 if (!ptx::mbar_wait_bounded(&bars->tempty, tphase ^ 1u, abort, GB_WAIT_NS)) {
                     ok = false;
@@ -301,10 +303,8 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
                     for (int ks = 0; ks < GB_BK / 16; ++ks) {
 #pragma unroll
                         for (int p = 2; p >= 0; --p) {
-                            const uint32_t a_addr =
-                                s0 + (kind == 0 ? p : 0) * GB_A_TILE + ks * 32;
-                            const uint32_t b_addr =
-                                s0 + sa * GB_A_TILE + (kind == 1 ? p : 0) * GB_B_TILE + ks * 32;
+                            const uint32_t a_addr = s0 + p * GB_A_TILE + ks * 32;
+                            const uint32_t b_addr = s0 + sa * GB_A_TILE + ks * 32;
                             const bool first = kb == 0 && ks == 0 && (p == 0 || p == 2);
                             ptx::mma_f16(tmem + (p == 0 ? 0u : (uint32_t)GB_BN),
                                          ptx::sdesc_kmajor_sw64(a_addr),
@@ -369,6 +369,21 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
             const bool bad = flags[g.flag] != 0;
             float* sm = epi + (warp - 2) * 32 * 33;
             const int64_t mbase = (int64_t)tl.y * GB_BM + q * 32;
+            if (g.kind == 1) {
+                // Case B: the tile is Z^T, element (m, n) goes to Z[n][m];
+                // lanes hold consecutive m, so stores are 128-byte row
+                // segments without the shared-memory turn.
+                const int64_t m = mbase + lane;
+                const int64_t n0 = (int64_t)tl.z * GB_BN + h * 128;
+                if (m < g.n) {
+                    float* zc = g.Z + m;
+#pragma unroll
+                    for (int j = 0; j < 128; ++j)
+                        if (n0 + j < g.n)
+                            zc[(n0 + j) * g.ldz] = bad ? __int_as_float(0x7fc00000) : sum[j];
+                }
+                continue;
+            }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
 #pragma unroll

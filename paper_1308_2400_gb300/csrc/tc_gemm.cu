@@ -91,11 +91,13 @@ __device__ __forceinline__ void raise_abort(TcBars* b, int* status) {
     atomicCAS(status, 0, (int)AFMM_ERR_TIMEOUT);
 }
 
-template <int SA, int SB, int MODE>
+// TOUT: the product computed is Z^T (A = the operand whose rows are Z's
+// columns); the epilogue stores tile element (m, n) at Z[n][m].
+template <int SA, int SB, int MODE, bool TOUT = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB, void* __restrict__ Zv,
-               int64_t ldz, int m0, int M, int N, int K, int kb_per_chunk, int vec,
+               int64_t ldz, int m0, int M, int n0, int N, int K, int kb_per_chunk, int vec,
                int* status) {
     using Cfg = TcCfg<SA, SB>;
     extern __shared__ uint8_t smem_raw[];
@@ -104,8 +106,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     TcBars* bars = reinterpret_cast<TcBars*>(tiles + Cfg::STAGES * Cfg::STAGE_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // Rows [m0, M) of Z: tile row tm covers rows m0 + tm*BM ..
-    const int tiles_m = (M - m0 + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
+    // Product rows [m0, M) and columns [n0, N): tile (tm, tn) covers rows
+    // m0 + tm*BM .. and columns n0 + tn*BN ..
+    const int tiles_m = (M - m0 + TC_BM - 1) / TC_BM, tiles_n = (N - n0 + TC_BN - 1) / TC_BN;
     const int num_tiles = tiles_m * tiles_n;
     const int num_kb = (K + TC_BK - 1) / TC_BK;
 
@@ -161,7 +164,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
 #pragma unroll
                     for (int s = 0; s < SB; ++s)
                         ptx::tma_load_3d(st + SA * A_TILE_BYTES + s * B_TILE_BYTES, &tmB,
-                                         &bars->full[stage], kb * TC_BK, tn * TC_BN, s);
+                                         &bars->full[stage], kb * TC_BK, n0 + tn * TC_BN, s);
                     issued_phase[stage] = (int)phase;
                     if (++stage == Cfg::STAGES) {
                         stage = 0;
@@ -358,8 +361,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
             }
             if (!ok) break;
             const int64_t m = (int64_t)m0 + (int64_t)tm * TC_BM + row;
-            const int col0 = tn * TC_BN + h * 128;
-            if (m < M) {
+            const int col0 = n0 + tn * TC_BN + h * 128;
+            if (TOUT && m < M) {
+                // Element (m, col0 + j) of Z^T is Z[col0 + j][m]: the lanes of
+                // a warp hold consecutive m, so each store writes one
+                // 128-byte segment of a row of Z.
+                Acc* zc = static_cast<Acc*>(Zv) + m;
+#pragma unroll
+                for (int j = 0; j < 128; ++j)
+                    if (col0 + j < N) zc[(int64_t)(col0 + j) * ldz] = sum[j];
+            } else if (m < M) {
                 Acc* zr = static_cast<Acc*>(Zv) + m * ldz + col0;
                 if (vec && col0 + 128 <= N) {
 #pragma unroll
@@ -426,26 +437,28 @@ afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
 
 namespace {
 
-template <int SA, int SB, int MODE>
+template <int SA, int SB, int MODE, bool TOUT = false>
 afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
-                      int* status, cudaStream_t st, int m0 = 0, int m1 = -1) {
+                      int* status, cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0,
+                      int n1 = -1) {
     using Cfg = TcCfg<SA, SB>;
     DeviceProps dp;
     AFMM_TRY(device_props(&dp));
     const int n = (int)t->n;
     if (m1 < 0) m1 = n;
-    const int tiles = ((m1 - m0 + TC_BM - 1) / TC_BM) * ((n + TC_BN - 1) / TC_BN);
+    if (n1 < 0) n1 = n;
+    const int tiles = ((m1 - m0 + TC_BM - 1) / TC_BM) * ((n1 - n0 + TC_BN - 1) / TC_BN);
     const int grid = tiles < dp.sm_count ? tiles : dp.sm_count;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, MODE>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, MODE, TOUT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
     CUtensorMap ma, mb;
-    std::memcpy(&ma, t->tmap_a, sizeof ma);
-    std::memcpy(&mb, t->tmap_b, sizeof mb);
+    std::memcpy(&ma, TOUT ? t->tmap_at : t->tmap_a, sizeof ma);
+    std::memcpy(&mb, TOUT ? t->tmap_bt : t->tmap_b, sizeof mb);
     main_kernel_begin(st);
-    tc_gemm_kernel<SA, SB, MODE><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
-        ma, mb, Z, ldz, m0, m1, n, n, kb_per_chunk, vec, status);
+    tc_gemm_kernel<SA, SB, MODE, TOUT><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
+        ma, mb, Z, ldz, m0, m1, n0, n1, n, kb_per_chunk, vec, status);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, grid);
     count_launches(1);
@@ -547,6 +560,11 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b) {
     const int sa = t->sliced_a ? sl : 1, sb = t->sliced_a ? 1 : sl;
     AFMM_TRY(tc_encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM));
     AFMM_TRY(tc_encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN));
+    if (!t->sliced_a && t->slices > 0) {
+        // Case B as Z^T = Y^T X^T: the sliced Y^T rows are the A side.
+        AFMM_TRY(tc_encode_map(t->tmap_at, b, t->n, t->n, t->ld_b, sb, TC_BM));
+        AFMM_TRY(tc_encode_map(t->tmap_bt, a, t->n, t->n, t->ld_a, sa, TC_BN));
+    }
     t->maps_ready = true;
     return AFMM_OK;
 }
@@ -587,9 +605,11 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
     else
         AFMM_TRY((tc_widen_transpose(2, false, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                    0.f, status, st)));
+    // Computed as Z^T = Y^T X^T: the slices on the A side, as in Case A, so
+    // a stage holds S + 1 tiles of 8 + 16 KiB instead of 1 + S of 8 + 16 x S.
     return t->slices == 3
-               ? launch_tc<1, 3, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
-               : launch_tc<1, 2, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
+               ? launch_tc<3, 1, 0, true>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
+               : launch_tc<2, 1, 0, true>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
 }
 
 afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
@@ -632,12 +652,17 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
     if (d.kase == AFMM_CASE_A)
         return sl == 3 ? launch_tc<3, 1, 0>(t, Z, d.ldz, 0, status, st, m0, m1)
                        : launch_tc<2, 1, 0>(t, Z, d.ldz, 0, status, st, m0, m1);
-    return sl == 3 ? launch_tc<1, 3, 0>(t, Z, d.ldz, 0, status, st, m0, m1)
-                   : launch_tc<1, 2, 0>(t, Z, d.ldz, 0, status, st, m0, m1);
+    // Case B (Z^T = Y^T X^T): rows [r0, r1) of Z are columns of the product.
+    return sl == 3 ? launch_tc<3, 1, 0, true>(t, Z, d.ldz, 0, status, st, 0, -1, m0, m1)
+                   : launch_tc<2, 1, 0, true>(t, Z, d.ldz, 0, status, st, 0, -1, m0, m1);
 }
 
-int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks) {
-    const int64_t tm = (n + TC_BM - 1) / TC_BM, tn = (n + TC_BN - 1) / TC_BN;
+int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb) {
+    // Rows of Z are product rows (tiles of TC_BM) in Case A and product
+    // columns (tiles of TC_BN) in Case B.
+    const int64_t unit_rows = caseb ? TC_BN : TC_BM;
+    const int64_t tm = (n + unit_rows - 1) / unit_rows,
+                  tn = caseb ? (n + TC_BM - 1) / TC_BM : (n + TC_BN - 1) / TC_BN;
     // Smallest number of tile rows whose tiles fill whole waves.
     int64_t g = sms, b = tn;
     while (b) { const int64_t r = g % b; g = b; b = r; }
@@ -647,7 +672,7 @@ int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks) {
     if (per >= tm) per = (tm + 1) / 2;                   // at least two blocks
     int k = 0;
     bounds[k++] = 0;
-    for (int64_t r = per; r < tm && k < max_blocks; r += per) bounds[k++] = r * TC_BM;
+    for (int64_t r = per; r < tm && k < max_blocks; r += per) bounds[k++] = r * unit_rows;
     bounds[k] = n;
     return k;                                            // number of blocks
 }

@@ -24,6 +24,9 @@ struct TcPlan {
     float lim_a = 256.f, lim_b = 256.f;  // exact form: largest |value| allowed
     alignas(64) unsigned char tmap_a[128];
     alignas(64) unsigned char tmap_b[128];
+    // Case B split form computed as Z^T = Y^T X^T: A side = the b buffer.
+    alignas(64) unsigned char tmap_at[128];
+    alignas(64) unsigned char tmap_bt[128];
     bool maps_ready = false;
 };
 
@@ -64,9 +67,11 @@ afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int
                                cudaStream_t st);
 afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
                           int64_t r0, int64_t r1, int* status, cudaStream_t st);
-// Row blocks for pipelining an n x n product: boundaries multiple of 128
-// chosen so each block's tile count fills whole waves of `sms` CTAs.
-int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks);
+// Row blocks of Z for pipelining an n x n product: boundaries multiples of
+// the tile extent along Z's rows (128 in Case A, 256 in Case B, whose
+// product is Z^T), chosen so each block's tile count fills whole waves of
+// `sms` CTAs.
+int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb);
 // Case A, three slices, X FP32 with 16-byte aligned rows: the fused kernel
 // (tc_fused.cu) reads X directly and splits it in shared memory.
 bool tc_fused_usable(const afmm_desc& d, const void* X);
