@@ -118,6 +118,10 @@ afmm_status launch_slice_rows_i8(const void* A, int dtype, int64_t n,
                                  int64_t lda, const int32_t* E, int slices,
                                  int bits, int8_t* Q, int64_t ldq,
                                  cudaStream_t st);
+// Both of the above in one pass (one launch) when ldq <= 1024.
+afmm_status launch_exp_slice_rows_i8(const void* A, int dtype, int64_t n,
+                                     int64_t lda, int32_t* E, int slices, int bits,
+                                     int8_t* Q, int64_t ldq, cudaStream_t st);
 // Z[r][c] = sum_s P[s*n + r][c] * 2^(E[r] - bits*(s+1)), in FP64.
 afmm_status launch_recombine_f64(const int32_t* P, int64_t ldp,
                                  const int32_t* E, int slices, int bits,

@@ -143,6 +143,66 @@ __global__ void slice_rows_kernel(const void* __restrict__ A, int64_t n,
     }
 }
 
+// 2^k as a double: built from its exponent field when normal, else ldexp.
+__device__ __forceinline__ double pow2(int k) {
+    if (k >= -1022 && k <= 1023)
+        return __longlong_as_double((long long)(k + 1023) << 52);
+    return ldexp(1.0, k);
+}
+
+// Row exponent and slicing in one pass for rows of at most 256 * PER
+// elements: block r keeps row r in registers, reduces its exponent bound
+// E[r] (as row_exponent_kernel) and writes the digit slices (as
+// slice_rows_kernel).
+template <int DT, int PER>
+__global__ void __launch_bounds__(kThreads)
+exp_slice_rows_kernel(const void* __restrict__ A, int64_t n, int64_t lda,
+                      int32_t* __restrict__ E, int slices, int bits,
+                      int8_t* __restrict__ Q, int64_t ldq) {
+    __shared__ int red[kThreads / 32];
+    const int W = bits * slices;
+    const unsigned long long dmask = (1ull << bits) - 1ull;
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        double v[PER];
+        int e = kEmptyRowExp;
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            const int64_t c = threadIdx.x + (int64_t)kThreads * p;
+            v[p] = c < n ? (double)Elem<DT>::get(A, r * lda + c) : 0.0;
+            if (v[p] != 0.0) e = max(e, exp_bound(v[p]));
+        }
+        for (int off = 16; off > 0; off >>= 1)
+            e = max(e, __shfl_down_sync(0xffffffffu, e, off));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+        __syncthreads();
+        int er = red[0];
+        for (int w = 1; w < kThreads / 32; ++w) er = max(er, red[w]);
+        if (threadIdx.x == 0) E[r] = er;
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            const int64_t c = threadIdx.x + (int64_t)kThreads * p;
+            if (c >= ldq) break;
+            unsigned long long T = 0;
+            bool neg = false;
+            if (v[p] != 0.0) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(v[p]);
+                neg = (b >> 63) != 0;
+                const int be = (int)((b >> 52) & 0x7ff);
+                unsigned long long m = b & ((1ull << 52) - 1ull);
+                if (be != 0) m |= (1ull << 52);
+                const int shift = (be == 0 ? 1 : be) - 1075 + W - er;
+                if (shift >= 0) T = m << shift;
+                else T = (-shift >= 64) ? 0ull : (m >> (-shift));
+            }
+            for (int s = 0; s < slices; ++s) {
+                const int d = (int)((T >> (W - bits * (s + 1))) & dmask);
+                Q[((int64_t)s * n + r) * ldq + c] = (int8_t)(neg ? -d : d);
+            }
+        }
+        __syncthreads();                   // red[] is reused by the next row
+    }
+}
+
 __global__ void recombine_f64_kernel(const int32_t* __restrict__ P,
                                      int64_t ldp, const int32_t* __restrict__ E,
                                      int slices, int bits, int64_t n,
@@ -156,7 +216,7 @@ __global__ void recombine_f64_kernel(const int32_t* __restrict__ P,
         // power of two), only the additions round.
         for (int s = slices - 1; s >= 0; --s) {
             const int32_t p = P[((int64_t)s * n + r) * ldp + c];
-            z += ldexp((double)p, e - bits * (s + 1));
+            z += (double)p * pow2(e - bits * (s + 1));
         }
         Z[r * ldz + c] = z;
     }
@@ -276,6 +336,32 @@ afmm_status launch_slice_rows_i8(const void* A, int dtype, int64_t n,
     afmm_status rc = dispatch_dtype(dtype, [&]<int DT>() -> afmm_status {
         slice_rows_kernel<DT><<<grid2d(ldq, n), kThreads, 0, st>>>(
             A, n, lda, E, slices, bits, Q, ldq);
+        return AFMM_OK;
+    });
+    AFMM_TRY(rc);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
+}
+
+afmm_status launch_exp_slice_rows_i8(const void* A, int dtype, int64_t n,
+                                     int64_t lda, int32_t* E, int slices, int bits,
+                                     int8_t* Q, int64_t ldq, cudaStream_t st) {
+    if (n <= 0) return AFMM_OK;
+    if (bits < 1 || bits > 7 || slices < 1 || bits * slices > 63)
+        return AFMM_ERR_INVALID_ARG;
+    if (ldq > 4 * kThreads) {
+        AFMM_TRY(launch_row_exponents(A, dtype, n, lda, E, st));
+        return launch_slice_rows_i8(A, dtype, n, lda, E, slices, bits, Q, ldq, st);
+    }
+    const unsigned nb = (unsigned)(n < 65535 ? n : 65535);
+    afmm_status rc = dispatch_dtype(dtype, [&]<int DT>() -> afmm_status {
+        if (ldq <= kThreads)
+            exp_slice_rows_kernel<DT, 1><<<nb, kThreads, 0, st>>>(A, n, lda, E, slices, bits, Q,
+                                                                  ldq);
+        else
+            exp_slice_rows_kernel<DT, 4><<<nb, kThreads, 0, st>>>(A, n, lda, E, slices, bits, Q,
+                                                                  ldq);
         return AFMM_OK;
     });
     AFMM_TRY(rc);

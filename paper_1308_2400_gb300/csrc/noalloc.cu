@@ -90,8 +90,7 @@ afmm_status run_case_a(char* s, int64_t n, const void* X, int xdt, int64_t ldx,
     int8_t* Q = reinterpret_cast<int8_t*>(s + kOffQ);
     int32_t* W = reinterpret_cast<int32_t*>(s + kOffW);
     int32_t* P = reinterpret_cast<int32_t*>(s + kOffP);
-    AFMM_TRY(launch_row_exponents(X, xdt, n, ldx, E, st));
-    AFMM_TRY(launch_slice_rows_i8(X, xdt, n, ldx, E, kNoAllocSlices, kNoAllocBits, Q,
+    AFMM_TRY(launch_exp_slice_rows_i8(X, xdt, n, ldx, E, kNoAllocSlices, kNoAllocBits, Q,
                                   ld, st));
     AFMM_TRY(launch_pack_b_i8(Y, ydt, n, ldy, W, ld, status, st));
     AFMM_TRY(launch_simt_dp4a(Q, ld, W, ld, P, n, (int64_t)kNoAllocSlices * n, n, n,

@@ -119,7 +119,7 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
                                           int64_t ldb, typename Op::Acc* __restrict__ C,
                                           int64_t ldc, int64_t M, int64_t N, int64_t K,
                                           int vec, int64_t m0, int64_t n0,
-                                          unsigned char* smem_raw) {
+                                          unsigned char* smem_raw, bool accumulate = false) {
     using Elt = typename Op::Elt;
     using Acc = typename Op::Acc;
     using V4 = typename std::conditional<std::is_same<Elt, float>::value,
@@ -231,7 +231,26 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
             for (int c = 0; c < 8; ++c) acc[r][c] = part[r][c];
     }
 
-    // Epilogue: rows m0+row0+r, columns n0 + lane*4 (+128).
+    // Epilogue: rows m0+row0+r, columns n0 + lane*4 (+128).  With
+    // `accumulate` (integer K splits) the sums are added into C atomically,
+    // which is exact in any order.
+    if constexpr (std::is_same<Acc, int32_t>::value) {
+        if (accumulate) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int64_t gm = m0 + row0 + r;
+                if (gm >= M) break;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t gn = n0 + h * 128 + lane * 4;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (gn + c < N) atomicAdd(C + gm * ldc + gn + c, acc[r][4 * h + c]);
+                }
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int64_t gm = m0 + row0 + r;
@@ -261,10 +280,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 simt_gemm_kernel(const typename Op::Elt* __restrict__ A, int64_t lda,
                  const typename Op::Elt* __restrict__ B, int64_t ldb,
                  typename Op::Acc* __restrict__ C, int64_t ldc, int64_t M,
-                 int64_t N, int64_t K, int vec) {
+                 int64_t N, int64_t K, int vec, int64_t kchunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    simt_tile<Op>(A, lda, B, ldb, C, ldc, M, N, K, vec, (int64_t)blockIdx.y * BM,
-                  (int64_t)blockIdx.x * BN, smem_raw);
+    // blockIdx.z: the K split [k0, k0 + kchunk) (one split: all of K).
+    const int64_t k0 = (int64_t)blockIdx.z * kchunk;
+    const int64_t kn = K - k0 < kchunk ? K - k0 : kchunk;
+    simt_tile<Op>(A + k0, lda, B + k0 * ldb, ldb, C, ldc, M, N, kn, vec,
+                  (int64_t)blockIdx.y * BM, (int64_t)blockIdx.x * BN, smem_raw,
+                  gridDim.z > 1);
 }
 
 // Grouped form: block b runs tile b - tile_prefix[j] of job j, where
@@ -304,10 +327,27 @@ afmm_status launch_simt(const typename Op::Elt* A, int64_t lda,
                     aligned16(A) && aligned16(B) && aligned16(C);
     const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
     if (gy > 65535) return AFMM_ERR_UNSUPPORTED;
-    dim3 grid((unsigned)gx, (unsigned)gy);
+    // Integer products with fewer tiles than SMs split K (partial sums
+    // added atomically into a zeroed C; exact, so the order does not show).
+    int64_t kchunk = K > 0 ? K : 1, splits = 1;
+    if constexpr (std::is_same<typename Op::Acc, int32_t>::value) {
+        DeviceProps dp;
+        AFMM_TRY(device_props(&dp));
+        const int64_t tiles = gx * gy, ktiles = (K + BK - 1) / BK;
+        if (tiles < dp.sm_count && ktiles > 1) {
+            int64_t want = (2 * (int64_t)dp.sm_count + tiles - 1) / tiles;
+            if (want > ktiles) want = ktiles;
+            kchunk = (ktiles + want - 1) / want * BK;
+            splits = (K + kchunk - 1) / kchunk;
+        }
+    }
+    if (splits > 1)
+        AFMM_CUDA_TRY(cudaMemset2DAsync(C, ldc * sizeof(typename Op::Acc), 0,
+                                        N * sizeof(typename Op::Acc), M, st));
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)splits);
     main_kernel_begin(st);
     simt_gemm_kernel<Op><<<grid, THREADS, SMEM_BYTES, st>>>(A, lda, B, ldb, C,
-                                                           ldc, M, N, K, vec);
+                                                           ldc, M, N, K, vec, kchunk);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, (int)(gx * gy));
     count_launches(1);
