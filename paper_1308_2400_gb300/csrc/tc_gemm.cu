@@ -437,6 +437,231 @@ afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
 
 namespace {
 
+// Exact form with 256 x 256 output tiles: the two 128-row halves of a tile
+// share each B tile, so one 32-wide K step moves 2 x 8 KiB of A and 16 KiB
+// of B through shared memory for two 128 x 256 x 32 MMAs, two thirds of the
+// bytes per flop of a 128 x 256 tile (whose load path, not the tensor pipe,
+// bounds it).  The halves accumulate into TMEM columns [0,256) and
+// [256,512).  K is cut into chunks of kb_per_chunk k-blocks whose FP32
+// partial sums are exact integers; the epilogue converts each chunk to
+// int32 and stores it (first chunk) or adds it into Z (later chunks, exact).
+// Roles, bounded waits and the abort path are those of tc_gemm_kernel.
+constexpr int X2_BM = 256, X2_BN = 256;
+constexpr int X2_STAGE = 2 * A_TILE_BYTES + B_TILE_BYTES;   // 32 KiB
+constexpr int X2_STAGES = 6;
+constexpr int X2_SMEM = 1024 + X2_STAGES * X2_STAGE + 256;
+static_assert(X2_SMEM <= SMEM_OPTIN, "shared memory");
+static_assert(X2_STAGES <= 8, "barrier block");
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_exact2_kernel(const __grid_constant__ CUtensorMap tmA,
+                 const __grid_constant__ CUtensorMap tmB, int32_t* __restrict__ Z,
+                 int64_t ldz, int M, int N, int K, int kb_per_chunk, int vec, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = ptx::smem_addr(smem_raw);
+    uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    TcBars* bars = reinterpret_cast<TcBars*>(tiles + X2_STAGES * X2_STAGE);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_m = (M + X2_BM - 1) / X2_BM, tiles_n = (N + X2_BN - 1) / X2_BN;
+    const int num_tiles = tiles_m * tiles_n;
+    const int num_kb = (K + TC_BK - 1) / TC_BK;
+    const int kbpc = kb_per_chunk > 0 ? kb_per_chunk : num_kb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < X2_STAGES; ++s) {
+            ptx::mbar_init(&bars->full[s], 1);
+            ptx::mbar_init(&bars->empty[s], 1);
+        }
+        ptx::mbar_init(&bars->tfull[0], 1);
+        ptx::mbar_init(&bars->tempty[0], TC_EPI_THREADS);
+        ptx::mbar_init(&bars->drain, 1);
+        bars->abort = 0;
+        ptx::fence_barrier_init();
+        ptx::fence_proxy_async_smem();
+        ptx::prefetch_tmap(&tmA);
+        ptx::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(&bars->tmem_base, TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile int* abort = &bars->abort;
+
+    if (warp == 0) {
+        // ---------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued_phase[X2_STAGES];
+            for (int s = 0; s < X2_STAGES; ++s) issued_phase[s] = -1;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+                int tm, tn;
+                tile_coords(tile, tiles_m, tiles_n, tm, tn);
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!ptx::mbar_wait_bounded(&bars->empty[stage], phase ^ 1u, abort,
+                                                WAIT_LIMIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::mbar_arrive_expect_tx(&bars->full[stage], X2_STAGE);
+                    uint8_t* st = tiles + stage * X2_STAGE;
+                    ptx::tma_load_3d(st, &tmA, &bars->full[stage], kb * TC_BK, tm * X2_BM, 0);
+                    ptx::tma_load_3d(st + A_TILE_BYTES, &tmA, &bars->full[stage], kb * TC_BK,
+                                     tm * X2_BM + TC_BM, 0);
+                    ptx::tma_load_3d(st + 2 * A_TILE_BYTES, &tmB, &bars->full[stage],
+                                     kb * TC_BK, tn * X2_BN, 0);
+                    issued_phase[stage] = (int)phase;
+                    if (++stage == X2_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                raise_abort(bars, status);
+                // Let this CTA's copies in flight land before it exits.
+                volatile int never = 0;
+                for (int s = 0; s < X2_STAGES; ++s)
+                    if (issued_phase[s] >= 0)
+                        ptx::mbar_wait_bounded(&bars->full[s], (uint32_t)issued_phase[s],
+                                               &never, WAIT_LIMIT_NS);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t IDESC = ptx::idesc_bf16_f32(TC_BM, TC_BN);
+            int stage = 0;
+            uint32_t phase = 0, tphase = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+                for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kbpc) {
+                    // Both halves' accumulators are read out before a chunk starts.
+                    if (!ptx::mbar_wait_bounded(&bars->tempty[0], tphase ^ 1u, abort,
+                                                WAIT_LIMIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const int kb1 = min(kb0 + kbpc, num_kb);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
+                                                    WAIT_LIMIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        const uint32_t s0 = ptx::smem_addr(tiles + stage * X2_STAGE);
+                        const uint32_t b0 = s0 + 2 * A_TILE_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < TC_BK / 16; ++ks) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+                                ptx::mma_f16(tmem + (uint32_t)(h * TC_BN),
+                                             ptx::sdesc_kmajor_sw64(s0 + h * A_TILE_BYTES +
+                                                                    ks * 32),
+                                             ptx::sdesc_kmajor_sw64(b0 + ks * 32), IDESC,
+                                             (kb != kb0 || ks != 0) ? 1u : 0u);
+                        }
+                        ptx::mma_commit(&bars->empty[stage]);
+                        if (++stage == X2_STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    ptx::mma_commit(&bars->tfull[0]);
+                    tphase ^= 1u;
+                }
+            }
+            if (!ok) raise_abort(bars, status);
+            // Every MMA issued above completes before TMEM is released.
+            ptx::mma_commit(&bars->drain);
+            volatile int never = 0;
+            ptx::mbar_wait_bounded(&bars->drain, 0u, &never, WAIT_LIMIT_NS);
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------- epilogue
+        // Warp w reads TMEM lanes 32*(w%4).. of half h = (w-2)/4: tile row
+        // h*128 + 32*(w%4) + lane, 256 columns in two passes of 128.
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * TC_BN);
+        uint32_t tphase = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+            int tm, tn;
+            tile_coords(tile, tiles_m, tiles_n, tm, tn);
+            const int64_t m = (int64_t)tm * X2_BM + h * TC_BM + q * 32 + lane;
+            for (int kb0 = 0; kb0 < num_kb; kb0 += kbpc) {
+                const bool got = ptx::mbar_wait_bounded(&bars->tfull[0], tphase, abort,
+                                                        WAIT_LIMIT_NS);
+                // TMEM loads below are warp-collective: decide as a warp.
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) raise_abort(bars, status);
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const bool first = kb0 == 0;
+#pragma unroll 1
+                for (int ch = 0; ch < 2; ++ch) {
+                    int32_t v[128];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        uint32_t r[32];
+                        ptx::tmem_ld_32cols(lane_base + (uint32_t)(ch * 128 + c * 32), r);
+                        ptx::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[c * 32 + j] = __float2int_rn(__uint_as_float(r[j]));
+                    }
+                    const int col0 = tn * X2_BN + ch * 128;
+                    if (m < M) {
+                        int32_t* zr = Z + m * ldz + col0;
+                        if (vec && col0 + 128 <= N) {
+#pragma unroll
+                            for (int j = 0; j < 128; j += 4) {
+                                int4 o = make_int4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                                if (!first) {
+                                    const int4 z = *reinterpret_cast<const int4*>(zr + j);
+                                    o.x += z.x;
+                                    o.y += z.y;
+                                    o.z += z.z;
+                                    o.w += z.w;
+                                }
+                                *reinterpret_cast<int4*>(zr + j) = o;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 128; ++j)
+                                if (col0 + j < N) zr[j] = first ? v[j] : zr[j] + v[j];
+                        }
+                    }
+                }
+                // TMEM is free again.
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&bars->tempty[0]);
+                tphase ^= 1u;
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
 template <int SA, int SB, int MODE, bool TOUT = false>
 afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
                       int* status, cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0,
@@ -459,6 +684,28 @@ afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
     main_kernel_begin(st);
     tc_gemm_kernel<SA, SB, MODE, TOUT><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
         ma, mb, Z, ldz, m0, m1, n0, n1, n, kb_per_chunk, vec, status);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    main_kernel_end(st, grid);
+    count_launches(1);
+    return AFMM_OK;
+}
+
+afmm_status launch_exact2(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
+                          int* status, cudaStream_t st) {
+    DeviceProps dp;
+    AFMM_TRY(device_props(&dp));
+    const int n = (int)t->n;
+    const int tiles = ((n + X2_BM - 1) / X2_BM) * ((n + X2_BN - 1) / X2_BN);
+    const int grid = tiles < dp.sm_count ? tiles : dp.sm_count;
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_exact2_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, X2_SMEM));
+    const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
+    CUtensorMap ma, mb;
+    std::memcpy(&ma, t->tmap_a, sizeof ma);
+    std::memcpy(&mb, t->tmap_b, sizeof mb);
+    main_kernel_begin(st);
+    tc_exact2_kernel<<<grid, TC_THREADS, X2_SMEM, st>>>(ma, mb, static_cast<int32_t*>(Z), ldz,
+                                                         n, n, n, kb_per_chunk, vec, status);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, grid);
     count_launches(1);
@@ -623,7 +870,7 @@ afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
                                          status, st)));
     AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                               t->lim_b, status, st)));
-    return launch_tc<1, 1, 1>(t, Z, d.ldz, t->kb_per_chunk, status, st);
+    return launch_exact2(t, Z, d.ldz, t->kb_per_chunk, status, st);
 }
 
 afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int* status,
