@@ -23,6 +23,8 @@ mu') with explicit laws:
   batched_512        512 instances, n log-uniform in [64,2048], d1, d2
                      U[0.05,1], mu in {0.5,1,2,4,8} (Poisson Rep-factors),
                      real factor FP32 N(0,1), cases A/B half and half.
+  table1_point       case A at Table 1's points: n 250..2000, (mu', d1, d2)
+                     in {1,3,5,7} x (1/3, 1/2) and {14,21} x (1/5, 2/5).
 
 Density reading: values are drawn from the law, then each entry is kept with
 probability d / (1 - P(value == 0)) (capped at 1), so the realised fraction
@@ -39,7 +41,7 @@ from typing import List, Optional
 import numpy as np
 
 __all__ = ["Instance", "WORKLOADS", "make", "batched_mix", "rng_for",
-           "encode_e4m3_integers"]
+           "encode_e4m3_integers", "table1_point", "TABLE1_POINTS", "TABLE1_SIZES"]
 
 
 @dataclass
@@ -162,6 +164,35 @@ def make(workload: str, n: Optional[int] = None, seed: int = 0) -> Instance:
     inst = fn(int(n_default if n is None else n), int(seed))
     inst.name = f"{workload}" if n is None else f"{workload}@n={n}"
     return inst
+
+
+# Table 1's parameter points (Sec. 3): (mu', d1, d2) and the sizes n.
+TABLE1_POINTS = ((1.0, 1 / 3, 1 / 2), (3.0, 1 / 3, 1 / 2), (5.0, 1 / 3, 1 / 2),
+                 (7.0, 1 / 3, 1 / 2), (14.0, 1 / 5, 2 / 5), (21.0, 1 / 5, 2 / 5))
+TABLE1_SIZES = (250, 500, 750, 1000, 1250, 1500, 1750, 2000)
+
+
+def table1_point(n: int, mu_prime: float, d1: float, d2: float,
+                 seed: int = 0) -> Instance:
+    """Case A at one of Table 1's parameter points.
+
+    X FP32 U(-1,1) with density d1.  Y Rep-factors (uint8) with density d2
+    whose non-zero values are 1 + Poisson(mu' - 1) -- all ones for mu' = 1 --
+    so that their mean is mu' (the paper names mu', d1 and d2 only).
+    """
+    rx, ry, rm1, rm2 = (rng_for(seed, 11), rng_for(seed, 12), rng_for(seed, 13),
+                        rng_for(seed, 14))
+    X = rx.uniform(-1.0, 1.0, size=(n, n)).astype(np.float32)
+    X[~_keep_mask(rm1, (n, n), d1, 1.0)] = 0.0
+    if mu_prime > 1.0:
+        Y = 1 + ry.poisson(mu_prime - 1.0, size=(n, n))
+    else:
+        Y = np.ones((n, n), dtype=np.int64)
+    Y = np.minimum(Y, 255).astype(np.uint8)
+    Y[~_keep_mask(rm2, (n, n), d2, 1.0)] = 0
+    return Instance("A", X, Y, name=f"table1[n={n},mu'={mu_prime:g}]", x_dtype="f32",
+                    y_dtype="u8", z_dtype="f32", target="fp32",
+                    params={"mu_prime": mu_prime, "d1": d1, "d2": d2})
 
 
 def batched_mix(count: int = 512, seed: int = 0, n_min: int = 64,

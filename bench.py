@@ -543,6 +543,83 @@ def run_batched(args):
     return 0
 
 
+# Table 1 of the paper (Sec. 3): mean seconds on a 1.6 GHz Pentium for the
+# classical ikj loop and AFMM at mu' = 1, 3, 5, 7 (d1 = 1/3, d2 = 1/2) and
+# 14, 21 (d1 = 1/5, d2 = 2/5).  Context only: other hardware and precision.
+TABLE1_SECONDS = {
+    250: (0.328, 0.1752, 0.2784, 0.3316, 0.3498, 0.3188, 0.2874),
+    500: (2.32, 0.918, 1.5406, 1.943, 2.331, 1.9122, 1.9874),
+    750: (7.75533, 2.8475, 4.9718, 6.38, 7.6826, 6.3218, 6.4328),
+    1000: (18.43233, 6.67175, 11.8064, 15.073, 18.2756, 14.9158, 15.3374),
+    1250: (35.75, 13.0897, 23.0705, 29.489, 35.594, 29.172, 29.9267),
+    1500: (61.688, 22.5625, 40.078, 50.9295, 61.718, 50.3515, 52.2),
+    1750: (98.515, 36.0235, 63.2655, 80.6235, 97.6955, 80.281, 81.9335),
+    2000: (147.078, 53.375, 94.6875, 120.8515, 145.8985, 119.516, 122.491),
+}
+
+
+def run_table1(args):
+    """The paper's own parameter grid (Table 1: n = 250..2000, six (mu', d1,
+    d2) points), Case A, FP32 target, planner's choice of variant: GPU time
+    per product beside the paper's CPU times, which are context only."""
+    import numpy as np
+    import torch
+    import afmm_inputs as W
+    from oracle import afmm_case_a, realised_parameters
+    from paper_1308_2400_gb300 import Plan, make_desc
+    from paper_1308_2400_gb300.afmm import VARIANT_NAMES
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    rows_out, worst = [], 0.0
+    clk = ClockSampler(0)
+    clk.start()
+    for n in W.TABLE1_SIZES:
+        for j, (mu, d1, d2) in enumerate(W.TABLE1_POINTS):
+            inst = W.table1_point(n, mu, d1, d2, seed=n)
+            prm = realised_parameters(inst.X, inst.Y, "A")
+            X = torch.from_numpy(inst.X).cuda()
+            Y = torch.from_numpy(inst.Y).cuda()
+            Z = torch.empty((n, n), dtype=torch.float32, device="cuda")
+            plan = Plan(make_desc(n, "A", "f32", "u8", "f32", "fp32", d1=prm["d1"],
+                                  d2=prm["d2"], mu_prime=prm["mu_prime"]))
+            with torch.cuda.stream(stream):
+                for _ in range(max(3, args.warmup)):
+                    plan(X, Y, Z, stream)
+                plan.sync(stream)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    plan(X, Y, Z, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                plan.sync(stream)
+            ms = e0.elapsed_time(e1) / args.steps
+            r = np.arange(0, n, max(1, n // 8))
+            R = afmm_case_a(inst.X, inst.Y, r)[0]
+            err = float(np.linalg.norm(Z.cpu().numpy()[r] - R) / np.linalg.norm(R))
+            worst = max(worst, err)
+            paper = TABLE1_SECONDS[n]
+            rows_out.append({
+                "n": n, "mu_prime": mu, "d1": round(d1, 4), "d2": round(d2, 4),
+                "variant": VARIANT_NAMES.get(plan.info["variant"], "?"),
+                "gpu_ms": ms, "gpu_tflops_2n3": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                "additions_mu_d1_d2_n3": mu * d1 * d2 * n ** 3,
+                "paper_afmm_s": paper[1 + j], "paper_ikj_s": paper[0],
+                "rel_fro_err_rows": err})
+            plan.close()
+    clocks = clk.stop()
+    tot = sum(r["gpu_ms"] for r in rows_out)
+    line = {"metric": "Table 1 grid: GPU ms per product (FP32 target)",
+            "value": tot / len(rows_out), "unit": "ms (mean over the grid)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "table1_sweep", "points": len(rows_out)},
+            "max_rel_fro_err": worst, "clocks": clocks, "table": rows_out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -563,6 +640,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched_512":
         return run_batched(args)
+    if args.workload == "table1_sweep":
+        return run_table1(args)
     return run_afmm(args)
 
 
