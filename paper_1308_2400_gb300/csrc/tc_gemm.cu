@@ -1,5 +1,5 @@
 // Tensor-core AFMM product on sm_103a: tcgen05 MMA with TMEM accumulators,
-// operands brought in by TMA, warp-specialised persistent kernel.
+// operands brought in by TMA, warp-specialised persistent kernels.
 //
 // The AFMM term Rep * Base (Sec. 2: Base added Rep-factor times) is an exact
 // integer multiple of the Base value.  On the tensor cores it is formed as a
@@ -9,17 +9,23 @@
 //  - the real Base factor is split into S BF16 slices, hi + mid + lo, each
 //    the round-to-nearest BF16 of the previous residual, so that for S = 3 the
 //    slices sum exactly to an FP32 value;
-//  - Z = sum_s X_s * Y (case A) or X * sum_s Y_s (case B): one FP32 TMEM
-//    accumulator per output tile takes all S products of every k step, the
-//    Rep-factor tile being loaded once and reused for the S slices.
+//  - the slices are always the A operand: Case A multiplies X's slices by
+//    Y, Case B computes Z^T = Y^T X^T with Y's slices and stores the tiles
+//    transposed; the Rep-factor tile of a k step is loaded once and used by
+//    the S MMAs.
 //
-// Kernel layout (one CTA per SM, persistent over 128 x 256 output tiles):
+// tc_gemm_kernel (split form; one CTA per SM, persistent over 128 x 256
+// output tiles):
 //   warp 0      TMA producer: K steps of 32 (64-byte swizzled rows) of every
-//               slice of A and B into a ring of shared-memory stages;
-//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32
-//               accumulators) and issues the MMAs (128 x 256 x 16 each);
-//   warps 2..5  epilogue: TMEM -> registers -> Z (FP32), overlapping the
-//               next tile's MMAs through the second accumulator.
+//               slice of A and of B into a ring of shared-memory stages;
+//   warp 1      allocates 512 TMEM columns and issues the MMAs
+//               (128 x 256 x 16): the hi slice's products into columns
+//               [0,256), the smaller slices' into [256,512), so that a small
+//               product is never added into a much larger sum;
+//   warps 2..9  epilogue: TMEM -> registers (the two sums added with one
+//               rounding) -> Z; the next tile's MMAs start as soon as the
+//               TMEM has been read, while the stores are in flight.
+// tc_exact2_kernel (exact form; 256 x 256 tiles): see there.
 // Every wait on an mbarrier is bounded (2 s); a wait that runs out records
 // AFMM_ERR_TIMEOUT in the status word, stops the other roles, lets copies
 // and MMAs in flight finish (bounded) and frees TMEM before returning.
@@ -93,12 +99,11 @@ __device__ __forceinline__ void raise_abort(TcBars* b, int* status) {
 
 // TOUT: the product computed is Z^T (A = the operand whose rows are Z's
 // columns); the epilogue stores tile element (m, n) at Z[n][m].
-template <int SA, int SB, int MODE, bool TOUT = false>
+template <int SA, int SB, bool TOUT = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-               const __grid_constant__ CUtensorMap tmB, void* __restrict__ Zv,
-               int64_t ldz, int m0, int M, int n0, int N, int K, int kb_per_chunk, int vec,
-               int* status) {
+               const __grid_constant__ CUtensorMap tmB, float* __restrict__ Z,
+               int64_t ldz, int m0, int M, int n0, int N, int K, int vec, int* status) {
     using Cfg = TcCfg<SA, SB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
@@ -190,111 +195,53 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            if constexpr (MODE == 0) {
-                // Split form: per tile two 128 x 256 FP32 accumulators in
-                // TMEM, columns [0,256) for the products of the hi slice and
-                // [256,512) for those of the smaller slices, so a small
-                // product is never added into a sum of much larger
-                // magnitude.  The epilogue adds the two.
-                uint32_t tphase = 0;
-                for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-                    if (!ptx::mbar_wait_bounded(&bars->tempty[0], tphase ^ 1u, abort,
+            // Split form: per tile two 128 x 256 FP32 accumulators in
+            // TMEM, columns [0,256) for the products of the hi slice and
+            // [256,512) for those of the smaller slices, so a small
+            // product is never added into a sum of much larger
+            // magnitude.  The epilogue adds the two.
+            uint32_t tphase = 0;
+            for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+                if (!ptx::mbar_wait_bounded(&bars->tempty[0], tphase ^ 1u, abort,
+                                            WAIT_LIMIT_NS)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
                                                 WAIT_LIMIT_NS)) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    for (int kb = 0; kb < num_kb; ++kb) {
-                        if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
-                                                    WAIT_LIMIT_NS)) {
-                            ok = false;
-                            break;
-                        }
-                        ptx::tc_fence_after();
-                        const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
+                    const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
 #pragma unroll
-                        for (int ks = 0; ks < TC_BK / 16; ++ks) {
+                    for (int ks = 0; ks < TC_BK / 16; ++ks) {
 #pragma unroll
-                            for (int p = Cfg::P - 1; p >= 0; --p) {
-                                const uint32_t a_addr =
-                                    s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
-                                const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
-                                                        (SB > 1 ? p : 0) * B_TILE_BYTES +
-                                                        ks * 32;
-                                const bool first = kb == 0 && ks == 0 &&
-                                                   (p == 0 || p == Cfg::P - 1);
-                                ptx::mma_f16(tmem + (p == 0 ? 0u : (uint32_t)TC_BN),
-                                             ptx::sdesc_kmajor_sw64(a_addr),
-                                             ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                             first ? 0u : 1u);
-                            }
-                        }
-                        ptx::mma_commit(&bars->empty[stage]);
-                        if (++stage == Cfg::STAGES) {
-                            stage = 0;
-                            phase ^= 1u;
+                        for (int p = Cfg::P - 1; p >= 0; --p) {
+                            const uint32_t a_addr =
+                                s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
+                            const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
+                                                    (SB > 1 ? p : 0) * B_TILE_BYTES +
+                                                    ks * 32;
+                            const bool first = kb == 0 && ks == 0 &&
+                                               (p == 0 || p == Cfg::P - 1);
+                            ptx::mma_f16(tmem + (p == 0 ? 0u : (uint32_t)TC_BN),
+                                         ptx::sdesc_kmajor_sw64(a_addr),
+                                         ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                         first ? 0u : 1u);
                         }
                     }
-                    if (!ok) break;
-                    ptx::mma_commit(&bars->tfull[0]);
-                    tphase ^= 1u;
-                }
-            } else {
-                // Exact form: each tile's K range is cut into chunks of kbpc
-                // k-blocks short enough that every partial sum stays an
-                // exact integer in FP32; chunk c of the CTA accumulates from
-                // zero into TMEM slot c % 2 while the epilogue converts the
-                // previous one to int32.
-                const int kbpc = kb_per_chunk > 0 ? kb_per_chunk : num_kb;
-                uint32_t slot_phase[2] = {0u, 0u};
-                int chunk = 0;
-                for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-                    for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kbpc) {
-                        const int slot = chunk & 1;
-                        if (!ptx::mbar_wait_bounded(&bars->tempty[slot],
-                                                    slot_phase[slot] ^ 1u, abort,
-                                                    WAIT_LIMIT_NS)) {
-                            ok = false;
-                            break;
-                        }
-                        ptx::tc_fence_after();
-                        const uint32_t d = tmem + (uint32_t)(slot * TC_BN);
-                        const int kb1 = min(kb0 + kbpc, num_kb);
-                        for (int kb = kb0; kb < kb1; ++kb) {
-                            if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
-                                                        WAIT_LIMIT_NS)) {
-                                ok = false;
-                                break;
-                            }
-                            ptx::tc_fence_after();
-                            const uint32_t s0 =
-                                ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
-#pragma unroll
-                            for (int ks = 0; ks < TC_BK / 16; ++ks) {
-#pragma unroll
-                                for (int p = 0; p < Cfg::P; ++p) {
-                                    const uint32_t a_addr =
-                                        s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
-                                    const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
-                                                            (SB > 1 ? p : 0) * B_TILE_BYTES +
-                                                            ks * 32;
-                                    ptx::mma_f16(d, ptx::sdesc_kmajor_sw64(a_addr),
-                                                 ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                                 (kb != kb0 || ks != 0 || p != 0) ? 1u : 0u);
-                                }
-                            }
-                            ptx::mma_commit(&bars->empty[stage]);
-                            if (++stage == Cfg::STAGES) {
-                                stage = 0;
-                                phase ^= 1u;
-                            }
-                        }
-                        if (!ok) break;
-                        ptx::mma_commit(&bars->tfull[slot]);
-                        slot_phase[slot] ^= 1u;
-                        ++chunk;
+                    ptx::mma_commit(&bars->empty[stage]);
+                    if (++stage == Cfg::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
                     }
                 }
+                if (!ok) break;
+                ptx::mma_commit(&bars->tfull[0]);
+                tphase ^= 1u;
             }
             if (!ok) raise_abort(bars, status);
             // Every MMA issued above completes before TMEM is released.
@@ -307,81 +254,55 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
         // ---------------------------------------------------- epilogue
         // 8 warps: warp w reads TMEM lanes 32*(w%4).. (its rows) and half
         // h of the 256 columns, 128 values per thread.
-        using Acc = typename std::conditional<MODE == 0, float, int32_t>::type;
         const int q = warp & 3;
         const int h = (warp - 2) >> 2;
         const int row = q * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
-        uint32_t slot_phase[2] = {0u, 0u};
-        int chunk = 0;
-        const int kbpc = (MODE == 0 || kb_per_chunk <= 0) ? num_kb : kb_per_chunk;
-        bool ok = true;
-        for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+        uint32_t tphase = 0;
+        for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
             int tm, tn;
             tile_coords(tile, tiles_m, tiles_n, tm, tn);
-            Acc sum[128];
-#pragma unroll
-            for (int j = 0; j < 128; ++j) sum[j] = Acc(0);
-            for (int kb0 = 0; kb0 < num_kb; kb0 += kbpc) {
-                const int slot = MODE == 0 ? 0 : (chunk & 1);
-                const bool got = ptx::mbar_wait_bounded(&bars->tfull[slot],
-                                                        slot_phase[slot], abort,
-                                                        WAIT_LIMIT_NS);
-                // TMEM loads below are warp-collective: decide as a warp.
-                if (!__all_sync(0xffffffffu, got)) {
-                    if (lane == 0) raise_abort(bars, status);
-                    ok = false;
-                    break;
-                }
-                ptx::tc_fence_after();
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t r0[32], r1[32];
-                    if constexpr (MODE == 0) {
-                        // hi-slice sum + small-slice sum, one rounding.
-                        ptx::tmem_ld_32cols(lane_base + (uint32_t)(c * 32), r0);
-                        ptx::tmem_ld_32cols(lane_base + (uint32_t)(TC_BN + c * 32), r1);
-                        ptx::tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            sum[c * 32 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
-                    } else {
-                        ptx::tmem_ld_32cols(lane_base + (uint32_t)(slot * TC_BN + c * 32), r0);
-                        ptx::tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            sum[c * 32 + j] += __float2int_rn(__uint_as_float(r0[j]));
-                    }
-                }
-                // TMEM is free again before the stores below.
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(&bars->tempty[slot]);
-                slot_phase[slot] ^= 1u;
-                ++chunk;
+            const bool got = ptx::mbar_wait_bounded(&bars->tfull[0], tphase, abort,
+                                                    WAIT_LIMIT_NS);
+            // TMEM loads below are warp-collective: decide as a warp.
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) raise_abort(bars, status);
+                break;
             }
-            if (!ok) break;
+            ptx::tc_fence_after();
+            float sum[128];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                // hi-slice sum + small-slice sum, one rounding.
+                uint32_t r0[32], r1[32];
+                ptx::tmem_ld_32cols(lane_base + (uint32_t)(c * 32), r0);
+                ptx::tmem_ld_32cols(lane_base + (uint32_t)(TC_BN + c * 32), r1);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    sum[c * 32 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+            }
+            // TMEM is free again before the stores below.
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars->tempty[0]);
+            tphase ^= 1u;
             const int64_t m = (int64_t)m0 + (int64_t)tm * TC_BM + row;
             const int col0 = n0 + tn * TC_BN + h * 128;
             if (TOUT && m < M) {
                 // Element (m, col0 + j) of Z^T is Z[col0 + j][m]: the lanes of
                 // a warp hold consecutive m, so each store writes one
                 // 128-byte segment of a row of Z.
-                Acc* zc = static_cast<Acc*>(Zv) + m;
+                float* zc = Z + m;
 #pragma unroll
                 for (int j = 0; j < 128; ++j)
                     if (col0 + j < N) zc[(int64_t)(col0 + j) * ldz] = sum[j];
             } else if (m < M) {
-                Acc* zr = static_cast<Acc*>(Zv) + m * ldz + col0;
+                float* zr = Z + m * ldz + col0;
                 if (vec && col0 + 128 <= N) {
 #pragma unroll
-                    for (int j = 0; j < 128; j += 4) {
-                        if constexpr (MODE == 0)
-                            *reinterpret_cast<float4*>(zr + j) =
-                                make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
-                        else
-                            *reinterpret_cast<int4*>(zr + j) =
-                                make_int4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
-                    }
+                    for (int j = 0; j < 128; j += 4)
+                        *reinterpret_cast<float4*>(zr + j) =
+                            make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
                 } else {
 #pragma unroll
                     for (int j = 0; j < 128; ++j)
@@ -662,10 +583,9 @@ tc_exact2_kernel(const __grid_constant__ CUtensorMap tmA,
     }
 }
 
-template <int SA, int SB, int MODE, bool TOUT = false>
-afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
-                      int* status, cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0,
-                      int n1 = -1) {
+template <int SA, int SB, bool TOUT = false>
+afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaStream_t st,
+                      int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
     using Cfg = TcCfg<SA, SB>;
     DeviceProps dp;
     AFMM_TRY(device_props(&dp));
@@ -674,7 +594,7 @@ afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
     if (n1 < 0) n1 = n;
     const int tiles = ((m1 - m0 + TC_BM - 1) / TC_BM) * ((n1 - n0 + TC_BN - 1) / TC_BN);
     const int grid = tiles < dp.sm_count ? tiles : dp.sm_count;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, MODE, TOUT>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, TOUT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
@@ -682,8 +602,8 @@ afmm_status launch_tc(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
     std::memcpy(&ma, TOUT ? t->tmap_at : t->tmap_a, sizeof ma);
     std::memcpy(&mb, TOUT ? t->tmap_bt : t->tmap_b, sizeof mb);
     main_kernel_begin(st);
-    tc_gemm_kernel<SA, SB, MODE, TOUT><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
-        ma, mb, Z, ldz, m0, m1, n0, n1, n, kb_per_chunk, vec, status);
+    tc_gemm_kernel<SA, SB, TOUT><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
+        ma, mb, Z, ldz, m0, m1, n0, n1, n, vec, status);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, grid);
     count_launches(1);
@@ -840,8 +760,8 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
         AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                   256.f, status, st)));
         return t->slices == 3
-                   ? launch_tc<3, 1, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
-                   : launch_tc<2, 1, 0>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
+                   ? launch_tc<3, 1>(t, Zf, d.ldz, status, st)
+                   : launch_tc<2, 1>(t, Zf, d.ldz, status, st);
     }
     // Case B: A = Rep-factors X (rows), B = slices of the real Y transposed.
     AFMM_TRY((tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, A, t->ld_a, 256.f,
@@ -855,8 +775,8 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
     // Computed as Z^T = Y^T X^T: the slices on the A side, as in Case A, so
     // a stage holds S + 1 tiles of 8 + 16 KiB instead of 1 + S of 8 + 16 x S.
     return t->slices == 3
-               ? launch_tc<3, 1, 0, true>(t, Zf, d.ldz, t->kb_per_chunk, status, st)
-               : launch_tc<2, 1, 0, true>(t, Zf, d.ldz, t->kb_per_chunk, status, st);
+               ? launch_tc<3, 1, true>(t, Zf, d.ldz, status, st)
+               : launch_tc<2, 1, true>(t, Zf, d.ldz, status, st);
 }
 
 afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
@@ -896,12 +816,13 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
         AFMM_TRY(tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 256.f, status,
                                st, r0, r1));
     const int m0 = (int)r0, m1 = (int)r1;
+    float* Zf = static_cast<float*>(Z);
     if (d.kase == AFMM_CASE_A)
-        return sl == 3 ? launch_tc<3, 1, 0>(t, Z, d.ldz, 0, status, st, m0, m1)
-                       : launch_tc<2, 1, 0>(t, Z, d.ldz, 0, status, st, m0, m1);
+        return sl == 3 ? launch_tc<3, 1>(t, Zf, d.ldz, status, st, m0, m1)
+                       : launch_tc<2, 1>(t, Zf, d.ldz, status, st, m0, m1);
     // Case B (Z^T = Y^T X^T): rows [r0, r1) of Z are columns of the product.
-    return sl == 3 ? launch_tc<3, 1, 0, true>(t, Z, d.ldz, 0, status, st, 0, -1, m0, m1)
-                   : launch_tc<2, 1, 0, true>(t, Z, d.ldz, 0, status, st, 0, -1, m0, m1);
+    return sl == 3 ? launch_tc<3, 1, true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1)
+                   : launch_tc<2, 1, true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1);
 }
 
 int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb) {
