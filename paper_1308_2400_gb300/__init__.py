@@ -4,7 +4,7 @@ The compute path is ``libafmm.so`` (hand-written CUDA behind the C ABI in
 ``include/afmm.h``); this package only marshals arguments to it.
 """
 from . import afmm  # noqa: F401
-from .afmm import (AfmmError, Plan, afmm_error_norm,  # noqa: F401
+from .afmm import (AfmmError, Plan, afmm_batched_sync, afmm_error_norm,  # noqa: F401
                    afmm_error_norm_workspace_size, afmm_get_info,
                    afmm_mul_batched, afmm_mul_caseA,
                    afmm_plan_counters, afmm_plan_enable_kernel_timing, afmm_mul_caseB,

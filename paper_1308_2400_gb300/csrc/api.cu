@@ -282,6 +282,7 @@ void plan_layout(afmm_plan_s* p) {
                             : 1;
             p->off_a = L.take(p->tc.a_bytes);
             p->off_b = L.take(p->tc.b_bytes);
+            p->off_c = L.take(p->tc.z_bytes);
             break;
         }
         default:
@@ -313,8 +314,8 @@ afmm_status ensure_workspace(afmm_plan_s* p, cudaStream_t st) {
         if (p->variant == AFMM_VARIANT_TC_BF16X3 ||
             p->variant == AFMM_VARIANT_TC_BF16X2 ||
             p->variant == AFMM_VARIANT_TC_EXACT)
-            AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a,
-                                       p->ws + p->off_b));
+            AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a, p->ws + p->off_b,
+                                       p->ws + p->off_c));
         if (p->variant == AFMM_VARIANT_SPARSE) AFMM_TRY(sparse_reset(p->ws + p->off_a, st));
         p->ws_ready = true;
     }

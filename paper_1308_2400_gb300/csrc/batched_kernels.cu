@@ -91,11 +91,18 @@ __device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags
     bool bad = false;
     for (int64_t c = 8 * threadIdx.x; c < ldk; c += 8 * 128) {
         float v[8];
+        // FP32 rows that start off a 16-byte boundary: aligned loads and a shift.
+        constexpr bool kF32 = DT == AFMM_F32;
+        const bool shifted = kF32 && !vec && (reinterpret_cast<uintptr_t>(g.X) & 15u) == 0 &&
+                             c + 12 <= n;
         if (vec && c + 8 <= n) {
             alignas(16) T e[8];
             load8<DT>(x, c, e);
 #pragma unroll
             for (int t = 0; t < 8; ++t) v[t] = value_checked<DT>(e[t], 256.f, bad);
+        } else if (shifted) {
+            const float* p = reinterpret_cast<const float*>(x) + c;
+            load8_f32_shifted(p, (int)((reinterpret_cast<uintptr_t>(p) & 15u) >> 2), v);
         } else {
 #pragma unroll
             for (int t = 0; t < 8; ++t)

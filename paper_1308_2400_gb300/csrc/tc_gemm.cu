@@ -716,11 +716,17 @@ void tc_layout(TcPlan* t, const afmm_desc& d, int slices) {
     t->rows_b = d.n;
     t->a_bytes = (size_t)sa * d.n * t->ld_a * 2;
     t->b_bytes = (size_t)sb * d.n * t->ld_b * 2;
+    const int64_t ldz = d.ldz ? d.ldz : d.n;
+    if (t->sliced_a && ldz % 4 != 0) {
+        t->ld_z = (d.n + 3) / 4 * 4;
+        t->z_bytes = (size_t)d.n * t->ld_z * 4;
+    }
 }
 
-afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b) {
+afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z) {
     t->a = a;
     t->b = b;
+    t->z = t->z_bytes ? z : nullptr;
     t->maps_ready = false;
     if (t->n <= 0) return AFMM_OK;
     const int sl = t->slices > 0 ? t->slices : 1;
@@ -759,6 +765,17 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                                                   0.f, status, st)));
         AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                   256.f, status, st)));
+        if (t->z) {
+            // Rows of Z off 16-byte boundaries: product into the aligned
+            // buffer, then one 2-D copy.
+            float* zt = static_cast<float*>(t->z);
+            AFMM_TRY((t->slices == 3 ? launch_tc<3, 1>(t, zt, t->ld_z, status, st)
+                                     : launch_tc<2, 1>(t, zt, t->ld_z, status, st)));
+            AFMM_CUDA_TRY(cudaMemcpy2DAsync(Zf, d.ldz * sizeof(float), zt,
+                                            t->ld_z * sizeof(float), n * sizeof(float), n,
+                                            cudaMemcpyDeviceToDevice, st));
+            return AFMM_OK;
+        }
         return t->slices == 3
                    ? launch_tc<3, 1>(t, Zf, d.ldz, status, st)
                    : launch_tc<2, 1>(t, Zf, d.ldz, status, st);

@@ -22,6 +22,12 @@ struct TcPlan {
     bool sliced_a = true;           // real factor on the A side (case A)
     int kb_per_chunk = 0;           // exact form: K chunk in 32-wide k-blocks
     float lim_a = 256.f, lim_b = 256.f;  // exact form: largest |value| allowed
+    // Case A split form with rows of Z not 16-byte aligned (ldz % 4 != 0):
+    // the product goes to this buffer (ld_z = n rounded up to 4, so its
+    // epilogue stores stay 16-byte wide) and is copied into Z.
+    size_t z_bytes = 0;
+    int64_t ld_z = 0;
+    void* z = nullptr;
     alignas(64) unsigned char tmap_a[128];
     alignas(64) unsigned char tmap_b[128];
     // Case B split form computed as Z^T = Y^T X^T: A side = the b buffer.
@@ -55,7 +61,7 @@ void tc_layout(TcPlan* t, const afmm_desc& d, int slices);
 // Largest K chunk (multiple of 32) with chunk * amax * bmax < 2^24, or 0
 // when even one 32-wide block could overflow.
 int tc_exact_chunk_k(double amax, double bmax);
-afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b);
+afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z);
 // Split / widen the operands and run the tcgen05 product into Z (F32).
 afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st);

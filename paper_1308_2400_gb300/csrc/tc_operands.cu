@@ -68,11 +68,20 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
             }
         }
         if constexpr (DT == AFMM_F32) {
-            if (vec && c + 8 <= n) {
-                const float4* p = reinterpret_cast<const float4*>(
-                    static_cast<const float*>(src) + r * lds + c);
-                const float4 a = p[0], b = p[1];
-                const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            const float* p = static_cast<const float*>(src) + r * lds + c;
+            // Aligned rows: two 16-byte loads; rows that start off a 16-byte
+            // boundary (lds % 4 != 0): three aligned loads and a shift.
+            const bool al = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+            if ((vec && c + 8 <= n) || (al && c + 12 <= n)) {
+                float v[8];
+                if (vec) {
+                    const float4 a = reinterpret_cast<const float4*>(p)[0];
+                    const float4 b = reinterpret_cast<const float4*>(p)[1];
+                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                } else {
+                    load8_f32_shifted(p, (int)((reinterpret_cast<uintptr_t>(p) & 15u) >> 2), v);
+                }
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                     __nv_bfloat16 o0[S], o1[S];

@@ -30,6 +30,34 @@ __device__ __forceinline__ void load8(const void* p, int64_t i,
     }
 }
 
+// p[0 .. 7] for a float pointer p that lies `off` floats (0..3) past a
+// 16-byte boundary: three aligned 16-byte loads from p - off and the eight
+// wanted values.  The caller keeps p - off .. p - off + 11 inside the
+// allocation.
+__device__ __forceinline__ void load8_f32_shifted(const float* p, int off, float (&v)[8]) {
+    const float4* q = reinterpret_cast<const float4*>(p - off);
+    const float4 a = q[0], b = q[1], c = q[2];
+    const float f[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    switch (off) {
+        case 0:
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = f[t];
+            break;
+        case 1:
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = f[t + 1];
+            break;
+        case 2:
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = f[t + 2];
+            break;
+        default:
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = f[t + 3];
+            break;
+    }
+}
+
 // Element value as float; `bad` records an int32 beyond lim (checked in
 // integer arithmetic, so values past 2^24 cannot slip through a rounding)
 // or an FP64 value that FP32 does not hold.
