@@ -46,36 +46,46 @@
 #include <omp.h>
 #endif
 
-/* Case A (Sec. 2, Case-A): X real, Y integer Rep-factors. */
+/* Case A (Sec. 2, Case-A): X real, Y integer Rep-factors.  The *_cols
+ * forms compute the columns [j0, j1) of the rows [i0, i1) of Z (Z holds
+ * j1 - j0 values per row), with every element formed exactly as in the
+ * full row; the plain forms are the window [0, n). */
+int afmm_oracle_caseA_f64_cols(int64_t n, int64_t i0, int64_t i1, int64_t j0,
+                               int64_t j1, const double* X, const int64_t* Y,
+                          double* Z, uint64_t* adds_out)
+{
+    int64_t bad = 0;
+    uint64_t adds = 0;
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : adds, bad)
+    for (i = i0; i < i1; ++i) {
+        double* z = Z + (i - i0) * (j1 - j0);
+        for (int64_t j = j0; j < j1; ++j) z[j - j0] = 0.0;          /* Z starts at zero */
+        for (int64_t k = 0; k < n; ++k) {
+            const double base = X[i * n + k];                  /* Base <- X[I,K] */
+            if (base == 0.0) continue;                         /* zero Base: next K */
+            for (int64_t j = j0; j < j1; ++j) {
+                const int64_t rep = Y[k * n + j];              /* Rep-factor <- Y[K,J] */
+                if (rep < 0) { bad += 1; continue; }
+                for (int64_t p = 0; p < rep; ++p) z[j - j0] += base; /* Rep additions */
+                adds += (uint64_t)rep;
+            }
+        }
+    }
+    if (adds_out) *adds_out = adds;
+    return bad ? -1 : 0;
+}
+
 int afmm_oracle_caseA_f64(int64_t n, int64_t i0, int64_t i1,
                           const double* X, const int64_t* Y,
                           double* Z, uint64_t* adds_out)
 {
-    int64_t bad = 0;
-    uint64_t adds = 0;
-    int64_t i;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : adds, bad)
-    for (i = i0; i < i1; ++i) {
-        double* z = Z + (i - i0) * n;
-        for (int64_t j = 0; j < n; ++j) z[j] = 0.0;          /* Z starts at zero */
-        for (int64_t k = 0; k < n; ++k) {
-            const double base = X[i * n + k];                  /* Base <- X[I,K] */
-            if (base == 0.0) continue;                         /* zero Base: next K */
-            for (int64_t j = 0; j < n; ++j) {
-                const int64_t rep = Y[k * n + j];              /* Rep-factor <- Y[K,J] */
-                if (rep < 0) { bad += 1; continue; }
-                for (int64_t p = 0; p < rep; ++p) z[j] += base; /* Rep additions */
-                adds += (uint64_t)rep;
-            }
-        }
-    }
-    if (adds_out) *adds_out = adds;
-    return bad ? -1 : 0;
+    return afmm_oracle_caseA_f64_cols(n, i0, i1, 0, n, X, Y, Z, adds_out);
 }
 
 /* Case B (Sec. 2, Case-B): X integer Rep-factors, Y real. */
-int afmm_oracle_caseB_f64(int64_t n, int64_t i0, int64_t i1,
-                          const int64_t* X, const double* Y,
+int afmm_oracle_caseB_f64_cols(int64_t n, int64_t i0, int64_t i1, int64_t j0,
+                               int64_t j1, const int64_t* X, const double* Y,
                           double* Z, uint64_t* adds_out)
 {
     int64_t bad = 0;
@@ -83,15 +93,15 @@ int afmm_oracle_caseB_f64(int64_t n, int64_t i0, int64_t i1,
     int64_t i;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : adds, bad)
     for (i = i0; i < i1; ++i) {
-        double* z = Z + (i - i0) * n;
-        for (int64_t j = 0; j < n; ++j) z[j] = 0.0;
+        double* z = Z + (i - i0) * (j1 - j0);
+        for (int64_t j = j0; j < j1; ++j) z[j - j0] = 0.0;
         for (int64_t k = 0; k < n; ++k) {
             const int64_t rep = X[i * n + k];                  /* Rep-factor <- X[I,K] */
             if (rep < 0) { bad += 1; continue; }
-            for (int64_t j = 0; j < n; ++j) {
+            for (int64_t j = j0; j < j1; ++j) {
                 const double base = Y[k * n + j];              /* Base <- Y[K,J] */
                 if (base == 0.0) continue;                     /* zero Base: next J */
-                for (int64_t p = 0; p < rep; ++p) z[j] += base;
+                for (int64_t p = 0; p < rep; ++p) z[j - j0] += base;
                 adds += (uint64_t)rep;
             }
         }
@@ -100,25 +110,66 @@ int afmm_oracle_caseB_f64(int64_t n, int64_t i0, int64_t i1,
     return bad ? -1 : 0;
 }
 
+int afmm_oracle_caseB_f64(int64_t n, int64_t i0, int64_t i1,
+                          const int64_t* X, const double* Y,
+                          double* Z, uint64_t* adds_out)
+{
+    return afmm_oracle_caseB_f64_cols(n, i0, i1, 0, n, X, Y, Z, adds_out);
+}
+
 /* Case A with an integer-valued Base (both factors integer): exact int64. */
+int afmm_oracle_caseA_i64_cols(int64_t n, int64_t i0, int64_t i1, int64_t j0,
+                               int64_t j1, const int64_t* X, const int64_t* Y,
+                          int64_t* Z, uint64_t* adds_out)
+{
+    int64_t bad = 0;
+    uint64_t adds = 0;
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : adds, bad)
+    for (i = i0; i < i1; ++i) {
+        int64_t* z = Z + (i - i0) * (j1 - j0);
+        for (int64_t j = j0; j < j1; ++j) z[j - j0] = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t base = X[i * n + k];
+            if (base == 0) continue;
+            for (int64_t j = j0; j < j1; ++j) {
+                const int64_t rep = Y[k * n + j];
+                if (rep < 0) { bad += 1; continue; }
+                for (int64_t p = 0; p < rep; ++p) z[j - j0] += base;
+                adds += (uint64_t)rep;
+            }
+        }
+    }
+    if (adds_out) *adds_out = adds;
+    return bad ? -1 : 0;
+}
+
 int afmm_oracle_caseA_i64(int64_t n, int64_t i0, int64_t i1,
                           const int64_t* X, const int64_t* Y,
                           int64_t* Z, uint64_t* adds_out)
 {
+    return afmm_oracle_caseA_i64_cols(n, i0, i1, 0, n, X, Y, Z, adds_out);
+}
+
+/* Case B with an integer-valued Base (both factors integer): exact int64. */
+int afmm_oracle_caseB_i64_cols(int64_t n, int64_t i0, int64_t i1, int64_t j0,
+                               int64_t j1, const int64_t* X, const int64_t* Y,
+                          int64_t* Z, uint64_t* adds_out)
+{
     int64_t bad = 0;
     uint64_t adds = 0;
     int64_t i;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : adds, bad)
     for (i = i0; i < i1; ++i) {
-        int64_t* z = Z + (i - i0) * n;
-        for (int64_t j = 0; j < n; ++j) z[j] = 0;
+        int64_t* z = Z + (i - i0) * (j1 - j0);
+        for (int64_t j = j0; j < j1; ++j) z[j - j0] = 0;
         for (int64_t k = 0; k < n; ++k) {
-            const int64_t base = X[i * n + k];
-            if (base == 0) continue;
-            for (int64_t j = 0; j < n; ++j) {
-                const int64_t rep = Y[k * n + j];
-                if (rep < 0) { bad += 1; continue; }
-                for (int64_t p = 0; p < rep; ++p) z[j] += base;
+            const int64_t rep = X[i * n + k];
+            if (rep < 0) { bad += 1; continue; }
+            for (int64_t j = j0; j < j1; ++j) {
+                const int64_t base = Y[k * n + j];
+                if (base == 0) continue;
+                for (int64_t p = 0; p < rep; ++p) z[j - j0] += base;
                 adds += (uint64_t)rep;
             }
         }
@@ -127,31 +178,11 @@ int afmm_oracle_caseA_i64(int64_t n, int64_t i0, int64_t i1,
     return bad ? -1 : 0;
 }
 
-/* Case B with an integer-valued Base (both factors integer): exact int64. */
 int afmm_oracle_caseB_i64(int64_t n, int64_t i0, int64_t i1,
                           const int64_t* X, const int64_t* Y,
                           int64_t* Z, uint64_t* adds_out)
 {
-    int64_t bad = 0;
-    uint64_t adds = 0;
-    int64_t i;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : adds, bad)
-    for (i = i0; i < i1; ++i) {
-        int64_t* z = Z + (i - i0) * n;
-        for (int64_t j = 0; j < n; ++j) z[j] = 0;
-        for (int64_t k = 0; k < n; ++k) {
-            const int64_t rep = X[i * n + k];
-            if (rep < 0) { bad += 1; continue; }
-            for (int64_t j = 0; j < n; ++j) {
-                const int64_t base = Y[k * n + j];
-                if (base == 0) continue;
-                for (int64_t p = 0; p < rep; ++p) z[j] += base;
-                adds += (uint64_t)rep;
-            }
-        }
-    }
-    if (adds_out) *adds_out = adds;
-    return bad ? -1 : 0;
+    return afmm_oracle_caseB_i64_cols(n, i0, i1, 0, n, X, Y, Z, adds_out);
 }
 
 /*

@@ -41,6 +41,11 @@ def _load(path: str):
         f = getattr(lib, name)
         f.argtypes = [_i64, _i64, _i64, _p, _p, _p, _p]
         f.restype = ctypes.c_int
+    for name in ("afmm_oracle_caseA_f64_cols", "afmm_oracle_caseB_f64_cols",
+                 "afmm_oracle_caseA_i64_cols", "afmm_oracle_caseB_i64_cols"):
+        f = getattr(lib, name)
+        f.argtypes = [_i64, _i64, _i64, _i64, _i64, _p, _p, _p, _p]
+        f.restype = ctypes.c_int
     for name in ("afmm_classical_ijk_f64", "afmm_classical_ikj_f64"):
         f = getattr(lib, name)
         f.argtypes = [_i64, _i64, _i64, _p, _p, _p]
@@ -130,14 +135,19 @@ def _rep_factors(a: np.ndarray, name: str) -> np.ndarray:
     return a
 
 
-def _run(fn, n, X, Y, rows, out_dtype):
+def _run(fn, n, X, Y, rows, out_dtype, cols=None):
+    """Rows `rows` of Z, restricted to the column window cols = (j0, j1)
+    when given (each element formed exactly as in the full row)."""
     idx, runs = _row_runs(n, rows)
-    Z = np.zeros((idx.size, n), dtype=out_dtype)
+    j0, j1 = (0, n) if cols is None else (int(cols[0]), int(cols[1]))
+    if not 0 <= j0 <= j1 <= n:
+        raise ValueError("column window out of range")
+    Z = np.zeros((idx.size, j1 - j0), dtype=out_dtype)
     total = 0
     adds = ctypes.c_uint64(0)
     for a, b in runs:
         i0, i1 = int(idx[a]), int(idx[b - 1]) + 1
-        rc = fn(n, i0, i1, X.ctypes.data, Y.ctypes.data,
+        rc = fn(n, i0, i1, j0, j1, X.ctypes.data, Y.ctypes.data,
                 Z[a:b].ctypes.data, ctypes.byref(adds))
         if rc != 0:
             raise ValueError("negative Rep-factor")
@@ -145,12 +155,13 @@ def _run(fn, n, X, Y, rows, out_dtype):
     return Z, total
 
 
-def afmm_case_a(X: np.ndarray, Y: np.ndarray, rows: RowSel = None):
+def afmm_case_a(X: np.ndarray, Y: np.ndarray, rows: RowSel = None, cols=None):
     """Case A (Sec. 2): X real Base values, Y integer Rep-factors.
 
     Returns ``(Z_rows, additions)``: the selected rows of Z = X * Y formed
     by repeated addition (FP64, or exact int64 when X is integer-typed) and
-    the number of additions performed on those rows.
+    the number of additions performed on those rows; ``cols = (j0, j1)``
+    restricts them to those columns.
     """
     n = _square(np.asarray(X), "X")
     if _square(np.asarray(Y), "Y") != n:
@@ -159,12 +170,12 @@ def afmm_case_a(X: np.ndarray, Y: np.ndarray, rows: RowSel = None):
     lib = _lib()
     if np.asarray(X).dtype.kind in "iu":
         Xi = np.ascontiguousarray(X, dtype=np.int64)
-        return _run(lib.afmm_oracle_caseA_i64, n, Xi, Yi, rows, np.int64)
+        return _run(lib.afmm_oracle_caseA_i64_cols, n, Xi, Yi, rows, np.int64, cols)
     Xf = np.ascontiguousarray(X, dtype=np.float64)
-    return _run(lib.afmm_oracle_caseA_f64, n, Xf, Yi, rows, np.float64)
+    return _run(lib.afmm_oracle_caseA_f64_cols, n, Xf, Yi, rows, np.float64, cols)
 
 
-def afmm_case_b(X: np.ndarray, Y: np.ndarray, rows: RowSel = None):
+def afmm_case_b(X: np.ndarray, Y: np.ndarray, rows: RowSel = None, cols=None):
     """Case B (Sec. 2): X integer Rep-factors, Y real Base values.
 
     A zero Base skips that single j (the reading under which the listing
@@ -177,9 +188,9 @@ def afmm_case_b(X: np.ndarray, Y: np.ndarray, rows: RowSel = None):
     lib = _lib()
     if np.asarray(Y).dtype.kind in "iu":
         Yi = np.ascontiguousarray(Y, dtype=np.int64)
-        return _run(lib.afmm_oracle_caseB_i64, n, Xi, Yi, rows, np.int64)
+        return _run(lib.afmm_oracle_caseB_i64_cols, n, Xi, Yi, rows, np.int64, cols)
     Yf = np.ascontiguousarray(Y, dtype=np.float64)
-    return _run(lib.afmm_oracle_caseB_f64, n, Xi, Yf, rows, np.float64)
+    return _run(lib.afmm_oracle_caseB_f64_cols, n, Xi, Yf, rows, np.float64, cols)
 
 
 def _classical(fn, X, Y, rows):

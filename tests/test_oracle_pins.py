@@ -332,22 +332,23 @@ def test_realised_parameters():
 
 # ---------------------------------------------------------------- mutants
 MUTANTS = [
-    # (id, function, text to find, replacement)
-    ("caseB_literal_leave_J_loop", "afmm_oracle_caseB_f64",
+    # (id, function, text to find, replacement); the loops live in the
+    # column-window forms that the plain entry points call.
+    ("caseB_literal_leave_J_loop", "afmm_oracle_caseB_f64_cols",
      "if (base == 0.0) continue;", "if (base == 0.0) break;"),
-    ("caseA_dropped_last_k", "afmm_oracle_caseA_f64",
+    ("caseA_dropped_last_k", "afmm_oracle_caseA_f64_cols",
      "for (int64_t k = 0; k < n; ++k)", "for (int64_t k = 0; k < n - 1; ++k)"),
-    ("caseA_transposed_Y", "afmm_oracle_caseA_f64",
+    ("caseA_transposed_Y", "afmm_oracle_caseA_f64_cols",
      "Y[k * n + j]", "Y[j * n + k]"),
-    ("caseA_floor_mu_upper_limit", "afmm_oracle_caseA_f64",
+    ("caseA_floor_mu_upper_limit", "afmm_oracle_caseA_f64_cols",
      "p < rep;", "p < 4;"),
-    ("caseB_wrong_sign", "afmm_oracle_caseB_f64",
-     "z[j] += base;", "z[j] -= base;"),
-    ("caseA_count_off_by_one", "afmm_oracle_caseA_f64",
+    ("caseB_wrong_sign", "afmm_oracle_caseB_f64_cols",
+     "z[j - j0] += base;", "z[j - j0] -= base;"),
+    ("caseA_count_off_by_one", "afmm_oracle_caseA_f64_cols",
      "adds += (uint64_t)rep;", "adds += (uint64_t)rep + 1;"),
-    ("caseA_int_skip_inverted", "afmm_oracle_caseA_i64",
+    ("caseA_int_skip_inverted", "afmm_oracle_caseA_i64_cols",
      "if (base == 0) continue;", "if (base != 0) continue;"),
-    ("caseB_int_rep_from_Y", "afmm_oracle_caseB_i64",
+    ("caseB_int_rep_from_Y", "afmm_oracle_caseB_i64_cols",
      "const int64_t rep = X[i * n + k];", "const int64_t rep = X[k * n + i];"),
 ]
 
@@ -378,3 +379,27 @@ def test_planted_mistakes_are_caught(tmp_path, mid, func, old, new):
             except (AssertionError, ValueError):
                 caught.append(pin.__name__)
     assert caught, f"no pin caught the planted mistake {mid}"
+
+
+@pytest.mark.parametrize("case", ["A", "B"])
+@pytest.mark.parametrize("integer", [False, True])
+def test_column_window_is_the_full_rows_restricted(case, integer):
+    """A column window (used to bound the timed CPU samples) forms every
+    element exactly as the full rows do, and counts the additions of its own
+    columns: sum over k of [Base != 0] * Rep for those j."""
+    rng = np.random.default_rng(41)
+    n = 29
+    real = (rng.integers(-3, 4, (n, n)) if integer else rng.uniform(-1, 1, (n, n)))
+    real = real * (rng.random((n, n)) < 0.7)
+    rep = rng.integers(0, 4, (n, n))
+    X, Y = (real, rep) if case == "A" else (rep, real)
+    fn = afmm_case_a if case == "A" else afmm_case_b
+    Zf, _ = fn(X, Y, (4, 17))
+    Zw, aw = fn(X, Y, (4, 17), cols=(6, 23))
+    assert np.array_equal(Zw, Zf[:, 6:23])
+    rows = slice(4, 17)
+    if case == "A":
+        want = int(((X[rows] != 0).astype(np.int64) @ Y[:, 6:23]).sum())
+    else:
+        want = int((X[rows] @ (Y[:, 6:23] != 0).astype(np.int64)).sum())
+    assert aw == want
