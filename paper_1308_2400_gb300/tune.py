@@ -3,8 +3,8 @@
 The autotuner times every candidate kernel variant on each instance as
 part of a batch (the batched entry point with copies of the instance and a
 forced variant, CUDA events, median of repeats, divided by the copies).
-Its table is both the judge of a dispatch policy (the per-instance best
-variant) and the training data of the MLP cost model, which maps
+Its table is both the yardstick of a dispatch policy (the per-instance
+best variant) and the training data of the MLP cost model, which maps
 afmm_dispatch_features() of an instance to one predicted log2-time per
 variant.  The network is trained on the GPU with the library's own
 kernels (afmm_mlp_loss_grad, afmm_mlp_adam) and saved as JSON;
