@@ -19,8 +19,12 @@
  *  - X, Y, Z may be device pointers or host pointers (pageable or pinned);
  *    the library asks the CUDA runtime which.  Host buffers are staged
  *    through device buffers the plan owns: the call copies X and Y in,
- *    computes, copies Z out and synchronises the stream before returning.
- *    With device pointers the call is asynchronous on `stream`.
+ *    computes, copies Z out and synchronises the stream before returning
+ *    (the split tensor-core forms at n >= 1024 overlap the copies of row
+ *    blocks with the products on two extra streams).  With device pointers
+ *    the call is asynchronous on `stream`; from the third call in a row on
+ *    the same device buffers, problems with n <= 2048 are replayed from a
+ *    CUDA graph captured by the plan.
  *  - The caller owns X, Y, Z.  A plan owns its workspace unless the caller
  *    lends one (afmm_plan_set_workspace).
  *  - Errors are returned as afmm_status, never thrown.  Errors found by a
@@ -79,9 +83,11 @@ typedef enum {
     /* CUDA cores, FP32 FMA, skips k where the Base is zero for a group of
      * rows, K-blocked accumulation.  FP32 target. */
     AFMM_VARIANT_SIMT_F32 = 0,
-    /* Tensor cores (tcgen05, TMEM accumulator): the real factor split into
-     * three BF16 slices (hi+mid+lo represent FP32 exactly), the Rep-factors
-     * widened to BF16 (exact up to 256), FP32 accumulation.  FP32 target. */
+    /* Tensor cores (tcgen05, TMEM accumulators): the real factor split
+     * into three BF16 slices (hi+mid+lo represent FP32 exactly), the
+     * Rep-factors widened to BF16 (exact up to 256), FP32 accumulation
+     * with the hi slice's products kept apart from the smaller slices'.
+     * Case B is computed as Z^T = Y^T X^T.  FP32 target. */
     AFMM_VARIANT_TC_BF16X3 = 1,
     /* As above with two slices: does not reach the FP32 target in general;
      * offered for error studies only (never chosen automatically). */
@@ -93,14 +99,17 @@ typedef enum {
     AFMM_VARIANT_SIMT_EXACT = 4,
     /* Tensor cores, exact integers: operands exact in BF16 (|v| <= 256),
      * K cut into chunks whose FP32 partial sums stay below 2^24 (so every
-     * partial sum is an exact integer), chunks added in int32. */
+     * partial sum is an exact integer), chunks added in int32; 256 x 256
+     * output tiles. */
     AFMM_VARIANT_TC_EXACT = 5,
     /* CUDA cores, both factors compacted to per-row (column, value) lists
      * -- the zero-skip of Sec. 2 on both sides -- for the quadratic regime
      * of Sec. 2.2 (d1 d2 n small): HBM-bound, FP32 target.  Its workspace
-     * holds the non-zeros planned from the d1, d2 hints (with a margin; all
-     * n^2 without hints); more non-zeros than planned is reported as
-     * AFMM_ERR_OVERFLOW_RISK by afmm_plan_sync and Z is not written. */
+     * holds, per row, a slot sized from the d1, d2 hints (expected count
+     * plus six standard deviations; all n without hints) and an overflow
+     * region for longer rows (2 d n^2 + 32 n + 1024 entries); more
+     * non-zeros than that is reported as AFMM_ERR_OVERFLOW_RISK by
+     * afmm_plan_sync and Z is not written. */
     AFMM_VARIANT_SPARSE = 6,
     AFMM_VARIANT_COUNT_ = 7
 } afmm_variant;
