@@ -181,8 +181,9 @@ def oracle_rows_timed(inst, budget_s, min_rows=1):
 def run_reference(args):
     """The oracle (the CPU AFMM of Sec. 2) on the host cores, in the same
     metric.  Each step computes one element block of Z -- one row per
-    oracle thread and a column window sized so that the K + W steps take
-    about two minutes -- and the value scales the elements to 2n^3."""
+    oracle thread and a column window (at least 256 wide) sized so that the
+    K + W steps take about two minutes -- and the value scales the elements
+    to 2n^3."""
     ws, rank, _ = dist_info()
     if rank != 0:
         return 0
@@ -192,14 +193,15 @@ def run_reference(args):
     from oracle import afmm_case_a, afmm_case_b, oracle_threads
     fn = afmm_case_a if inst.case == "A" else afmm_case_b
     thr = min(oracle_threads(), n)
-    # Calibrate the column window on one block of 32 columns.
-    w0 = min(n, 32)
+    # Calibrate the column window on one block of 256 columns; windows are
+    # at least that wide (narrower ones read Y in short pieces).
+    w0 = min(n, 256)
     t0 = time.perf_counter()
     fn(inst.X, inst.Y, (0, thr), cols=(0, w0))
     t_cal = max(time.perf_counter() - t0, 1e-6)
-    per_step = 120.0 / max(1, args.steps + args.warmup)
+    per_step = 100.0 / max(1, args.steps + args.warmup)
     w = int(w0 * per_step / t_cal) // 32 * 32
-    w = max(32, min(n, w)) if n >= 32 else n
+    w = max(w0, min(n, w))
     times = []
     for i in range(args.warmup + args.steps):
         r0 = (i * thr) % max(1, n - thr + 1)
