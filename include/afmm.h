@@ -238,9 +238,10 @@ afmm_status afmm_selftest_bounded_wait(uint64_t limit_ns, void* stream);
  * different n, Case A or B), each described by descs[t], FP32 target
  * (z_dtype F32).  Each instance runs either the tcgen05 split-BF16 form or
  * the CUDA-core zero-skip form: descs[t].variant = AFMM_VARIANT_TC_BF16X3 or
- * AFMM_VARIANT_SIMT_F32 forces the route, AFMM_VARIANT_AUTO applies the
- * built-in rule (tensor cores unless the Base density hint is below 0.02
- * or n < 32).  All tensor-core instances run in one persistent grouped
+ * AFMM_VARIANT_SIMT_F32 forces the route, AFMM_VARIANT_AUTO asks the
+ * installed dispatch model (afmm_set_dispatch_model) or, without one,
+ * applies the built-in rule (tensor cores unless the Base density hint is
+ * below 0.02 or n < 32).  All tensor-core instances run in one persistent grouped
  * launch, all CUDA-core instances in another; the first call with a given
  * descriptor array builds the plan (workspace, TMA descriptors, tile lists)
  * and a CUDA graph of the launches, later calls with an identical array
