@@ -54,7 +54,7 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr int A_TILE_BYTES = TC_BM * TC_BK * 2;   // 8 KiB
 constexpr int B_TILE_BYTES = TC_BN * TC_BK * 2;   // 16 KiB
 constexpr int SMEM_OPTIN = 232448;                // 227 KiB per CTA
-constexpr int GROUP_M = 16;                       // tile raster band
+constexpr int GROUP_M = 10;                       // tile raster band
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 template <int SA, int SB>
