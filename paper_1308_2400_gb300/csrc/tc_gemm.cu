@@ -369,7 +369,7 @@ namespace {
 // Roles, bounded waits and the abort path are those of tc_gemm_kernel.
 constexpr int X2_BM = 256, X2_BN = 256;
 constexpr int X2_STAGE = 2 * A_TILE_BYTES + B_TILE_BYTES;   // 32 KiB
-constexpr int X2_STAGES = 6;
+constexpr int X2_STAGES = 7;
 constexpr int X2_SMEM = 1024 + X2_STAGES * X2_STAGE + 256;
 static_assert(X2_SMEM <= SMEM_OPTIN, "shared memory");
 static_assert(X2_STAGES <= 8, "barrier block");
