@@ -757,3 +757,45 @@ def test_batched_small_mix():
     afmm_mul_batched(descs, Xs, Ys, Zs)
     torch.cuda.synchronize()
     _check_batch(insts, Zs)
+
+
+_DEGENERATE_FORMS = {   # variant: (X dtype, Y dtype, Z dtype, target)
+    0: ("f32", "i32", "f32", "fp32"), 1: ("f32", "i32", "f32", "fp32"),
+    6: ("f32", "i32", "f32", "fp32"), 3: ("f64", "i32", "f64", "fp64"),
+    4: ("i8", "i8", "i32", "exact"), 5: ("i8", "i8", "i32", "exact"),
+}
+
+
+@pytest.mark.parametrize("kind", ["zero_base", "zero_rep", "unit_rep"])
+@pytest.mark.parametrize("variant", sorted(_DEGENERATE_FORMS))
+def test_degenerate_inputs(variant, kind):
+    """The method's degenerate cases on every form: no non-zero Base
+    (Z = 0, no additions), no non-zero Rep-factor (Z = 0), and every
+    Rep-factor 1 (each Z[i,j] is a row sum of the Base values)."""
+    xd, yd, zd, target = _DEGENERATE_FORMS[variant]
+    rng = np.random.default_rng(variant * 7 + len(kind))
+    n = 200
+    if xd == "i8":
+        X = rng.integers(-127, 128, size=(n, n)).astype(np.int8)
+    else:
+        X = rng.uniform(-1, 1, size=(n, n)).astype(np.float32 if xd == "f32" else np.float64)
+    Y = rng.integers(0, 9, size=(n, n)).astype(np.int8 if yd == "i8" else np.int32)
+    if kind == "zero_base":
+        X[:] = 0
+    elif kind == "zero_rep":
+        Y[:] = 0
+    else:
+        Y[:] = 1
+    inst = W.Instance("A", X, Y, x_dtype=xd, y_dtype=yd, z_dtype=zd, target=target)
+    Z, info = run_gpu(inst, variant=variant)
+    assert info["variant"] == variant
+    if kind != "unit_rep":
+        assert np.all(Z == 0), kind
+        return
+    R = oracle_rows(inst)
+    if target == "exact":
+        assert np.array_equal(Z.astype(np.int64), R)
+    elif target == "fp64":
+        assert rel_fro(Z, R) <= FP64_REL_FRO
+    else:
+        assert rel_fro(Z, R) <= FP32_REL_FRO
