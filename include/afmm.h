@@ -26,7 +26,9 @@
  *    the same device buffers, problems with n <= 2048 are replayed from a
  *    CUDA graph captured by the plan.
  *  - The caller owns X, Y, Z.  A plan owns its workspace unless the caller
- *    lends one (afmm_plan_set_workspace).
+ *    lends one (afmm_plan_set_workspace).  A plan holds per-call state
+ *    (workspace, staging buffers, replay graph): calls on one plan must be
+ *    made from one thread at a time; separate plans are independent.
  *  - Errors are returned as afmm_status, never thrown.  Errors found by a
  *    kernel (a negative or non-integer Rep-factor, a bounded wait that ran
  *    out) are written to the plan's device status word and returned by the
