@@ -416,6 +416,22 @@ def run_afmm(args):
         Z_two = Z.cpu().numpy() if ws == 1 else None
         p4.close()
 
+    # The FP8 form on the same data: four E4M3 slices on the kind::f8f6f4
+    # tensor path (twice the BF16 rate); its error is taken below too.
+    f8 = None
+    Z_f8 = None
+    if rank == 0 and vname == "tc_bf16x3" and not args.quick:
+        p5 = Plan(desc(7))
+        ms5, kms5, _, _ = timed(p5, max(2, min(args.steps // 4, 100)), 3)
+        f8_peak = 2.0 * peaks.get("bf16_tflops_sustained", 1700.0)
+        f8_tf = 4 * flops / (kms5 * 1e-3) / 1e12
+        f8 = {"variant": "tc_fp8x4", "value": flops / (ms5 * 1e-3) / 1e12,
+              "ms_per_step": ms5, "kernel_ms": kms5, "tensor_tflops": f8_tf,
+              "peak": f8_peak, "frac": f8_tf / f8_peak,
+              "peak_src": f"2 x bf16 sustained (nominal fp8/bf16 ratio), {peak_src}"}
+        Z_f8 = Z.cpu().numpy() if ws == 1 else None
+        p5.close()
+
     # End to end through the C ABI with pinned host buffers: copies in,
     # product, copy out, every step.
     e2e = None
@@ -459,6 +475,9 @@ def run_afmm(args):
         if two is not None and Z_two is not None:
             d2 = float(np.linalg.norm(Z_two[rows].astype(np.float64) - Zr))
             two["rel_fro_err_vs_oracle"] = d2 / den if den else 0.0
+        if f8 is not None and Z_f8 is not None:
+            d8 = float(np.linalg.norm(Z_f8[rows].astype(np.float64) - Zr))
+            f8["rel_fro_err_vs_oracle"] = d8 / den if den else 0.0
 
     if rank == 0:
         line = {
@@ -478,7 +497,7 @@ def run_afmm(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches) * ws, "clocks": clocks,
             "accuracy": acc, "plain_fp32": plain, "fused_split": fused,
-            "two_slices": two,
+            "two_slices": two, "fp8_slices": f8,
         }
         print(json.dumps(line), flush=True)
     plan.close()

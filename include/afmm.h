@@ -113,7 +113,18 @@ typedef enum {
      * non-zeros than that is reported as AFMM_ERR_OVERFLOW_RISK by
      * afmm_plan_sync and Z is not written. */
     AFMM_VARIANT_SPARSE = 6,
-    AFMM_VARIANT_COUNT_ = 7
+    /* Tensor cores with 8-bit floats (tcgen05 kind::f8f6f4, FP32 TMEM
+     * accumulators): each row of the real factor scaled by a power of two
+     * (its largest |value| into [128, 256)) and split into four E4M3
+     * slices -- three round-to-nearest slices and one of the third
+     * residual times 2^12 -- so the slices hold about 20 significant bits;
+     * Rep-factors held as E4M3, exact for 0..16 and every integral E4M3
+     * value up to 448 (others, and non-finite real values: the call
+     * records AFMM_ERR_OVERFLOW_RISK, reported by afmm_plan_sync).  Four
+     * E4M3 MMAs per K step in place of three BF16 ones at twice the
+     * rate.  FP32 target; never chosen automatically. */
+    AFMM_VARIANT_TC_FP8X4 = 7,
+    AFMM_VARIANT_COUNT_ = 8
 } afmm_variant;
 
 /* Flags for afmm_desc.flags. */

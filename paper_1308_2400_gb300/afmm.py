@@ -40,6 +40,7 @@ AFMM_VARIANT_SIMT_F64SLICE = 3
 AFMM_VARIANT_SIMT_EXACT = 4
 AFMM_VARIANT_TC_EXACT = 5
 AFMM_VARIANT_SPARSE = 6
+AFMM_VARIANT_TC_FP8X4 = 7
 AFMM_FLAG_VALIDATE = 0x1
 AFMM_FLAG_FUSED_SPLIT = 0x2
 
@@ -48,7 +49,7 @@ VARIANT_NAMES = {
     AFMM_VARIANT_TC_BF16X2: "tc_bf16x2",
     AFMM_VARIANT_SIMT_F64SLICE: "simt_f64slice",
     AFMM_VARIANT_SIMT_EXACT: "simt_exact", AFMM_VARIANT_TC_EXACT: "tc_exact",
-    AFMM_VARIANT_SPARSE: "sparse",
+    AFMM_VARIANT_SPARSE: "sparse", AFMM_VARIANT_TC_FP8X4: "tc_fp8x4",
 }
 DTYPE_CODES = {"f64": AFMM_F64, "f32": AFMM_F32, "bf16": AFMM_BF16,
                "e4m3": AFMM_E4M3, "i32": AFMM_I32, "i8": AFMM_I8,

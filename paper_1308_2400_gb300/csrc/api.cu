@@ -187,6 +187,7 @@ bool variant_serves(int v, const afmm_desc* d) {
             return d->target == AFMM_TARGET_FP32;
         case AFMM_VARIANT_TC_BF16X3:
         case AFMM_VARIANT_TC_BF16X2:
+        case AFMM_VARIANT_TC_FP8X4:
             return d->target == AFMM_TARGET_FP32 && tc_available();
         case AFMM_VARIANT_SIMT_F64SLICE:
             return d->target == AFMM_TARGET_FP64;
@@ -285,6 +286,14 @@ void plan_layout(afmm_plan_s* p) {
             p->off_c = L.take(p->tc.z_bytes);
             break;
         }
+        case AFMM_VARIANT_TC_FP8X4: {
+            tc_layout(&p->tc, d, p->slices, true);
+            p->off_a = L.take(p->tc.a_bytes);
+            p->off_b = L.take(p->tc.b_bytes);
+            p->off_c = L.take(p->tc.z_bytes);
+            p->off_e = L.take(p->tc.s_bytes);
+            break;
+        }
         default:
             break;
     }
@@ -313,9 +322,9 @@ afmm_status ensure_workspace(afmm_plan_s* p, cudaStream_t st) {
         AFMM_CUDA_TRY(cudaMemsetAsync(p->ws + p->off_status, 0, kAlign, st));
         if (p->variant == AFMM_VARIANT_TC_BF16X3 ||
             p->variant == AFMM_VARIANT_TC_BF16X2 ||
-            p->variant == AFMM_VARIANT_TC_EXACT)
+            p->variant == AFMM_VARIANT_TC_EXACT || p->variant == AFMM_VARIANT_TC_FP8X4)
             AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a, p->ws + p->off_b,
-                                       p->ws + p->off_c));
+                                       p->ws + p->off_c, p->ws + p->off_e));
         if (p->variant == AFMM_VARIANT_SPARSE) AFMM_TRY(sparse_reset(p->ws + p->off_a, st));
         p->ws_ready = true;
     }
@@ -424,6 +433,8 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
             return tc_run_split(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_TC_EXACT:
             return tc_run_exact(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
+        case AFMM_VARIANT_TC_FP8X4:
+            return tc_run_fp8(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_SPARSE:
             return launch_sparse(X, d.x_dtype, d.ldx ? d.ldx : n, Y, d.y_dtype,
                                  d.ldy ? d.ldy : n, static_cast<float*>(Z),
@@ -569,7 +580,8 @@ afmm_status mul_impl(afmm_plan p, const void* X, const void* Y, void* Z,
     const size_t bz = span_bytes(n, d.ldz ? d.ldz : n, d.z_dtype);
     const bool hx = is_host_ptr(X), hy = is_host_ptr(Y), hz = is_host_ptr(Z);
     if (hx && hy && hz && n >= 1024 && !(d.flags & (AFMM_FLAG_VALIDATE | AFMM_FLAG_FUSED_SPLIT)) &&
-        (p->variant == AFMM_VARIANT_TC_BF16X3 || p->variant == AFMM_VARIANT_TC_BF16X2)) {
+        (p->variant == AFMM_VARIANT_TC_BF16X3 || p->variant == AFMM_VARIANT_TC_BF16X2 ||
+         p->variant == AFMM_VARIANT_TC_FP8X4)) {
         const int64_t l0 = launch_counter();
         afmm_status rc = run_pipelined_host(p, X, Y, Z, st);
         p->launches += launch_counter() - l0;
@@ -700,6 +712,8 @@ afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc) {
         p->slices = 3;
     } else if (v == AFMM_VARIANT_TC_BF16X2) {
         p->slices = 2;
+    } else if (v == AFMM_VARIANT_TC_FP8X4) {
+        p->slices = 4;
     }
     plan_layout(p);
     *out = p;

@@ -35,11 +35,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
 #include "afmm_common.cuh"
 #include "elem.cuh"
+#include "fp8_split.cuh"
 #include "ptx_sm100.cuh"
 #include "tc_gemm.cuh"
 
@@ -56,6 +58,8 @@ constexpr int B_TILE_BYTES = TC_BN * TC_BK * 2;   // 16 KiB
 constexpr int SMEM_OPTIN = 232448;                // 227 KiB per CTA
 constexpr int GROUP_M = 10;                       // tile raster band
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+// FP8 form: k-blocks of 64 per chunk of the hi sum (0: one chunk per tile).
+constexpr int kF8ChunkKb = 16;
 
 template <int SA, int SB>
 struct TcCfg {
@@ -99,12 +103,26 @@ __device__ __forceinline__ void raise_abort(TcBars* b, int* status) {
 
 // TOUT: the product computed is Z^T (A = the operand whose rows are Z's
 // columns); the epilogue stores tile element (m, n) at Z[n][m].
-template <int SA, int SB, bool TOUT = false>
+// F8: E4M3 operands (kind::f8f6f4), SA = 4 slices of the row-scaled real
+// factor (tc_fp8.cu): slices 1-3 accumulate into the hi sum, slice 4 (cut
+// from the residual times 2^12) into the small sum; amax[m] holds the bits
+// of A row m's largest |value|, from which f8_row_shift() gives the power
+// of two the row was scaled by, undone in the epilogue.  The tensor pipe
+// adds E4M3 products into its FP32 accumulator less precisely than BF16
+// ones, an error that grows with the number of additions; so the hi sum is
+// closed every kbpc k-blocks (kbpc > 0) and handed to the epilogue, which
+// adds the chunks in FP32 registers (round to nearest) while the MMAs wait.
+template <int SA, int SB, bool TOUT = false, bool F8 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB, float* __restrict__ Z,
-               int64_t ldz, int m0, int M, int n0, int N, int K, int vec, int* status) {
+               int64_t ldz, int m0, int M, int n0, int N, int K, int vec, int* status,
+               const uint32_t* __restrict__ amax, int kbpc) {
     using Cfg = TcCfg<SA, SB>;
+    // Elements per 64-byte K block; slices whose products go to the hi sum.
+    constexpr int BK = F8 ? 64 : TC_BK;
+    constexpr int HI = F8 ? 3 : 1;
+    static_assert(!F8 || (SA == 4 && SB == 1), "FP8 form: four A slices");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
     uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -115,7 +133,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     // m0 + tm*BM .. and columns n0 + tn*BN ..
     const int tiles_m = (M - m0 + TC_BM - 1) / TC_BM, tiles_n = (N - n0 + TC_BN - 1) / TC_BN;
     const int num_tiles = tiles_m * tiles_n;
-    const int num_kb = (K + TC_BK - 1) / TC_BK;
+    const int num_kb = (K + BK - 1) / BK;
+    // k-blocks per chunk of the hi sum, and chunks per tile.
+    const int kc = (F8 && kbpc > 0 && kbpc < num_kb) ? kbpc : num_kb;
+    const int nch = (num_kb + kc - 1) / kc;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -165,11 +186,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
 #pragma unroll
                     for (int s = 0; s < SA; ++s)
                         ptx::tma_load_3d(st + s * A_TILE_BYTES, &tmA, &bars->full[stage],
-                                         kb * TC_BK, m0 + tm * TC_BM, s);
+                                         kb * BK, m0 + tm * TC_BM, s);
 #pragma unroll
                     for (int s = 0; s < SB; ++s)
                         ptx::tma_load_3d(st + SA * A_TILE_BYTES + s * B_TILE_BYTES, &tmB,
-                                         &bars->full[stage], kb * TC_BK, n0 + tn * TC_BN, s);
+                                         &bars->full[stage], kb * BK, n0 + tn * TC_BN, s);
                     issued_phase[stage] = (int)phase;
                     if (++stage == Cfg::STAGES) {
                         stage = 0;
@@ -191,12 +212,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     } else if (warp == 1) {
         // ---------------------------------------------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t IDESC = ptx::idesc_bf16_f32(TC_BM, TC_BN);
+            constexpr uint32_t IDESC = F8 ? ptx::idesc_e4m3_f32(TC_BM, TC_BN)
+                                          : ptx::idesc_bf16_f32(TC_BM, TC_BN);
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
             // Split form: per tile two 128 x 256 FP32 accumulators in
-            // TMEM, columns [0,256) for the products of the hi slice and
+            // TMEM, columns [0,256) for the products of the hi slice(s) and
             // [256,512) for those of the smaller slices, so a small
             // product is never added into a sum of much larger
             // magnitude.  The epilogue adds the two.
@@ -209,6 +231,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                 }
                 ptx::tc_fence_after();
                 for (int kb = 0; kb < num_kb; ++kb) {
+                    const bool chunk0 = kb % kc == 0;
+                    if (kb > 0 && chunk0) {
+                        // Chunk boundary: the epilogue takes the hi sum;
+                        // the next chunk overwrites it once it has.
+                        ptx::mma_commit(&bars->tfull[0]);
+                        tphase ^= 1u;
+                        if (!ptx::mbar_wait_bounded(&bars->tempty[0], tphase ^ 1u, abort,
+                                                    WAIT_LIMIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                    }
                     if (!ptx::mbar_wait_bounded(&bars->full[stage], phase, abort,
                                                 WAIT_LIMIT_NS)) {
                         ok = false;
@@ -217,7 +252,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                     ptx::tc_fence_after();
                     const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
 #pragma unroll
-                    for (int ks = 0; ks < TC_BK / 16; ++ks) {
+                    for (int ks = 0; ks < 2; ++ks) {     // two 32-byte MMA steps
 #pragma unroll
                         for (int p = Cfg::P - 1; p >= 0; --p) {
                             const uint32_t a_addr =
@@ -225,12 +260,20 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                             const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
                                                     (SB > 1 ? p : 0) * B_TILE_BYTES +
                                                     ks * 32;
-                            const bool first = kb == 0 && ks == 0 &&
-                                               (p == 0 || p == Cfg::P - 1);
-                            ptx::mma_f16(tmem + (p == 0 ? 0u : (uint32_t)TC_BN),
-                                         ptx::sdesc_kmajor_sw64(a_addr),
-                                         ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                         first ? 0u : 1u);
+                            // Slices are issued from the last: the first MMA
+                            // into each accumulator overwrites it.
+                            const bool first =
+                                ks == 0 && ((chunk0 && p == HI - 1) ||
+                                            (kb == 0 && p == Cfg::P - 1));
+                            const uint32_t d = tmem + (p < HI ? 0u : (uint32_t)TC_BN);
+                            if constexpr (F8)
+                                ptx::mma_f8(d, ptx::sdesc_kmajor_sw64(a_addr),
+                                            ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                            first ? 0u : 1u);
+                            else
+                                ptx::mma_f16(d, ptx::sdesc_kmajor_sw64(a_addr),
+                                             ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                             first ? 0u : 1u);
                         }
                     }
                     ptx::mma_commit(&bars->empty[stage]);
@@ -262,31 +305,81 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
         for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
             int tm, tn;
             tile_coords(tile, tiles_m, tiles_n, tm, tn);
-            const bool got = ptx::mbar_wait_bounded(&bars->tfull[0], tphase, abort,
-                                                    WAIT_LIMIT_NS);
+            float sum[128];
+            bool got = true;
+            // F8, chunks before the last: add the hi sum into sum[].
+            for (int ch = 0; F8 && ch + 1 < nch; ++ch) {
+                got = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&bars->tfull[0], tphase,
+                                                                      abort, WAIT_LIMIT_NS));
+                if (!got) break;
+                ptx::tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    uint32_t r0[16];
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
+                    ptx::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        sum[c * 16 + j] = ch == 0 ? __uint_as_float(r0[j])
+                                                  : sum[c * 16 + j] + __uint_as_float(r0[j]);
+                }
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&bars->tempty[0]);
+                tphase ^= 1u;
+            }
             // TMEM loads below are warp-collective: decide as a warp.
-            if (!__all_sync(0xffffffffu, got)) {
+            if (got)
+                got = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&bars->tfull[0], tphase,
+                                                                      abort, WAIT_LIMIT_NS));
+            if (!got) {
                 if (lane == 0) raise_abort(bars, status);
                 break;
             }
             ptx::tc_fence_after();
-            float sum[128];
+            const int64_t m = (int64_t)m0 + (int64_t)tm * TC_BM + row;
+            // F8: row m was scaled by 2^sh; 2^-sh as two exact factors.
+            float f1 = 1.f, f2 = 1.f;
+            if constexpr (F8) {
+                const int sh = m < M ? f8_row_shift(amax[m]) : 0;
+                const int e1 = max(-sh, -126);
+                f1 = f8_pow2(e1);
+                f2 = f8_pow2(-sh - e1);
+            }
+            if constexpr (F8) {
+                // Last chunk of the hi sum plus the small sum times 2^-12
+                // (one rounding), times the row's scale (exact); 16 columns
+                // per load, so sum[] and the loads fit the registers.
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                // hi-slice sum + small-slice sum, one rounding.
-                uint32_t r0[32], r1[32];
-                ptx::tmem_ld_32cols(lane_base + (uint32_t)(c * 32), r0);
-                ptx::tmem_ld_32cols(lane_base + (uint32_t)(TC_BN + c * 32), r1);
-                ptx::tmem_ld_wait();
+                for (int c = 0; c < 8; ++c) {
+                    uint32_t r0[16], r1[16];
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(TC_BN + c * 16), r1);
+                    ptx::tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    sum[c * 32 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    for (int j = 0; j < 16; ++j) {
+                        const float hi = nch > 1 ? sum[c * 16 + j] + __uint_as_float(r0[j])
+                                                 : __uint_as_float(r0[j]);
+                        sum[c * 16 + j] =
+                            fmaf(__uint_as_float(r1[j]), 0x1p-12f, hi) * f1 * f2;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    // hi-slice sum + small-slice sum, one rounding.
+                    uint32_t r0[16], r1[16];
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(TC_BN + c * 16), r1);
+                    ptx::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        sum[c * 16 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                }
             }
             // TMEM is free again before the stores below.
             ptx::tc_fence_before();
             ptx::mbar_arrive(&bars->tempty[0]);
             tphase ^= 1u;
-            const int64_t m = (int64_t)m0 + (int64_t)tm * TC_BM + row;
             const int col0 = n0 + tn * TC_BN + h * 128;
             if (TOUT && m < M) {
                 // Element (m, col0 + j) of Z^T is Z[col0 + j][m]: the lanes of
@@ -339,17 +432,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
 
 }  // namespace
 
-// 3-D map over a stack of `slices` BF16 matrices of `rows` x `cols` (K)
-// with leading dimension `ld`; box = 32 (K) x box_rows x 1.
+// 3-D map over a stack of `slices` matrices of `rows` x `cols` (K) es-byte
+// elements with leading dimension `ld`; box = 64 bytes (K) x box_rows x 1.
 afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
-                       int64_t ld, int slices, int box_rows) {
+                       int64_t ld, int slices, int box_rows, int es) {
     auto fn = get_encode_fn();
-    if (!fn) return AFMM_ERR_CUDA;
+    if (!fn || (es != 1 && es != 2)) return AFMM_ERR_CUDA;
     cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)slices};
-    cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(ld * 2 * rows)};
-    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(ld * es * rows)};
+    cuuint32_t box[3] = {(cuuint32_t)(64 / es), (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(out),
+                    es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
                     3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -583,7 +677,7 @@ tc_exact2_kernel(const __grid_constant__ CUtensorMap tmA,
     }
 }
 
-template <int SA, int SB, bool TOUT = false>
+template <int SA, int SB, bool TOUT = false, bool F8 = false>
 afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaStream_t st,
                       int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
     using Cfg = TcCfg<SA, SB>;
@@ -594,7 +688,7 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
     if (n1 < 0) n1 = n;
     const int tiles = ((m1 - m0 + TC_BM - 1) / TC_BM) * ((n1 - n0 + TC_BN - 1) / TC_BN);
     const int grid = tiles < dp.sm_count ? tiles : dp.sm_count;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, TOUT>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, TOUT, F8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
@@ -602,8 +696,8 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
     std::memcpy(&ma, TOUT ? t->tmap_at : t->tmap_a, sizeof ma);
     std::memcpy(&mb, TOUT ? t->tmap_bt : t->tmap_b, sizeof mb);
     main_kernel_begin(st);
-    tc_gemm_kernel<SA, SB, TOUT><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
-        ma, mb, Z, ldz, m0, m1, n0, n1, n, vec, status);
+    tc_gemm_kernel<SA, SB, TOUT, F8><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
+        ma, mb, Z, ldz, m0, m1, n0, n1, n, vec, status, t->amax, t->f8_kbpc);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, grid);
     count_launches(1);
@@ -690,11 +784,30 @@ double dtype_bound(int dt) {
 }
 }  // namespace
 
-void tc_layout(TcPlan* t, const afmm_desc& d, int slices) {
+void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8) {
     t->n = d.n;
     t->slices = slices;
     t->sliced_a = d.kase == AFMM_CASE_A;
+    t->f8 = f8;
     t->ld_a = t->ld_b = (d.n + 7) / 8 * 8;
+    if (f8) {
+        // E4M3 operands: 16-byte aligned rows of one-byte elements; the
+        // row maxima of the sliced operand.
+        t->ld_a = t->ld_b = (d.n + 15) / 16 * 16;
+        t->f8_kbpc = kF8ChunkKb;
+        if (const char* e = std::getenv("AFMM_FP8_CHUNK_KB")) t->f8_kbpc = std::atoi(e);
+        const int sa = t->sliced_a ? slices : 1, sb = t->sliced_a ? 1 : slices;
+        t->rows_a = t->rows_b = d.n;
+        t->a_bytes = (size_t)sa * d.n * t->ld_a;
+        t->b_bytes = (size_t)sb * d.n * t->ld_b;
+        t->s_bytes = (size_t)d.n * sizeof(uint32_t);
+        const int64_t ldz = d.ldz ? d.ldz : d.n;
+        if (t->sliced_a && ldz % 4 != 0) {
+            t->ld_z = (d.n + 3) / 4 * 4;
+            t->z_bytes = (size_t)d.n * t->ld_z * 4;
+        }
+        return;
+    }
     if (slices == 0) {
         // Exact form: A = X, B = Y^T, one BF16 operand each.
         const int rep_dt = d.kase == AFMM_CASE_A ? d.y_dtype : d.x_dtype;
@@ -723,20 +836,22 @@ void tc_layout(TcPlan* t, const afmm_desc& d, int slices) {
     }
 }
 
-afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z) {
+afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z, void* s) {
     t->a = a;
     t->b = b;
     t->z = t->z_bytes ? z : nullptr;
+    t->amax = t->s_bytes ? static_cast<uint32_t*>(s) : nullptr;
     t->maps_ready = false;
     if (t->n <= 0) return AFMM_OK;
     const int sl = t->slices > 0 ? t->slices : 1;
     const int sa = t->sliced_a ? sl : 1, sb = t->sliced_a ? 1 : sl;
-    AFMM_TRY(tc_encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM));
-    AFMM_TRY(tc_encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN));
+    const int es = t->f8 ? 1 : 2;
+    AFMM_TRY(tc_encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM, es));
+    AFMM_TRY(tc_encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN, es));
     if (!t->sliced_a && t->slices > 0) {
         // Case B as Z^T = Y^T X^T: the sliced Y^T rows are the A side.
-        AFMM_TRY(tc_encode_map(t->tmap_at, b, t->n, t->n, t->ld_b, sb, TC_BM));
-        AFMM_TRY(tc_encode_map(t->tmap_bt, a, t->n, t->n, t->ld_a, sa, TC_BN));
+        AFMM_TRY(tc_encode_map(t->tmap_at, b, t->n, t->n, t->ld_b, sb, TC_BM, es));
+        AFMM_TRY(tc_encode_map(t->tmap_bt, a, t->n, t->n, t->ld_a, sa, TC_BN, es));
     }
     t->maps_ready = true;
     return AFMM_OK;
@@ -796,6 +911,33 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                : launch_tc<2, 1, true>(t, Zf, d.ldz, status, st);
 }
 
+afmm_status tc_run_fp8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
+                       void* Z, int* status, cudaStream_t st) {
+    if (!t->maps_ready || !t->f8) return AFMM_ERR_INVALID_ARG;
+    const int64_t n = d.n;
+    float* Zf = static_cast<float*>(Z);
+    if (d.kase == AFMM_CASE_A) {
+        // A = four slices of the real X (rows), B = Rep-factors Y transposed.
+        AFMM_TRY(tc_f8_rows(false, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, t->amax, status, st));
+        AFMM_TRY(tc_f8_transpose(true, Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, t->amax, status,
+                                 st));
+        if (t->z) {
+            float* zt = static_cast<float*>(t->z);
+            AFMM_TRY((launch_tc<4, 1, false, true>(t, zt, t->ld_z, status, st)));
+            AFMM_CUDA_TRY(cudaMemcpy2DAsync(Zf, d.ldz * sizeof(float), zt,
+                                            t->ld_z * sizeof(float), n * sizeof(float), n,
+                                            cudaMemcpyDeviceToDevice, st));
+            return AFMM_OK;
+        }
+        return launch_tc<4, 1, false, true>(t, Zf, d.ldz, status, st);
+    }
+    // Case B as Z^T = Y^T X^T: A = four slices of Y^T (Y's columns), B = X.
+    AFMM_TRY(tc_f8_rows(true, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, t->amax, status, st));
+    AFMM_TRY(tc_f8_transpose(false, Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, t->amax, status,
+                             st));
+    return launch_tc<4, 1, true, true>(t, Zf, d.ldz, status, st);
+}
+
 afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st) {
     if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;
@@ -814,6 +956,9 @@ afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int
                                cudaStream_t st) {
     if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;
     const int sl = t->slices;
+    if (t->f8)
+        return tc_f8_transpose(d.kase == AFMM_CASE_A, Y, d.y_dtype, d.n, d.ldy, t->b, t->ld_b,
+                               t->amax, status, st);
     if (d.kase == AFMM_CASE_A)        // B = Rep-factors Y transposed
         return tc_widen_transpose(1, true, Y, d.y_dtype, d.n, d.ldy, t->b, t->ld_b, 256.f,
                                   status, st);
@@ -826,14 +971,21 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
     if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;
     const int64_t n = d.n;
     const int sl = t->slices;
+    const int m0 = (int)r0, m1 = (int)r1;
+    float* Zf = static_cast<float*>(Z);
+    if (t->f8) {
+        AFMM_TRY(tc_f8_rows(d.kase == AFMM_CASE_B, X, d.x_dtype, n, d.ldx, t->a, t->ld_a,
+                            t->amax, status, st, r0, r1));
+        return d.kase == AFMM_CASE_A
+                   ? launch_tc<4, 1, false, true>(t, Zf, d.ldz, status, st, m0, m1)
+                   : launch_tc<4, 1, true, true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1);
+    }
     if (d.kase == AFMM_CASE_A)
         AFMM_TRY(tc_widen_rows(sl, false, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 0.f, status,
                                st, r0, r1));
     else
         AFMM_TRY(tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 256.f, status,
                                st, r0, r1));
-    const int m0 = (int)r0, m1 = (int)r1;
-    float* Zf = static_cast<float*>(Z);
     if (d.kase == AFMM_CASE_A)
         return sl == 3 ? launch_tc<3, 1>(t, Zf, d.ldz, status, st, m0, m1)
                        : launch_tc<2, 1>(t, Zf, d.ldz, status, st, m0, m1);

@@ -17,8 +17,8 @@ struct TcPlan {
     int64_t ld_a = 0, ld_b = 0;     // leading dims (elements) of A / B operands
     int64_t rows_a = 0, rows_b = 0; // rows of the stacked A / B buffers
     size_t a_bytes = 0, b_bytes = 0;
-    void* a = nullptr;              // BF16 A operand(s), K-major
-    void* b = nullptr;              // BF16 B operand(s), K-major (B^T rows)
+    void* a = nullptr;              // A operand(s), K-major (BF16 or E4M3)
+    void* b = nullptr;              // B operand(s), K-major (B^T rows)
     bool sliced_a = true;           // real factor on the A side (case A)
     int kb_per_chunk = 0;           // exact form: K chunk in 32-wide k-blocks
     float lim_a = 256.f, lim_b = 256.f;  // exact form: largest |value| allowed
@@ -28,6 +28,15 @@ struct TcPlan {
     size_t z_bytes = 0;
     int64_t ld_z = 0;
     void* z = nullptr;
+    // FP8 form (E4M3 operands, one byte per element, ld_a / ld_b multiples
+    // of 16): amax[m] = FP32 bits of the largest |value| of A row m, which
+    // sets the power of two the row's slices were scaled by.
+    bool f8 = false;
+    size_t s_bytes = 0;
+    uint32_t* amax = nullptr;
+    // k-blocks (of 64) after which the hi sum is added into FP32 registers
+    // (0: once per tile); AFMM_FP8_CHUNK_KB in the environment overrides.
+    int f8_kbpc = 0;
     alignas(64) unsigned char tmap_a[128];
     alignas(64) unsigned char tmap_b[128];
     // Case B split form computed as Z^T = Y^T X^T: A side = the b buffer.
@@ -37,10 +46,11 @@ struct TcPlan {
 };
 
 // TMA descriptor (written to `out`, 128 bytes, 64-byte aligned) of a stack
-// of `slices` BF16 matrices, `rows` x `cols` with leading dimension `ld`
-// elements; boxes of 32 columns x box_rows rows x 1 slice, 64-byte swizzle.
+// of `slices` matrices of es-byte elements (2: BF16, 1: E4M3), `rows` x
+// `cols` with leading dimension `ld` elements; boxes of 64 bytes of
+// columns x box_rows rows x 1 slice, 64-byte swizzle.
 afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
-                          int64_t ld, int slices, int box_rows);
+                          int64_t ld, int slices, int box_rows, int es = 2);
 
 // Operand conversions (tc_operands.cu): dst BF16 [slices][n][ldk].  Rows
 // kept (K-major A) or transposed (K-major B, dst row = source column).
@@ -54,21 +64,40 @@ afmm_status tc_widen_transpose(int slices, bool exact, const void* src, int dt, 
                                int64_t lds, void* dst, int64_t ldk, float lim, int* status,
                                cudaStream_t st);
 
+// FP8 form conversions (tc_fp8.cu): dst E4M3 [slices][n][ldk], ldk a
+// multiple of 16.  rep: one slice that must equal the source (Rep-factors;
+// AFMM_ERR_OVERFLOW_RISK in *status otherwise).  Else four slices of each
+// row (tc_f8_rows) or column (tc_f8_transpose) scaled by a power of two
+// from its largest |value|, whose FP32 bits go to amax[row or column]
+// (a non-finite value: AFMM_ERR_OVERFLOW_RISK).  tc_f8_rows converts rows
+// [r0, r1) only; r1 < 0 means n.
+afmm_status tc_f8_rows(bool rep, const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                       int64_t ldk, uint32_t* amax, int* status, cudaStream_t st,
+                       int64_t r0 = 0, int64_t r1 = -1);
+afmm_status tc_f8_transpose(bool rep, const void* src, int dt, int64_t n, int64_t lds,
+                            void* dst, int64_t ldk, uint32_t* amax, int* status,
+                            cudaStream_t st);
+
 // True when this device can run the tensor-core kernels (sm_103).
 bool tc_available();
-// slices = 0 selects the exact-integer form (one BF16 operand each side).
-void tc_layout(TcPlan* t, const afmm_desc& d, int slices);
+// slices = 0 selects the exact-integer form (one BF16 operand each side);
+// f8 the FP8 form (four E4M3 slices).
+void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8 = false);
 // Largest K chunk (multiple of 32) with chunk * amax * bmax < 2^24, or 0
 // when even one 32-wide block could overflow.
 int tc_exact_chunk_k(double amax, double bmax);
-afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z);
+afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z, void* s);
 // Split / widen the operands and run the tcgen05 product into Z (F32).
 afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st);
+// The FP8 form: E4M3 slices and Rep-factors, the tcgen05 product into Z.
+afmm_status tc_run_fp8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
+                       void* Z, int* status, cudaStream_t st);
 // The same product in pieces for transfer pipelining: tc_split_prepare_b
 // converts the B operand (all of the factor that is not split by rows);
 // tc_split_rows converts rows [r0, r1) of the A operand and computes rows
-// [r0, r1) of Z.  Case A or B, 2 or 3 slices, the separate-split path.
+// [r0, r1) of Z.  Case A or B, 2 or 3 BF16 slices (the separate-split
+// path) or the FP8 form.
 afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int* status,
                                cudaStream_t st);
 afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,

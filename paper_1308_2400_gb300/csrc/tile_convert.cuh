@@ -75,20 +75,15 @@ __device__ __forceinline__ float value_checked(typename Elem<DT>::T v, float lim
 }
 
 // Rows r0 .. r0+63 and columns c0 .. c0+63 of the row-major n x n source
-// become rows c (K-major) of the destination: dst[(s * n + c) * ldk + r] =
-// slice s of src[r][c], for S BF16 slices (S = 1 and EXACT: the value must
-// be exact in BF16 and |v| <= lim, else the return value is true).
-// Loads: 16 bytes per thread and pass when `vec` (16-byte aligned rows) and
-// the tile is whole in columns, element loads otherwise; the tile goes
-// through shared memory as FP32; stores: four threads write one 128-byte
-// segment of an output row per slice.  256 threads; `tile` is [64][65].
-template <int DT, int S, bool EXACT>
-__device__ __forceinline__ bool tile_transpose_convert(const void* __restrict__ src,
-                                                       int64_t n, int64_t lds, int64_t r0,
-                                                       int64_t c0,
-                                                       __nv_bfloat16* __restrict__ dst,
-                                                       int64_t ldk, float lim, bool vec,
-                                                       float (*tile)[65]) {
+// into tile[r - r0][c - c0] as FP32, zero outside the matrix (value_checked
+// flags into `bad`).  16 bytes per thread and pass when `vec` (16-byte
+// aligned rows) and the tile is whole in columns, element loads otherwise.
+// 256 threads; `tile` is [64][65]; the caller synchronises before reading.
+template <int DT>
+__device__ __forceinline__ void tile_load_f32(const void* __restrict__ src, int64_t n,
+                                              int64_t lds, int64_t r0, int64_t c0,
+                                              float lim, bool vec, float (*tile)[65],
+                                              bool& bad) {
     using T = typename Elem<DT>::T;
     constexpr int V = 16 / (int)sizeof(T);     // elements per 16-byte load
     constexpr int TPR = 64 / V;                 // threads per tile row
@@ -97,7 +92,6 @@ __device__ __forceinline__ bool tile_transpose_convert(const void* __restrict__ 
     const int tid = threadIdx.x;
     const int lc = (tid % TPR) * V, lr = tid / TPR;
     const T* s = static_cast<const T*>(src);
-    bool bad = false;
     if (vec && c0 + 64 <= n) {
         uint4 q[P];
 #pragma unroll
@@ -124,6 +118,25 @@ __device__ __forceinline__ bool tile_transpose_convert(const void* __restrict__ 
             }
         }
     }
+}
+
+// Rows r0 .. r0+63 and columns c0 .. c0+63 of the row-major n x n source
+// become rows c (K-major) of the destination: dst[(s * n + c) * ldk + r] =
+// slice s of src[r][c], for S BF16 slices (S = 1 and EXACT: the value must
+// be exact in BF16 and |v| <= lim, else the return value is true).
+// Loads: tile_load_f32; the tile goes through shared memory as FP32;
+// stores: four threads write one 128-byte segment of an output row per
+// slice.  256 threads; `tile` is [64][65].
+template <int DT, int S, bool EXACT>
+__device__ __forceinline__ bool tile_transpose_convert(const void* __restrict__ src,
+                                                       int64_t n, int64_t lds, int64_t r0,
+                                                       int64_t c0,
+                                                       __nv_bfloat16* __restrict__ dst,
+                                                       int64_t ldk, float lim, bool vec,
+                                                       float (*tile)[65]) {
+    const int tid = threadIdx.x;
+    bool bad = false;
+    tile_load_f32<DT>(src, n, lds, r0, c0, lim, vec, tile, bad);
     if (!EXACT) bad = false;
     __syncthreads();
     const int cc = tid >> 2, qq = tid & 3;

@@ -763,6 +763,7 @@ _DEGENERATE_FORMS = {   # variant: (X dtype, Y dtype, Z dtype, target)
     0: ("f32", "i32", "f32", "fp32"), 1: ("f32", "i32", "f32", "fp32"),
     6: ("f32", "i32", "f32", "fp32"), 3: ("f64", "i32", "f64", "fp64"),
     4: ("i8", "i8", "i32", "exact"), 5: ("i8", "i8", "i32", "exact"),
+    7: ("f32", "i32", "f32", "fp32"),
 }
 
 
