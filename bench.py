@@ -242,7 +242,7 @@ def traffic_from_profile(kernel_tag, workload):
     if not os.path.exists(path):
         return None
     src = {"simt_gemm": "simt_gemm.cu", "tc_gemm": "tc_gemm.cu",
-           "sparse": "sparse.cu"}.get(kernel_tag)
+           "tc_gemm_fp8": "tc_gemm.cu", "sparse": "sparse.cu"}.get(kernel_tag)
     vals = {}
     with open(path) as f:
         for ln in f:
@@ -364,6 +364,13 @@ def run_afmm(args):
                 "traffic": traffic_from_profile("sparse", args.workload),
                 "kernel": "sp_mul", "kernel_ms": kms, "ctas": ctas,
                 "algorithmic_bytes_per_launch": alg}
+    elif vname == "tc_fp8x4":
+        # E4M3 MMAs: the measured BF16 rate times the nominal FP8/BF16 ratio.
+        alg = slices * flops
+        peak = 2.0 * peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_src": f"2 x bf16 sustained (nominal fp8/bf16 ratio), {peak_src}"}
+        tag = "tc_gemm_fp8"
     elif tc:
         alg = slices * flops
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -484,7 +491,8 @@ def run_afmm(args):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if tc else ("f64" if inst.target == "fp64" else
+            "dtype": ("e4m3" if vname == "tc_fp8x4" else "bf16") if tc else
+                     ("f64" if inst.target == "fp64" else
                                         ("i8" if inst.target == "exact" else "f32")),
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "case": inst.case,
