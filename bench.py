@@ -282,6 +282,7 @@ def run_afmm(args):
     Ys = inst.y_store if inst.y_store is not None else inst.Y
     X = torch.from_numpy(np.ascontiguousarray(Xs)).cuda()
     Y = torch.from_numpy(np.ascontiguousarray(Ys)).cuda()
+    Xd, Yd = X, Y
     zt = {"f32": torch.float32, "f64": torch.float64, "i32": torch.int32}[inst.z_dtype]
     Z = torch.empty((n, n), dtype=zt, device="cuda")
 
@@ -305,10 +306,11 @@ def run_afmm(args):
 
     stream = torch.cuda.Stream()
 
-    def timed(plan, steps, warmup):
+    def timed(plan, steps, warmup, ops=None):
         """Step time over `steps` calls (no per-kernel events in them, so
         small problems replay their CUDA graph), then the dominant kernel's
         duration from events around it on its stream in a second pass."""
+        X, Y = ops if ops is not None else (Xd, Yd)
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 plan(X, Y, Z, stream)
@@ -439,6 +441,21 @@ def run_afmm(args):
         Z_f8 = Z.cpu().numpy() if ws == 1 else None
         p5.close()
 
+    # A product of two real matrices (no Rep-factor) with the workload's X as
+    # both factors: both split into three BF16 slices, six slice products.
+    rr = None
+    Z_rr = None
+    if rank == 0 and vname == "tc_bf16x3" and inst.case == "A" and not args.quick:
+        p6 = Plan(make_desc(n, "REAL", inst.x_dtype, inst.x_dtype, "f32", "fp32"))
+        ms6, kms6, _, _ = timed(p6, max(2, min(args.steps // 8, 50)), 3, (Xd, Xd))
+        tf6 = 6 * flops / (kms6 * 1e-3) / 1e12
+        rr = {"variant": VARIANT_NAMES.get(p6.info["variant"], "?"), "operands": "X, X",
+              "value": flops / (ms6 * 1e-3) / 1e12, "ms_per_step": ms6,
+              "kernel_ms": kms6, "tensor_tflops": tf6,
+              "frac": tf6 / peaks.get("bf16_tflops_sustained", 1700.0)}
+        Z_rr = Z.cpu().numpy() if ws == 1 else None
+        p6.close()
+
     # End to end through the C ABI with pinned host buffers: copies in,
     # product, copy out, every step.
     e2e = None
@@ -485,6 +502,13 @@ def run_afmm(args):
         if f8 is not None and Z_f8 is not None:
             d8 = float(np.linalg.norm(Z_f8[rows].astype(np.float64) - Zr))
             f8["rel_fro_err_vs_oracle"] = d8 / den if den else 0.0
+        if rr is not None and Z_rr is not None:
+            from oracle import classical_ikj
+            r16 = rows[:16]
+            Rr = classical_ikj(inst.X, inst.X, r16)
+            rr["rel_fro_err_vs_oracle"] = float(
+                np.linalg.norm(Z_rr[r16].astype(np.float64) - Rr) / np.linalg.norm(Rr))
+            rr["rows_checked"] = int(r16.size)
 
     if rank == 0:
         line = {
@@ -505,7 +529,7 @@ def run_afmm(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches) * ws, "clocks": clocks,
             "accuracy": acc, "plain_fp32": plain, "fused_split": fused,
-            "two_slices": two, "fp8_slices": f8,
+            "two_slices": two, "fp8_slices": f8, "real_x_real": rr,
         }
         print(json.dumps(line), flush=True)
     plan.close()

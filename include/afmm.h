@@ -59,8 +59,10 @@ typedef enum {
     AFMM_ERR_NONINTEGER_REP = 9   /* a Rep-factor is not an integer */
 } afmm_status;
 
-/* Which factor holds the Rep-factors (Sec. 2). */
-typedef enum { AFMM_CASE_A = 0, AFMM_CASE_B = 1 } afmm_case;
+/* Which factor holds the Rep-factors (Sec. 2).  AFMM_CASE_REAL: neither --
+ * both factors real, the generalisation the paper's conclusion (Sec. 4)
+ * leaves open; such plans multiply with afmm_mul_real, FP32 target. */
+typedef enum { AFMM_CASE_A = 0, AFMM_CASE_B = 1, AFMM_CASE_REAL = 2 } afmm_case;
 
 /* Element types.  AFMM_E4M3 is FP8 e4m3 (OCP, "fn"); it holds the integers
  * 0..16 exactly.  Rep-factor matrices may be I32, I8, U8, E4M3, BF16 or F32
@@ -124,7 +126,15 @@ typedef enum {
      * E4M3 MMAs per K step in place of three BF16 ones at twice the
      * rate.  FP32 target; never chosen automatically. */
     AFMM_VARIANT_TC_FP8X4 = 7,
-    AFMM_VARIANT_COUNT_ = 8
+    /* Tensor cores for two real factors (AFMM_CASE_REAL): both split into
+     * three BF16 slices (hi+mid+lo = the FP32 value), and the six slice
+     * products down to 2^-16 of the hi product -- (hi,hi), (hi,mid),
+     * (mid,hi), (hi,lo), (mid,mid), (lo,hi) -- with the (hi,hi) products
+     * kept in their own FP32 accumulator (an Ozaki-style split; Ozaki,
+     * Ogita, Oishi and Rump, Numer. Algorithms 59, 2012; Ootomo and Yokota,
+     * IJHPCA 36, 2022).  FP32 target. */
+    AFMM_VARIANT_TC_BF16X3X3 = 8,
+    AFMM_VARIANT_COUNT_ = 9
 } afmm_variant;
 
 /* Flags for afmm_desc.flags. */
@@ -213,6 +223,14 @@ afmm_status afmm_mul_caseA(afmm_plan plan, const void* X, const void* Y,
  * The plan must have been created with kase == AFMM_CASE_B. */
 afmm_status afmm_mul_caseB(afmm_plan plan, const void* X, const void* Y,
                            void* Z, void* stream);
+
+/* Product of two real matrices, Z = X * Y (no Rep-factor: the Sec. 4
+ * generalisation).  X and Y F32, F64, BF16 or integer typed, Z F32, FP32
+ * target.  The plan must have been created with kase == AFMM_CASE_REAL;
+ * its variant is AFMM_VARIANT_TC_BF16X3X3 (tensor cores) or
+ * AFMM_VARIANT_SIMT_F32 (CUDA cores, skipping zero entries of X). */
+afmm_status afmm_mul_real(afmm_plan plan, const void* X, const void* Y, void* Z,
+                          void* stream);
 
 /* Wait for the plan's work on `stream` and return the first error a kernel
  * recorded since the previous sync (clearing it), else AFMM_OK. */

@@ -29,7 +29,7 @@ AFMM_ERR_TIMEOUT = 7
 AFMM_ERR_NO_DEVICE = 8
 AFMM_ERR_NONINTEGER_REP = 9
 
-AFMM_CASE_A, AFMM_CASE_B = 0, 1
+AFMM_CASE_A, AFMM_CASE_B, AFMM_CASE_REAL = 0, 1, 2
 AFMM_F64, AFMM_F32, AFMM_BF16, AFMM_E4M3, AFMM_I32, AFMM_I8, AFMM_U8 = range(7)
 AFMM_TARGET_FP32, AFMM_TARGET_FP64, AFMM_TARGET_EXACT = 0, 1, 2
 AFMM_VARIANT_AUTO = -1
@@ -41,6 +41,7 @@ AFMM_VARIANT_SIMT_EXACT = 4
 AFMM_VARIANT_TC_EXACT = 5
 AFMM_VARIANT_SPARSE = 6
 AFMM_VARIANT_TC_FP8X4 = 7
+AFMM_VARIANT_TC_BF16X3X3 = 8
 AFMM_FLAG_VALIDATE = 0x1
 AFMM_FLAG_FUSED_SPLIT = 0x2
 
@@ -50,7 +51,9 @@ VARIANT_NAMES = {
     AFMM_VARIANT_SIMT_F64SLICE: "simt_f64slice",
     AFMM_VARIANT_SIMT_EXACT: "simt_exact", AFMM_VARIANT_TC_EXACT: "tc_exact",
     AFMM_VARIANT_SPARSE: "sparse", AFMM_VARIANT_TC_FP8X4: "tc_fp8x4",
+    AFMM_VARIANT_TC_BF16X3X3: "tc_bf16x3x3",
 }
+CASE_CODES = {"A": AFMM_CASE_A, "B": AFMM_CASE_B, "REAL": AFMM_CASE_REAL}
 DTYPE_CODES = {"f64": AFMM_F64, "f32": AFMM_F32, "bf16": AFMM_BF16,
                "e4m3": AFMM_E4M3, "i32": AFMM_I32, "i8": AFMM_I8,
                "u8": AFMM_U8}
@@ -133,6 +136,7 @@ def _lib():
             "afmm_plan_set_workspace": ([_VP, _VP, ctypes.c_size_t], st),
             "afmm_mul_caseA": ([_VP, _VP, _VP, _VP, _VP], st),
             "afmm_mul_caseB": ([_VP, _VP, _VP, _VP, _VP], st),
+            "afmm_mul_real": ([_VP, _VP, _VP, _VP, _VP], st),
             "afmm_plan_sync": ([_VP, _VP], st),
             "afmm_get_info": ([_VP, ctypes.POINTER(afmm_info)], st),
             "afmm_plan_enable_kernel_timing": ([_VP, ctypes.c_int], st),
@@ -227,11 +231,13 @@ def make_desc(n: int, case: str = "A", x_dtype="f32", y_dtype="f32",
               mu_prime: float = -1.0, ldx: int = 0, ldy: int = 0,
               ldz: int = 0, rep_max: float = -1.0,
               base_max: float = -1.0) -> afmm_desc:
-    """Fill an ``afmm_desc`` from readable names ("A"/"B", "f32", "fp32")."""
+    """Fill an ``afmm_desc`` from readable names ("A"/"B"/"REAL", "f32",
+    "fp32")."""
     def code(v, table):
         return table[v] if isinstance(v, str) else int(v)
     return afmm_desc(n=int(n), ldx=int(ldx), ldy=int(ldy), ldz=int(ldz),
-                     kase=AFMM_CASE_A if str(case).upper() == "A" else AFMM_CASE_B,
+                     kase=code(str(case).upper() if isinstance(case, str) else case,
+                               CASE_CODES),
                      x_dtype=code(x_dtype, DTYPE_CODES),
                      y_dtype=code(y_dtype, DTYPE_CODES),
                      z_dtype=code(z_dtype, DTYPE_CODES),
@@ -272,6 +278,11 @@ def afmm_mul_caseA(plan: int, X, Y, Z, stream=None) -> None:
 def afmm_mul_caseB(plan: int, X, Y, Z, stream=None) -> None:
     _check(_lib().afmm_mul_caseB(plan, _ptr(X), _ptr(Y), _ptr(Z),
                                  _stream(stream)), "afmm_mul_caseB")
+
+
+def afmm_mul_real(plan: int, X, Y, Z, stream=None) -> None:
+    _check(_lib().afmm_mul_real(plan, _ptr(X), _ptr(Y), _ptr(Z),
+                                _stream(stream)), "afmm_mul_real")
 
 
 def afmm_plan_sync(plan: int, stream=None) -> None:
@@ -441,6 +452,8 @@ class Plan:
     def __call__(self, X, Y, Z, stream=None) -> None:
         if self.desc.kase == AFMM_CASE_A:
             afmm_mul_caseA(self.handle, X, Y, Z, stream)
+        elif self.desc.kase == AFMM_CASE_REAL:
+            afmm_mul_real(self.handle, X, Y, Z, stream)
         else:
             afmm_mul_caseB(self.handle, X, Y, Z, stream)
 

@@ -151,7 +151,7 @@ size_t span_bytes(int64_t n, int64_t ld, int dt) {
 afmm_status check_desc(const afmm_desc* d) {
     if (!d) return AFMM_ERR_INVALID_ARG;
     if (d->n < 0 || d->reserved_ != 0) return AFMM_ERR_INVALID_ARG;
-    if (d->kase != AFMM_CASE_A && d->kase != AFMM_CASE_B)
+    if (d->kase != AFMM_CASE_A && d->kase != AFMM_CASE_B && d->kase != AFMM_CASE_REAL)
         return AFMM_ERR_INVALID_ARG;
     if (d->target < AFMM_TARGET_FP32 || d->target > AFMM_TARGET_EXACT)
         return AFMM_ERR_INVALID_ARG;
@@ -163,6 +163,14 @@ afmm_status check_desc(const afmm_desc* d) {
     const int64_t ldx = d->ldx ? d->ldx : n, ldy = d->ldy ? d->ldy : n,
                   ldz = d->ldz ? d->ldz : n;
     if (ldx < n || ldy < n || ldz < n) return AFMM_ERR_INVALID_ARG;
+    if (d->kase == AFMM_CASE_REAL) {
+        // Two real factors: FP32 target only.
+        for (int dt : {d->x_dtype, d->y_dtype})
+            if (!real_dtype_ok(dt) && !dtype_is_integer(dt)) return AFMM_ERR_INVALID_ARG;
+        if (d->target != AFMM_TARGET_FP32 || d->z_dtype != AFMM_F32)
+            return AFMM_ERR_INVALID_ARG;
+        return AFMM_OK;
+    }
     const int rep_dt = d->kase == AFMM_CASE_A ? d->y_dtype : d->x_dtype;
     const int base_dt = d->kase == AFMM_CASE_A ? d->x_dtype : d->y_dtype;
     if (!rep_dtype_ok(rep_dt)) return AFMM_ERR_INVALID_ARG;
@@ -182,6 +190,9 @@ afmm_status check_desc(const afmm_desc* d) {
 }
 
 bool variant_serves(int v, const afmm_desc* d) {
+    if (d->kase == AFMM_CASE_REAL)
+        return v == AFMM_VARIANT_SIMT_F32 ||
+               (v == AFMM_VARIANT_TC_BF16X3X3 && tc_available());
     switch (v) {
         case AFMM_VARIANT_SIMT_F32:
             return d->target == AFMM_TARGET_FP32;
@@ -203,6 +214,9 @@ bool variant_serves(int v, const afmm_desc* d) {
 }
 
 int auto_variant(const afmm_desc* d) {
+    if (d->kase == AFMM_CASE_REAL)
+        return (tc_available() && d->n >= 128) ? AFMM_VARIANT_TC_BF16X3X3
+                                               : AFMM_VARIANT_SIMT_F32;
     if (d->target == AFMM_TARGET_EXACT)
         return (tc_available() && d->n >= 128) ? AFMM_VARIANT_TC_EXACT
                                                : AFMM_VARIANT_SIMT_EXACT;
@@ -286,6 +300,13 @@ void plan_layout(afmm_plan_s* p) {
             p->off_c = L.take(p->tc.z_bytes);
             break;
         }
+        case AFMM_VARIANT_TC_BF16X3X3: {
+            tc_layout(&p->tc, d, p->slices);
+            p->off_a = L.take(p->tc.a_bytes);
+            p->off_b = L.take(p->tc.b_bytes);
+            p->off_c = L.take(p->tc.z_bytes);
+            break;
+        }
         case AFMM_VARIANT_TC_FP8X4: {
             tc_layout(&p->tc, d, p->slices, true);
             p->off_a = L.take(p->tc.a_bytes);
@@ -322,7 +343,8 @@ afmm_status ensure_workspace(afmm_plan_s* p, cudaStream_t st) {
         AFMM_CUDA_TRY(cudaMemsetAsync(p->ws + p->off_status, 0, kAlign, st));
         if (p->variant == AFMM_VARIANT_TC_BF16X3 ||
             p->variant == AFMM_VARIANT_TC_BF16X2 ||
-            p->variant == AFMM_VARIANT_TC_EXACT || p->variant == AFMM_VARIANT_TC_FP8X4)
+            p->variant == AFMM_VARIANT_TC_EXACT || p->variant == AFMM_VARIANT_TC_FP8X4 ||
+            p->variant == AFMM_VARIANT_TC_BF16X3X3)
             AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a, p->ws + p->off_b,
                                        p->ws + p->off_c, p->ws + p->off_e));
         if (p->variant == AFMM_VARIANT_SPARSE) AFMM_TRY(sparse_reset(p->ws + p->off_a, st));
@@ -414,12 +436,14 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
     const afmm_desc& d = p->d;
     const int64_t n = d.n;
     if (d.flags & AFMM_FLAG_VALIDATE) {
-        const bool a = d.kase == AFMM_CASE_A;
+        // Rep-factors are checked (non-negative integers); real factors of
+        // a real x real plan only counted.
+        const bool x_rep = d.kase == AFMM_CASE_B, y_rep = d.kase == AFMM_CASE_A;
         int* status = wsp<int>(p, p->off_status);
         ScanStats* part = wsp<ScanStats>(p, p->off_part);
-        AFMM_TRY(launch_scan(X, d.x_dtype, n, d.ldx ? d.ldx : n, !a, part,
+        AFMM_TRY(launch_scan(X, d.x_dtype, n, d.ldx ? d.ldx : n, x_rep, part,
                              wsp<ScanStats>(p, p->off_sx), status, st));
-        AFMM_TRY(launch_scan(Y, d.y_dtype, n, d.ldy ? d.ldy : n, a, part,
+        AFMM_TRY(launch_scan(Y, d.y_dtype, n, d.ldy ? d.ldy : n, y_rep, part,
                              wsp<ScanStats>(p, p->off_sy), status, st));
         p->validated = true;
     }
@@ -435,6 +459,8 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
             return tc_run_exact(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_TC_FP8X4:
             return tc_run_fp8(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
+        case AFMM_VARIANT_TC_BF16X3X3:
+            return tc_run_real(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_SPARSE:
             return launch_sparse(X, d.x_dtype, d.ldx ? d.ldx : n, Y, d.y_dtype,
                                  d.ldy ? d.ldy : n, static_cast<float*>(Z),
@@ -714,6 +740,8 @@ afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc) {
         p->slices = 2;
     } else if (v == AFMM_VARIANT_TC_FP8X4) {
         p->slices = 4;
+    } else if (v == AFMM_VARIANT_TC_BF16X3X3) {
+        p->slices = 3;
     }
     plan_layout(p);
     *out = p;
@@ -770,6 +798,11 @@ afmm_status afmm_mul_caseA(afmm_plan p, const void* X, const void* Y, void* Z,
     return mul_impl(p, X, Y, Z, stream, AFMM_CASE_A);
 }
 
+afmm_status afmm_mul_real(afmm_plan p, const void* X, const void* Y, void* Z,
+                          void* stream) {
+    return mul_impl(p, X, Y, Z, stream, AFMM_CASE_REAL);
+}
+
 afmm_status afmm_mul_caseB(afmm_plan p, const void* X, const void* Y, void* Z,
                            void* stream) {
     return mul_impl(p, X, Y, Z, stream, AFMM_CASE_B);
@@ -816,10 +849,12 @@ afmm_status afmm_get_info(afmm_plan p, afmm_info* out) {
         const ScanStats& rep = p->d.kase == AFMM_CASE_A ? sy : sx;
         o.d1 = n2 > 0 ? (double)sx.nnz / n2 : 0.0;
         o.d2 = n2 > 0 ? (double)sy.nnz / n2 : 0.0;
-        o.mu_prime = rep.nnz ? rep.sum / (double)rep.nnz : 0.0;
-        o.mu = n2 > 0 ? rep.sum / n2 : 0.0;
-        o.rep_max = rep.maxv;
-        o.expected_additions = o.mu_prime * o.d1 * o.d2 * n * n2;
+        if (p->d.kase != AFMM_CASE_REAL) {       // no Rep-factor otherwise
+            o.mu_prime = rep.nnz ? rep.sum / (double)rep.nnz : 0.0;
+            o.mu = n2 > 0 ? rep.sum / n2 : 0.0;
+            o.rep_max = rep.maxv;
+            o.expected_additions = o.mu_prime * o.d1 * o.d2 * n * n2;
+        }
     }
     return AFMM_OK;
 }

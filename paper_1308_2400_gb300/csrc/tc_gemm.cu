@@ -13,6 +13,10 @@
 //    Y, Case B computes Z^T = Y^T X^T with Y's slices and stores the tiles
 //    transposed; the Rep-factor tile of a k step is loaded once and used by
 //    the S MMAs.
+// The same kernel runs the FP8 form (F8: four E4M3 slices of the row-scaled
+// real factor, kind::f8f6f4, tc_fp8.cu / fp8_split.cuh) and the real x real
+// product (no Rep-factor: three BF16 slices of both factors, six of the nine
+// slice products).
 //
 // tc_gemm_kernel (split form; one CTA per SM, persistent over 128 x 256
 // output tiles):
@@ -58,8 +62,10 @@ constexpr int B_TILE_BYTES = TC_BN * TC_BK * 2;   // 16 KiB
 constexpr int SMEM_OPTIN = 232448;                // 227 KiB per CTA
 constexpr int GROUP_M = 10;                       // tile raster band
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
-// FP8 form: k-blocks of 64 per chunk of the hi sum (0: one chunk per tile).
+// k-blocks per chunk of the hi sum (0: one chunk per tile): FP8 form
+// (blocks of 64), real x real form (blocks of 32).
 constexpr int kF8ChunkKb = 16;
+constexpr int kRealChunkKb = 12;
 
 template <int SA, int SB>
 struct TcCfg {
@@ -67,8 +73,11 @@ struct TcCfg {
     static constexpr int STAGES_FIT = (SMEM_OPTIN - 2048) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
     static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256;
-    static constexpr int P = SA > SB ? SA : SB;   // MMAs per 16-wide k step
-    static_assert(SA == 1 || SB == 1, "slices on one side only");
+    // Both factors sliced (three slices each: the real x real form) or one.
+    static constexpr bool BOTH = SA > 1 && SB > 1;
+    // MMAs per 32-byte K step: one per slice, or six slice pairs.
+    static constexpr int P = BOTH ? 6 : (SA > SB ? SA : SB);
+    static_assert(!BOTH || (SA == 3 && SB == 3), "both sides: three slices each");
     static_assert(STAGES >= 2, "pipeline needs two stages");
     static_assert(SMEM <= SMEM_OPTIN, "shared memory");
 };
@@ -83,6 +92,20 @@ struct TcBars {
     int abort;
 };
 static_assert(sizeof(TcBars) <= 256, "barrier block");
+
+// (A slice, B slice) of product p.  One-sided forms pair slice p with the
+// other side's only tile.  With three BF16 slices on both sides (a real x
+// real product) the six pairs whose products reach down to 2^-16 of the hi
+// product: (0,0), (0,1), (1,0), (0,2), (1,1), (2,0); the pairs left out,
+// (1,2), (2,1), (2,2), are below 2^-23 of it.
+template <int SA, int SB>
+__device__ __forceinline__ constexpr int slice_a(int p) {
+    return SA > 1 && SB > 1 ? (p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0)) : (SA > 1 ? p : 0);
+}
+template <int SA, int SB>
+__device__ __forceinline__ constexpr int slice_b(int p) {
+    return SA > 1 && SB > 1 ? (p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0)) : (SB > 1 ? p : 0);
+}
 
 __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n,
                                             int& tm, int& tn) {
@@ -135,7 +158,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     const int num_tiles = tiles_m * tiles_n;
     const int num_kb = (K + BK - 1) / BK;
     // k-blocks per chunk of the hi sum, and chunks per tile.
-    const int kc = (F8 && kbpc > 0 && kbpc < num_kb) ? kbpc : num_kb;
+    // The FP8 and real x real forms close their hi sum every kbpc k-blocks.
+    constexpr bool CH = F8 || Cfg::BOTH;
+    const int kc = (CH && kbpc > 0 && kbpc < num_kb) ? kbpc : num_kb;
     const int nch = (num_kb + kc - 1) / kc;
 
     if (threadIdx.x == 0) {
@@ -256,12 +281,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
 #pragma unroll
                         for (int p = Cfg::P - 1; p >= 0; --p) {
                             const uint32_t a_addr =
-                                s0 + (SA > 1 ? p : 0) * A_TILE_BYTES + ks * 32;
+                                s0 + slice_a<SA, SB>(p) * A_TILE_BYTES + ks * 32;
                             const uint32_t b_addr = s0 + SA * A_TILE_BYTES +
-                                                    (SB > 1 ? p : 0) * B_TILE_BYTES +
+                                                    slice_b<SA, SB>(p) * B_TILE_BYTES +
                                                     ks * 32;
-                            // Slices are issued from the last: the first MMA
-                            // into each accumulator overwrites it.
+                            // Products are issued from the last (smallest):
+                            // the first MMA into each accumulator overwrites it.
                             const bool first =
                                 ks == 0 && ((chunk0 && p == HI - 1) ||
                                             (kb == 0 && p == Cfg::P - 1));
@@ -308,7 +333,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
             float sum[128];
             bool got = true;
             // F8, chunks before the last: add the hi sum into sum[].
-            for (int ch = 0; F8 && ch + 1 < nch; ++ch) {
+            for (int ch = 0; CH && ch + 1 < nch; ++ch) {
                 got = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&bars->tfull[0], tphase,
                                                                       abort, WAIT_LIMIT_NS));
                 if (!got) break;
@@ -366,14 +391,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
             } else {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    // hi-slice sum + small-slice sum, one rounding.
+                    // hi-slice sum (its last chunk added to the earlier ones)
+                    // + small-slice sum, one rounding.
                     uint32_t r0[16], r1[16];
                     ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
                     ptx::tmem_ld_16cols(lane_base + (uint32_t)(TC_BN + c * 16), r1);
                     ptx::tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        sum[c * 16 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    for (int j = 0; j < 16; ++j) {
+                        const float hi = CH && nch > 1
+                                             ? sum[c * 16 + j] + __uint_as_float(r0[j])
+                                             : __uint_as_float(r0[j]);
+                        sum[c * 16 + j] = hi + __uint_as_float(r1[j]);
+                    }
                 }
             }
             // TMEM is free again before the stores below.
@@ -697,7 +727,7 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
     std::memcpy(&mb, TOUT ? t->tmap_bt : t->tmap_b, sizeof mb);
     main_kernel_begin(st);
     tc_gemm_kernel<SA, SB, TOUT, F8><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
-        ma, mb, Z, ldz, m0, m1, n0, n1, n, vec, status, t->amax, t->f8_kbpc);
+        ma, mb, Z, ldz, m0, m1, n0, n1, n, vec, status, t->amax, t->chunk_kb);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, grid);
     count_launches(1);
@@ -787,15 +817,16 @@ double dtype_bound(int dt) {
 void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8) {
     t->n = d.n;
     t->slices = slices;
-    t->sliced_a = d.kase == AFMM_CASE_A;
+    t->sliced_a = d.kase != AFMM_CASE_B;
+    t->both = d.kase == AFMM_CASE_REAL;
     t->f8 = f8;
     t->ld_a = t->ld_b = (d.n + 7) / 8 * 8;
     if (f8) {
         // E4M3 operands: 16-byte aligned rows of one-byte elements; the
         // row maxima of the sliced operand.
         t->ld_a = t->ld_b = (d.n + 15) / 16 * 16;
-        t->f8_kbpc = kF8ChunkKb;
-        if (const char* e = std::getenv("AFMM_FP8_CHUNK_KB")) t->f8_kbpc = std::atoi(e);
+        t->chunk_kb = kF8ChunkKb;
+        if (const char* e = std::getenv("AFMM_TC_CHUNK_KB")) t->chunk_kb = std::atoi(e);
         const int sa = t->sliced_a ? slices : 1, sb = t->sliced_a ? 1 : slices;
         t->rows_a = t->rows_b = d.n;
         t->a_bytes = (size_t)sa * d.n * t->ld_a;
@@ -824,7 +855,11 @@ void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8) {
         t->b_bytes = (size_t)d.n * t->ld_b * 2;
         return;
     }
-    const int sa = t->sliced_a ? slices : 1, sb = t->sliced_a ? 1 : slices;
+    const int sa = t->sliced_a ? slices : 1, sb = t->sliced_a && !t->both ? 1 : slices;
+    if (t->both) {
+        t->chunk_kb = kRealChunkKb;
+        if (const char* e = std::getenv("AFMM_TC_CHUNK_KB")) t->chunk_kb = std::atoi(e);
+    }
     t->rows_a = d.n;
     t->rows_b = d.n;
     t->a_bytes = (size_t)sa * d.n * t->ld_a * 2;
@@ -844,7 +879,7 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z, void* s) {
     t->maps_ready = false;
     if (t->n <= 0) return AFMM_OK;
     const int sl = t->slices > 0 ? t->slices : 1;
-    const int sa = t->sliced_a ? sl : 1, sb = t->sliced_a ? 1 : sl;
+    const int sa = t->sliced_a ? sl : 1, sb = t->sliced_a && !t->both ? 1 : sl;
     const int es = t->f8 ? 1 : 2;
     AFMM_TRY(tc_encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM, es));
     AFMM_TRY(tc_encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN, es));
@@ -909,6 +944,27 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
     return t->slices == 3
                ? launch_tc<3, 1, true>(t, Zf, d.ldz, status, st)
                : launch_tc<2, 1, true>(t, Zf, d.ldz, status, st);
+}
+
+afmm_status tc_run_real(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
+                        void* Z, int* status, cudaStream_t st) {
+    if (!t->maps_ready || !t->both) return AFMM_ERR_INVALID_ARG;
+    const int64_t n = d.n;
+    float* Zf = static_cast<float*>(Z);
+    // A = three slices of X (rows), B = three slices of Y transposed.
+    AFMM_TRY((tc_widen_rows(3, false, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 0.f, status,
+                            st)));
+    AFMM_TRY((tc_widen_transpose(3, false, Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, 0.f,
+                                 status, st)));
+    if (t->z) {
+        float* zt = static_cast<float*>(t->z);
+        AFMM_TRY((launch_tc<3, 3>(t, zt, t->ld_z, status, st)));
+        AFMM_CUDA_TRY(cudaMemcpy2DAsync(Zf, d.ldz * sizeof(float), zt,
+                                        t->ld_z * sizeof(float), n * sizeof(float), n,
+                                        cudaMemcpyDeviceToDevice, st));
+        return AFMM_OK;
+    }
+    return launch_tc<3, 3>(t, Zf, d.ldz, status, st);
 }
 
 afmm_status tc_run_fp8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,

@@ -20,6 +20,7 @@ struct TcPlan {
     void* a = nullptr;              // A operand(s), K-major (BF16 or E4M3)
     void* b = nullptr;              // B operand(s), K-major (B^T rows)
     bool sliced_a = true;           // real factor on the A side (case A)
+    bool both = false;              // both factors sliced (real x real)
     int kb_per_chunk = 0;           // exact form: K chunk in 32-wide k-blocks
     float lim_a = 256.f, lim_b = 256.f;  // exact form: largest |value| allowed
     // Case A split form with rows of Z not 16-byte aligned (ldz % 4 != 0):
@@ -34,9 +35,10 @@ struct TcPlan {
     bool f8 = false;
     size_t s_bytes = 0;
     uint32_t* amax = nullptr;
-    // k-blocks (of 64) after which the hi sum is added into FP32 registers
-    // (0: once per tile); AFMM_FP8_CHUNK_KB in the environment overrides.
-    int f8_kbpc = 0;
+    // FP8 and real x real forms: k-blocks after which the hi sum is added
+    // into FP32 registers (0: once per tile); AFMM_TC_CHUNK_KB in the
+    // environment overrides.
+    int chunk_kb = 0;
     alignas(64) unsigned char tmap_a[128];
     alignas(64) unsigned char tmap_b[128];
     // Case B split form computed as Z^T = Y^T X^T: A side = the b buffer.
@@ -90,6 +92,10 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z, void* s);
 // Split / widen the operands and run the tcgen05 product into Z (F32).
 afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                          const void* Y, void* Z, int* status, cudaStream_t st);
+// Real x real (AFMM_CASE_REAL): three BF16 slices of X and of Y^T, six
+// slice products into Z (F32).
+afmm_status tc_run_real(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
+                        void* Z, int* status, cudaStream_t st);
 // The FP8 form: E4M3 slices and Rep-factors, the tcgen05 product into Z.
 afmm_status tc_run_fp8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
                        void* Z, int* status, cudaStream_t st);

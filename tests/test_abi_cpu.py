@@ -87,6 +87,31 @@ def test_planner_choices_and_workspace():
     assert e.value.status == A.AFMM_ERR_UNSUPPORTED
 
 
+def test_real_by_real_descriptors():
+    """Two real factors (no Rep-factor): FP32 target only, and only the
+    CUDA-core form or the two-sided tensor-core split serve them."""
+    import paper_1308_2400_gb300 as P
+    A = P.afmm
+    for kw in (dict(target="fp64", z_dtype="f64"), dict(z_dtype="f64"),
+               dict(x_dtype="e4m3")):
+        base = dict(n=64, case="REAL", x_dtype="f32", y_dtype="f64", z_dtype="f32",
+                    target="fp32")
+        base.update(kw)
+        with pytest.raises(P.AfmmError) as e:
+            P.afmm_plan_create(P.make_desc(**base))
+        assert e.value.status == A.AFMM_ERR_INVALID_ARG
+    h = P.afmm_plan_create(P.make_desc(64, "REAL", "f32", "f64", "f32", "fp32",
+                                       variant=A.AFMM_VARIANT_SIMT_F32))
+    assert P.afmm_get_info(h)["variant"] == A.AFMM_VARIANT_SIMT_F32
+    P.afmm_plan_destroy(h)
+    for kase, v in (("REAL", A.AFMM_VARIANT_TC_FP8X4), ("REAL", A.AFMM_VARIANT_TC_BF16X3),
+                    ("A", A.AFMM_VARIANT_TC_BF16X3X3)):
+        with pytest.raises(P.AfmmError) as e:
+            P.afmm_plan_create(P.make_desc(64, kase, "f32", "i32", "f32", "fp32",
+                                           variant=v))
+        assert e.value.status == A.AFMM_ERR_UNSUPPORTED
+
+
 def test_null_arguments(lib):
     import paper_1308_2400_gb300 as P
     assert lib.afmm_plan_create(None, None) == P.afmm.AFMM_ERR_INVALID_ARG
