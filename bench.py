@@ -242,7 +242,8 @@ def traffic_from_profile(kernel_tag, workload):
     if not os.path.exists(path):
         return None
     src = {"simt_gemm": "simt_gemm.cu", "tc_gemm": "tc_gemm.cu",
-           "tc_gemm_fp8": "tc_gemm.cu", "sparse": "sparse.cu"}.get(kernel_tag)
+           "tc_gemm_fp8": "tc_gemm.cu", "tc_gemm_real": "tc_gemm.cu",
+           "sparse": "sparse.cu"}.get(kernel_tag)
     vals = {}
     with open(path) as f:
         for ln in f:
@@ -339,13 +340,18 @@ def run_afmm(args):
         launches = c1["kernel_launches"] - c0["kernel_launches"]
         return ms, kms, launches, c2["main_kernel_ctas"]
 
-    plan = Plan(desc(args.variant))
+    # --variant 8: the real x real form as the main product, the workload's
+    # X times itself (no Rep-factor).
+    real_main = args.variant == 8
+    main_ops = (Xd, Xd) if real_main else None
+    plan = Plan(make_desc(n, "REAL", inst.x_dtype, inst.x_dtype, "f32", "fp32", variant=8)
+                if real_main else desc(args.variant))
     vname = VARIANT_NAMES.get(plan.info["variant"], "?")
     slices = plan.info["slices"]
     clk = ClockSampler(dev) if rank == 0 else None
     if clk:
         clk.start()
-    ms, kms, launches, ctas = timed(plan, args.steps, args.warmup)
+    ms, kms, launches, ctas = timed(plan, args.steps, args.warmup, main_ops)
     clocks = clk.stop() if clk else None
     Z_main = Z.cpu().numpy() if (rank == 0 and ws == 1) else None
     ms_max = max_over_ranks(ws, ms)
@@ -366,6 +372,12 @@ def run_afmm(args):
                 "traffic": traffic_from_profile("sparse", args.workload),
                 "kernel": "sp_mul", "kernel_ms": kms, "ctas": ctas,
                 "algorithmic_bytes_per_launch": alg}
+    elif vname == "tc_bf16x3x3":
+        alg = 6 * flops                    # six slice products
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_src": f"bf16 sustained, {peak_src}"}
+        tag = "tc_gemm_real"
     elif vname == "tc_fp8x4":
         # E4M3 MMAs: the measured BF16 rate times the nominal FP8/BF16 ratio.
         alg = slices * flops
@@ -461,9 +473,10 @@ def run_afmm(args):
     e2e = None
     if not args.quick:
         Xh = torch.from_numpy(np.ascontiguousarray(Xs)).pin_memory()
-        Yh = torch.from_numpy(np.ascontiguousarray(Ys)).pin_memory()
+        Yh = Xh if real_main else torch.from_numpy(np.ascontiguousarray(Ys)).pin_memory()
         Zh = torch.empty((n, n), dtype=zt).pin_memory()
-        ph = Plan(desc(args.variant))
+        ph = Plan(make_desc(n, "REAL", inst.x_dtype, inst.x_dtype, "f32", "fp32", variant=8)
+                  if real_main else desc(args.variant))
         with torch.cuda.stream(stream):
             for _ in range(2):
                 ph(Xh, Yh, Zh, stream)
@@ -477,7 +490,7 @@ def run_afmm(args):
             t_e2e = (time.perf_counter() - t0) / ksteps
         t_e2e = max_over_ranks(ws, t_e2e)
         e2e = {"value": ws * flops / t_e2e / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": int(Xh.nbytes + Yh.nbytes),
+               "h2d_bytes_per_step": int(Xh.nbytes + (0 if real_main else Yh.nbytes)),
                "d2h_bytes_per_step": int(Zh.nbytes), "ms_per_step": 1e3 * t_e2e}
         ph.close()
 
@@ -496,6 +509,13 @@ def run_afmm(args):
         den = float(np.linalg.norm(Zr))
         acc = {"rel_fro_err_vs_oracle": num / den if den else 0.0,
                "rows_checked": int(rows.size)}
+        if real_main:
+            from oracle import classical_ikj
+            r16 = rows[:16]
+            Rr = classical_ikj(inst.X, inst.X, r16)
+            acc = {"rel_fro_err_vs_oracle": float(
+                np.linalg.norm(Z_main[r16].astype(np.float64) - Rr) / np.linalg.norm(Rr)),
+                "rows_checked": int(r16.size), "oracle": "classical FP64 product X X"}
         if two is not None and Z_two is not None:
             d2 = float(np.linalg.norm(Z_two[rows].astype(np.float64) - Zr))
             two["rel_fro_err_vs_oracle"] = d2 / den if den else 0.0
@@ -519,9 +539,10 @@ def run_afmm(args):
                      ("f64" if inst.target == "fp64" else
                                         ("i8" if inst.target == "exact" else "f32")),
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "case": inst.case,
-                       "x": inst.x_dtype, "y": inst.y_dtype, "z": inst.z_dtype,
-                       "variant": vname, "slices": slices,
+            "config": {"workload": args.workload, "n": n,
+                       "case": "REAL (X X)" if real_main else inst.case,
+                       "x": inst.x_dtype, "y": inst.x_dtype if real_main else inst.y_dtype,
+                       "z": inst.z_dtype, "variant": vname, "slices": slices,
                        "d1": prm["d1"], "d2": prm["d2"],
                        "mu_prime": prm["mu_prime"],
                        "l2": "inputs larger than L2 (X 256 MiB, Z 256 MiB)",
