@@ -1050,6 +1050,35 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
                    : launch_tc<2, 1, true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1);
 }
 
+int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb) {
+    const int64_t unit_rows = caseb ? TC_BN : TC_BM;
+    const int64_t tm = (n + unit_rows - 1) / unit_rows,
+                  tn = caseb ? (n + TC_BM - 1) / TC_BM : (n + TC_BN - 1) / TC_BN;
+    // First and last blocks of about one wave of tiles: the first product
+    // starts after Y and a small piece of X have arrived, and the last
+    // block's product and copy-out are short.  Middle blocks fill whole
+    // waves where they can.
+    const int64_t edge = std::max<int64_t>(1, sms / tn);
+    const int64_t mid = tm - 2 * edge;
+    if (mid < 1 || max_blocks < 3) return tc_row_blocks(n, sms, bounds, max_blocks, caseb);
+    int64_t g = sms, b = tn;
+    while (b) { const int64_t r = g % b; g = b; b = r; }
+    int64_t unit = std::max<int64_t>(1, sms / g);        // tile rows of whole waves
+    while (mid / unit + (mid % unit ? 1 : 0) > max_blocks - 2) unit *= 2;
+    int k = 0;
+    bounds[k++] = 0;
+    int64_t r = edge;
+    bounds[k++] = r * unit_rows;
+    for (int64_t left = mid; left > 0;) {                // whole-wave blocks, then the rest
+        const int64_t take = std::min(unit, left);
+        r += take;
+        left -= take;
+        bounds[k++] = std::min<int64_t>(r * unit_rows, n);
+    }
+    bounds[k] = n;
+    return k;                                            // number of blocks
+}
+
 int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb) {
     // Rows of Z are product rows (tiles of TC_BM) in Case A and product
     // columns (tiles of TC_BN) in Case B.

@@ -113,6 +113,10 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
 // product is Z^T), chosen so each block's tile count fills whole waves of
 // `sms` CTAs.
 int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb);
+// The schedule of the host-buffer pipeline: first and last blocks of about
+// one wave of tiles, whole-wave blocks between (tc_row_blocks when n is too
+// small for that).  Returns the number of blocks; bounds[0..k] are Z rows.
+int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb);
 // Case A, three slices, X FP32 with 16-byte aligned rows: the fused kernel
 // (tc_fused.cu) reads X directly and splits it in shared memory.
 bool tc_fused_usable(const afmm_desc& d, const void* X);
