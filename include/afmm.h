@@ -124,15 +124,20 @@ typedef enum {
      * value up to 448 (others, and non-finite real values: the call
      * records AFMM_ERR_OVERFLOW_RISK, reported by afmm_plan_sync).  Four
      * E4M3 MMAs per K step in place of three BF16 ones at twice the
-     * rate.  FP32 target; never chosen automatically. */
+     * rate.  The hi sum is closed every 16 K blocks of 64 and the chunks
+     * added in FP32 (AFMM_TC_CHUNK_KB in the environment, read at plan
+     * creation, overrides the count; 0 = never).  FP32 target; never
+     * chosen automatically. */
     AFMM_VARIANT_TC_FP8X4 = 7,
     /* Tensor cores for two real factors (AFMM_CASE_REAL): both split into
      * three BF16 slices (hi+mid+lo = the FP32 value), and the six slice
      * products down to 2^-16 of the hi product -- (hi,hi), (hi,mid),
      * (mid,hi), (hi,lo), (mid,mid), (lo,hi) -- with the (hi,hi) products
-     * kept in their own FP32 accumulator (an Ozaki-style split; Ozaki,
-     * Ogita, Oishi and Rump, Numer. Algorithms 59, 2012; Ootomo and Yokota,
-     * IJHPCA 36, 2022).  FP32 target. */
+     * kept in their own FP32 accumulator, closed every 12 K blocks of 32
+     * and the chunks added in FP32 (AFMM_TC_CHUNK_KB overrides, as above)
+     * (an Ozaki-style split; Ozaki, Ogita, Oishi and Rump, Numer.
+     * Algorithms 59, 2012; Ootomo and Yokota, IJHPCA 36, 2022).  FP32
+     * target. */
     AFMM_VARIANT_TC_BF16X3X3 = 8,
     AFMM_VARIANT_COUNT_ = 9
 } afmm_variant;

@@ -171,3 +171,31 @@ def test_real_leading_dimensions():
     Z = Zb.cpu().numpy()
     check(np.ascontiguousarray(Xb[:, :n]), np.ascontiguousarray(Yb[:, :n]), Z[:, :n])
     assert np.all(Z[:, n:] == 7.0)
+
+
+def test_real_repeated_calls_replay_a_graph():
+    """From the third call on the same device buffers the product is
+    replayed from a CUDA graph; replays give the eager call's bits and read
+    the buffers' current contents."""
+    from paper_1308_2400_gb300 import Plan, make_desc
+    rng = np.random.default_rng(8)
+    n = 300
+    X = rng.uniform(-1, 1, (n, n)).astype(np.float32)
+    Y = rng.standard_normal((n, n)).astype(np.float32)
+    Xt, Yt = torch_of(X), torch_of(Y)
+    Z = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    p = Plan(make_desc(n, "REAL", "f32", "f32", "f32", "fp32"))
+    outs = []
+    for _ in range(4):
+        p(Xt, Yt, Z)
+        p.sync()
+        outs.append(Z.clone())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    check(X, Y, outs[0].cpu().numpy())
+    X2 = rng.uniform(-1, 1, (n, n)).astype(np.float32)
+    Xt.copy_(torch_of(X2))
+    p(Xt, Yt, Z)
+    p.sync()
+    check(X2, Y, Z.cpu().numpy())
+    p.close()
