@@ -405,6 +405,16 @@ def run_afmm(args):
                      "kernel": tag, "kernel_ms": kms, "ctas": ctas,
                      "algorithmic_flops_per_launch": alg})
 
+    # Tensor and ALU rates scale with the SM clock: the fraction at the clock
+    # the peak itself was measured at (the sustained BF16 figure's median
+    # clock; the ALU peak's own) puts a fraction above 1 in context.
+    pk_mhz = (peaks.get("clocks_under_load", {}).get("sm_mhz_median")
+              if roof["bound"] == "tensor" else SM_MAX_MHZ if roof["bound"] == "alu" else None)
+    if pk_mhz and clocks and clocks.get("sm_mhz"):
+        roof["peak_clock_mhz"] = pk_mhz
+        roof["kernel_clock_mhz"] = clocks["sm_mhz"]
+        roof["frac_at_peak_clock"] = roof["frac"] * pk_mhz / clocks["sm_mhz"]
+
     # Plain FP32 CUDA-core form on the same data, when the main form differs.
     plain = None
     if rank == 0 and vname != "simt_f32" and inst.target == "fp32" and not args.quick:
