@@ -10,6 +10,13 @@ Metric: effective TFLOP/s = 2 n^3 / time per product (whole job: summed
 over ranks; each rank computes its own independent product, no collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl afmm|reference]
+                  [--workload W] [--n N] [--variant V] [--quick]
+
+Beside the main form the line reports, on the same data, the plain FP32
+CUDA-core form (plain_fp32), two BF16 slices (two_slices), the FP8 form
+(fp8_slices), the split done inside the product kernel (fused_split) and a
+product of two real matrices, X times itself (real_x_real); --quick leaves
+them out.  --variant 8 makes that real x real product the main one.
 
 The reference arm (--impl reference) times the CPU oracle (repeated
 addition in FP64, Sec. 2) on the host cores on a bounded row sample of the
