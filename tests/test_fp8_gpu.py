@@ -269,3 +269,15 @@ def test_fp8_error_between_two_and_three_bf16_slices():
     R = oracle_rows(inst)
     e8, e2 = rel_fro(Z8, R), rel_fro(Z2, R)
     assert e8 < 1e-6 and e8 < e2 / 2
+
+
+def test_fp8_empty_problem():
+    """n = 0: nothing to do, no error, for either case."""
+    from paper_1308_2400_gb300 import Plan, make_desc
+    for case, xd, yd in (("A", "f32", "e4m3"), ("B", "i32", "f32")):
+        p = Plan(make_desc(0, case, xd, yd, "f32", "fp32", variant=FP8))
+        e = torch.empty((0, 0), dtype=torch.float32, device="cuda")
+        p(e, e, e)
+        p.sync()
+        assert p.info["variant"] == FP8
+        p.close()

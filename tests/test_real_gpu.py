@@ -199,3 +199,14 @@ def test_real_repeated_calls_replay_a_graph():
     p.sync()
     check(X2, Y, Z.cpu().numpy())
     p.close()
+
+
+@pytest.mark.parametrize("variant", [TC_REAL, SIMT])
+def test_real_empty_problem(variant):
+    from paper_1308_2400_gb300 import Plan, make_desc
+    p = Plan(make_desc(0, "REAL", "f32", "f32", "f32", "fp32", variant=variant))
+    e = torch.empty((0, 0), dtype=torch.float32, device="cuda")
+    p(e, e, e)
+    p.sync()
+    assert p.info["variant"] == variant
+    p.close()
