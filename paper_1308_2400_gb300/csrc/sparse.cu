@@ -34,7 +34,7 @@ constexpr int SP_CW = 6144;                 // widest Z row piece a product warp
 constexpr int SP_G = 8;                     // X entries whose Y pairs load together
 constexpr int SP_PRE = 2;                   // 16-byte loads (2 pairs) per lane loaded ahead
 constexpr int SP_MUL_WARPS = 7;             // most warps per product block
-constexpr int SP_UNROLL = 8;                // 16-byte loads in flight per lane
+constexpr int SP_UNROLL = 4;                // 16-byte loads per lane and round (two rounds in flight)
 
 // One factor's compaction.  Row r's pairs start at ptr[r] (r * R, or in the
 // overflow region after the n * R slots) and number cnt[r]; spl[r * (C-1) +
@@ -87,12 +87,22 @@ __device__ __forceinline__ void compact_row(const SpArgs& a, const SpMat& A, int
     if (A.vec) {
         const uint4* row4 = reinterpret_cast<const uint4*>(row);
         const int64_t units = n / V;
-        for (int64_t u0 = 0; u0 < units; u0 += 32 * SP_UNROLL) {
-            uint4 q[SP_UNROLL];
+        // The next round of 16-byte pieces is loaded while this one is
+        // placed, so the row streams in without gaps.
+        uint4 q[SP_UNROLL], qn[SP_UNROLL];
 #pragma unroll
-            for (int s = 0; s < SP_UNROLL; ++s) {
-                const int64_t u = u0 + 32 * s + lane;
-                q[s] = u < units ? row4[u] : make_uint4(0, 0, 0, 0);
+        for (int s = 0; s < SP_UNROLL; ++s) {
+            const int64_t u = 32 * s + lane;
+            q[s] = u < units ? row4[u] : make_uint4(0, 0, 0, 0);
+        }
+        for (int64_t u0 = 0; u0 < units; u0 += 32 * SP_UNROLL) {
+            const int64_t un = u0 + 32 * SP_UNROLL;
+            if (un < units) {
+#pragma unroll
+                for (int s = 0; s < SP_UNROLL; ++s) {
+                    const int64_t u = un + 32 * s + lane;
+                    qn[s] = u < units ? row4[u] : make_uint4(0, 0, 0, 0);
+                }
             }
 #pragma unroll
             for (int s = 0; s < SP_UNROLL; ++s) {
@@ -135,6 +145,8 @@ __device__ __forceinline__ void compact_row(const SpArgs& a, const SpMat& A, int
                 }
                 c += tot;
             }
+#pragma unroll
+            for (int s = 0; s < SP_UNROLL; ++s) q[s] = qn[s];
         }
     } else {
         for (int64_t j0 = 0; j0 < n; j0 += 32) {
