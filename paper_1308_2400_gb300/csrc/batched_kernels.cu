@@ -158,7 +158,7 @@ g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix
 // Block b converts one 64 x 64 tile of the B operand (Y transposed to
 // K-major) of instance j = tt_job[b]: Case A widens the Rep-factors Y
 // (exact, |v| <= 256); Case B splits the real Y into 3 slices.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 6)
 g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_prefix,
                    const int* __restrict__ tt_job, int* __restrict__ flags) {
     __shared__ float tile[64][65];
