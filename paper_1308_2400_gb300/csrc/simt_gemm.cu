@@ -1,9 +1,9 @@
 // K1: CUDA-core AFMM product with zero-skipping.
 //
 // The paper's loop (Sec. 2, Case-A) reads Base = X[i,k] and skips the whole
-// J loop when it is zero.  Here one warp owns 8 rows of a 64 x 256 output
-// tile and all 256 columns, so the Base values X[i..i+7, k] it needs are the
-// same for every lane: the zero test is warp-uniform and a k whose 8 Base
+// J loop when it is zero.  Here one warp owns 4 rows of a 64 x 256 output
+// tile and all 256 columns, so the Base values X[i..i+3, k] it needs are the
+// same for every lane: the zero test is warp-uniform and a k whose 4 Base
 // values are all zero is skipped by the whole warp at no divergence cost.
 // The term Rep * Base is formed with one FMA (FP32) or one 4-way int8 dot
 // product (exact integers) instead of Rep additions: the same value, formed
@@ -11,9 +11,11 @@
 //
 // Layout: A (M x K) and B (K x N) row-major in global memory, staged by
 // cp.async into shared memory (A as [64][32], B as [32][256] elements of
-// 4 bytes, two stages).  Each thread accumulates 8 rows x 8 columns; FP32
-// sums are K-blocked (a fresh partial per 32-wide k tile, added to the
-// running sum afterwards) to keep the rounding error of long sums low.
+// 4 bytes, two stages).  Each of the 16 warps' threads accumulates 4 rows x
+// 8 columns; FP32 sums are K-blocked (a fresh partial per 32-wide k tile,
+// added to the running sum afterwards) to keep the rounding error of long
+// sums low.  The running sums and the partials of 4 rows fit 128 registers,
+// so the CTA runs 16 warps.
 #include <cstdint>
 
 #include "afmm_common.cuh"
@@ -22,7 +24,9 @@ namespace afmm {
 
 namespace {
 
-constexpr int BM = 64, BN = 256, BK = 32, THREADS = 256;
+constexpr int BM = 64, BN = 256, BK = 32;
+constexpr int RW = 4;                       // rows of the tile per warp
+constexpr int THREADS = BM / RW * 32;       // 16 warps
 constexpr int SMEM_BYTES = 2 * (BM * BK + BK * BN) * 4;
 
 struct OpF32 {
@@ -130,12 +134,12 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
     Elt* Bs = As + 2 * BM * BK;                          // [2][BK][BN]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = warp * 8;
+    const int row0 = warp * RW;
 
-    Acc acc[8][8];
-    Acc part[8][8];
+    Acc acc[RW][8];
+    Acc part[RW][8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < RW; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             acc[r][c] = Acc(0);
@@ -162,10 +166,10 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
         const Elt* as = As + s * BM * BK + row0 * BK;
         const Elt* bs = Bs + s * BK * BN;
 
-        // Which k of this tile have a non-zero Base in the warp's 8 rows.
+        // Which k of this tile have a non-zero Base in the warp's rows.
         bool any = false;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) any |= Op::nz(as[r * BK + lane]);
+        for (int r = 0; r < RW; ++r) any |= Op::nz(as[r * BK + lane]);
         const unsigned mask = __ballot_sync(0xffffffffu, any);
 
         if (__popc(mask) >= 24) {
@@ -180,7 +184,7 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
                     y[kk][1] = *reinterpret_cast<const V4*>(row + 128 + lane * 4);
                 }
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < RW; ++r) {
                     const V4 xv = *reinterpret_cast<const V4*>(as + r * BK + kq * 4);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
@@ -203,7 +207,7 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
                 const V4 y0 = *reinterpret_cast<const V4*>(row + lane * 4);
                 const V4 y1 = *reinterpret_cast<const V4*>(row + 128 + lane * 4);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < RW; ++r) {
                     const Elt x = as[r * BK + k];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -215,7 +219,7 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
         }
         if (Op::kBlocked) {
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+            for (int r = 0; r < RW; ++r)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     acc[r][c] += part[r][c];
@@ -226,7 +230,7 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
     }
     if (!Op::kBlocked) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < RW; ++r)
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[r][c] = part[r][c];
     }
@@ -237,7 +241,7 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
     if constexpr (std::is_same<Acc, int32_t>::value) {
         if (accumulate) {
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < RW; ++r) {
                 const int64_t gm = m0 + row0 + r;
                 if (gm >= M) break;
 #pragma unroll
@@ -252,7 +256,7 @@ __device__ __forceinline__ void simt_tile(const typename Op::Elt* __restrict__ A
         }
     }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < RW; ++r) {
         const int64_t gm = m0 + row0 + r;
         if (gm >= M) break;
 #pragma unroll
