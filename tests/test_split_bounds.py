@@ -84,7 +84,7 @@ def test_fp8_four_slices_bound(law):
     assert err < (1e-6 if law == "wide" else 5e-7)
 
 
-def test_three_slices_fewer_fail_the_fp32_bar():
+def test_three_e4m3_slices_miss_the_fp32_bar():
     """Three E4M3 slices (no rescaled fourth) miss the 1e-6 bar; this is
     why the form keeps four."""
     rng = np.random.default_rng(8)
