@@ -112,6 +112,26 @@ def test_real_by_real_descriptors():
         assert e.value.status == A.AFMM_ERR_UNSUPPORTED
 
 
+def test_lent_workspace_is_checked():
+    """A lent workspace smaller than the plan needs, or off a 256-byte
+    boundary, is refused on the host before any device work (the pointer
+    is never dereferenced here); a large enough aligned one is taken."""
+    import paper_1308_2400_gb300 as P
+    A = P.afmm
+    h = P.afmm_plan_create(P.make_desc(256, "A", "f64", "i32", "f64", "fp64"))
+    need = P.afmm_plan_workspace_size(h)
+    assert need > 0
+    base = 1 << 40                                   # an address, not memory
+    with pytest.raises(P.AfmmError) as e:
+        P.afmm_plan_set_workspace(h, base, need - 1)
+    assert e.value.status == A.AFMM_ERR_INVALID_ARG
+    with pytest.raises(P.AfmmError) as e:
+        P.afmm_plan_set_workspace(h, base + 64, need)
+    assert e.value.status == A.AFMM_ERR_INVALID_ARG
+    P.afmm_plan_set_workspace(h, base, need)
+    P.afmm_plan_destroy(h)                           # does not free a lent buffer
+
+
 def test_null_arguments(lib):
     import paper_1308_2400_gb300 as P
     assert lib.afmm_plan_create(None, None) == P.afmm.AFMM_ERR_INVALID_ARG
