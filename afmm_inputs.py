@@ -41,7 +41,8 @@ from typing import List, Optional
 import numpy as np
 
 __all__ = ["Instance", "WORKLOADS", "make", "batched_mix", "rng_for",
-           "encode_e4m3_integers", "table1_point", "TABLE1_POINTS", "TABLE1_SIZES"]
+           "encode_e4m3_integers", "table1_point", "TABLE1_POINTS", "TABLE1_SIZES",
+           "density_hints"]
 
 
 @dataclass
@@ -64,6 +65,28 @@ class Instance:
     @property
     def n(self) -> int:
         return int(self.X.shape[0])
+
+
+def density_hints(X: np.ndarray, Y: np.ndarray, case: str) -> dict:
+    """Counts of a drawn instance that a caller passes as plan hints.
+
+    d1, d2: fractions of non-zero entries of X and Y; mu_prime: the mean of
+    the non-zero entries of the integer factor (Y in case A, X in case B);
+    rep_max / base_max: the largest integer entry and the largest |real|
+    entry.  Counting only: these are the parameters the paper assumes known
+    in advance, read off the arrays this module drew.
+    """
+    X = np.asarray(X)
+    Y = np.asarray(Y)
+    n2 = X.size
+    rep, real = (Y, X) if case.upper() == "A" else (X, Y)
+    nz = int(np.count_nonzero(rep))
+    total = float(rep.sum(dtype=np.float64))
+    return {"d1": float(np.count_nonzero(X)) / n2 if n2 else 0.0,
+            "d2": float(np.count_nonzero(Y)) / n2 if n2 else 0.0,
+            "mu_prime": total / nz if nz else 0.0,
+            "rep_max": float(rep.max()) if rep.size else 0.0,
+            "base_max": float(np.abs(real.astype(np.float64)).max()) if real.size else 0.0}
 
 
 def rng_for(seed: int, stream: int = 0) -> np.random.Generator:

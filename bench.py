@@ -55,8 +55,14 @@ def load_peaks():
                 "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+_REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8,
+                "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    """SM clock, power and clock-event reasons sampled while the timed
+    region runs: NVML queried every ~2 ms from a thread (read-only calls;
+    a short region still gets many samples), else nvidia-smi every 20 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,"
@@ -69,16 +75,72 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.thread = None
+        self.samples = []          # (sm_mhz, max_mhz, reasons bitmask)
+        self.stop_flag = False
+        self.source = None
+        self.nvml = None
+        self.handle = None
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return False
+        if lib.nvmlInit_v2() != 0:
+            return False
+        h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.dev)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok:
+            # CUDA ordinal -> NVML index through CUDA_VISIBLE_DEVICES when it
+            # lists plain indices.
+            idx = self.dev
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+            if self.dev < len(vis) and vis[self.dev].strip().isdigit():
+                idx = int(vis[self.dev])
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(h)) == 0
+        if not ok:
+            lib.nvmlShutdown()
+            return False
+        self.nvml, self.handle = lib, h
+        return True
+
+    def _nvml_loop(self):
+        import ctypes
+        lib, h = self.nvml, self.handle
+        clk, mx = ctypes.c_uint(), ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        get_r = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_flag:
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    get_r(h, ctypes.byref(rs)) == 0):
+                self.samples.append((float(clk.value), float(mx.value), int(rs.value)))
+            time.sleep(0.002)
 
     def start(self):
+        if self._nvml_open():
+            self.source = "nvml, every 2 ms"
+            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.thread.start()
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
+        self.source = "nvidia-smi, every 20 ms"
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
 
@@ -87,6 +149,12 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            self.stop_flag = True
+            if self.thread:
+                self.thread.join(timeout=2)
+            self.nvml.nvmlShutdown()
+            return summarise_clocks(self.samples, self.source)
         if not self.proc:
             return None
         self.proc.terminate()
@@ -96,25 +164,43 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
+        samples = []
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                sm, mx = float(parts[0]), float(parts[1])
             except ValueError:
                 continue
+            bits = 0
             for nm, v in zip(names, parts[4:8]):
                 if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "samples": len(sm), "reasons": sorted(reasons)}
+                    bits |= _REASON_BITS[nm]
+            samples.append((sm, mx, bits))
+        return summarise_clocks(samples, self.source)
+
+
+def summarise_clocks(samples, source):
+    """Median SM clock, largest max clock and the reasons seen."""
+    if not samples:
+        return None
+    reasons = sorted(nm for nm, b in _REASON_BITS.items()
+                     if any(s[2] & b for s in samples))
+    return {"sm_mhz": statistics.median(s[0] for s in samples),
+            "sm_max_mhz": max(s[1] for s in samples), "samples": len(samples),
+            "reasons": reasons, "source": source}
+
+
+def tensor_peak(peaks, region_s):
+    """Measured BF16 dense peak for a kernel timed over region_s seconds:
+    the burst figure below one second, the sustained (power-capped) one
+    beyond."""
+    if region_s < 1.0:
+        return peaks.get("bf16_tflops", 1900.0), "bf16 burst"
+    return peaks.get("bf16_tflops_sustained", 1700.0), "bf16 sustained"
 
 
 def dist_info():
@@ -161,28 +247,70 @@ def make_instance(workload, n):
     return W.make(workload, n=n)
 
 
+def input_hints(inst):
+    """Plan hints (d1, d2, mu', magnitudes) counted off the drawn inputs."""
+    import afmm_inputs as W
+    return W.density_hints(inst.X, inst.Y, inst.case)
+
+
+# ---------------------------------------------------------------- oracle legs
+# The oracle (test infrastructure) runs only in these helpers: the CPU
+# baseline and the accuracy checks of results the GPU already produced.  No
+# input of a product comes from here.
+
+def workload_config(workload, inst, ws, real_main=False):
+    """The `config` object of both arms' JSON lines: the workload alone
+    (its name, size, case, dtypes, realised densities, L2 note, ranks)."""
+    h = input_hints(inst)
+    n = inst.n
+    xb = n * n * inst.X.dtype.itemsize
+    zb = n * n * {"f32": 4, "f64": 8, "i32": 4}[inst.z_dtype]
+    l2 = (f"inputs larger than L2 (X {xb / 2**20:.0f} MiB, Z {zb / 2**20:.0f} MiB)"
+          if max(xb, zb) > 129e6 else
+          f"operands fit in L2 (X {xb / 2**20:.1f} MiB, Z {zb / 2**20:.1f} MiB)")
+    return {"workload": workload, "n": n,
+            "case": "REAL (X X)" if real_main else inst.case,
+            "x": inst.x_dtype, "y": inst.x_dtype if real_main else inst.y_dtype,
+            "z": inst.z_dtype, "d1": h["d1"], "d2": h["d2"], "mu_prime": h["mu_prime"],
+            "l2": l2, "parallelism": f"replicas x{ws}"}
+
+
 def oracle_rows_timed(inst, budget_s, min_rows=1):
-    """Oracle on whole batches of rows until ~budget_s seconds have passed."""
+    """CPU baseline: the oracle on contiguous blocks of rows (one row per
+    oracle thread, so one parallel region spreads over every host core)
+    at random block positions, until ~budget_s seconds have passed.
+    Returns (rows, Z rows, seconds, threads)."""
     import numpy as np
     from oracle import afmm_case_a, afmm_case_b, oracle_threads
     fn = afmm_case_a if inst.case == "A" else afmm_case_b
-    thr = oracle_threads()
     n = inst.n
+    thr = max(1, min(oracle_threads(), n))
     rng = np.random.default_rng(1234)
-    order = rng.permutation(n)
+    order = rng.permutation(n // thr) * thr
     done, rows_out, Z_out = 0, [], []
     t0 = time.perf_counter()
-    while done < n:
-        batch = np.sort(order[done:done + thr])
-        Zr, _ = fn(inst.X, inst.Y, batch)
-        rows_out.append(batch)
+    for r0 in order:
+        Zr, _ = fn(inst.X, inst.Y, (int(r0), int(r0) + thr))
+        rows_out.append(np.arange(r0, r0 + thr, dtype=np.int64))
         Z_out.append(Zr)
-        done += batch.size
+        done += thr
         if time.perf_counter() - t0 >= budget_s and done >= min_rows:
             break
     el = time.perf_counter() - t0
     rows = np.concatenate(rows_out)
     return rows, np.concatenate(Z_out), el, thr
+
+
+def oracle_product_rows(inst, rows):
+    """Rows of the oracle's Z (Sec. 2 loops) for an accuracy check."""
+    from oracle import afmm_case_a, afmm_case_b
+    return (afmm_case_a if inst.case == "A" else afmm_case_b)(inst.X, inst.Y, rows)[0]
+
+
+def oracle_classical_rows(X, Y, rows):
+    """Rows of the oracle's classical FP64 product X Y (real x real check)."""
+    from oracle import classical_ikj
+    return classical_ikj(X, Y, rows)
 
 
 def run_reference(args):
@@ -230,8 +358,7 @@ def run_reference(args):
         "ms_per_step": 1e3 * tot_t / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "case": inst.case,
-                   "x": inst.x_dtype, "y": inst.y_dtype, "z": inst.z_dtype},
+        "config": workload_config(args.workload, inst, ws),
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": thr,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -250,6 +377,7 @@ def traffic_from_profile(kernel_tag, workload):
         return None
     src = {"simt_gemm": "simt_gemm.cu", "tc_gemm": "tc_gemm.cu",
            "tc_gemm_fp8": "tc_gemm.cu", "tc_gemm_real": "tc_gemm.cu",
+           "tc_exact2": "tc_gemm.cu",
            "sparse": "sparse.cu"}.get(kernel_tag)
     vals = {}
     with open(path) as f:
@@ -294,17 +422,13 @@ def run_afmm(args):
     zt = {"f32": torch.float32, "f64": torch.float64, "i32": torch.int32}[inst.z_dtype]
     Z = torch.empty((n, n), dtype=zt, device="cuda")
 
-    from oracle import realised_parameters
-    prm = realised_parameters(inst.X, inst.Y, inst.case)
+    prm = input_hints(inst)
 
     # Magnitude hints (the paper's "known in advance" parameters extend to
     # the largest Rep-factor and Base value); they size the exact form's
     # K chunks and are checked on the device every call.
-    rep = inst.Y if inst.case == "A" else inst.X
-    real = inst.X if inst.case == "A" else inst.Y
-    rep_max = float(np.max(rep)) if inst.target == "exact" else -1.0
-    base_max = float(np.max(np.abs(real.astype(np.float64)))) \
-        if inst.target == "exact" else -1.0
+    rep_max = prm["rep_max"] if inst.target == "exact" else -1.0
+    base_max = prm["base_max"] if inst.target == "exact" else -1.0
 
     def desc(variant, flags=0):
         return make_desc(n, inst.case, inst.x_dtype, inst.y_dtype,
@@ -365,8 +489,12 @@ def run_afmm(args):
     flops = 2.0 * n ** 3
     value = whole_job_value([1] * ws, flops, ms_max)
 
-    # Roofline of the dominant (product) kernel.
+    # Roofline of the dominant (product) kernel.  Tensor peaks: the burst
+    # figure when the timed region is short (the GPU stays near its boost
+    # clock), the sustained one for regions of a second or more.
     tc = vname.startswith("tc_")
+    region_s = ms * args.steps * 1e-3
+    bf16_peak, bf16_src = tensor_peak(peaks, region_s)
     if vname == "sparse":
         # HBM-bound: the product kernel reads the compacted lists (8 bytes per
         # non-zero of X and Y) and writes Z once (4 n^2 bytes).
@@ -381,23 +509,23 @@ def run_afmm(args):
                 "algorithmic_bytes_per_launch": alg}
     elif vname == "tc_bf16x3x3":
         alg = 6 * flops                    # six slice products
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = bf16_peak
         roof = {"bound": "tensor", "unit": "TFLOP/s",
-                "peak_src": f"bf16 sustained, {peak_src}"}
+                "peak_src": f"{bf16_src}, {peak_src}"}
         tag = "tc_gemm_real"
     elif vname == "tc_fp8x4":
         # E4M3 MMAs: the measured BF16 rate times the nominal FP8/BF16 ratio.
         alg = slices * flops
-        peak = 2.0 * peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = 2.0 * bf16_peak
         roof = {"bound": "tensor", "unit": "TFLOP/s",
-                "peak_src": f"2 x bf16 sustained (nominal fp8/bf16 ratio), {peak_src}"}
+                "peak_src": f"2 x {bf16_src} (nominal fp8/bf16 ratio), {peak_src}"}
         tag = "tc_gemm_fp8"
     elif tc:
-        alg = slices * flops
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        alg = (1 if vname == "tc_exact" else slices) * flops
+        peak = bf16_peak
         roof = {"bound": "tensor", "unit": "TFLOP/s",
-                "peak_src": f"bf16 sustained, {peak_src}"}
-        tag = "tc_gemm"
+                "peak_src": f"{bf16_src}, {peak_src}"}
+        tag = "tc_exact2" if vname == "tc_exact" else "tc_gemm"
     else:
         alg = flops
         sm_mhz = SM_MAX_MHZ
@@ -411,16 +539,7 @@ def run_afmm(args):
                      "traffic": traffic_from_profile(tag, args.workload),
                      "kernel": tag, "kernel_ms": kms, "ctas": ctas,
                      "algorithmic_flops_per_launch": alg})
-
-    # Tensor and ALU rates scale with the SM clock: the fraction at the clock
-    # the peak itself was measured at (the sustained BF16 figure's median
-    # clock; the ALU peak's own) puts a fraction above 1 in context.
-    pk_mhz = (peaks.get("clocks_under_load", {}).get("sm_mhz_median")
-              if roof["bound"] == "tensor" else SM_MAX_MHZ if roof["bound"] == "alu" else None)
-    if pk_mhz and clocks and clocks.get("sm_mhz"):
-        roof["peak_clock_mhz"] = pk_mhz
-        roof["kernel_clock_mhz"] = clocks["sm_mhz"]
-        roof["frac_at_peak_clock"] = roof["frac"] * pk_mhz / clocks["sm_mhz"]
+    roof["timed_region_s"] = region_s
 
     # Plain FP32 CUDA-core form on the same data, when the main form differs.
     plain = None
@@ -461,12 +580,12 @@ def run_afmm(args):
     if rank == 0 and vname == "tc_bf16x3" and not args.quick:
         p5 = Plan(desc(7))
         ms5, kms5, _, _ = timed(p5, max(2, min(args.steps // 4, 100)), 3)
-        f8_peak = 2.0 * peaks.get("bf16_tflops_sustained", 1700.0)
+        f8_peak = 2.0 * tensor_peak(peaks, ms5 * max(2, min(args.steps // 4, 100)) * 1e-3)[0]
         f8_tf = 4 * flops / (kms5 * 1e-3) / 1e12
         f8 = {"variant": "tc_fp8x4", "value": flops / (ms5 * 1e-3) / 1e12,
               "ms_per_step": ms5, "kernel_ms": kms5, "tensor_tflops": f8_tf,
               "peak": f8_peak, "frac": f8_tf / f8_peak,
-              "peak_src": f"2 x bf16 sustained (nominal fp8/bf16 ratio), {peak_src}"}
+              "peak_src": f"2 x bf16 measured (nominal fp8/bf16 ratio), {peak_src}"}
         Z_f8 = Z.cpu().numpy() if ws == 1 else None
         p5.close()
 
@@ -481,7 +600,7 @@ def run_afmm(args):
         rr = {"variant": VARIANT_NAMES.get(p6.info["variant"], "?"), "operands": "X, X",
               "value": flops / (ms6 * 1e-3) / 1e12, "ms_per_step": ms6,
               "kernel_ms": kms6, "tensor_tflops": tf6,
-              "frac": tf6 / peaks.get("bf16_tflops_sustained", 1700.0)}
+              "frac": tf6 / tensor_peak(peaks, ms6 * max(2, min(args.steps // 8, 50)) * 1e-3)[0]}
         Z_rr = Z.cpu().numpy() if ws == 1 else None
         p6.close()
 
@@ -527,9 +646,8 @@ def run_afmm(args):
         acc = {"rel_fro_err_vs_oracle": num / den if den else 0.0,
                "rows_checked": int(rows.size)}
         if real_main:
-            from oracle import classical_ikj
             r16 = rows[:16]
-            Rr = classical_ikj(inst.X, inst.X, r16)
+            Rr = oracle_classical_rows(inst.X, inst.X, r16)
             acc = {"rel_fro_err_vs_oracle": float(
                 np.linalg.norm(Z_main[r16].astype(np.float64) - Rr) / np.linalg.norm(Rr)),
                 "rows_checked": int(r16.size), "oracle": "classical FP64 product X X"}
@@ -540,9 +658,8 @@ def run_afmm(args):
             d8 = float(np.linalg.norm(Z_f8[rows].astype(np.float64) - Zr))
             f8["rel_fro_err_vs_oracle"] = d8 / den if den else 0.0
         if rr is not None and Z_rr is not None:
-            from oracle import classical_ikj
             r16 = rows[:16]
-            Rr = classical_ikj(inst.X, inst.X, r16)
+            Rr = oracle_classical_rows(inst.X, inst.X, r16)
             rr["rel_fro_err_vs_oracle"] = float(
                 np.linalg.norm(Z_rr[r16].astype(np.float64) - Rr) / np.linalg.norm(Rr))
             rr["rows_checked"] = int(r16.size)
@@ -556,14 +673,8 @@ def run_afmm(args):
                      ("f64" if inst.target == "fp64" else
                                         ("i8" if inst.target == "exact" else "f32")),
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": n,
-                       "case": "REAL (X X)" if real_main else inst.case,
-                       "x": inst.x_dtype, "y": inst.x_dtype if real_main else inst.y_dtype,
-                       "z": inst.z_dtype, "variant": vname, "slices": slices,
-                       "d1": prm["d1"], "d2": prm["d2"],
-                       "mu_prime": prm["mu_prime"],
-                       "l2": "inputs larger than L2 (X 256 MiB, Z 256 MiB)",
-                       "parallelism": f"replicas x{ws}"},
+            "config": workload_config(args.workload, inst, ws, real_main),
+            "variant": vname, "slices": slices,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches) * ws, "clocks": clocks,
             "accuracy": acc, "plain_fp32": plain, "fused_split": fused,
@@ -587,7 +698,6 @@ def run_batched(args):
     import afmm_inputs as W
     from paper_1308_2400_gb300 import afmm as A
     from paper_1308_2400_gb300 import tune
-    from oracle import afmm_case_a, afmm_case_b
 
     torch.cuda.set_device(0)
     peaks, peak_src = load_peaks()
@@ -615,7 +725,7 @@ def run_batched(args):
     for i in range(0, len(insts), max(1, len(insts) // 12)):
         t = insts[i]
         rows = np.arange(0, t.n, max(1, t.n // 16))
-        R = (afmm_case_a if t.case == "A" else afmm_case_b)(t.X, t.Y, rows)[0]
+        R = oracle_product_rows(t, rows)
         Zg = Zs[i].cpu().numpy()[rows].astype(np.float64)
         errs.append(float(np.linalg.norm(Zg - R) / max(np.linalg.norm(R), 1e-300)))
     dispatch = None
@@ -688,7 +798,6 @@ def run_table1(args):
     import numpy as np
     import torch
     import afmm_inputs as W
-    from oracle import afmm_case_a, realised_parameters
     from paper_1308_2400_gb300 import Plan, make_desc
     from paper_1308_2400_gb300.afmm import VARIANT_NAMES
     torch.cuda.set_device(0)
@@ -699,7 +808,7 @@ def run_table1(args):
     for n in W.TABLE1_SIZES:
         for j, (mu, d1, d2) in enumerate(W.TABLE1_POINTS):
             inst = W.table1_point(n, mu, d1, d2, seed=n)
-            prm = realised_parameters(inst.X, inst.Y, "A")
+            prm = W.density_hints(inst.X, inst.Y, "A")
             X = torch.from_numpy(inst.X).cuda()
             Y = torch.from_numpy(inst.Y).cuda()
             Z = torch.empty((n, n), dtype=torch.float32, device="cuda")
@@ -719,7 +828,7 @@ def run_table1(args):
                 plan.sync(stream)
             ms = e0.elapsed_time(e1) / args.steps
             r = np.arange(0, n, max(1, n // 8))
-            R = afmm_case_a(inst.X, inst.Y, r)[0]
+            R = oracle_product_rows(inst, r)
             err = float(np.linalg.norm(Z.cpu().numpy()[r] - R) / np.linalg.norm(R))
             worst = max(worst, err)
             paper = TABLE1_SECONDS[n]

@@ -143,8 +143,9 @@ typedef enum {
 } afmm_variant;
 
 /* Flags for afmm_desc.flags. */
-#define AFMM_FLAG_VALIDATE 0x1u  /* scan the Rep-factors on every call and
-                                    report bad ones through afmm_plan_sync */
+#define AFMM_FLAG_VALIDATE 0x1u  /* also scan both factors on every call
+                                    for the paper's parameters (realised
+                                    d1, d2, mu', read by afmm_get_info) */
 #define AFMM_FLAG_FUSED_SPLIT 0x2u  /* Case A, FP32 X with 16-byte aligned
                                     rows: split X into BF16 slices inside
                                     the product kernel instead of in a
@@ -220,7 +221,15 @@ afmm_status afmm_plan_set_workspace(afmm_plan plan, void* workspace,
 
 /* Case A product (Sec. 2, Case-A): X real Base values, Y Rep-factors.
  * Z = X * Y, overwritten.  The plan must have been created with
- * kase == AFMM_CASE_A. */
+ * kase == AFMM_CASE_A.
+ * Every call of either case checks the Rep-factors (Sec. 2 types them as
+ * non-negative integers; no flag needed): a negative one is reported as
+ * AFMM_ERR_NEGATIVE_REP, a non-integer one (NaN and infinities included)
+ * as AFMM_ERR_NONINTEGER_REP, by afmm_plan_sync (or the next call's
+ * status); Z is then unspecified.  Most forms check in the conversion that
+ * reads the Rep-factors anyway; the FP32 CUDA-core and sparse forms read
+ * them in place and run one check pass first (none for u8 Rep-factors,
+ * which cannot be invalid).  Negative Base values are valid. */
 afmm_status afmm_mul_caseA(afmm_plan plan, const void* X, const void* Y,
                            void* Z, void* stream);
 
@@ -284,16 +293,20 @@ afmm_status afmm_selftest_bounded_wait(uint64_t limit_ns, void* stream);
  * only refresh the pointer table and launch the graph (a few plans are
  * cached).  X[t], Y[t], Z[t] are device pointers; Z[t] depends only on X[t]
  * and Y[t].  Asynchronous on `stream`; calls with the same descriptor array
- * must not overlap on different streams.  A Rep-factor that is not an
- * integer of magnitude <= 256 turns that instance's Z into NaN; a bounded
- * wait that runs out is reported by afmm_batched_sync. */
+ * must not overlap on different streams.  Rep-factors are checked on
+ * every call: a negative one, a non-integer one or one above 256 is
+ * reported by afmm_batched_sync (AFMM_ERR_NEGATIVE_REP,
+ * AFMM_ERR_NONINTEGER_REP, AFMM_ERR_OVERFLOW_RISK) and turns a
+ * tensor-core instance's Z into NaN (a CUDA-core instance's Z is then
+ * unspecified); a bounded wait that runs out is reported the same way. */
 afmm_status afmm_mul_batched(int count, const afmm_desc* descs,
                              const void* const* X, const void* const* Y,
                              void* const* Z, void* stream);
 
 /* Synchronise `stream` and return the status recorded by the kernels of the
- * cached batch with this descriptor array (AFMM_OK, or AFMM_ERR_TIMEOUT);
- * AFMM_ERR_INVALID_ARG when no such batch ran. */
+ * cached batch with this descriptor array (AFMM_OK, a Rep-factor error, or
+ * AFMM_ERR_TIMEOUT), clearing it; AFMM_ERR_INVALID_ARG when no such batch
+ * ran. */
 afmm_status afmm_batched_sync(int count, const afmm_desc* descs, void* stream);
 
 /* Relative error of a result against a reference, in FP64 on the GPU:
@@ -379,19 +392,26 @@ int32_t afmm_dispatch_variant(const afmm_desc* desc);
  *
  * Scratch: one fixed device array of about 3.8 MiB inside this library,
  * enough for n <= 256; n > 256 returns AFMM_ERR_UNSUPPORTED (and
- * afmm_last_error_detail says so).  Every GPU that loads the library holds
- * the array until the process exits.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress, once per device, with
- * that device current); make that first call before any stream capture.
+ * afmm_last_error_detail says so).  Under CUDA's default lazy module
+ * loading the array and this library's device code take their device
+ * memory on the first use on each device (a call of this or any other
+ * entry point), unless CUDA_MODULE_LOADING=EAGER is set; a device then
+ * holds them until the process exits.  So a caller whose memory will later
+ * be taken over by another allocator makes one small warm-up call per
+ * device first, and that first call should also come before any stream
+ * capture.  Each call looks up the array's device address
+ * (cudaGetSymbolAddress with the device current), which allocates nothing
+ * once the code is loaded and stays right after a cudaDeviceReset.
  *
  * Calls share the array and keep its last contents (the call clears what
  * must start at zero).  Calls that overlap on the GPU -- issued on several
  * streams or from several threads without ordering -- race on it.
  *
- * Asynchronous on `stream`.  A Rep-factor outside [-128, 127] cannot be
- * reported through a status word without allocating one per call, so it
- * turns every element of Z into NaN instead.  Returns AFMM_ERR_INVALID_ARG
- * for a bad descriptor or a host pointer. */
+ * Asynchronous on `stream`.  A negative or non-integer Rep-factor (NaN
+ * included) or one above 127 cannot be reported through a status word
+ * without allocating one per call, so it turns every element of Z into NaN
+ * instead.  Returns AFMM_ERR_INVALID_ARG for a bad descriptor, a host
+ * pointer, or a device pointer of another device than the current one. */
 afmm_status afmm_mul_noalloc(const afmm_desc* desc, const void* X,
                              const void* Y, void* Z, void* stream);
 

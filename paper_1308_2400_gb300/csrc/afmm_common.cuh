@@ -89,6 +89,12 @@ afmm_status launch_scan(const void* M, int dtype, int64_t n, int64_t ld,
                         bool is_rep, ScanStats* partials, ScanStats* out,
                         int* status, cudaStream_t st);
 
+// Rep-factor check alone (no statistics): a negative entry records
+// AFMM_ERR_NEGATIVE_REP in `status`, else a non-integer one (NaN, infinity)
+// AFMM_ERR_NONINTEGER_REP.  Launches nothing for u8 (always valid).
+afmm_status launch_rep_check(const void* M, int dtype, int64_t n, int64_t ld, int* status,
+                             cudaStream_t st);
+
 // K2: conversions.
 // dst[r*ldd + c] = (float) src[r*lds + c]
 afmm_status launch_to_f32(const void* src, int dtype, int64_t n, int64_t lds,
@@ -99,16 +105,18 @@ afmm_status launch_transpose(const void* src, size_t esize, int64_t rows,
                              cudaStream_t st);
 // Pack an integer-valued n x n matrix B (row-major) into int8 words
 // W[kw*ldw + c] = bytes B[4kw..4kw+3][c] (k-word-major, zero padded to a
-// multiple of 4 rows).  Values outside [-128, 127] record
-// AFMM_ERR_OVERFLOW_RISK in `status`.
+// multiple of 4 rows).  Values outside [-128, 127] or not integers record
+// AFMM_ERR_OVERFLOW_RISK in `status`; with `rep` (the matrix holds
+// Rep-factors) a negative value records AFMM_ERR_NEGATIVE_REP and a
+// non-integer AFMM_ERR_NONINTEGER_REP.
 afmm_status launch_pack_b_i8(const void* B, int dtype, int64_t n, int64_t ldb,
                              int32_t* W, int64_t ldw, int* status,
-                             cudaStream_t st);
+                             cudaStream_t st, bool rep);
 // Copy an integer-valued n x n matrix A (row-major) into int8 rows
-// D[r*ldd + c] (ldd a multiple of 4, padding zeroed).  Same range check.
+// D[r*ldd + c] (ldd a multiple of 4, padding zeroed).  Same checks.
 afmm_status launch_pack_a_i8(const void* A, int dtype, int64_t n, int64_t lda,
                              int8_t* D, int64_t ldd, int* status,
-                             cudaStream_t st);
+                             cudaStream_t st, bool rep);
 // Row-scaled integer slicing of a real matrix for the FP64 target:
 // E[r] = smallest e with max_c |A[r][c]| < 2^e; digit slices
 // Q[s*n + r][c] (int8, ldq) with A[r][c] ~= sum_s Q * 2^(E[r]-w(s+1)).

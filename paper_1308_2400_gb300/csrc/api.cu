@@ -385,9 +385,11 @@ afmm_status run_simt_exact(afmm_plan_s* p, const void* X, const void* Y,
     const int64_t n = d.n;
     int* status = wsp<int>(p, p->off_status);
     AFMM_TRY(launch_pack_a_i8(X, d.x_dtype, n, d.ldx ? d.ldx : n,
-                              wsp<int8_t>(p, p->off_a), p->lda, status, st));
+                              wsp<int8_t>(p, p->off_a), p->lda, status, st,
+                              d.kase == AFMM_CASE_B));
     AFMM_TRY(launch_pack_b_i8(Y, d.y_dtype, n, d.ldy ? d.ldy : n,
-                              wsp<int32_t>(p, p->off_b), p->ldb, status, st));
+                              wsp<int32_t>(p, p->off_b), p->ldb, status, st,
+                              d.kase == AFMM_CASE_A));
     return launch_simt_dp4a(wsp<int8_t>(p, p->off_a), p->lda,
                             wsp<int32_t>(p, p->off_b), p->ldb,
                             static_cast<int32_t*>(Z), d.ldz ? d.ldz : n, n, n,
@@ -406,7 +408,7 @@ afmm_status run_f64slice_a(afmm_plan_s* p, const void* X, int xdt, int64_t ldx,
     int32_t* P = wsp<int32_t>(p, p->off_c);
     AFMM_TRY(launch_exp_slice_rows_i8(X, xdt, n, ldx, E, p->slices, p->bits, Q, p->lda,
                                       st));
-    AFMM_TRY(launch_pack_b_i8(Y, ydt, n, ldy, W, p->ldb, status, st));
+    AFMM_TRY(launch_pack_b_i8(Y, ydt, n, ldy, W, p->ldb, status, st, true));
     AFMM_TRY(launch_simt_dp4a(Q, p->lda, W, p->ldb, P, n,
                               (int64_t)p->slices * n, n, n, st));
     return launch_recombine_f64(P, n, E, p->slices, p->bits, n, Z, ldz, st);
@@ -435,10 +437,10 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
                         cudaStream_t st) {
     const afmm_desc& d = p->d;
     const int64_t n = d.n;
+    const bool x_rep = d.kase == AFMM_CASE_B, y_rep = d.kase == AFMM_CASE_A;
     if (d.flags & AFMM_FLAG_VALIDATE) {
         // Rep-factors are checked (non-negative integers); real factors of
         // a real x real plan only counted.
-        const bool x_rep = d.kase == AFMM_CASE_B, y_rep = d.kase == AFMM_CASE_A;
         int* status = wsp<int>(p, p->off_status);
         ScanStats* part = wsp<ScanStats>(p, p->off_part);
         AFMM_TRY(launch_scan(X, d.x_dtype, n, d.ldx ? d.ldx : n, x_rep, part,
@@ -446,6 +448,15 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
         AFMM_TRY(launch_scan(Y, d.y_dtype, n, d.ldy ? d.ldy : n, y_rep, part,
                              wsp<ScanStats>(p, p->off_sy), status, st));
         p->validated = true;
+    } else if ((x_rep || y_rep) &&
+               (p->variant == AFMM_VARIANT_SIMT_F32 || p->variant == AFMM_VARIANT_SPARSE)) {
+        // Every call checks the Rep-factors (Sec. 2 types: non-negative
+        // integers).  The other forms check them in the conversion that
+        // reads them; these two read them in place, so a check pass runs
+        // first (no launch for u8 Rep-factors, which are always valid).
+        AFMM_TRY(launch_rep_check(x_rep ? X : Y, x_rep ? d.x_dtype : d.y_dtype, n,
+                                  x_rep ? (d.ldx ? d.ldx : n) : (d.ldy ? d.ldy : n),
+                                  wsp<int>(p, p->off_status), st));
     }
     if (n == 0) return AFMM_OK;
     switch (p->variant) {

@@ -140,18 +140,21 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
     // widening jobs for CUDA-core instances with non-FP32 operands
     std::vector<int> wprefix(1, 0);
     size_t wbytes = 0;
+    // (an FP32 Rep-factor operand gets a check-only job: it is read in place)
     for (int i : b->simt_ids) {
         for (int which = 0; which < 2; ++which) {
             const int dt = which == 0 ? descs[i].x_dtype : descs[i].y_dtype;
-            if (dt == AFMM_F32) continue;
+            const bool rep = which == (descs[i].kase == AFMM_CASE_A ? 1 : 0);
+            if (dt == AFMM_F32 && !rep) continue;
             WJob w{};
             w.n = descs[i].n;
             w.dtype = dt;
+            w.rep = rep ? 1 : 0;
             b->wjobs.push_back(w);
             b->wjob_owner.push_back(i);
             b->wjob_which.push_back(which);
             wprefix.push_back(wprefix.back() + (int)w.n);
-            wbytes += ((size_t)w.n * w.n * 4 + 255) / 256 * 256;
+            if (dt != AFMM_F32) wbytes += ((size_t)w.n * w.n * 4 + 255) / 256 * 256;
         }
     }
     std::vector<int> sprefix(1, 0);
@@ -254,6 +257,7 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
             o += ((size_t)sb * n * ldk * 2 + 255) / 256 * 256;
         }
         for (size_t w = 0; w < b->wjobs.size(); ++w) {
+            if (b->wjobs[w].dtype == AFMM_F32) continue;      // check only
             b->wjobs[w].dst = reinterpret_cast<float*>(ops + o);
             o += ((size_t)b->wjobs[w].n * b->wjobs[w].n * 4 + 255) / 256 * 256;
         }
@@ -306,7 +310,7 @@ afmm_status enqueue(BatchState* b, cudaStream_t st, cudaStream_t side,
     if (ntc > 0) {
         AFMM_TRY(launch_batch_convert(b->d_ginst, b->d_row_prefix, b->d_row_job,
                                       b->d_tt_prefix, b->d_tt_job, ntc, b->rows_total,
-                                      b->tt_total, b->d_flags, st));
+                                      b->tt_total, b->d_flags, b->d_status, st));
         AFMM_TRY(launch_batch_tc(b->d_ginst, b->d_maps, b->d_cta_off,
                                  reinterpret_cast<const int*>(b->d_tiles), b->tc_grid,
                                  b->d_flags, b->d_status, st));
@@ -314,7 +318,8 @@ afmm_status enqueue(BatchState* b, cudaStream_t st, cudaStream_t side,
     }
     const int nw = (int)b->wjobs.size(), ns = (int)b->sjobs.size();
     if (nw > 0) {
-        AFMM_TRY(launch_batch_widen(b->d_wjobs, b->d_wprefix, nw, b->wrows_total, side));
+        AFMM_TRY(launch_batch_widen(b->d_wjobs, b->d_wprefix, nw, b->wrows_total,
+                                    b->d_status, side));
         ++k;
     }
     if (ns > 0) {
@@ -519,7 +524,7 @@ afmm_status batched_run(int count, const afmm_desc* descs, const void* const* X,
         j.B = static_cast<const float*>(Y[i]);
         j.ldb = d.ldy ? d.ldy : d.n;
         for (size_t w = 0; w < b->wjobs.size(); ++w)
-            if (b->wjob_owner[w] == i) {
+            if (b->wjob_owner[w] == i && b->wjobs[w].dst) {
                 if (b->wjob_which[w] == 0) { j.A = b->wjobs[w].dst; j.lda = d.n; }
                 else { j.B = b->wjobs[w].dst; j.ldb = d.n; }
             }
@@ -556,6 +561,10 @@ afmm_status batched_status(int count, const afmm_desc* descs, int* out) {
             int h[2] = {0, 0};
             AFMM_CUDA_TRY(cudaMemcpy(&h[0], b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
             *out = h[0];
+            // A reported error is cleared, so the next call starts clean.
+            if (h[0] != 0)
+                AFMM_CUDA_TRY(cudaMemcpy(b->d_status, &h[1], sizeof(int),
+                                         cudaMemcpyHostToDevice));
             return AFMM_OK;
         }
     return AFMM_ERR_INVALID_ARG;

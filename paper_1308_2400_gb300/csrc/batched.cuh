@@ -25,13 +25,14 @@ struct GInst {
     int flag;              // index into the per-instance error flags
 };
 
-// Device record of one operand widened to FP32 for the CUDA-core form.
+// Device record of one operand widened to FP32 for the CUDA-core form
+// (dst null: an FP32 Rep-factor operand that is only checked).
 struct WJob {
     const void* src;
     float* dst;
     int64_t n, lds;
     int dtype;
-    int pad;
+    int rep;               // the operand holds Rep-factors: check them
 };
 
 // One tensor-core tile: instance, tile row, tile column.
@@ -43,12 +44,12 @@ struct TileRec {
 afmm_status launch_batch_convert(const GInst* inst, const int* row_prefix,
                                  const int* row_job, const int* tt_prefix,
                                  const int* tt_job, int ninst, int rows_total,
-                                 int tt_total, int* flags, cudaStream_t st);
+                                 int tt_total, int* flags, int* status, cudaStream_t st);
 afmm_status launch_batch_tc(const GInst* inst, const void* maps, const int* cta_off,
                             const int* tiles, int grid, const int* flags, int* status,
                             cudaStream_t st);
 afmm_status launch_batch_widen(const WJob* jobs, const int* prefix, int njobs,
-                               int rows_total, cudaStream_t st);
+                               int rows_total, int* status, cudaStream_t st);
 
 // Route of an instance under the built-in rule: 1 tensor cores, 0 CUDA cores.
 int batch_rule_route(const afmm_desc& d);

@@ -81,7 +81,7 @@ __device__ __forceinline__ int find_job(const int* prefix, int n, int b) {
 // its Z becomes NaN).  Eight columns per thread and step (vector loads when
 // the rows are aligned), one 16-byte store per slice.
 template <int DT, int KIND>
-__device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags) {
+__device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags, int* status) {
     using T = typename Elem<DT>::T;
     const int64_t n = g.n, ldk = g.ldk;
     const int64_t va = sizeof(T) * 8 < 16 ? sizeof(T) * 8 : 16;
@@ -89,6 +89,7 @@ __device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags
                      (g.ldx * (int64_t)sizeof(T)) % va == 0;
     const T* x = static_cast<const T*>(g.X) + r * g.ldx;
     bool bad = false;
+    int bits = 0;
     for (int64_t c = 8 * threadIdx.x; c < ldk; c += 8 * 128) {
         float v[8];
         // FP32 rows that start off a 16-byte boundary: aligned loads and a shift.
@@ -127,6 +128,7 @@ __device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags
             uint32_t w[4];
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
+                bits |= rep_bits(v[t]) | rep_bits(v[t + 1]);
                 const __nv_bfloat16 b0 = __float2bfloat16_rn(v[t]);
                 const __nv_bfloat16 b1 = __float2bfloat16_rn(v[t + 1]);
                 bad |= __bfloat162float(b0) != v[t] || __bfloat162float(b1) != v[t + 1] ||
@@ -137,30 +139,37 @@ __device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags
                 make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
-    if (KIND == 1 && bad) atomicExch(&flags[g.flag], 1);
+    if (KIND == 1 && bad) bits |= kBadRange;
+    if (KIND == 1 && bits) {
+        atomicExch(&flags[g.flag], 1);
+        atomicCAS(status, 0, bad_status(bits));
+    }
 }
 
 // Block b converts row b - row_prefix[j] of the A operand of instance
 // j = row_job[b].
 __global__ void __launch_bounds__(128)
 g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix,
-              const int* __restrict__ row_job, int rows_total, int* __restrict__ flags) {
+              const int* __restrict__ row_job, int rows_total, int* __restrict__ flags,
+              int* __restrict__ status) {
     const int j = row_job[blockIdx.x];
     const GInst& g = inst[j];
     const int64_t r = blockIdx.x - row_prefix[j];
     if (g.kind == 0) {
-        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 0>(g, r, flags)))
+        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 0>(g, r, flags, status)))
     } else {
-        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 1>(g, r, flags)))
+        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 1>(g, r, flags, status)))
     }
 }
 
 // Block b converts one 64 x 64 tile of the B operand (Y transposed to
 // K-major) of instance j = tt_job[b]: Case A widens the Rep-factors Y
-// (exact, |v| <= 256); Case B splits the real Y into 3 slices.
+// (exact non-negative integers, |v| <= 256); Case B splits the real Y into
+// 3 slices.
 __global__ void __launch_bounds__(256, 6)
 g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_prefix,
-                   const int* __restrict__ tt_job, int* __restrict__ flags) {
+                   const int* __restrict__ tt_job, int* __restrict__ flags,
+                   int* __restrict__ status) {
     __shared__ float tile[64][65];
     const int j = tt_job[blockIdx.x];
     const GInst& g = inst[j];
@@ -169,29 +178,43 @@ g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_pr
     const int64_t t = blockIdx.x - tt_prefix[j];
     const int64_t r0 = (t / tpr) * 64, c0 = (t % tpr) * 64;
     auto* B = static_cast<__nv_bfloat16*>(g.B);
-    bool bad = false;
+    int bits = 0;
     if (g.kind == 0) {
-        G_DTYPE_SWITCH(g.y_dtype, (bad = tile_transpose_convert<DT, 1, true>(
+        G_DTYPE_SWITCH(g.y_dtype, (bits = tile_transpose_convert<DT, 1, true>(
                                        g.Y, n, g.ldy, r0, c0, B, g.ldk, 256.f,
                                        rows_aligned16(g.Y, g.ldy, sizeof(typename Elem<DT>::T)),
-                                       tile)))
+                                       tile, true)))
     } else {
         G_DTYPE_SWITCH(g.y_dtype, (tile_transpose_convert<DT, 3, false>(
                                        g.Y, n, g.ldy, r0, c0, B, g.ldk, 0.f,
                                        rows_aligned16(g.Y, g.ldy, sizeof(typename Elem<DT>::T)),
                                        tile)))
     }
-    if (bad) atomicExch(&flags[g.flag], 1);
+    if (bits) {
+        atomicExch(&flags[g.flag], 1);
+        atomicCAS(status, 0, bad_status(bits));
+    }
 }
 
-// Block b widens one row of one operand to FP32 for the CUDA-core form.
+// Block b widens one row of one operand to FP32 for the CUDA-core form;
+// a Rep-factor operand (w.rep) is checked on the way (non-negative
+// integers, else the batch status records the error), and a job without a
+// destination (an FP32 Rep-factor operand the kernel reads in place) is
+// only checked.
 __global__ void __launch_bounds__(256)
-g_widen_kernel(const WJob* __restrict__ jobs, const int* __restrict__ prefix, int njobs) {
+g_widen_kernel(const WJob* __restrict__ jobs, const int* __restrict__ prefix, int njobs,
+               int* __restrict__ status) {
     const int j = find_job(prefix, njobs, blockIdx.x);
     const WJob& w = jobs[j];
     const int64_t r = blockIdx.x - prefix[j];
-    for (int64_t c = threadIdx.x; c < w.n; c += 256)
-        w.dst[r * w.n + c] = load_any_f(w.src, r * w.lds + c, w.dtype);
+    int bits = 0;
+    for (int64_t c = threadIdx.x; c < w.n; c += 256) {
+        const float v = load_any_f(w.src, r * w.lds + c, w.dtype);
+        if (w.rep) bits |= rep_bits(v);
+        if (w.dst) w.dst[r * w.n + c] = v;
+    }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicCAS(status, 0, bad_status(bits));
 }
 
 // ----------------------------------------------------------- grouped TC
@@ -424,12 +447,13 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
 afmm_status launch_batch_convert(const GInst* inst, const int* row_prefix,
                                  const int* row_job, const int* tt_prefix,
                                  const int* tt_job, int ninst, int rows_total,
-                                 int tt_total, int* flags, cudaStream_t st) {
+                                 int tt_total, int* flags, int* status, cudaStream_t st) {
     if (ninst <= 0) return AFMM_OK;
     AFMM_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (ninst + 1), st));
-    g_rows_kernel<<<rows_total, 128, 0, st>>>(inst, row_prefix, row_job, rows_total, flags);
+    g_rows_kernel<<<rows_total, 128, 0, st>>>(inst, row_prefix, row_job, rows_total, flags,
+                                              status);
     AFMM_CUDA_TRY(cudaGetLastError());
-    g_transpose_kernel<<<tt_total, 256, 0, st>>>(inst, tt_prefix, tt_job, flags);
+    g_transpose_kernel<<<tt_total, 256, 0, st>>>(inst, tt_prefix, tt_job, flags, status);
     AFMM_CUDA_TRY(cudaGetLastError());
     count_launches(2);
     return AFMM_OK;
@@ -451,9 +475,9 @@ afmm_status launch_batch_tc(const GInst* inst, const void* maps, const int* cta_
 }
 
 afmm_status launch_batch_widen(const WJob* jobs, const int* prefix, int njobs,
-                               int rows_total, cudaStream_t st) {
+                               int rows_total, int* status, cudaStream_t st) {
     if (njobs <= 0) return AFMM_OK;
-    g_widen_kernel<<<rows_total, 256, 0, st>>>(jobs, prefix, njobs);
+    g_widen_kernel<<<rows_total, 256, 0, st>>>(jobs, prefix, njobs, status);
     AFMM_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return AFMM_OK;

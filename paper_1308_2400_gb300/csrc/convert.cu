@@ -29,7 +29,21 @@ __global__ void to_f32_kernel(const void* __restrict__ src, int64_t n,
         dst[r * ldd + c] = (float)Elem<DT>::get(src, r * lds + c);
 }
 
-__device__ __forceinline__ int to_i8_checked(double v, int* status) {
+// int8 value of an integer-valued entry.  A value that int8 cannot hold
+// exactly records an error and packs as 0: a non-integer (NaN included) as
+// AFMM_ERR_NONINTEGER_REP for a Rep-factor (`rep`), else
+// AFMM_ERR_OVERFLOW_RISK; a negative Rep-factor (Sec. 2 types) as
+// AFMM_ERR_NEGATIVE_REP; a value outside [-128, 127] as
+// AFMM_ERR_OVERFLOW_RISK.
+__device__ __forceinline__ int to_i8_checked(double v, int* status, int rep) {
+    if (!(trunc(v) == v)) {
+        atomicCAS(status, 0, rep ? (int)AFMM_ERR_NONINTEGER_REP : (int)AFMM_ERR_OVERFLOW_RISK);
+        return 0;
+    }
+    if (rep && v < 0.0) {
+        atomicCAS(status, 0, (int)AFMM_ERR_NEGATIVE_REP);
+        return 0;
+    }
     if (v < -128.0 || v > 127.0) {
         atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
         return 0;
@@ -40,7 +54,7 @@ __device__ __forceinline__ int to_i8_checked(double v, int* status) {
 template <int DT>
 __global__ void pack_b_i8_kernel(const void* __restrict__ B, int64_t n,
                                  int64_t ldb, int32_t* __restrict__ W,
-                                 int64_t ldw, int64_t kwords, int* status) {
+                                 int64_t ldw, int64_t kwords, int* status, int rep) {
     const int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (c >= ldw) return;
     for (int64_t kw = blockIdx.y; kw < kwords; kw += gridDim.y) {
@@ -51,7 +65,7 @@ __global__ void pack_b_i8_kernel(const void* __restrict__ B, int64_t n,
                 const int64_t k = kw * 4 + t;
                 if (k < n) {
                     const int q = to_i8_checked(Elem<DT>::get(B, k * ldb + c),
-                                                status);
+                                                status, rep);
                     w |= (uint32_t)(q & 0xff) << (8 * t);
                 }
             }
@@ -63,12 +77,12 @@ __global__ void pack_b_i8_kernel(const void* __restrict__ B, int64_t n,
 template <int DT>
 __global__ void pack_a_i8_kernel(const void* __restrict__ A, int64_t n,
                                  int64_t lda, int8_t* __restrict__ D,
-                                 int64_t ldd, int* status) {
+                                 int64_t ldd, int* status, int rep) {
     const int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (c >= ldd) return;
     for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
         int q = 0;
-        if (c < n) q = to_i8_checked(Elem<DT>::get(A, r * lda + c), status);
+        if (c < n) q = to_i8_checked(Elem<DT>::get(A, r * lda + c), status, rep);
         D[r * ldd + c] = (int8_t)q;
     }
 }
@@ -283,12 +297,12 @@ afmm_status launch_to_f32(const void* src, int dtype, int64_t n, int64_t lds,
 
 afmm_status launch_pack_b_i8(const void* B, int dtype, int64_t n, int64_t ldb,
                              int32_t* W, int64_t ldw, int* status,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool rep) {
     if (n <= 0) return AFMM_OK;
     const int64_t kwords = (n + 3) / 4;
     afmm_status rc = dispatch_dtype(dtype, [&]<int DT>() -> afmm_status {
         pack_b_i8_kernel<DT><<<grid2d(ldw, kwords), kThreads, 0, st>>>(
-            B, n, ldb, W, ldw, kwords, status);
+            B, n, ldb, W, ldw, kwords, status, rep ? 1 : 0);
         return AFMM_OK;
     });
     AFMM_TRY(rc);
@@ -299,11 +313,11 @@ afmm_status launch_pack_b_i8(const void* B, int dtype, int64_t n, int64_t ldb,
 
 afmm_status launch_pack_a_i8(const void* A, int dtype, int64_t n, int64_t lda,
                              int8_t* D, int64_t ldd, int* status,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool rep) {
     if (n <= 0) return AFMM_OK;
     afmm_status rc = dispatch_dtype(dtype, [&]<int DT>() -> afmm_status {
         pack_a_i8_kernel<DT><<<grid2d(ldd, n), kThreads, 0, st>>>(
-            A, n, lda, D, ldd, status);
+            A, n, lda, D, ldd, status, rep ? 1 : 0);
         return AFMM_OK;
     });
     AFMM_TRY(rc);

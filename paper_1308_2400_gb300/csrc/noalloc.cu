@@ -12,14 +12,14 @@
 // The array holds the scratch of the FP64-target form for n <= 256: row
 // exponents, eight 7-bit digit slices of the real factor, the packed
 // Rep-factors, the exact int32 digit products and, for Case B, transposes.
-// Every GPU that loads this library holds the array until the process
-// exits.  All calls share it: calls that overlap on the GPU (several
-// streams or threads at once) race on it and must not be issued.
+// A device holds the array from the first call on it (CUDA loads this
+// library's device code lazily unless CUDA_MODULE_LOADING=EAGER) until the
+// process exits.  All calls share it: calls that overlap on the GPU
+// (several streams or threads at once) race on it and must not be issued.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "afmm_common.cuh"
 
@@ -48,30 +48,28 @@ static_assert(kOffQ % 256 == 0 && kOffW % 256 == 0 && kOffP % 256 == 0 &&
 // object; its device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Per-device address of g_noalloc_scratch, looked up once per device with
-// that device current.
-std::mutex g_mu;
-char* g_scratch_ptr[64] = {nullptr};
-
+// Device address of g_noalloc_scratch on the current device, looked up on
+// every call with that device current: after a cudaDeviceReset the module
+// is loaded again and the array may sit elsewhere, so no address is kept
+// between calls.  Once the module is loaded on the device the lookup
+// allocates nothing; the first lookup (or launch) on a device loads it
+// under CUDA's default lazy module loading, which is when the array and
+// the code take their device memory.
 afmm_status scratch_for_current_device(char** out) {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
         cudaGetLastError();
         return AFMM_ERR_NO_DEVICE;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        AFMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_scratch_ptr[dev] = static_cast<char*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    AFMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = static_cast<char*>(p);
     return AFMM_OK;
 }
 
-// Z = NaN everywhere when a conversion recorded an error (a Rep-factor
-// outside the int8 range of the digit products), so a bad result cannot be
-// mistaken for a good one.
+// Z = NaN everywhere when a conversion recorded an error (a negative or
+// non-integer Rep-factor, or one outside the int8 range of the digit
+// products), so a bad result cannot be mistaken for a good one.
 __global__ void poison_if_flagged(double* Z, int64_t n, int64_t ldz,
                                   const int* status) {
     if (*status == 0) return;
@@ -92,7 +90,7 @@ afmm_status run_case_a(char* s, int64_t n, const void* X, int xdt, int64_t ldx,
     int32_t* P = reinterpret_cast<int32_t*>(s + kOffP);
     AFMM_TRY(launch_exp_slice_rows_i8(X, xdt, n, ldx, E, kNoAllocSlices, kNoAllocBits, Q,
                                   ld, st));
-    AFMM_TRY(launch_pack_b_i8(Y, ydt, n, ldy, W, ld, status, st));
+    AFMM_TRY(launch_pack_b_i8(Y, ydt, n, ldy, W, ld, status, st, true));
     AFMM_TRY(launch_simt_dp4a(Q, ld, W, ld, P, n, (int64_t)kNoAllocSlices * n, n, n,
                               st));
     return launch_recombine_f64(P, n, E, kNoAllocSlices, kNoAllocBits, n, Z, ldz, st);
@@ -126,7 +124,13 @@ extern "C" afmm_status afmm_mul_noalloc(const afmm_desc* d, const void* X,
         return AFMM_ERR_INVALID_ARG;
     if (n == 0) return AFMM_OK;
     if (!X || !Y || !Z) return AFMM_ERR_INVALID_ARG;
-    // Device pointers only: host buffers would need staging memory.
+    // Device pointers of the current device only: host buffers would need
+    // staging memory, and another device's memory may not be reachable.
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return AFMM_ERR_NO_DEVICE;
+    }
     for (const void* p : {X, Y, static_cast<const void*>(Z)}) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -135,6 +139,7 @@ extern "C" afmm_status afmm_mul_noalloc(const afmm_desc* d, const void* X,
         }
         if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
             return AFMM_ERR_INVALID_ARG;
+        if (a.type == cudaMemoryTypeDevice && a.device != cur) return AFMM_ERR_INVALID_ARG;
     }
     char* s = nullptr;
     AFMM_TRY(scratch_for_current_device(&s));

@@ -101,7 +101,66 @@ scan_finalize(const ScanStats* __restrict__ partials, int nb,
     }
 }
 
+// Rep-factor check only (Sec. 2 types: non-negative integers): one read of
+// the matrix with 16-byte loads where rows allow, flags reduced per warp,
+// one atomic per warp that saw a bad entry.  A negative entry records
+// AFMM_ERR_NEGATIVE_REP; otherwise a non-integer (NaN and infinities
+// included) records AFMM_ERR_NONINTEGER_REP.
+template <int DT>
+__device__ __forceinline__ uint32_t rep_flags(typename Elem<DT>::T e) {
+    if constexpr (DT == AFMM_U8) {
+        return 0u;
+    } else if constexpr (DT == AFMM_I8 || DT == AFMM_I32) {
+        return e < 0 ? 1u : 0u;
+    } else {
+        const double v = Elem<DT>::get(&e, 0);
+        return (v < 0.0 ? 1u : 0u) | ((!isfinite(v) || trunc(v) != v) ? 2u : 0u);
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kScanThreads)
+rep_check_kernel(const void* __restrict__ M, int64_t n, int64_t ld, int vec, int* status) {
+    using T = typename Elem<DT>::T;
+    constexpr int V = 16 / (int)sizeof(T);
+    const T* m = static_cast<const T*>(M);
+    uint32_t bits = 0;
+    const int64_t chunks = vec ? n / V : 0;          // whole 16-byte pieces per row
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const T* row = m + r * ld;
+        for (int64_t c = threadIdx.x; c < chunks; c += kScanThreads) {
+            const uint4 q = reinterpret_cast<const uint4*>(row)[c];
+            const T* e = reinterpret_cast<const T*>(&q);
+#pragma unroll
+            for (int t = 0; t < V; ++t) bits |= rep_flags<DT>(e[t]);
+        }
+        for (int64_t c = chunks * V + threadIdx.x; c < n; c += kScanThreads)
+            bits |= rep_flags<DT>(row[c]);
+    }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && bits)
+        atomicCAS(status, 0, (int)((bits & 1u) ? AFMM_ERR_NEGATIVE_REP : AFMM_ERR_NONINTEGER_REP));
+}
+
 }  // namespace
+
+afmm_status launch_rep_check(const void* M, int dtype, int64_t n, int64_t ld, int* status,
+                             cudaStream_t st) {
+    if (n <= 0 || dtype == AFMM_U8) return AFMM_OK;      // u8 holds only valid values
+    DeviceProps dp;
+    AFMM_TRY(device_props(&dp));
+    const int64_t es = (int64_t)dtype_size(dtype);
+    const int vec = (reinterpret_cast<uintptr_t>(M) & 15u) == 0 && (ld * es) % 16 == 0;
+    const int nb = (int)(n < dp.sm_count * 4 ? n : dp.sm_count * 4);
+    afmm_status rc = dispatch_dtype(dtype, [&]<int DT>() -> afmm_status {
+        rep_check_kernel<DT><<<nb, kScanThreads, 0, st>>>(M, n, ld, vec, status);
+        return AFMM_OK;
+    });
+    AFMM_TRY(rc);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
+}
 
 afmm_status launch_scan(const void* M, int dtype, int64_t n, int64_t ld,
                         bool is_rep, ScanStats* partials, ScanStats* out,

@@ -71,7 +71,8 @@ __device__ __forceinline__ void f8_encode16(const float (&v)[16], uint32_t (&w)[
 
 // Rows [r0, r1) of the row-major n x n source kept as K-major E4M3 rows,
 // dst[(s * n + r) * ldk + c] (zero for n <= c < ldk; ldk a multiple of 16).
-// REP: one exact slice (Rep-factors).  Else the row's largest |value| (its
+// REP: one exact slice (Rep-factors, which must also be non-negative
+// integers: AFMM_ERR_NEGATIVE_REP / _NONINTEGER_REP).  Else the row's largest |value| (its
 // FP32 bits in amax[r]) sets the shift and the four slices are written; a
 // non-finite value is reported as AFMM_ERR_OVERFLOW_RISK.  One block per
 // row: the maximum pass reads the row, the slicing pass reads it again
@@ -84,6 +85,7 @@ f8_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds, uint8_t* __
     __shared__ uint32_t red[8];
     using T = typename Elem<DT>::T;
     bool bad = false;
+    int bits = 0;
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const T* row = static_cast<const T*>(src) + r * lds;
         int sh = 0;
@@ -108,6 +110,10 @@ f8_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds, uint8_t* __
 #pragma unroll
                 for (int t = 0; t < 16; ++t) v[t] = f8_scale(v[t], sh);
             }
+            if constexpr (REP) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) bits |= rep_bits(v[t]);
+            }
             uint32_t w[4][4];
             f8_encode16<REP>(v, w, bad);
 #pragma unroll
@@ -116,7 +122,8 @@ f8_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds, uint8_t* __
                     make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
         }
     }
-    if (bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+    if (bad) bits |= kBadRange;
+    if (bits) atomicCAS(status, 0, bad_status(bits));
 }
 
 // amax[c] = FP32 bits of the largest |src[r][c]| over rows r (the caller
@@ -163,14 +170,20 @@ f8_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
 #pragma unroll
             for (int e = 0; e < 16; ++e) v[e] = f8_scale(v[e], sh);
         }
+        int bits = 0;
+        if constexpr (REP) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) bits |= rep_bits(v[e]);
+        }
         uint32_t w[4][4];
         f8_encode16<REP>(v, w, bad);
 #pragma unroll
         for (int s = 0; s < (REP ? 1 : 4); ++s)
             *reinterpret_cast<uint4*>(dst + ((int64_t)s * n + c) * ldk + r) =
                 make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+        if (bad) bits |= kBadRange;
+        if (bits) atomicCAS(status, 0, bad_status(bits));
     }
-    if (bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
 }
 
 }  // namespace

@@ -902,7 +902,7 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
     if (d.kase == AFMM_CASE_A && t->slices == 3 && tc_fused_usable(d, X)) {
         // B = Rep-factors Y transposed; X is split inside the product kernel.
         AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
-                                                  256.f, status, st)));
+                                                  256.f, status, st, true)));
         return tc_run_fused_caseA(t, d, X, Z, status, st);
     }
     if (d.kase == AFMM_CASE_A) {
@@ -914,7 +914,7 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
             AFMM_TRY((tc_widen_rows(2, false, X, d.x_dtype, n, d.ldx, A, t->ld_a,
                                                   0.f, status, st)));
         AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
-                                                  256.f, status, st)));
+                                                  256.f, status, st, true)));
         if (t->z) {
             // Rows of Z off 16-byte boundaries: product into the aligned
             // buffer, then one 2-D copy.
@@ -932,7 +932,7 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
     }
     // Case B: A = Rep-factors X (rows), B = slices of the real Y transposed.
     AFMM_TRY((tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, A, t->ld_a, 256.f,
-                                         status, st)));
+                                         status, st, 0, -1, true)));
     if (t->slices == 3)
         AFMM_TRY((tc_widen_transpose(3, false, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
                                                    0.f, status, st)));
@@ -1002,9 +1002,9 @@ afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,
     auto* A = static_cast<__nv_bfloat16*>(t->a);
     auto* B = static_cast<__nv_bfloat16*>(t->b);
     AFMM_TRY((tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, A, t->ld_a, t->lim_a,
-                                         status, st)));
+                                         status, st, 0, -1, d.kase == AFMM_CASE_B)));
     AFMM_TRY((tc_widen_transpose(1, true, Y, d.y_dtype, n, d.ldy, B, t->ld_b,
-                                              t->lim_b, status, st)));
+                                              t->lim_b, status, st, d.kase == AFMM_CASE_A)));
     return launch_exact2(t, Z, d.ldz, t->kb_per_chunk, status, st);
 }
 
@@ -1017,7 +1017,7 @@ afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int
                                t->amax, status, st);
     if (d.kase == AFMM_CASE_A)        // B = Rep-factors Y transposed
         return tc_widen_transpose(1, true, Y, d.y_dtype, d.n, d.ldy, t->b, t->ld_b, 256.f,
-                                  status, st);
+                                  status, st, true);
     return tc_widen_transpose(sl, false, Y, d.y_dtype, d.n, d.ldy, t->b, t->ld_b, 0.f,
                               status, st);
 }
@@ -1041,7 +1041,7 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
                                st, r0, r1));
     else
         AFMM_TRY(tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 256.f, status,
-                               st, r0, r1));
+                               st, r0, r1, true));
     if (d.kase == AFMM_CASE_A)
         return sl == 3 ? launch_tc<3, 1>(t, Zf, d.ldz, status, st, m0, m1)
                        : launch_tc<2, 1>(t, Zf, d.ldz, status, st, m0, m1);

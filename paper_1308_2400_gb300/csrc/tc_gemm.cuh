@@ -58,13 +58,16 @@ afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
 // kept (K-major A) or transposed (K-major B, dst row = source column).
 // exact: one slice that must equal the source and stay within |lim|
 // (AFMM_ERR_OVERFLOW_RISK in *status otherwise); else 2 or 3 RN slices.
+// rep: the source holds Rep-factors, checked to be non-negative integers
+// (AFMM_ERR_NEGATIVE_REP / AFMM_ERR_NONINTEGER_REP in *status otherwise).
 // (tc_widen_rows converts rows [r0, r1) only; r1 < 0 means n.)
 afmm_status tc_widen_rows(int slices, bool exact, const void* src, int dt, int64_t n,
                           int64_t lds, void* dst, int64_t ldk, float lim, int* status,
-                          cudaStream_t st, int64_t r0 = 0, int64_t r1 = -1);
+                          cudaStream_t st, int64_t r0 = 0, int64_t r1 = -1,
+                          bool rep = false);
 afmm_status tc_widen_transpose(int slices, bool exact, const void* src, int dt, int64_t n,
                                int64_t lds, void* dst, int64_t ldk, float lim, int* status,
-                               cudaStream_t st);
+                               cudaStream_t st, bool rep = false);
 
 // FP8 form conversions (tc_fp8.cu): dst E4M3 [slices][n][ldk], ldk a
 // multiple of 16.  rep: one slice that must equal the source (Rep-factors;

@@ -34,14 +34,17 @@ __device__ __forceinline__ float load_checked(const void* p, int64_t i, float li
 
 // Rows kept as rows (K-major A operand): dst[(s*n + r)*ldk + c], eight
 // columns per thread (one 16-byte store per slice).  EXACT: one slice that
-// must equal the source (Rep-factors); otherwise OVERFLOW_RISK is recorded.
+// must equal the source; otherwise OVERFLOW_RISK is recorded.  rep: the
+// source holds Rep-factors, which must be non-negative integers (Sec. 2
+// types; NEGATIVE_REP / NONINTEGER_REP otherwise).
 template <int DT, int S, bool EXACT>
 __global__ void __launch_bounds__(256)
 widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                   __nv_bfloat16* __restrict__ dst, int64_t ldk, int vec,
-                  float lim, int* status, int64_t r0, int64_t r1) {
+                  float lim, int* status, int64_t r0, int64_t r1, int rep) {
     const int64_t c = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 8;
     if (c >= ldk) return;
+    int bits = 0;
     for (int64_t r = r0 + blockIdx.y; r < r1; r += gridDim.y) {
         uint32_t w[S][4];
         bool done = false;
@@ -60,10 +63,11 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                     if (EXACT)
                         bad |= __bfloat162float(o0[0]) != v0 || fabsf(v0) > lim ||
                                __bfloat162float(o1[0]) != v1 || fabsf(v1) > lim;
+                    if (rep) bits |= rep_bits(v0) | rep_bits(v1);
 #pragma unroll
                     for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o0[s], o1[s]);
                 }
-                if (EXACT && bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+                if (EXACT && bad) bits |= kBadRange;
                 done = true;
             }
         }
@@ -87,6 +91,10 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                     __nv_bfloat16 o0[S], o1[S];
                     split_bf16<S>(v[j], o0);
                     split_bf16<S>(v[j + 1], o1);
+                    if (EXACT && (__bfloat162float(o0[0]) != v[j] || fabsf(v[j]) > lim ||
+                                  __bfloat162float(o1[0]) != v[j + 1] || fabsf(v[j + 1]) > lim))
+                        bits |= kBadRange;
+                    if (rep) bits |= rep_bits(v[j]) | rep_bits(v[j + 1]);
 #pragma unroll
                     for (int s = 0; s < S; ++s) w[s][j / 2] = pack2(o0[s], o1[s]);
                 }
@@ -104,7 +112,8 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                     const float v = load_checked<DT>(src, r * lds + cc, lim, bad);
                     split_bf16<S>(v, o[t]);
                     if (EXACT && (bad || __bfloat162float(o[t][0]) != v || fabsf(v) > lim))
-                        atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+                        bits |= kBadRange;
+                    if (rep) bits |= rep_bits(v);
                 } else {
 #pragma unroll
                     for (int s = 0; s < S; ++s) o[t][s] = __float2bfloat16_rn(0.0f);
@@ -118,6 +127,7 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
             *reinterpret_cast<uint4*>(dst + ((int64_t)s * n + r) * ldk + c) =
                 make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
     }
+    if (bits) atomicCAS(status, 0, bad_status(bits));
 }
 
 // Rows become columns (K-major B operand from a row-major K x N matrix):
@@ -129,18 +139,19 @@ template <int DT, int S, bool EXACT>
 __global__ void __launch_bounds__(256)
 widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                        __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
-                       int vec, int* status) {
+                       int vec, int* status, int rep) {
     __shared__ float tile[64][65];
-    const bool bad = tile_transpose_convert<DT, S, EXACT>(
+    const int bits = tile_transpose_convert<DT, S, EXACT>(
         src, n, lds, (int64_t)blockIdx.y * 64, (int64_t)blockIdx.x * 64, dst, ldk, lim,
-        vec != 0, tile);
-    if (EXACT && bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+        vec != 0, tile, rep != 0);
+    if (bits) atomicCAS(status, 0, bad_status(bits));
 }
 
 template <int S, bool EXACT>
 afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
                               __nv_bfloat16* dst, int64_t ldk, float lim,
-                              int* status, cudaStream_t st, int64_t r0, int64_t r1) {
+                              int* status, cudaStream_t st, int64_t r0, int64_t r1,
+                              bool rep) {
     const int64_t per_row = ldk / 8;
     const int64_t rows = r1 - r0;
     if (rows <= 0) return AFMM_OK;
@@ -151,7 +162,7 @@ afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
     const int vec = (lds * es) % va == 0 && (reinterpret_cast<uintptr_t>(src) % va) == 0;
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
         widen_rows_kernel<DT, S, EXACT><<<grid, 256, 0, st>>>(src, n, lds, dst, ldk, vec,
-                                                              lim, status, r0, r1);
+                                                              lim, status, r0, r1, rep ? 1 : 0);
         return AFMM_OK;
     });
     AFMM_TRY(rc);
@@ -163,14 +174,14 @@ afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
 template <int S, bool EXACT>
 afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
                                    int64_t lds, __nv_bfloat16* dst, int64_t ldk,
-                                   float lim, int* status, cudaStream_t st) {
+                                   float lim, int* status, cudaStream_t st, bool rep) {
     const int64_t g = (n + 63) / 64;
     if (g > 65535) return AFMM_ERR_UNSUPPORTED;
     const dim3 grid((unsigned)g, (unsigned)g), block(256);
     const int vec = rows_aligned16(src, lds, (int64_t)dtype_size(dt));
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
-        widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(src, n, lds, dst,
-                                                                     ldk, lim, vec, status);
+        widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(
+            src, n, lds, dst, ldk, lim, vec, status, rep ? 1 : 0);
         return AFMM_OK;
     });
     AFMM_TRY(rc);
@@ -183,25 +194,28 @@ afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
 
 afmm_status tc_widen_rows(int slices, bool exact, const void* src, int dt, int64_t n,
                           int64_t lds, void* dst, int64_t ldk, float lim, int* status,
-                          cudaStream_t st, int64_t r0, int64_t r1) {
+                          cudaStream_t st, int64_t r0, int64_t r1, bool rep) {
     auto* d = static_cast<__nv_bfloat16*>(dst);
     if (r1 < 0) r1 = n;
     if (exact && slices == 1)
-        return launch_widen_rows<1, true>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1);
+        return launch_widen_rows<1, true>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1, rep);
     if (!exact && slices == 3)
-        return launch_widen_rows<3, false>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1);
+        return launch_widen_rows<3, false>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1, rep);
     if (!exact && slices == 2)
-        return launch_widen_rows<2, false>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1);
+        return launch_widen_rows<2, false>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1, rep);
     return AFMM_ERR_INVALID_ARG;
 }
 
 afmm_status tc_widen_transpose(int slices, bool exact, const void* src, int dt, int64_t n,
                                int64_t lds, void* dst, int64_t ldk, float lim, int* status,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool rep) {
     auto* d = static_cast<__nv_bfloat16*>(dst);
-    if (exact && slices == 1) return launch_widen_transpose<1, true>(src, dt, n, lds, d, ldk, lim, status, st);
-    if (!exact && slices == 3) return launch_widen_transpose<3, false>(src, dt, n, lds, d, ldk, lim, status, st);
-    if (!exact && slices == 2) return launch_widen_transpose<2, false>(src, dt, n, lds, d, ldk, lim, status, st);
+    if (exact && slices == 1)
+        return launch_widen_transpose<1, true>(src, dt, n, lds, d, ldk, lim, status, st, rep);
+    if (!exact && slices == 3)
+        return launch_widen_transpose<3, false>(src, dt, n, lds, d, ldk, lim, status, st, rep);
+    if (!exact && slices == 2)
+        return launch_widen_transpose<2, false>(src, dt, n, lds, d, ldk, lim, status, st, rep);
     return AFMM_ERR_INVALID_ARG;
 }
 

@@ -9,6 +9,7 @@
 #include <cstdint>
 
 #include "bf16_split.cuh"
+#include "afmm.h"
 #include "elem.cuh"
 
 namespace afmm {
@@ -120,24 +121,43 @@ __device__ __forceinline__ void tile_load_f32(const void* __restrict__ src, int6
     }
 }
 
+// Check bits of a converted value: kBadRange (not exact in the operand type
+// or beyond its limit), and for Rep-factors (Sec. 2 types: non-negative
+// integers) kBadNegative and kBadNonInteger (NaN and infinities included).
+constexpr int kBadRange = 1, kBadNegative = 2, kBadNonInteger = 4;
+
+__device__ __forceinline__ int rep_bits(float v) {
+    return (v < 0.f ? kBadNegative : 0) | ((!isfinite(v) || truncf(v) != v) ? kBadNonInteger : 0);
+}
+
+// The status code of a set of check bits (0 when none is set): a negative
+// Rep-factor first, then a non-integer one, then a range error.
+__device__ __forceinline__ int bad_status(int bits) {
+    return (bits & kBadNegative) ? (int)AFMM_ERR_NEGATIVE_REP
+           : (bits & kBadNonInteger) ? (int)AFMM_ERR_NONINTEGER_REP
+           : bits ? (int)AFMM_ERR_OVERFLOW_RISK : 0;
+}
+
 // Rows r0 .. r0+63 and columns c0 .. c0+63 of the row-major n x n source
 // become rows c (K-major) of the destination: dst[(s * n + c) * ldk + r] =
-// slice s of src[r][c], for S BF16 slices (S = 1 and EXACT: the value must
-// be exact in BF16 and |v| <= lim, else the return value is true).
+// slice s of src[r][c], for S BF16 slices.  S = 1 and EXACT: the value must
+// be exact in BF16 and |v| <= lim, else kBadRange is returned; `rep` adds
+// the Rep-factor checks (rep_bits) of every value in the matrix.
 // Loads: tile_load_f32; the tile goes through shared memory as FP32;
 // stores: four threads write one 128-byte segment of an output row per
 // slice.  256 threads; `tile` is [64][65].
 template <int DT, int S, bool EXACT>
-__device__ __forceinline__ bool tile_transpose_convert(const void* __restrict__ src,
-                                                       int64_t n, int64_t lds, int64_t r0,
-                                                       int64_t c0,
-                                                       __nv_bfloat16* __restrict__ dst,
-                                                       int64_t ldk, float lim, bool vec,
-                                                       float (*tile)[65]) {
+__device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ src,
+                                                      int64_t n, int64_t lds, int64_t r0,
+                                                      int64_t c0,
+                                                      __nv_bfloat16* __restrict__ dst,
+                                                      int64_t ldk, float lim, bool vec,
+                                                      float (*tile)[65], bool rep = false) {
     const int tid = threadIdx.x;
     bool bad = false;
     tile_load_f32<DT>(src, n, lds, r0, c0, lim, vec, tile, bad);
     if (!EXACT) bad = false;
+    int bits = bad ? kBadRange : 0;
     __syncthreads();
     const int cc = tid >> 2, qq = tid & 3;
     const int64_t c = c0 + cc, r = r0 + 16 * qq;
@@ -152,9 +172,11 @@ __device__ __forceinline__ bool tile_transpose_convert(const void* __restrict__ 
             __nv_bfloat16 o0[S], o1[S];
             split_bf16<S>(v[e], o0);
             split_bf16<S>(v[e + 1], o1);
-            if (EXACT)
-                bad |= __bfloat162float(o0[0]) != v[e] || __bfloat162float(o1[0]) != v[e + 1] ||
-                       fabsf(v[e]) > lim || fabsf(v[e + 1]) > lim;
+            if (EXACT && (__bfloat162float(o0[0]) != v[e] ||
+                          __bfloat162float(o1[0]) != v[e + 1] || fabsf(v[e]) > lim ||
+                          fabsf(v[e + 1]) > lim))
+                bits |= kBadRange;
+            if (rep) bits |= rep_bits(v[e]) | rep_bits(v[e + 1]);
 #pragma unroll
             for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
         }
@@ -167,7 +189,7 @@ __device__ __forceinline__ bool tile_transpose_convert(const void* __restrict__ 
                     make_uint4(w[sl][4], w[sl][5], w[sl][6], w[sl][7]);
         }
     }
-    return bad;
+    return bits;
 }
 
 // Whether rows of a dtype-dt source start 16-byte aligned.

@@ -33,11 +33,11 @@ def z_torch_dtype(z):
 
 
 def desc_for(inst, variant=-1, flags=0, hints=True):
+    from afmm_inputs import density_hints
     from paper_1308_2400_gb300 import make_desc
-    from oracle import realised_parameters
     d1 = d2 = mp = -1.0
     if hints:
-        p = realised_parameters(inst.X, inst.Y, inst.case)
+        p = density_hints(inst.X, inst.Y, inst.case)
         d1, d2, mp = p["d1"], p["d2"], p["mu_prime"]
     return make_desc(inst.n, inst.case, inst.x_dtype, inst.y_dtype,
                      inst.z_dtype, inst.target, variant=variant, flags=flags,

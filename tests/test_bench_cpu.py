@@ -30,3 +30,27 @@ def test_reference_arm_prints_one_contract_line():
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "caseA_n256_f64"
+    # The reference line's config is the main line's workload config.
+    sys.path.insert(0, ROOT)
+    import bench
+    import afmm_inputs as W
+    want = bench.workload_config("caseA_n256_f64", W.make("caseA_n256_f64"), 1)
+    assert d["config"] == json.loads(json.dumps(want))
+
+
+def test_cpu_baseline_rows_are_whole_thread_blocks():
+    """The CPU baseline hands the oracle contiguous blocks of one row per
+    oracle thread, so each call runs one parallel region over all cores."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import afmm_inputs as W
+    from oracle import oracle_threads
+    inst = W.make("caseB_n4096_f32", n=96, seed=3)
+    rows, Zr, el, thr = bench.oracle_rows_timed(inst, 0.0, min_rows=2 * min(oracle_threads(), 96))
+    assert thr == min(oracle_threads(), 96)
+    assert rows.size % thr == 0 and rows.size >= min(2 * thr, 96 - 96 % thr)
+    blocks = rows.reshape(-1, thr)
+    assert np.all(np.diff(blocks, axis=1) == 1)
+    assert np.all(blocks[:, 0] % thr == 0)
+    assert Zr.shape == (rows.size, 96)

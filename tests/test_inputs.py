@@ -39,3 +39,19 @@ def test_workload_densities():
         if d_y is not None:
             want_y = d_y if wl != "caseB_n4096_sparse" else 1 / math.sqrt(n)
             assert abs(p["d2"] - want_y) <= 5 * math.sqrt(want_y * (1 - want_y) / n ** 2), wl
+
+
+@pytest.mark.parametrize("wl", ["caseA_n256_f64", "caseB_n4096_f32", "caseA_n8192_e4m3",
+                                "caseA_n16384_i8", "caseB_n4096_sparse"])
+def test_plan_hints_match_the_oracle_parameters(wl):
+    """The hints the GPU legs pass (counted in afmm_inputs, no oracle) equal
+    the oracle's statement of d1, d2 and mu' (Sec. 2.2)."""
+    inst = W.make(wl, n=96, seed=5)
+    h = W.density_hints(inst.X, inst.Y, inst.case)
+    p = realised_parameters(inst.X, inst.Y, inst.case)
+    for k in ("d1", "d2", "mu_prime"):
+        assert h[k] == p[k], k
+    rep = inst.Y if inst.case == "A" else inst.X
+    real = inst.X if inst.case == "A" else inst.Y
+    assert h["rep_max"] == float(rep.max())
+    assert h["base_max"] == float(np.abs(real.astype(np.float64)).max())

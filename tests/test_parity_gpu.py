@@ -687,12 +687,25 @@ def _batch(insts, routes=None):
     return descs, Xs, Ys, Zs
 
 
-def _check_batch(insts, Zs):
-    for inst, Z in zip(insts, Zs):
-        R = oracle_rows(inst)
+def _check_batch(insts, Zs, descs=None, rows_per_instance=None):
+    """Every instance against the oracle: relative Frobenius error and the
+    element bound of the route it took (tensor cores or CUDA cores; the
+    route read back from the dispatcher when descriptors are given), on
+    all rows or on a sampled set per instance."""
+    from paper_1308_2400_gb300 import afmm as A
+    for t, (inst, Z) in enumerate(zip(insts, Zs)):
+        rows = None if rows_per_instance is None else \
+            sample_rows(inst.n, rows_per_instance, seed=t)
+        R = oracle_rows(inst, rows)
         Zn = Z.cpu().numpy()
+        Zn = Zn if rows is None else Zn[rows]
         assert np.all(np.isfinite(Zn)), inst.name
         assert rel_fro(Zn, R) <= FP32_REL_FRO, inst.name
+        if descs is not None:
+            tc = A.afmm_dispatch_variant(descs[t]) == A.AFMM_VARIANT_TC_BF16X3
+            bound = (tc_elem_bound if tc else simt_f32_elem_bound)(inst, rows)
+            bad = np.abs(Zn.astype(np.float64) - R) > bound
+            assert not bad.any(), (inst.name, "tc" if tc else "simt", int(bad.sum()))
 
 
 @pytest.mark.parametrize("route", ["auto", "tc", "simt", "mixed"])
@@ -705,7 +718,7 @@ def test_batched_grouped_routes(route):
     descs, Xs, Ys, Zs = _batch(insts, routes)
     afmm_mul_batched(descs, Xs, Ys, Zs)
     afmm_batched_sync(descs)
-    _check_batch(insts, Zs)
+    _check_batch(insts, Zs, descs=descs)
 
 
 def test_batched_graph_replay_with_new_data():
@@ -748,6 +761,26 @@ def test_batched_bad_rep_factor_poisons_only_its_instance():
     afmm_batched_sync(descs)
     assert np.all(np.isnan(Zs[0].cpu().numpy()))
     _check_batch(insts[1:], Zs[1:])
+
+
+def test_batched_law_with_learned_dispatch():
+    """The batched workload's own law (n log-uniform up to 2048, d1, d2 in
+    [0.05, 1], Poisson Rep-factors, cases A and B) at 64 instances, routed
+    by the installed dispatch network: every instance checked against the
+    oracle on sampled rows, with the element bound of its route."""
+    from paper_1308_2400_gb300 import afmm_mul_batched
+    from paper_1308_2400_gb300 import tune
+    from paper_1308_2400_gb300.afmm import afmm_batched_sync, afmm_set_dispatch_model
+    insts = W.batched_mix(count=64, seed=17)
+    assert max(t.n for t in insts) > 1024 and {t.case for t in insts} == {"A", "B"}
+    tune.install(tune.load(tune.DEFAULT_MODEL))
+    try:
+        descs, Xs, Ys, Zs = _batch(insts)
+        afmm_mul_batched(descs, Xs, Ys, Zs)
+        afmm_batched_sync(descs)
+        _check_batch(insts, Zs, descs=descs, rows_per_instance=10)
+    finally:
+        afmm_set_dispatch_model(None, None, None, None, None)
 
 
 def test_batched_small_mix():
