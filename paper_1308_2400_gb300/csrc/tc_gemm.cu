@@ -443,6 +443,291 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     }
 }
 
+// --------------------------------------------------- two-SM split form
+// tc_pair_kernel: the split form of tc_gemm_kernel (S BF16 slices of the real
+// factor on the A side, one Rep-factor tile on the B side, hi and small sums
+// in two TMEM accumulators) computed by clusters of two CTAs on the two SMs
+// of a pair with tcgen05 cta_group::2.  A pair owns a 256 x 256 output tile:
+// CTA r holds A rows [128 r, 128 r + 128) of the tile's slices and B rows
+// (product columns) [128 r, 128 r + 128) in its shared memory, and the
+// accumulator rows [128 r, 128 r + 128) x all 256 columns in its TMEM.  The
+// even CTA issues every MMA (M = 256, N = 256, K = 16), whose B operand
+// is read from both CTAs' halves, so each SM stages and reads half the B
+// bytes per flop of the one-CTA kernel: per 32-wide K step a CTA receives
+// S x 8 KiB + 8 KiB instead of S x 8 KiB + 16 KiB, and its tensor core reads
+// 4 + 4 KiB per MMA instead of 4 + 8 KiB.
+//   - Both CTAs' TMA copies of a stage complete on the even CTA's `full`
+//     barrier (cta_group::2 copies), which expects both CTAs' bytes.
+//   - The MMA commits free a stage in both CTAs and hand a finished tile to
+//     both CTAs' epilogues (multicast commits).
+//   - Each epilogue warp of either CTA arrives on the even CTA's `tempty`
+//     barrier (16 arrivals) once it has read its TMEM lanes.
+// Every wait is bounded; an abort raised in one CTA is written into the
+// peer's flag too, and both CTAs meet at cluster barriers at the start
+// (barriers initialised) and before releasing TMEM.
+constexpr int PR_BM = 256, PR_BN = 256;           // pair tile
+constexpr int PR_HALF = 128;                       // rows of A and of B per CTA
+constexpr int PR_B_BYTES = PR_HALF * TC_BK * 2;    // 8 KiB
+constexpr int PR_GROUP_M = 5;                      // tile raster band (tile rows)
+constexpr int PR_EPI_WARPS = 2 * (TC_EPI_THREADS / 32);   // tempty arrivals
+
+template <int SA>
+struct PairCfg {
+    static constexpr int STAGE_BYTES = SA * A_TILE_BYTES + PR_B_BYTES;
+    static constexpr int STAGES_FIT = (SMEM_OPTIN - 2048) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
+    static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+    static_assert(STAGES >= 2, "pipeline needs two stages");
+    static_assert(SMEM <= SMEM_OPTIN, "shared memory");
+};
+
+__device__ __forceinline__ void pair_tile_coords(int tile, int tiles_m, int tiles_n, int& tm,
+                                                 int& tn) {
+    const int per_group = PR_GROUP_M * tiles_n;
+    const int g = tile / per_group;
+    const int first_m = g * PR_GROUP_M;
+    const int gm = min(tiles_m - first_m, PR_GROUP_M);
+    const int r = tile % per_group;
+    tm = first_m + r % gm;
+    tn = r / gm;
+}
+
+__device__ __forceinline__ void raise_abort_pair(TcBars* b, uint32_t peer_abort, int* status) {
+    b->abort = 1;
+    ptx::st_shared_cluster_u32(peer_abort, 1u);
+    __threadfence_block();
+    atomicCAS(status, 0, (int)AFMM_ERR_TIMEOUT);
+}
+
+template <int SA, bool TOUT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
+               const __grid_constant__ CUtensorMap tmB, float* __restrict__ Z, int64_t ldz,
+               int m0, int M, int n0, int N, int K, int vec, int* status) {
+    using Cfg = PairCfg<SA>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = ptx::smem_addr(smem_raw);
+    uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    TcBars* bars = reinterpret_cast<TcBars*>(tiles + Cfg::STAGES * Cfg::STAGE_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = ptx::cluster_ctarank();
+    const bool leader = rank == 0;
+    const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+    const int tiles_m = (M - m0 + PR_BM - 1) / PR_BM, tiles_n = (N - n0 + PR_BN - 1) / PR_BN;
+    const int num_tiles = tiles_m * tiles_n;
+    const int num_kb = (K + TC_BK - 1) / TC_BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            ptx::mbar_init(&bars->full[s], 1);
+            ptx::mbar_init(&bars->empty[s], 1);
+        }
+        ptx::mbar_init(&bars->tfull[0], 1);
+        ptx::mbar_init(&bars->tempty[0], PR_EPI_WARPS);
+        ptx::mbar_init(&bars->drain, 1);
+        bars->abort = 0;
+        ptx::fence_barrier_init();
+        ptx::fence_proxy_async_smem();
+        ptx::prefetch_tmap(&tmA);
+        ptx::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc_pair(&bars->tmem_base, TMEM_COLS);
+        ptx::tmem_relinquish_pair();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::cluster_sync();           // both CTAs' barriers exist before any remote use
+    ptx::tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile int* abort = &bars->abort;
+    const uint32_t peer_abort = ptx::mapa_shared(ptx::smem_addr(&bars->abort), rank ^ 1u);
+
+    if (warp == 0) {
+        // ---------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued_phase[8];
+            for (int s = 0; s < 8; ++s) issued_phase[s] = -1;
+            bool ok = true;
+            for (int tile = pair; ok && tile < num_tiles; tile += npairs) {
+                int tm, tn;
+                pair_tile_coords(tile, tiles_m, tiles_n, tm, tn);
+                const int arow = m0 + tm * PR_BM + (int)rank * PR_HALF;
+                const int brow = n0 + tn * PR_BN + (int)rank * PR_HALF;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!ptx::mbar_wait_cluster_bounded(&bars->empty[stage], phase ^ 1u, abort,
+                                                        WAIT_LIMIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    // The even CTA's barrier counts both CTAs' bytes.
+                    if (leader)
+                        ptx::mbar_arrive_expect_tx(&bars->full[stage], 2 * Cfg::STAGE_BYTES);
+                    const uint32_t full0 =
+                        ptx::mapa_shared(ptx::smem_addr(&bars->full[stage]), 0u);
+                    uint8_t* st = tiles + stage * Cfg::STAGE_BYTES;
+#pragma unroll
+                    for (int s = 0; s < SA; ++s)
+                        ptx::tma_load_3d_pair(st + s * A_TILE_BYTES, &tmA, full0, kb * TC_BK,
+                                              arow, s);
+                    ptx::tma_load_3d_pair(st + SA * A_TILE_BYTES, &tmB, full0, kb * TC_BK,
+                                          brow, 0);
+                    issued_phase[stage] = (int)phase;
+                    if (++stage == Cfg::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                raise_abort_pair(bars, peer_abort, status);
+                // Let copies in flight land before this CTA can exit: the
+                // even CTA waits for the phases it expected; both wait a
+                // bounded while for the rest (copies take microseconds).
+                volatile int never = 0;
+                if (leader)
+                    for (int s = 0; s < Cfg::STAGES; ++s)
+                        if (issued_phase[s] >= 0)
+                            ptx::mbar_wait_cluster_bounded(&bars->full[s],
+                                                           (uint32_t)issued_phase[s], &never,
+                                                           WAIT_LIMIT_NS);
+                const uint64_t t0 = ptx::globaltimer_ns();
+                while (ptx::globaltimer_ns() - t0 < 2000000ull) {
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------------------------------------------- MMA issuer
+        if (lane == 0 && leader) {
+            constexpr uint32_t IDESC = ptx::idesc_bf16_f32(PR_BM, PR_BN);
+            int stage = 0;
+            uint32_t phase = 0, tphase = 0;
+            bool ok = true;
+            for (int tile = pair; ok && tile < num_tiles; tile += npairs) {
+                if (!ptx::mbar_wait_cluster_bounded(&bars->tempty[0], tphase ^ 1u, abort,
+                                                    WAIT_LIMIT_NS)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!ptx::mbar_wait_cluster_bounded(&bars->full[stage], phase, abort,
+                                                        WAIT_LIMIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {     // two 32-byte MMA steps
+#pragma unroll
+                        for (int p = SA - 1; p >= 0; --p) {
+                            const uint32_t a_addr = s0 + p * A_TILE_BYTES + ks * 32;
+                            const uint32_t b_addr = s0 + SA * A_TILE_BYTES + ks * 32;
+                            // Issued from the smallest slice: the first MMA
+                            // into each accumulator overwrites it.
+                            const bool first = kb == 0 && ks == 0 && (p == 0 || p == SA - 1);
+                            ptx::mma_f16_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
+                                              ptx::sdesc_kmajor_sw64(a_addr),
+                                              ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                              first ? 0u : 1u);
+                        }
+                    }
+                    ptx::mma_commit_pair_mc(&bars->empty[stage], (uint16_t)3u);
+                    if (++stage == Cfg::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                ptx::mma_commit_pair_mc(&bars->tfull[0], (uint16_t)3u);
+                tphase ^= 1u;
+            }
+            if (!ok) raise_abort_pair(bars, peer_abort, status);
+            // Every MMA issued above completes before either CTA frees TMEM.
+            ptx::mma_commit_pair_mc(&bars->drain, (uint16_t)3u);
+        }
+        if (lane == 0) {
+            volatile int never = 0;
+            ptx::mbar_wait_cluster_bounded(&bars->drain, 0u, &never, WAIT_LIMIT_NS);
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------- epilogue
+        // Warp w reads TMEM lanes 32*(w%4).. (its rows of this CTA's half)
+        // and half h of the 256 columns, 128 values per thread.
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const int row = q * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
+        const uint32_t tempty0 = ptx::mapa_shared(ptx::smem_addr(&bars->tempty[0]), 0u);
+        uint32_t tphase = 0;
+        for (int tile = pair; tile < num_tiles; tile += npairs) {
+            int tm, tn;
+            pair_tile_coords(tile, tiles_m, tiles_n, tm, tn);
+            const bool got = __all_sync(
+                0xffffffffu,
+                ptx::mbar_wait_cluster_bounded(&bars->tfull[0], tphase, abort, WAIT_LIMIT_NS));
+            if (!got) {
+                if (lane == 0) raise_abort_pair(bars, peer_abort, status);
+                break;
+            }
+            ptx::tc_fence_after();
+            float sum[128];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                // hi-slice sum + small-slice sum, one rounding.
+                uint32_t r0[16], r1[16];
+                ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
+                ptx::tmem_ld_16cols(lane_base + (uint32_t)(PR_BN + c * 16), r1);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    sum[c * 16 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+            }
+            // This warp's TMEM lanes are free again before the stores.
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive_cluster(tempty0);
+            tphase ^= 1u;
+            const int64_t m = (int64_t)m0 + (int64_t)tm * PR_BM + (int64_t)rank * PR_HALF + row;
+            const int col0 = n0 + tn * PR_BN + h * 128;
+            if (TOUT && m < M) {
+                // Element (m, col0 + j) of Z^T is Z[col0 + j][m]: a warp's
+                // lanes hold consecutive m, one 128-byte segment per store.
+                float* zc = Z + m;
+#pragma unroll
+                for (int j = 0; j < 128; ++j)
+                    if (col0 + j < N) zc[(int64_t)(col0 + j) * ldz] = sum[j];
+            } else if (m < M) {
+                float* zr = Z + m * ldz + col0;
+                if (vec && col0 + 128 <= N) {
+#pragma unroll
+                    for (int j = 0; j < 128; j += 4)
+                        *reinterpret_cast<float4*>(zr + j) =
+                            make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 128; ++j)
+                        if (col0 + j < N) zr[j] = sum[j];
+                }
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::cluster_sync();           // no remote access to either CTA after this
+    if (warp == 1) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc_pair(tmem, TMEM_COLS);
+    }
+}
+
 // --------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     static std::once_flag once;
@@ -734,6 +1019,95 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
     return AFMM_OK;
 }
 
+// Clusters of two CTAs (one per SM of a pair) that fit at once, for the
+// pair kernel's persistent grid; 0 when the device cannot co-schedule any.
+template <int SA, bool TOUT>
+int pair_clusters(int smem) {
+    static int cached[64];
+    static std::once_flag once;
+    std::call_once(once, [] { std::fill(cached, cached + 64, -1); });
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 0;
+    }
+    int& c = cached[dev];
+    if (c >= 0) return c;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    c = n;
+    return n;
+}
+
+// The two-SM split product over rows [m0, m1) and columns [n0, n1) of the
+// product (Z^T's when TOUT).
+template <int SA, bool TOUT = false>
+afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
+                           cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
+    using Cfg = PairCfg<SA>;
+    const int n = (int)t->n;
+    if (m1 < 0) m1 = n;
+    if (n1 < 0) n1 = n;
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg::SMEM));
+    const int tiles = ((m1 - m0 + PR_BM - 1) / PR_BM) * ((n1 - n0 + PR_BN - 1) / PR_BN);
+    const int cap = pair_clusters<SA, TOUT>(Cfg::SMEM);
+    if (cap < 1) return AFMM_ERR_UNSUPPORTED;
+    const int clusters = tiles < cap ? tiles : cap;
+    const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
+    CUtensorMap ma, mb;
+    std::memcpy(&ma, TOUT ? t->tmap_at : t->tmap_a, sizeof ma);
+    std::memcpy(&mb, TOUT ? t->tmap_bt2 : t->tmap_b2, sizeof mb);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)Cfg::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    main_kernel_begin(st);
+    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT>, ma, mb, Z, ldz, m0, m1,
+                                     n0, n1, n, vec, status));
+    main_kernel_end(st, 2 * clusters);
+    count_launches(1);
+    return AFMM_OK;
+}
+
+// The split product with S = t->slices BF16 slices: the two-SM kernel when
+// the plan chose it (t->pair), else the one-CTA kernel.
+template <bool TOUT>
+afmm_status split_product(const TcPlan* t, float* Z, int64_t ldz, int* status,
+                          cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
+    if (t->pair) {
+        const afmm_status rc =
+            t->slices == 3 ? launch_tc_pair<3, TOUT>(t, Z, ldz, status, st, m0, m1, n0, n1)
+                           : launch_tc_pair<2, TOUT>(t, Z, ldz, status, st, m0, m1, n0, n1);
+        if (rc != AFMM_ERR_UNSUPPORTED) return rc;
+    }
+    return t->slices == 3 ? launch_tc<3, 1, TOUT>(t, Z, ldz, status, st, m0, m1, n0, n1)
+                          : launch_tc<2, 1, TOUT>(t, Z, ldz, status, st, m0, m1, n0, n1);
+}
+
 afmm_status launch_exact2(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
                           int* status, cudaStream_t st) {
     DeviceProps dp;
@@ -856,6 +1230,11 @@ void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8) {
         return;
     }
     const int sa = t->sliced_a ? slices : 1, sb = t->sliced_a && !t->both ? 1 : slices;
+    // The two-SM kernel for the one-sided split form from n = 512 up (a
+    // pair tile is 256 x 256); AFMM_TC_PAIR=0 in the environment keeps the
+    // one-CTA kernel.
+    t->pair = !t->both && d.n >= 512;
+    if (const char* e = std::getenv("AFMM_TC_PAIR")) t->pair = t->pair && std::atoi(e) != 0;
     if (t->both) {
         t->chunk_kb = kRealChunkKb;
         if (const char* e = std::getenv("AFMM_TC_CHUNK_KB")) t->chunk_kb = std::atoi(e);
@@ -883,10 +1262,13 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z, void* s) {
     const int es = t->f8 ? 1 : 2;
     AFMM_TRY(tc_encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM, es));
     AFMM_TRY(tc_encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN, es));
+    // B side with 128-row boxes: each CTA of a pair loads half of a B tile.
+    AFMM_TRY(tc_encode_map(t->tmap_b2, b, t->n, t->n, t->ld_b, sb, PR_HALF, es));
     if (!t->sliced_a && t->slices > 0) {
         // Case B as Z^T = Y^T X^T: the sliced Y^T rows are the A side.
         AFMM_TRY(tc_encode_map(t->tmap_at, b, t->n, t->n, t->ld_b, sb, TC_BM, es));
         AFMM_TRY(tc_encode_map(t->tmap_bt, a, t->n, t->n, t->ld_a, sa, TC_BN, es));
+        AFMM_TRY(tc_encode_map(t->tmap_bt2, a, t->n, t->n, t->ld_a, sa, PR_HALF, es));
     }
     t->maps_ready = true;
     return AFMM_OK;
@@ -919,16 +1301,13 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
             // Rows of Z off 16-byte boundaries: product into the aligned
             // buffer, then one 2-D copy.
             float* zt = static_cast<float*>(t->z);
-            AFMM_TRY((t->slices == 3 ? launch_tc<3, 1>(t, zt, t->ld_z, status, st)
-                                     : launch_tc<2, 1>(t, zt, t->ld_z, status, st)));
+            AFMM_TRY((split_product<false>(t, zt, t->ld_z, status, st)));
             AFMM_CUDA_TRY(cudaMemcpy2DAsync(Zf, d.ldz * sizeof(float), zt,
                                             t->ld_z * sizeof(float), n * sizeof(float), n,
                                             cudaMemcpyDeviceToDevice, st));
             return AFMM_OK;
         }
-        return t->slices == 3
-                   ? launch_tc<3, 1>(t, Zf, d.ldz, status, st)
-                   : launch_tc<2, 1>(t, Zf, d.ldz, status, st);
+        return split_product<false>(t, Zf, d.ldz, status, st);
     }
     // Case B: A = Rep-factors X (rows), B = slices of the real Y transposed.
     AFMM_TRY((tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, A, t->ld_a, 256.f,
@@ -941,9 +1320,7 @@ afmm_status tc_run_split(TcPlan* t, const afmm_desc& d, const void* X,
                                                    0.f, status, st)));
     // Computed as Z^T = Y^T X^T: the slices on the A side, as in Case A, so
     // a stage holds S + 1 tiles of 8 + 16 KiB instead of 1 + S of 8 + 16 x S.
-    return t->slices == 3
-               ? launch_tc<3, 1, true>(t, Zf, d.ldz, status, st)
-               : launch_tc<2, 1, true>(t, Zf, d.ldz, status, st);
+    return split_product<true>(t, Zf, d.ldz, status, st);
 }
 
 afmm_status tc_run_real(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
@@ -1042,12 +1419,9 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
     else
         AFMM_TRY(tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 256.f, status,
                                st, r0, r1, true));
-    if (d.kase == AFMM_CASE_A)
-        return sl == 3 ? launch_tc<3, 1>(t, Zf, d.ldz, status, st, m0, m1)
-                       : launch_tc<2, 1>(t, Zf, d.ldz, status, st, m0, m1);
+    if (d.kase == AFMM_CASE_A) return split_product<false>(t, Zf, d.ldz, status, st, m0, m1);
     // Case B (Z^T = Y^T X^T): rows [r0, r1) of Z are columns of the product.
-    return sl == 3 ? launch_tc<3, 1, true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1)
-                   : launch_tc<2, 1, true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1);
+    return split_product<true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1);
 }
 
 int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb) {

@@ -58,6 +58,21 @@ def operands(case, xd, yd, n, rng):
 @pytest.mark.parametrize("n", [129, 300])
 @pytest.mark.parametrize("form", sorted(FORMS))
 def test_no_write_outside_z_and_workspace(form, n):
+    _guarded_run(form, n)
+
+
+@pytest.mark.parametrize("n", [641, 1283])
+@pytest.mark.parametrize("form", ["tc_bf16x3_A", "tc_bf16x3_B", "tc_bf16x2_A"])
+def test_two_sm_split_kernel_writes_only_z(form, n):
+    """From n = 512 the split form runs on CTA pairs (256 x 256 tiles);
+    ragged sizes leave partial pair tiles at the right and bottom edges."""
+    _guarded_run(form, n)
+
+
+FORMS["tc_bf16x2_A"] = (2, "A", "f32", "i32", "f32", "fp32")
+
+
+def _guarded_run(form, n):
     from paper_1308_2400_gb300 import Plan, make_desc
     variant, case, xd, yd, zd, target = FORMS[form]
     rng = np.random.default_rng(n + len(form))
@@ -94,5 +109,8 @@ def test_no_write_outside_z_and_workspace(form, n):
     if target == "exact":
         assert np.array_equal(Z.astype(np.int64), R)
     else:
-        assert rel_fro(Z, R) <= (FP64_REL_FRO if target == "fp64" else FP32_REL_FRO)
+        tol = FP64_REL_FRO if target == "fp64" else FP32_REL_FRO
+        if variant == 2:
+            tol = 1e-5           # two BF16 slices: short of FP32 by design
+        assert rel_fro(Z, R) <= tol
     p.close()

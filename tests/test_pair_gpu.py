@@ -1,0 +1,64 @@
+"""The two-SM split kernel (tcgen05 cta_group::2, 256 x 256 tiles per CTA
+pair) against the oracle (Sec. 2 loops, FP64).
+
+From n = 512 the split form runs on CTA pairs; these sizes put partial pair
+tiles at the edges (n not a multiple of 256) and single-tile problems.  The
+same inputs through the one-CTA kernel (AFMM_TC_PAIR=0 at plan creation)
+must agree with it within the tensor-core element bound, and the
+host-buffer pipeline, which multiplies row blocks, must too.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import afmm_inputs as W
+from _helpers import FP32_REL_FRO, rel_fro, run_gpu, sample_rows
+from test_parity_gpu import check_fp32, tc_elem_bound
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WORKLOAD = {"A": "caseA_n8192_e4m3", "B": "caseB_n4096_f32"}
+
+
+@pytest.mark.parametrize("n", [512, 515, 777, 1000, 2049])
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_pair_kernel_matches_the_oracle(case, n):
+    inst = W.make(WORKLOAD[case], n=n, seed=n)
+    Z, info = run_gpu(inst, variant=1)
+    assert info["variant"] == 1
+    check_fp32(inst, Z, sample_rows(n, 24), bound_fn=tc_elem_bound)
+
+
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_pair_and_one_cta_kernels_agree(case, monkeypatch):
+    n = 1283
+    inst = W.make(WORKLOAD[case], n=n, seed=3)
+    Zp, _ = run_gpu(inst, variant=1)
+    monkeypatch.setenv("AFMM_TC_PAIR", "0")
+    Z1, _ = run_gpu(inst, variant=1)
+    rows = sample_rows(n, 32)
+    bound = tc_elem_bound(inst, rows)
+    assert np.all(np.abs(Zp[rows].astype(np.float64) - Z1[rows]) <= 2 * bound)
+    check_fp32(inst, Zp, rows, bound_fn=tc_elem_bound)
+
+
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_pair_kernel_host_buffers_pipelined(case):
+    """Host X, Y, Z: the call pipelines copies with row blocks of the
+    product, each block a pair-kernel launch over a range of rows."""
+    from _helpers import desc_for
+    from paper_1308_2400_gb300 import Plan
+    n = 2304
+    inst = W.make(WORKLOAD[case], n=n, seed=8)
+    Xh = np.ascontiguousarray(inst.x_store if inst.x_store is not None else inst.X)
+    Yh = np.ascontiguousarray(inst.y_store if inst.y_store is not None else inst.Y)
+    Zh = np.full((n, n), np.nan, dtype=np.float32)
+    p = Plan(desc_for(inst, variant=1))
+    p(Xh, Yh, Zh)
+    p.sync()
+    p.close()
+    check_fp32(inst, Zh, sample_rows(n, 24), bound_fn=tc_elem_bound)

@@ -744,9 +744,10 @@ def test_batched_graph_replay_with_new_data():
 
 def test_batched_bad_rep_factor_poisons_only_its_instance():
     """A Rep-factor not exact in BF16 (300) on the tensor-core route turns
-    that instance's Z into NaN; the other instance is unaffected."""
-    from paper_1308_2400_gb300 import afmm_mul_batched
-    from paper_1308_2400_gb300.afmm import afmm_batched_sync
+    that instance's Z into NaN and is reported by afmm_batched_sync; the
+    other instance is unaffected."""
+    from paper_1308_2400_gb300 import AfmmError, afmm_mul_batched
+    from paper_1308_2400_gb300.afmm import AFMM_ERR_OVERFLOW_RISK, afmm_batched_sync
     rng = np.random.default_rng(9)
     insts = []
     for t in range(2):
@@ -758,7 +759,9 @@ def test_batched_bad_rep_factor_poisons_only_its_instance():
     insts[0].Y[3, 5] = 300
     descs, Xs, Ys, Zs = _batch(insts, [1, 1])
     afmm_mul_batched(descs, Xs, Ys, Zs)
-    afmm_batched_sync(descs)
+    with pytest.raises(AfmmError) as e:
+        afmm_batched_sync(descs)
+    assert e.value.status == AFMM_ERR_OVERFLOW_RISK
     assert np.all(np.isnan(Zs[0].cpu().numpy()))
     _check_batch(insts[1:], Zs[1:])
 
