@@ -710,8 +710,7 @@ def run_batched(args):
         model = tune.load(tune.DEFAULT_MODEL)
         tune.install(model)
     auto = [tune.instance_desc(t) for t in insts]
-    routes_mlp = [1 if A.afmm_dispatch_variant(d) == A.AFMM_VARIANT_TC_BF16X3 else 0
-                  for d in auto]
+    routes_mlp = [tune.route_index(A.afmm_dispatch_variant(d)) for d in auto]
 
     def forced(routes):
         return [tune.instance_desc(t, tune.VARIANTS[r]) for t, r in zip(insts, routes)]
@@ -734,25 +733,39 @@ def run_batched(args):
         best = [int(v) for v in table.argmin(axis=1)]
         thr = tune.fit_paper_threshold(insts, table)
         A.afmm_set_dispatch_model(None, None, None, None, None)
-        routes_rule = [1 if A.afmm_dispatch_variant(d) == A.AFMM_VARIANT_TC_BF16X3 else 0
-                       for d in auto]
+        routes_rule = [tune.route_index(A.afmm_dispatch_variant(d)) for d in auto]
         if model is not None:
             tune.install(model)
         policies = {"autotune_best": best, "learned": routes_mlp, "rule": routes_rule,
                     "paper_count_rule": tune.paper_count_choice(insts, thr),
-                    "all_tc": [1] * len(insts), "all_simt": [0] * len(insts)}
-        times = {}
-        for name, r in policies.items():
-            reps = max(2, min(args.steps, 10)) if name != "all_simt" else 2
-            times[name] = tune.time_batch(forced(r), Xs, Ys, Zs, reps=reps, warmup=1)
+                    "all_tc": [1] * len(insts), "all_tc_n128": [2] * len(insts),
+                    "all_simt": [0] * len(insts)}
+        # Timed in rounds, each policy once per round in turn, so that a
+        # drift of the clock over the run is shared by all of them.
+        samples = {name: [] for name in policies}
+        rounds = max(2, min(args.steps, 8))
+        for _ in range(rounds):
+            for name, r in policies.items():
+                reps = 3 if name != "all_simt" else 1
+                samples[name].append(tune.time_batch(forced(r), Xs, Ys, Zs, reps=reps,
+                                                     warmup=1))
+        times = {name: statistics.median(v) for name, v in samples.items()}
+        no_mlp = {k: v for k, v in times.items() if k not in ("learned", "autotune_best")}
+        best_no_mlp = min(no_mlp, key=no_mlp.get)
         dispatch = {
             "batch_ms": times,
+            "rounds": rounds,
             "regret_batch": times["learned"] / times["autotune_best"] - 1.0,
             "regret_table": tune.regret(table, routes_mlp),
+            "best_no_mlp_policy": best_no_mlp,
+            "gain_vs_best_no_mlp": times[best_no_mlp] / times["learned"],
             "gain_vs_paper_count_rule": times["paper_count_rule"] / times["learned"],
             "gain_vs_rule": times["rule"] / times["learned"],
             "paper_count_threshold": thr,
-            "autotune_tc_share": float(np.mean(best)),
+            "autotune_route_share": [float(np.mean(np.asarray(best) == v))
+                                     for v in range(len(tune.VARIANTS))],
+            "learned_route_share": [float(np.mean(np.asarray(routes_mlp) == v))
+                                    for v in range(len(tune.VARIANTS))],
         }
     line = {
         "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
@@ -760,13 +773,14 @@ def run_batched(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "batched_512", "count": len(insts),
-                   "sum_2n3": flops, "tc_instances": int(sum(routes_mlp)),
+                   "sum_2n3": flops, "tc_instances": int(sum(1 for r in routes_mlp if r > 0)),
                    "dispatch": "learned" if model else "rule"},
         "roofline": {"bound": "tensor", "unit": "TFLOP/s",
                      "achieved": 3 * flops / (ms * 1e-3) / 1e12,
-                     "peak": peaks.get("bf16_tflops_sustained", 1700.0),
+                     "peak": tensor_peak(peaks, ms * args.steps * 1e-3)[0],
+                     "peak_src": f"{tensor_peak(peaks, ms * args.steps * 1e-3)[1]}, {peak_src}",
                      "frac": 3 * flops / (ms * 1e-3) / 1e12 /
-                             peaks.get("bf16_tflops_sustained", 1700.0),
+                             tensor_peak(peaks, ms * args.steps * 1e-3)[0],
                      "note": "whole step (conversions + grouped products), 3 slices"},
         "dispatch": dispatch,
         "accuracy": {"max_rel_fro_err_sampled": max(errs), "instances": len(errs)},

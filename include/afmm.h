@@ -139,7 +139,12 @@ typedef enum {
      * Algorithms 59, 2012; Ootomo and Yokota, IJHPCA 36, 2022).  FP32
      * target. */
     AFMM_VARIANT_TC_BF16X3X3 = 8,
-    AFMM_VARIANT_COUNT_ = 9
+    /* The split BF16 form of AFMM_VARIANT_TC_BF16X3 with 128 x 128 output
+     * tiles in place of 128 x 256: less padding for sizes just above a
+     * multiple of 128, more staged bytes per flop.  A route of
+     * afmm_mul_batched only (a plan refuses it with AFMM_ERR_UNSUPPORTED). */
+    AFMM_VARIANT_TC_BF16X3_N128 = 9,
+    AFMM_VARIANT_COUNT_ = 10
 } afmm_variant;
 
 /* Flags for afmm_desc.flags. */
@@ -281,13 +286,15 @@ afmm_status afmm_selftest_bounded_wait(uint64_t limit_ns, void* stream);
 
 /* Batched product: `count` independent instances (Sec. 2 problems of
  * different n, Case A or B), each described by descs[t], FP32 target
- * (z_dtype F32).  Each instance runs either the tcgen05 split-BF16 form or
- * the CUDA-core zero-skip form: descs[t].variant = AFMM_VARIANT_TC_BF16X3 or
- * AFMM_VARIANT_SIMT_F32 forces the route, AFMM_VARIANT_AUTO asks the
- * installed dispatch model (afmm_set_dispatch_model) or, without one,
- * applies the built-in rule (tensor cores unless the Base density hint is
- * below 0.02 or n < 32).  All tensor-core instances run in one persistent grouped
- * launch, all CUDA-core instances in another; the first call with a given
+ * (z_dtype F32).  Each instance takes one of three routes: the tcgen05
+ * split-BF16 form with 128 x 256 output tiles (AFMM_VARIANT_TC_BF16X3) or
+ * with 128 x 128 tiles (AFMM_VARIANT_TC_BF16X3_N128), or the CUDA-core
+ * zero-skip form (AFMM_VARIANT_SIMT_F32).  descs[t].variant forces the
+ * route; AFMM_VARIANT_AUTO asks the installed dispatch model
+ * (afmm_set_dispatch_model) or, without one, applies the built-in rule
+ * (128 x 256 tensor-core tiles unless the Base density hint is below 0.02
+ * or n < 32).  All tensor-core instances, of both tile widths, run in one
+ * persistent grouped launch, all CUDA-core instances in another; the first call with a given
  * descriptor array builds the plan (workspace, TMA descriptors, tile lists)
  * and a CUDA graph of the launches, later calls with an identical array
  * only refresh the pointer table and launch the graph (a few plans are
@@ -331,14 +338,16 @@ afmm_status afmm_error_norm(const void* Z, int32_t z_dtype, int64_t ldz,
  * row-major: [W1 (F x H), b1 (H), W2 (H x H), b2 (H), W3 (H x V), b3 (V)];
  * H1 = relu(x W1 + b1), H2 = relu(H1 W2 + b2), p = H2 W3 + b3.
  * ------------------------------------------------------------------ */
-#define AFMM_DISPATCH_FEATURES 8
+#define AFMM_DISPATCH_FEATURES 10
 typedef struct {
     int32_t features, hidden, outputs, reserved_;
 } afmm_mlp_shape;
 
 /* Features of one instance, from its descriptor (hints used as given):
  * log2 n, Base density, Rep density, log2(1 + mu'), case (0 A, 1 B),
- * log2(1 + mu' d1 d2 n^3), log2 n^3, (1 - Base density)^8.  out holds
+ * log2(1 + mu' d1 d2 n^3), log2 n^3, (1 - Base density)^8, and the padded
+ * area of 256-wide and of 128-wide output tiles relative to n
+ * (ceil(n / 256) * 256 / n, ceil(n / 128) * 128 / n).  out holds
  * AFMM_DISPATCH_FEATURES floats (host memory). */
 afmm_status afmm_dispatch_features(const afmm_desc* desc, float* out);
 

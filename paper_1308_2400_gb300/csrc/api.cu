@@ -953,7 +953,9 @@ afmm_status afmm_set_dispatch_model(const afmm_mlp_shape* s, const float* params
 
 int32_t afmm_dispatch_variant(const afmm_desc* d) {
     if (!d) return -1;
-    return dispatch_route(*d) == 1 ? AFMM_VARIANT_TC_BF16X3 : AFMM_VARIANT_SIMT_F32;
+    const int r = dispatch_route(*d);
+    return r == 2 ? AFMM_VARIANT_TC_BF16X3_N128
+                  : r == 1 ? AFMM_VARIANT_TC_BF16X3 : AFMM_VARIANT_SIMT_F32;
 }
 
 afmm_status afmm_batched_sync(int count, const afmm_desc* descs, void* stream) {

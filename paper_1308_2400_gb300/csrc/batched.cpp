@@ -96,7 +96,7 @@ afmm_status check_batch_desc(const afmm_desc& d) {
     if ((d.ldx && d.ldx < d.n) || (d.ldy && d.ldy < d.n) || (d.ldz && d.ldz < d.n))
         return AFMM_ERR_INVALID_ARG;
     if (d.variant != AFMM_VARIANT_AUTO && d.variant != AFMM_VARIANT_SIMT_F32 &&
-        d.variant != AFMM_VARIANT_TC_BF16X3)
+        d.variant != AFMM_VARIANT_TC_BF16X3 && d.variant != AFMM_VARIANT_TC_BF16X3_N128)
         return AFMM_ERR_UNSUPPORTED;
     const int rep = d.kase == AFMM_CASE_A ? d.y_dtype : d.x_dtype;
     const int real = d.kase == AFMM_CASE_A ? d.x_dtype : d.y_dtype;
@@ -115,13 +115,15 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
     for (int i = 0; i < count; ++i) {
         AFMM_TRY(check_batch_desc(descs[i]));
         int r = dispatch_route(descs[i]);
-        if (r == 1 && !tc_ok) {
-            if (descs[i].variant == AFMM_VARIANT_TC_BF16X3) return AFMM_ERR_UNSUPPORTED;
+        if (r >= 1 && !tc_ok) {
+            if (descs[i].variant == AFMM_VARIANT_TC_BF16X3 ||
+                descs[i].variant == AFMM_VARIANT_TC_BF16X3_N128)
+                return AFMM_ERR_UNSUPPORTED;
             r = 0;
         }
         if (descs[i].n == 0) r = -1;     // nothing to do
         b->route.push_back(r);
-        if (r == 1) b->tc_ids.push_back(i);
+        if (r >= 1) b->tc_ids.push_back(i);
         else if (r == 0) b->simt_ids.push_back(i);
     }
     // ---- sizes
@@ -167,10 +169,13 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
     }
     // ---- tensor-core tiles, longest first onto the least loaded CTA
     std::vector<TileCost> tl;
+    // (a tile's cost: its K steps times its width in 128 columns, plus a
+    // fixed share for the epilogue and the hand-over)
     for (int j = 0; j < ntc; ++j) {
         const int64_t n = descs[b->tc_ids[j]].n;
-        const int tmn = (int)((n + GB_BM - 1) / GB_BM), tnn = (int)((n + GB_BN - 1) / GB_BN);
-        const int cost = (int)((n + GB_BK - 1) / GB_BK) + 4;
+        const int bn = b->route[b->tc_ids[j]] == 2 ? 128 : GB_BN;
+        const int tmn = (int)((n + GB_BM - 1) / GB_BM), tnn = (int)((n + bn - 1) / bn);
+        const int cost = (int)((n + GB_BK - 1) / GB_BK) * (bn / 128) + 4;
         for (int tm = 0; tm < tmn; ++tm)
             for (int tn = 0; tn < tnn; ++tn) tl.push_back({j, tm, tn, cost});
     }
@@ -251,6 +256,7 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
             g.ldy = d.ldy ? d.ldy : n;
             g.ldz = d.ldz ? d.ldz : n;
             g.flag = j;
+            g.bn = b->route[b->tc_ids[j]] == 2 ? 128 : GB_BN;
             g.A = ops + o;
             o += ((size_t)sa * n * ldk * 2 + 255) / 256 * 256;
             g.B = ops + o;
@@ -275,7 +281,7 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
         void* a_side = g.kind == 0 ? g.A : g.B;
         void* b_side = g.kind == 0 ? g.B : g.A;
         AFMM_TRY(tc_encode_map(maps + 2 * j * 128, a_side, g.n, g.n, g.ldk, 3, GB_BM));
-        AFMM_TRY(tc_encode_map(maps + (2 * j + 1) * 128, b_side, g.n, g.n, g.ldk, 1, GB_BN));
+        AFMM_TRY(tc_encode_map(maps + (2 * j + 1) * 128, b_side, g.n, g.n, g.ldk, 1, g.bn));
     }
     auto up = [](void* dst, const void* src, size_t bytes) -> afmm_status {
         if (bytes) AFMM_CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
@@ -360,6 +366,16 @@ afmm_status capture(BatchState* b) {
 }  // namespace
 
 // ---------------------------------------------------------- dispatch model
+// Route of a forced batched variant (-1: not a batched route).
+static int route_of_variant(int v) {
+    switch (v) {
+        case AFMM_VARIANT_SIMT_F32: return 0;
+        case AFMM_VARIANT_TC_BF16X3: return 1;
+        case AFMM_VARIANT_TC_BF16X3_N128: return 2;
+        default: return -1;
+    }
+}
+
 struct DispatchModel {
     afmm_mlp_shape shape{};
     std::vector<float> params, mean, scale;
@@ -382,6 +398,8 @@ static void features_of(const afmm_desc& d, float* f) {
     f[5] = (float)std::log2(1.0 + mu * d1 * d2 * n * n * n);
     f[6] = (float)(3.0 * std::log2(n));
     f[7] = (float)std::pow(1.0 - dbase, 8.0);
+    f[8] = (float)(std::ceil(n / 256.0) * 256.0 / n);
+    f[9] = (float)(std::ceil(n / 128.0) * 128.0 / n);
 }
 
 // Variant with the smallest predicted time, or -1 without a model.
@@ -450,17 +468,17 @@ afmm_status set_dispatch_model(const afmm_mlp_shape* s, const float* params,
     for (int i = 0; i < s->features; ++i)
         if (!(m->scale[i] > 0.f)) return AFMM_ERR_INVALID_ARG;
     for (int o = 0; o < s->outputs; ++o) {
-        if (variants[o] != AFMM_VARIANT_SIMT_F32 && variants[o] != AFMM_VARIANT_TC_BF16X3)
-            return AFMM_ERR_INVALID_ARG;
-        m->variant_of_output.push_back(variants[o] == AFMM_VARIANT_TC_BF16X3 ? 1 : 0);
+        const int r = route_of_variant(variants[o]);
+        if (r < 0) return AFMM_ERR_INVALID_ARG;
+        m->variant_of_output.push_back(r);
     }
     g_model = std::move(m);
     return AFMM_OK;
 }
 
 int dispatch_route(const afmm_desc& d) {
-    if (d.variant == AFMM_VARIANT_SIMT_F32) return 0;
-    if (d.variant == AFMM_VARIANT_TC_BF16X3) return 1;
+    const int forced = route_of_variant(d.variant);
+    if (forced >= 0) return forced;
     const int r = model_route(d);
     return r >= 0 ? r : batch_rule_route(d);
 }

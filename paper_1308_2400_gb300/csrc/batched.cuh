@@ -23,6 +23,8 @@ struct GInst {
     int kind;              // 0: X real, sliced on A; 1: Y real, sliced on B
     int x_dtype, y_dtype;
     int flag;              // index into the per-instance error flags
+    int bn;                // output tile width: 256, or 128 (route 2)
+    int pad_;
 };
 
 // Device record of one operand widened to FP32 for the CUDA-core form
@@ -51,7 +53,9 @@ afmm_status launch_batch_tc(const GInst* inst, const void* maps, const int* cta_
 afmm_status launch_batch_widen(const WJob* jobs, const int* prefix, int njobs,
                                int rows_total, int* status, cudaStream_t st);
 
-// Route of an instance under the built-in rule: 1 tensor cores, 0 CUDA cores.
+// Routes of a batched instance: 0 CUDA cores, 1 tensor cores with 128 x 256
+// tiles, 2 tensor cores with 128 x 128 tiles.
+// Route of an instance under the built-in rule (0 or 1).
 int batch_rule_route(const afmm_desc& d);
 // Enqueue `count` independent products on `stream`; `kernels_out` receives
 // the number of kernels one call launches.
@@ -66,6 +70,6 @@ afmm_status dispatch_features(const afmm_desc& d, float* out);
 afmm_status set_dispatch_model(const afmm_mlp_shape* s, const float* params,
                                const float* mean, const float* scale,
                                const int32_t* variants);
-int dispatch_route(const afmm_desc& d);   // 1 tensor cores, 0 CUDA cores
+int dispatch_route(const afmm_desc& d);   // route 0, 1 or 2 (see above)
 
 }  // namespace afmm

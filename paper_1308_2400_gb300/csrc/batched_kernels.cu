@@ -219,11 +219,13 @@ g_widen_kernel(const WJob* __restrict__ jobs, const int* __restrict__ prefix, in
 
 // ----------------------------------------------------------- grouped TC
 // Persistent: CTA b runs tiles[cta_off[b] .. cta_off[b+1]) in order; a tile
-// is (instance, tm, tn).  Roles as in the single-product kernel: warp 0 TMA,
-// warp 1 TMEM + MMA, warps 2..9 epilogue; two accumulators per tile (hi
-// slice | smaller slices).  Stage layout: the three A slices (8 KiB each)
-// then the B tile (16 KiB); Case B tiles are tiles of Z^T = Y^T X^T and are
-// stored transposed.
+// is (instance, tm, tn), 128 x bn with the instance's tile width bn: 256, or
+// 128 for the narrow-tile route (128 x 128 x 16 MMAs, a 128-row B tile,
+// only the h = 0 epilogue warps storing).  Roles as in the single-product
+// kernel: warp 0 TMA, warp 1 TMEM + MMA, warps 2..9 epilogue; two
+// accumulators per tile (hi slice | smaller slices).  Stage layout: the
+// three A slices (8 KiB each) then the B tile (bn x 64 bytes); Case B tiles
+// are tiles of Z^T = Y^T X^T and are stored transposed.
 __global__ void __launch_bounds__(GB_THREADS, 1)
 g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps,
             const int* __restrict__ cta_off, const int4* __restrict__ tiles,
@@ -270,8 +272,9 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
                 const GInst& g = inst[tl.x];
                 const CUtensorMap* ma = &maps[2 * tl.x];
                 const CUtensorMap* mb = &maps[2 * tl.x + 1];
-                constexpr int sa = 3, sb = 1;
-                constexpr uint32_t bytes = sa * GB_A_TILE + sb * GB_B_TILE;
+                constexpr int sa = 3;
+                // The B tile is bn rows of 64 bytes (bn = 256 or 128).
+                const uint32_t bytes = sa * GB_A_TILE + (uint32_t)g.bn * GB_BK * 2;
                 const int nkb = (int)((g.n + GB_BK - 1) / GB_BK);
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!ptx::mbar_wait_bounded(&bars->empty[stage], phase ^ 1u, abort,
@@ -284,9 +287,8 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
                     for (int s = 0; s < sa; ++s)
                         ptx::tma_load_3d(st + s * GB_A_TILE, ma, &bars->full[stage],
                                          kb * GB_BK, tl.y * GB_BM, s);
-                    for (int s = 0; s < sb; ++s)
-                        ptx::tma_load_3d(st + sa * GB_A_TILE + s * GB_B_TILE, mb,
-                                         &bars->full[stage], kb * GB_BK, tl.z * GB_BN, s);
+                    ptx::tma_load_3d(st + sa * GB_A_TILE, mb, &bars->full[stage], kb * GB_BK,
+                                     tl.z * g.bn, 0);
                     issued[stage] = (int)phase;
                     if (++stage == GB_STAGES) {
                         stage = 0;
@@ -307,13 +309,13 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t IDESC = ptx::idesc_bf16_f32(GB_BM, GB_BN);
             int stage = 0;
             uint32_t phase = 0, tphase = 0;
             bool ok = true;
             for (int t = t0; ok && t < t1; ++t) {
                 const int4 tl = tiles[t];
                 const GInst& g = inst[tl.x];
+                const uint32_t IDESC = ptx::idesc_bf16_f32(GB_BM, g.bn);
                 constexpr int sa = 3;
                 const int nkb = (int)((g.n + GB_BK - 1) / GB_BK);
                 if (!ptx::mbar_wait_bounded(&bars->tempty, tphase ^ 1u, abort, GB_WAIT_NS)) {
@@ -379,20 +381,26 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
                 break;
             }
             ptx::tc_fence_after();
+            // A 128-wide tile has columns for the h = 0 warps only; the
+            // others still hand the accumulator back.
+            const bool live = h * 128 < g.bn;
             float sum[128];
+            if (live) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                uint32_t r0[32], r1[32];
-                ptx::tmem_ld_32cols(lane_base + (uint32_t)(c * 32), r0);
-                ptx::tmem_ld_32cols(lane_base + (uint32_t)(GB_BN + c * 32), r1);
-                ptx::tmem_ld_wait();
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t r0[32], r1[32];
+                    ptx::tmem_ld_32cols(lane_base + (uint32_t)(c * 32), r0);
+                    ptx::tmem_ld_32cols(lane_base + (uint32_t)(GB_BN + c * 32), r1);
+                    ptx::tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    sum[c * 32 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    for (int j = 0; j < 32; ++j)
+                        sum[c * 32 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                }
             }
             ptx::tc_fence_before();
             ptx::mbar_arrive(&bars->tempty);
             tphase ^= 1u;
+            if (!live) continue;
             // Coalesced stores: each 32 x 32 block goes through this warp's
             // shared-memory tile (thread = row on the way in, thread =
             // column on the way out), one 128-byte row segment per store.
@@ -404,7 +412,7 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
                 // lanes hold consecutive m, so stores are 128-byte row
                 // segments without the shared-memory turn.
                 const int64_t m = mbase + lane;
-                const int64_t n0 = (int64_t)tl.z * GB_BN + h * 128;
+                const int64_t n0 = (int64_t)tl.z * g.bn + h * 128;
                 if (m < g.n) {
                     float* zc = g.Z + m;
 #pragma unroll
@@ -419,7 +427,7 @@ g_tc_kernel(const GInst* __restrict__ inst, const CUtensorMap* __restrict__ maps
 #pragma unroll
                 for (int j = 0; j < 32; ++j) sm[lane * 33 + j] = sum[c * 32 + j];
                 __syncwarp();
-                const int64_t col = (int64_t)tl.z * GB_BN + h * 128 + c * 32 + lane;
+                const int64_t col = (int64_t)tl.z * g.bn + h * 128 + c * 32 + lane;
                 if (col < g.n) {
                     for (int rr = 0; rr < 32; ++rr) {
                         const int64_t m = mbase + rr;

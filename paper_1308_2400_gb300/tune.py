@@ -26,7 +26,11 @@ import numpy as np
 
 from . import afmm as A
 
-VARIANTS = (A.AFMM_VARIANT_SIMT_F32, A.AFMM_VARIANT_TC_BF16X3)
+# The batched routes the tuner times and the network chooses among: the
+# CUDA-core zero-skip form, and the split BF16 tensor-core form with 128 x 256
+# or with 128 x 128 output tiles.
+VARIANTS = (A.AFMM_VARIANT_SIMT_F32, A.AFMM_VARIANT_TC_BF16X3,
+            A.AFMM_VARIANT_TC_BF16X3_N128)
 HIDDEN = 32
 DEFAULT_MODEL = os.path.join(os.path.dirname(os.path.abspath(__file__)),
                              "dispatch_mlp.json")
@@ -184,6 +188,11 @@ def regret(table_ms: np.ndarray, choice: Sequence[int]) -> float:
     return float(picked / table_ms.min(axis=1).sum() - 1.0)
 
 
+def route_index(variant: int) -> int:
+    """Index into VARIANTS of a batched variant code."""
+    return VARIANTS.index(int(variant))
+
+
 def paper_count_choice(insts, threshold: float) -> List[int]:
     """The method without the network: the paper's addition count
     mu' d1 d2 n^3 (Sec. 2.2) against one fitted threshold -- below it the
@@ -233,9 +242,11 @@ def main():
                           "seed": args.seed}
     with open(args.out, "w") as f:
         json.dump(model, f)
+    best = table.argmin(axis=1)
     print(json.dumps({"regret_train": model["train_regret"],
                       "loss": model["loss_history"][-1],
-                      "tc_share_best": float((table.argmin(axis=1) == 1).mean()),
+                      "best_route_share": [float((best == v).mean())
+                                           for v in range(len(VARIANTS))],
                       "seconds": model["train_seconds"]}))
 
 

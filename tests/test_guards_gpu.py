@@ -62,10 +62,12 @@ def test_no_write_outside_z_and_workspace(form, n):
 
 
 @pytest.mark.parametrize("n", [641, 1283])
-@pytest.mark.parametrize("form", ["tc_bf16x3_A", "tc_bf16x3_B", "tc_bf16x2_A"])
-def test_two_sm_split_kernel_writes_only_z(form, n):
-    """From n = 512 the split form runs on CTA pairs (256 x 256 tiles);
-    ragged sizes leave partial pair tiles at the right and bottom edges."""
+@pytest.mark.parametrize("form", ["tc_bf16x3_A", "tc_bf16x3_B", "tc_bf16x2_A",
+                                  "tc_exact_A", "tc_exact_B"])
+def test_two_sm_kernels_write_only_z(form, n):
+    """From n = 512 the split and exact forms run on CTA pairs (256 x 256
+    tiles); ragged sizes leave partial pair tiles at the right and bottom
+    edges."""
     _guarded_run(form, n)
 
 

@@ -128,6 +128,30 @@ def test_host_dispatch_uses_the_installed_model():
     assert afmm_dispatch_variant(d) == 0
 
 
+def test_dispatch_features_and_narrow_tile_route():
+    """The two tile-padding features, and a three-output model whose third
+    output (the 128 x 128 tensor-core tiles) is the lowest."""
+    from paper_1308_2400_gb300.afmm import (AFMM_DISPATCH_FEATURES,
+                                            AFMM_VARIANT_TC_BF16X3_N128,
+                                            afmm_dispatch_features,
+                                            afmm_dispatch_variant,
+                                            afmm_set_dispatch_model, make_desc,
+                                            mlp_shape)
+    assert AFMM_DISPATCH_FEATURES == 10
+    d = make_desc(300, "B", "u8", "f32", "f32", "fp32", d1=0.5, d2=0.5, mu_prime=2.0)
+    f = afmm_dispatch_features(d)
+    assert abs(f[8] - 512 / 300) < 1e-6 and abs(f[9] - 384 / 300) < 1e-6
+    F, H, V = 10, 4, 3
+    p = np.zeros(M.param_count(F, H, V), np.float32)
+    p[-3:] = [5.0, 4.0, -5.0]
+    afmm_set_dispatch_model(mlp_shape(F, H, V), p, np.zeros(F), np.ones(F),
+                            [0, 1, AFMM_VARIANT_TC_BF16X3_N128])
+    try:
+        assert afmm_dispatch_variant(d) == AFMM_VARIANT_TC_BF16X3_N128
+    finally:
+        afmm_set_dispatch_model(None, None, None, None, None)
+
+
 def test_autotuner_copies_fill_the_grouped_launch():
     """The in-batch cost of an instance is timed on copies of it that give
     the grouped launch about four waves of 128 x 256 tiles on 152 SMs."""

@@ -62,3 +62,32 @@ def test_pair_kernel_host_buffers_pipelined(case):
     p.sync()
     p.close()
     check_fp32(inst, Zh, sample_rows(n, 24), bound_fn=tc_elem_bound)
+
+
+@pytest.mark.parametrize("n", [512, 777, 1283])
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_exact_pair_kernel_is_bit_exact(case, n):
+    """The exact form on CTA pairs: int8 Base values at the extremes and u8
+    Rep-factors up to 255 make K chunks of 16 k-blocks, so a tile takes
+    several chunks through the two TMEM buffers; the result must equal the
+    oracle's integers."""
+    from _helpers import oracle_rows
+    rng = np.random.default_rng(n)
+    base = rng.choice(np.array([-127, -126, 0, 1, 126, 127], dtype=np.int8), size=(n, n))
+    rep = rng.integers(0, 256, size=(n, n)).astype(np.uint8)
+    rep[rng.random((n, n)) < 0.3] = 0
+    X, Y = (base, rep) if case == "A" else (rep, base)
+    inst = W.Instance(case, X, Y, x_dtype="i8" if case == "A" else "u8",
+                      y_dtype="u8" if case == "A" else "i8", z_dtype="i32", target="exact")
+    from _helpers import torch_of
+    from paper_1308_2400_gb300 import Plan, make_desc
+    Z = torch.full((n, n), -7, dtype=torch.int32, device="cuda")
+    p = Plan(make_desc(n, case, inst.x_dtype, inst.y_dtype, "i32", "exact", variant=5,
+                       rep_max=255.0, base_max=127.0))
+    assert p.info["k_split"] > 1 or n <= 512
+    p(torch_of(X), torch_of(Y), Z)
+    p.sync()
+    p.close()
+    rows = sample_rows(n, 40)
+    R = oracle_rows(inst, rows)
+    assert np.array_equal(Z.cpu().numpy()[rows].astype(np.int64), R)

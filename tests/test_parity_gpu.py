@@ -702,19 +702,23 @@ def _check_batch(insts, Zs, descs=None, rows_per_instance=None):
         assert np.all(np.isfinite(Zn)), inst.name
         assert rel_fro(Zn, R) <= FP32_REL_FRO, inst.name
         if descs is not None:
-            tc = A.afmm_dispatch_variant(descs[t]) == A.AFMM_VARIANT_TC_BF16X3
+            tc = A.afmm_dispatch_variant(descs[t]) in (A.AFMM_VARIANT_TC_BF16X3,
+                                                       A.AFMM_VARIANT_TC_BF16X3_N128)
             bound = (tc_elem_bound if tc else simt_f32_elem_bound)(inst, rows)
             bad = np.abs(Zn.astype(np.float64) - R) > bound
             assert not bad.any(), (inst.name, "tc" if tc else "simt", int(bad.sum()))
 
 
-@pytest.mark.parametrize("route", ["auto", "tc", "simt", "mixed"])
+@pytest.mark.parametrize("route", ["auto", "tc", "tc128", "simt", "mixed"])
 def test_batched_grouped_routes(route):
+    """Every route of the batched call, alone and mixed in one batch: the
+    CUDA-core form (variant 0), tensor cores with 128 x 256 tiles (1) and
+    with 128 x 128 tiles (9), both tile widths sharing one grouped launch."""
     from paper_1308_2400_gb300 import afmm_mul_batched
     from paper_1308_2400_gb300.afmm import afmm_batched_sync
     insts = W.batched_mix(count=14, seed=5, n_min=16, n_max=400)
-    routes = {"auto": None, "tc": [1] * 14, "simt": [0] * 14,
-              "mixed": [t % 2 for t in range(14)]}[route]
+    routes = {"auto": None, "tc": [1] * 14, "tc128": [9] * 14, "simt": [0] * 14,
+              "mixed": [(0, 1, 9)[t % 3] for t in range(14)]}[route]
     descs, Xs, Ys, Zs = _batch(insts, routes)
     afmm_mul_batched(descs, Xs, Ys, Zs)
     afmm_batched_sync(descs)
