@@ -10,13 +10,17 @@ Metric: effective TFLOP/s = 2 n^3 / time per product (whole job: summed
 over ranks; each rank computes its own independent product, no collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl afmm|reference]
-                  [--workload W] [--n N] [--variant V] [--quick]
+                  [--workload W] [--n N] [--variant V] [--quick] [--shard rows]
 
 Beside the main form the line reports, on the same data, the plain FP32
 CUDA-core form (plain_fp32), two BF16 slices (two_slices), the FP8 form
 (fp8_slices), the split done inside the product kernel (fused_split) and a
 product of two real matrices, X times itself (real_x_real); --quick leaves
 them out.  --variant 8 makes that real x real product the main one.
+
+--shard rows splits one product by row blocks over the ranks (Y broadcast
+over NCCL each step; "scaling": "strong"); by default every rank computes
+its own product.
 
 The reference arm (--impl reference) times the CPU oracle (repeated
 addition in FP64, Sec. 2) on the host cores on a bounded row sample of the
@@ -234,6 +238,22 @@ def shard(count, rank, ws):
     base, extra = divmod(count, ws)
     lo = rank * base + min(rank, extra)
     return range(lo, lo + base + (1 if rank < extra else 0))
+
+
+def row_blocks(n, ws, unit=256):
+    """Row blocks [r0, r1) of one n x n product for `ws` ranks: whole
+    multiples of `unit` rows (the two-SM tile height) except the last
+    block's end, as even as those units allow, covering [0, n) in rank
+    order.  Row I of Z needs row I of X and all of Y (Sec. 2.1), so each
+    rank multiplies its block of X by the whole Y."""
+    units = -(-n // unit) if n > 0 else 0
+    out = []
+    for r in range(ws):
+        lo = shard(units, r, ws)
+        r0 = min(n, lo.start * unit)
+        r1 = min(n, lo.stop * unit)
+        out.append((r0, r1))
+    return out
 
 
 def whole_job_value(units_per_rank, flops_per_unit, max_ms):
@@ -688,6 +708,89 @@ def run_afmm(args):
     return 0
 
 
+def run_shard_rows(args):
+    """One product split by row blocks over the ranks (Sec. 2.1: row I of Z
+    needs row I of X and all of Y).  Rank r holds rows row_blocks(n, N)[r]
+    of X and Z; each step rank 0 broadcasts Y over NCCL and every rank
+    multiplies its rows through afmm_mul_rows.  value = 2 n^3 over the
+    slowest rank's step ("strong": one product whatever N)."""
+    import numpy as np
+    import torch
+    from paper_1308_2400_gb300 import Plan, make_desc
+    from paper_1308_2400_gb300.afmm import VARIANT_NAMES, afmm_mul_rows
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    inst = make_instance(args.workload, args.n)
+    n = inst.n
+    r0, r1 = row_blocks(n, ws)[rank]
+    Xs = inst.x_store if inst.x_store is not None else inst.X
+    Ys = inst.y_store if inst.y_store is not None else inst.Y
+    Xd = torch.from_numpy(np.ascontiguousarray(Xs[r0:r1])).cuda()
+    Yd = torch.from_numpy(np.ascontiguousarray(Ys)).cuda()
+    if rank != 0:
+        Yd.zero_()                     # filled by the broadcast of each step
+    zt = {"f32": torch.float32, "f64": torch.float64, "i32": torch.int32}[inst.z_dtype]
+    Zd = torch.empty((max(r1 - r0, 1), n), dtype=zt, device="cuda")
+    h = input_hints(inst)
+    plan = Plan(make_desc(n, inst.case, inst.x_dtype, inst.y_dtype, inst.z_dtype,
+                          inst.target, variant=args.variant, d1=h["d1"], d2=h["d2"],
+                          mu_prime=h["mu_prime"]))
+    vname = VARIANT_NAMES.get(plan.info["variant"], "?")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        if ws > 1:
+            dist.broadcast(Yd, src=0)
+        afmm_mul_rows(plan, r0, r1, Xd, Yd, Zd, stream)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync(stream)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev) if rank == 0 else None
+    if clk:
+        clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.stop() if clk else None
+    plan.sync(stream)
+    ms = max_over_ranks(ws, e0.elapsed_time(e1) / args.steps)
+    value = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+    acc = None
+    if rank == 0 and not args.no_cpu_baseline and r1 > r0:
+        rows = np.arange(r0, r1, max(1, (r1 - r0) // 8))
+        R = oracle_product_rows(inst, rows)
+        Zg = Zd.cpu().numpy()[rows - r0].astype(np.float64)
+        acc = {"rel_fro_err_vs_oracle": float(np.linalg.norm(Zg - R) / np.linalg.norm(R)),
+               "rows_checked": int(rows.size)}
+    if rank == 0:
+        cfg = workload_config(args.workload, inst, ws)
+        cfg["parallelism"] = f"row blocks x{ws} (Y broadcast each step)"
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic", "config": cfg, "variant": vname,
+            "shard": "rows", "rows_per_rank": [b - a for a, b in row_blocks(n, ws)],
+            "accuracy": acc, "clocks": clocks}), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_batched(args):
     """The uneven batched workload: 512 independent instances in one
     afmm_mul_batched call per step (grouped launches in a CUDA graph), the
@@ -881,6 +984,8 @@ def main():
                     help="skip the plain-FP32 and end-to-end legs")
     ap.add_argument("--count", type=int, default=512,
                     help="instances of the batched workload")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "rows"],
+                    help="rows: split one product by row blocks over the ranks")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -888,6 +993,8 @@ def main():
         return run_batched(args)
     if args.workload == "table1_sweep":
         return run_table1(args)
+    if args.shard == "rows":
+        return run_shard_rows(args)
     return run_afmm(args)
 
 

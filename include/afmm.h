@@ -251,6 +251,19 @@ afmm_status afmm_mul_caseB(afmm_plan plan, const void* X, const void* Y,
 afmm_status afmm_mul_real(afmm_plan plan, const void* X, const void* Y, void* Z,
                           void* stream);
 
+/* Rows [r0, r1) of Z = X * Y from rows [r0, r1) of X and all of Y (Sec.
+ * 2.1: row I of Z is final once the K loop of row I is done, and it needs
+ * row I of X only), for splitting one product into row blocks, e.g. one
+ * block per GPU with Y copied to each.  Xrows points at row r0 of X (the
+ * plan's ldx), Zrows at row r0 of Z (ldz); both hold r1 - r0 rows; Y is the
+ * whole n x n factor.  Device pointers only (AFMM_ERR_INVALID_ARG for host
+ * memory).  Case A or B plans running AFMM_VARIANT_TC_BF16X3, _TC_BF16X2 or
+ * _TC_FP8X4 (others: AFMM_ERR_UNSUPPORTED); 0 <= r0 <= r1 <= n.  Each row
+ * block equals the same rows of a whole-product call bit for bit.
+ * Rep-factors are checked as in afmm_mul_caseA; asynchronous on `stream`. */
+afmm_status afmm_mul_rows(afmm_plan plan, int64_t r0, int64_t r1, const void* Xrows,
+                          const void* Y, void* Zrows, void* stream);
+
 /* Wait for the plan's work on `stream` and return the first error a kernel
  * recorded since the previous sync (clearing it), else AFMM_OK. */
 afmm_status afmm_plan_sync(afmm_plan plan, void* stream);

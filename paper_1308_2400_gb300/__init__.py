@@ -6,7 +6,7 @@ The compute path is ``libafmm.so`` (hand-written CUDA behind the C ABI in
 from . import afmm  # noqa: F401
 from .afmm import (AfmmError, Plan, afmm_batched_sync, afmm_error_norm,  # noqa: F401
                    afmm_error_norm_workspace_size, afmm_get_info,
-                   afmm_mul_batched, afmm_mul_caseA, afmm_mul_real,
+                   afmm_mul_batched, afmm_mul_caseA, afmm_mul_real, afmm_mul_rows,
                    afmm_plan_counters, afmm_plan_enable_kernel_timing, afmm_mul_caseB,
                    afmm_plan_create, afmm_plan_destroy, afmm_plan_set_workspace,
                    afmm_plan_sync, afmm_plan_workspace_size,

@@ -139,6 +139,7 @@ def _lib():
             "afmm_mul_caseA": ([_VP, _VP, _VP, _VP, _VP], st),
             "afmm_mul_caseB": ([_VP, _VP, _VP, _VP, _VP], st),
             "afmm_mul_real": ([_VP, _VP, _VP, _VP, _VP], st),
+            "afmm_mul_rows": ([_VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP, _VP], st),
             "afmm_plan_sync": ([_VP, _VP], st),
             "afmm_get_info": ([_VP, ctypes.POINTER(afmm_info)], st),
             "afmm_plan_enable_kernel_timing": ([_VP, ctypes.c_int], st),
@@ -321,6 +322,13 @@ def afmm_mul_noalloc(desc: afmm_desc, X, Y, Z, stream=None) -> None:
     _check(_lib().afmm_mul_noalloc(ctypes.byref(desc), _ptr(X), _ptr(Y),
                                    _ptr(Z), _stream(stream)),
            "afmm_mul_noalloc")
+
+
+def afmm_mul_rows(plan, r0: int, r1: int, Xrows, Y, Zrows, stream=None) -> None:
+    """Rows [r0, r1) of Z from rows [r0, r1) of X and all of Y."""
+    h = plan.handle if hasattr(plan, "handle") else plan
+    _check(_lib().afmm_mul_rows(h, int(r0), int(r1), _ptr(Xrows), _ptr(Y), _ptr(Zrows),
+                                _stream(stream)), "afmm_mul_rows")
 
 
 def afmm_mul_batched(descs: Sequence[afmm_desc], X: Sequence, Y: Sequence,

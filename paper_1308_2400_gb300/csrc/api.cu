@@ -819,6 +819,41 @@ afmm_status afmm_mul_caseB(afmm_plan p, const void* X, const void* Y, void* Z,
     return mul_impl(p, X, Y, Z, stream, AFMM_CASE_B);
 }
 
+afmm_status afmm_mul_rows(afmm_plan p, int64_t r0, int64_t r1, const void* Xrows,
+                          const void* Y, void* Zrows, void* stream) {
+    if (!p) return AFMM_ERR_INVALID_ARG;
+    const afmm_desc& d = p->d;
+    const int64_t n = d.n;
+    if (d.kase != AFMM_CASE_A && d.kase != AFMM_CASE_B) return AFMM_ERR_INVALID_ARG;
+    if (r0 < 0 || r1 < r0 || r1 > n) return AFMM_ERR_INVALID_ARG;
+    if (r1 == r0) return AFMM_OK;
+    if (!Xrows || !Y || !Zrows) return AFMM_ERR_INVALID_ARG;
+    if (p->variant != AFMM_VARIANT_TC_BF16X3 && p->variant != AFMM_VARIANT_TC_BF16X2 &&
+        p->variant != AFMM_VARIANT_TC_FP8X4)
+        return AFMM_ERR_UNSUPPORTED;
+    for (const void* q : {Xrows, Y, static_cast<const void*>(Zrows)})
+        if (is_host_ptr(q)) return AFMM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AFMM_TRY(ensure_workspace(p, st));
+    const int64_t ldx = d.ldx ? d.ldx : n, ldz = d.ldz ? d.ldz : n;
+    // The kernels address row r of X and of Z (r in [r0, r1)) from the
+    // start of the matrix; the caller holds rows [r0, r1) only, so the
+    // base handed down is r0 rows before its pointers (never dereferenced).
+    const uintptr_t xb = reinterpret_cast<uintptr_t>(Xrows) -
+                         (uintptr_t)(r0 * ldx * (int64_t)dtype_size(d.x_dtype));
+    const uintptr_t zb = reinterpret_cast<uintptr_t>(Zrows) -
+                         (uintptr_t)(r0 * ldz * (int64_t)dtype_size(d.z_dtype));
+    int* status = wsp<int>(p, p->off_status);
+    const int64_t l0 = launch_counter();
+    afmm_status rc = tc_split_prepare_b(&p->tc, d, Y, status, st);
+    if (rc == AFMM_OK)
+        rc = tc_split_rows(&p->tc, d, reinterpret_cast<const void*>(xb),
+                           reinterpret_cast<void*>(zb), r0, r1, status, st);
+    p->launches += launch_counter() - l0;
+    p->calls += 1;
+    return rc;
+}
+
 afmm_status afmm_plan_sync(afmm_plan p, void* stream) {
     if (!p) return AFMM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -501,11 +501,36 @@ __device__ __forceinline__ void raise_abort_pair(TcBars* b, uint32_t peer_abort,
     atomicCAS(status, 0, (int)AFMM_ERR_TIMEOUT);
 }
 
+// Work unit u of a pair: the first `whole` units are whole 256 x 256
+// tiles; the units after them cut each of the last tiles into `split`
+// column parts of 256 / split columns (256 x 128 for split = 2), so that a
+// last round with fewer tiles than pairs still spreads over all pairs.
+struct PairUnit {
+    int tm, tn;       // pair tile
+    int col;          // first column of the part inside the tile
+    int width;        // columns of the part: 256, or 128
+};
+__device__ __forceinline__ PairUnit pair_unit(int u, int whole, int split, int tiles_m,
+                                              int tiles_n) {
+    PairUnit w;
+    int tile = u, part = 0;
+    w.width = PR_BN;
+    if (u >= whole) {
+        tile = whole + (u - whole) / split;
+        part = (u - whole) % split;
+        w.width = PR_BN / split;
+    }
+    pair_tile_coords(tile, tiles_m, tiles_n, w.tm, w.tn);
+    w.col = part * w.width;
+    return w;
+}
+
 template <int SA, bool TOUT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
-               const __grid_constant__ CUtensorMap tmB, float* __restrict__ Z, int64_t ldz,
-               int m0, int M, int n0, int N, int K, int vec, int* status) {
+               const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmB64, float* __restrict__ Z, int64_t ldz,
+               int m0, int M, int n0, int N, int K, int vec, int split, int* status) {
     using Cfg = PairCfg<SA>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
@@ -519,6 +544,10 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
     const int tiles_m = (M - m0 + PR_BM - 1) / PR_BM, tiles_n = (N - n0 + PR_BN - 1) / PR_BN;
     const int num_tiles = tiles_m * tiles_n;
     const int num_kb = (K + TC_BK - 1) / TC_BK;
+    // The tiles of the last, partial round are split when split > 1.
+    const int rem = split > 1 ? num_tiles % npairs : 0;
+    const int whole = num_tiles - rem;
+    const int num_units = whole + split * rem;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -533,6 +562,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
         ptx::fence_proxy_async_smem();
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
+        ptx::prefetch_tmap(&tmB64);
     }
     if (warp == 1) {
         ptx::tmem_alloc_pair(&bars->tmem_base, TMEM_COLS);
@@ -554,11 +584,14 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
             int issued_phase[MAX_STAGES];
             for (int s = 0; s < MAX_STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
-            for (int tile = pair; ok && tile < num_tiles; tile += npairs) {
-                int tm, tn;
-                pair_tile_coords(tile, tiles_m, tiles_n, tm, tn);
-                const int arow = m0 + tm * PR_BM + (int)rank * PR_HALF;
-                const int brow = n0 + tn * PR_BN + (int)rank * PR_HALF;
+            for (int u = pair; ok && u < num_units; u += npairs) {
+                const PairUnit w = pair_unit(u, whole, split, tiles_m, tiles_n);
+                const int arow = m0 + w.tm * PR_BM + (int)rank * PR_HALF;
+                // Each CTA holds half of the unit's B rows (128, or 64).
+                const int bhalf = w.width / 2;
+                const int brow = n0 + w.tn * PR_BN + w.col + (int)rank * bhalf;
+                const CUtensorMap* mb = w.width == PR_BN ? &tmB : &tmB64;
+                const uint32_t bytes = SA * A_TILE_BYTES + (uint32_t)bhalf * TC_BK * 2;
                 for (int kb = 0; kb < num_kb; ++kb) {
                     if (!ptx::mbar_wait_cluster_bounded(&bars->empty[stage], phase ^ 1u, abort,
                                                         WAIT_LIMIT_NS)) {
@@ -566,8 +599,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         break;
                     }
                     // The even CTA's barrier counts both CTAs' bytes.
-                    if (leader)
-                        ptx::mbar_arrive_expect_tx(&bars->full[stage], 2 * Cfg::STAGE_BYTES);
+                    if (leader) ptx::mbar_arrive_expect_tx(&bars->full[stage], 2 * bytes);
                     const uint32_t full0 =
                         ptx::mapa_shared(ptx::smem_addr(&bars->full[stage]), 0u);
                     uint8_t* st = tiles + stage * Cfg::STAGE_BYTES;
@@ -575,8 +607,8 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                     for (int s = 0; s < SA; ++s)
                         ptx::tma_load_3d_pair(st + s * A_TILE_BYTES, &tmA, full0, kb * TC_BK,
                                               arow, s);
-                    ptx::tma_load_3d_pair(st + SA * A_TILE_BYTES, &tmB, full0, kb * TC_BK,
-                                          brow, 0);
+                    ptx::tma_load_3d_pair(st + SA * A_TILE_BYTES, mb, full0, kb * TC_BK, brow,
+                                          0);
                     issued_phase[stage] = (int)phase;
                     if (++stage == Cfg::STAGES) {
                         stage = 0;
@@ -605,11 +637,12 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
     } else if (warp == 1) {
         // ---------------------------------------------------- MMA issuer
         if (lane == 0 && leader) {
-            constexpr uint32_t IDESC = ptx::idesc_bf16_f32(PR_BM, PR_BN);
             int stage = 0;
             uint32_t phase = 0, tphase = 0;
             bool ok = true;
-            for (int tile = pair; ok && tile < num_tiles; tile += npairs) {
+            for (int u = pair; ok && u < num_units; u += npairs) {
+                const int width = u < whole ? PR_BN : PR_BN / split;
+                const uint32_t IDESC = ptx::idesc_bf16_f32(PR_BM, width);
                 if (!ptx::mbar_wait_cluster_bounded(&bars->tempty[0], tphase ^ 1u, abort,
                                                     WAIT_LIMIT_NS)) {
                     ok = false;
@@ -668,9 +701,8 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
         const uint32_t tempty0 = ptx::mapa_shared(ptx::smem_addr(&bars->tempty[0]), 0u);
         uint32_t tphase = 0;
-        for (int tile = pair; tile < num_tiles; tile += npairs) {
-            int tm, tn;
-            pair_tile_coords(tile, tiles_m, tiles_n, tm, tn);
+        for (int u = pair; u < num_units; u += npairs) {
+            const PairUnit w = pair_unit(u, whole, split, tiles_m, tiles_n);
             const bool got = __all_sync(
                 0xffffffffu,
                 ptx::mbar_wait_cluster_bounded(&bars->tfull[0], tphase, abort, WAIT_LIMIT_NS));
@@ -679,25 +711,31 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                 break;
             }
             ptx::tc_fence_after();
+            // A 128-wide part has columns for the h = 0 warps only.
+            const bool live = h * 128 < w.width;
             float sum[128];
+            if (live) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                // hi-slice sum + small-slice sum, one rounding.
-                uint32_t r0[16], r1[16];
-                ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
-                ptx::tmem_ld_16cols(lane_base + (uint32_t)(PR_BN + c * 16), r1);
-                ptx::tmem_ld_wait();
+                for (int c = 0; c < 8; ++c) {
+                    // hi-slice sum + small-slice sum, one rounding.
+                    uint32_t r0[16], r1[16];
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(PR_BN + c * 16), r1);
+                    ptx::tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    sum[c * 16 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    for (int j = 0; j < 16; ++j)
+                        sum[c * 16 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                }
             }
             // This warp's TMEM lanes are free again before the stores.
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive_cluster(tempty0);
             tphase ^= 1u;
+            if (!live) continue;
+            const int tm = w.tm, tn = w.tn;
             const int64_t m = (int64_t)m0 + (int64_t)tm * PR_BM + (int64_t)rank * PR_HALF + row;
-            const int col0 = n0 + tn * PR_BN + h * 128;
+            const int col0 = n0 + tn * PR_BN + w.col + h * 128;
             if (TOUT && m < M) {
                 // Element (m, col0 + j) of Z^T is Z[col0 + j][m]: a warp's
                 // lanes hold consecutive m, one 128-byte segment per store.
@@ -1317,9 +1355,14 @@ afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
     if (cap < 1) return AFMM_ERR_UNSUPPORTED;
     const int clusters = tiles < cap ? tiles : cap;
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, mb64;
     std::memcpy(&ma, TOUT ? t->tmap_at : t->tmap_a, sizeof ma);
     std::memcpy(&mb, TOUT ? t->tmap_bt2 : t->tmap_b2, sizeof mb);
+    std::memcpy(&mb64, TOUT ? t->tmap_bt3 : t->tmap_b3, sizeof mb64);
+    // A last round with at most half as many tiles as pairs is run as
+    // 256 x 128 halves.
+    const int rem = tiles % clusters;
+    const int split = (rem > 0 && 2 * rem <= clusters) ? 2 : 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
     cfg.blockDim = dim3(TC_THREADS, 1, 1);
@@ -1333,8 +1376,8 @@ afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     main_kernel_begin(st);
-    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT>, ma, mb, Z, ldz, m0, m1,
-                                     n0, n1, n, vec, status));
+    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT>, ma, mb, mb64, Z, ldz, m0,
+                                     m1, n0, n1, n, vec, split, status));
     main_kernel_end(st, 2 * clusters);
     count_launches(1);
     return AFMM_OK;
@@ -1584,11 +1627,13 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z, void* s) {
     AFMM_TRY(tc_encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN, es));
     // B side with 128-row boxes: each CTA of a pair loads half of a B tile.
     AFMM_TRY(tc_encode_map(t->tmap_b2, b, t->n, t->n, t->ld_b, sb, PR_HALF, es));
+    AFMM_TRY(tc_encode_map(t->tmap_b3, b, t->n, t->n, t->ld_b, sb, PR_HALF / 2, es));
     if (!t->sliced_a && t->slices > 0) {
         // Case B as Z^T = Y^T X^T: the sliced Y^T rows are the A side.
         AFMM_TRY(tc_encode_map(t->tmap_at, b, t->n, t->n, t->ld_b, sb, TC_BM, es));
         AFMM_TRY(tc_encode_map(t->tmap_bt, a, t->n, t->n, t->ld_a, sa, TC_BN, es));
         AFMM_TRY(tc_encode_map(t->tmap_bt2, a, t->n, t->n, t->ld_a, sa, PR_HALF, es));
+        AFMM_TRY(tc_encode_map(t->tmap_bt3, a, t->n, t->n, t->ld_a, sa, PR_HALF / 2, es));
     }
     t->maps_ready = true;
     return AFMM_OK;

@@ -44,9 +44,12 @@ struct TcPlan {
     // Case B split form computed as Z^T = Y^T X^T: A side = the b buffer.
     alignas(64) unsigned char tmap_at[128];
     alignas(64) unsigned char tmap_bt[128];
-    // B side with 128-row boxes (half a B tile per CTA of a two-SM pair).
+    // B side with 128-row boxes (half a B tile per CTA of a two-SM pair)
+    // and with 64-row boxes (half of a 128-column part of a last-round tile).
     alignas(64) unsigned char tmap_b2[128];
     alignas(64) unsigned char tmap_bt2[128];
+    alignas(64) unsigned char tmap_b3[128];
+    alignas(64) unsigned char tmap_bt3[128];
     bool maps_ready = false;
     // Split form: run the two-SM (cta_group::2) product kernel.
     bool pair = false;
