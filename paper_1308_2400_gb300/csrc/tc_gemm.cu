@@ -1032,251 +1032,6 @@ tc_exact2_kernel(const __grid_constant__ CUtensorMap tmA,
     }
 }
 
-// Exact form on CTA pairs (tcgen05 cta_group::2): a pair owns a 256 x 256
-// output tile.  CTA r stages A rows [128 r, 128 r + 128) and B rows
-// [128 r, 128 r + 128) of the tile; the even CTA issues M = 256, N = 256
-// MMAs that read B from both CTAs.  Per 32-wide K step a CTA receives
-// 8 + 8 KiB and its tensor core reads 2 x (4 + 4) KiB for 128 x 256 x 32
-// MACs -- per MAC two thirds of the staged and read bytes of
-// tc_exact2_kernel.  A tile's accumulator takes 256 TMEM columns, so two
-// buffers alternate: the MMAs of the next K chunk (or tile) run into one
-// while the epilogue converts and stores the other.  K chunks keep every
-// FP32 partial sum an exact integer below 2^24; the epilogue stores the
-// first chunk of a tile and adds later chunks into Z in int32.  Pair
-// protocol and bounded waits as in tc_pair_kernel.
-constexpr int XP_BM = 256, XP_BN = 256;
-constexpr int XP_STAGE = A_TILE_BYTES + PR_B_BYTES;    // 16 KiB
-// Thirteen stages: 208 KiB in flight, about 3300 cycles of MMA work, so
-// the copies' latency stays hidden behind two MMAs per stage.
-constexpr int XP_STAGES = 13;
-constexpr int XP_SMEM = 1024 + XP_STAGES * XP_STAGE + BARS_BYTES;
-static_assert(XP_SMEM <= SMEM_OPTIN, "shared memory");
-
-__global__ void __launch_bounds__(TC_THREADS, 1)
-tc_exact_pair_kernel(const __grid_constant__ CUtensorMap tmA,
-                     const __grid_constant__ CUtensorMap tmB, int32_t* __restrict__ Z,
-                     int64_t ldz, int M, int N, int K, int kb_per_chunk, int vec,
-                     int* status) {
-    extern __shared__ uint8_t smem_raw[];
-    const uint32_t raw = ptx::smem_addr(smem_raw);
-    uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-    TcBars* bars = reinterpret_cast<TcBars*>(tiles + XP_STAGES * XP_STAGE);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = ptx::cluster_ctarank();
-    const bool leader = rank == 0;
-    const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
-    const int tiles_m = (M + XP_BM - 1) / XP_BM, tiles_n = (N + XP_BN - 1) / XP_BN;
-    const int num_tiles = tiles_m * tiles_n;
-    const int num_kb = (K + TC_BK - 1) / TC_BK;
-    const int kbpc = kb_per_chunk > 0 ? kb_per_chunk : num_kb;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < XP_STAGES; ++s) {
-            ptx::mbar_init(&bars->full[s], 1);
-            ptx::mbar_init(&bars->empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            ptx::mbar_init(&bars->tfull[b], 1);
-            ptx::mbar_init(&bars->tempty[b], PR_EPI_WARPS);
-        }
-        ptx::mbar_init(&bars->drain, 1);
-        bars->abort = 0;
-        ptx::fence_barrier_init();
-        ptx::fence_proxy_async_smem();
-        ptx::prefetch_tmap(&tmA);
-        ptx::prefetch_tmap(&tmB);
-    }
-    if (warp == 1) {
-        ptx::tmem_alloc_pair(&bars->tmem_base, TMEM_COLS);
-        ptx::tmem_relinquish_pair();
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::cluster_sync();
-    ptx::tc_fence_after();
-    const uint32_t tmem = bars->tmem_base;
-    volatile int* abort = &bars->abort;
-    const uint32_t peer_abort = ptx::mapa_shared(ptx::smem_addr(&bars->abort), rank ^ 1u);
-
-    if (warp == 0) {
-        // ---------------------------------------------------- TMA producer
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int issued_phase[XP_STAGES];
-            for (int s = 0; s < XP_STAGES; ++s) issued_phase[s] = -1;
-            bool ok = true;
-            for (int tile = pair; ok && tile < num_tiles; tile += npairs) {
-                int tm, tn;
-                pair_tile_coords(tile, tiles_m, tiles_n, tm, tn);
-                const int arow = tm * XP_BM + (int)rank * PR_HALF;
-                const int brow = tn * XP_BN + (int)rank * PR_HALF;
-                for (int kb = 0; kb < num_kb; ++kb) {
-                    if (!ptx::mbar_wait_cluster_bounded(&bars->empty[stage], phase ^ 1u, abort,
-                                                        WAIT_LIMIT_NS)) {
-                        ok = false;
-                        break;
-                    }
-                    if (leader) ptx::mbar_arrive_expect_tx(&bars->full[stage], 2 * XP_STAGE);
-                    const uint32_t full0 =
-                        ptx::mapa_shared(ptx::smem_addr(&bars->full[stage]), 0u);
-                    uint8_t* st = tiles + stage * XP_STAGE;
-                    ptx::tma_load_3d_pair(st, &tmA, full0, kb * TC_BK, arow, 0);
-                    ptx::tma_load_3d_pair(st + A_TILE_BYTES, &tmB, full0, kb * TC_BK, brow, 0);
-                    issued_phase[stage] = (int)phase;
-                    if (++stage == XP_STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
-                }
-            }
-            if (!ok) {
-                raise_abort_pair(bars, peer_abort, status);
-                volatile int never = 0;
-                if (leader)
-                    for (int s = 0; s < XP_STAGES; ++s)
-                        if (issued_phase[s] >= 0)
-                            ptx::mbar_wait_cluster_bounded(&bars->full[s],
-                                                           (uint32_t)issued_phase[s], &never,
-                                                           WAIT_LIMIT_NS);
-                const uint64_t t0 = ptx::globaltimer_ns();
-                while (ptx::globaltimer_ns() - t0 < 2000000ull) {
-                }
-            }
-        }
-        __syncwarp();
-    } else if (warp == 1) {
-        // ---------------------------------------------------- MMA issuer
-        if (lane == 0 && leader) {
-            constexpr uint32_t IDESC = ptx::idesc_bf16_f32(PR_BM, PR_BN);
-            int stage = 0;
-            uint32_t phase = 0;
-            uint32_t tph[2] = {0u, 0u};      // completed uses of each buffer, mod 2
-            int unit = 0;                    // (tile, chunk) units issued
-            bool ok = true;
-            for (int tile = pair; ok && tile < num_tiles; tile += npairs) {
-                for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kbpc, ++unit) {
-                    const int buf = unit & 1;
-                    // This buffer was read out by both CTAs' epilogues.
-                    if (!ptx::mbar_wait_cluster_bounded(&bars->tempty[buf], tph[buf] ^ 1u,
-                                                        abort, WAIT_LIMIT_NS)) {
-                        ok = false;
-                        break;
-                    }
-                    ptx::tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(buf * XP_BN);
-                    const int kb1 = min(kb0 + kbpc, num_kb);
-                    for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!ptx::mbar_wait_cluster_bounded(&bars->full[stage], phase, abort,
-                                                            WAIT_LIMIT_NS)) {
-                            ok = false;
-                            break;
-                        }
-                        ptx::tc_fence_after();
-                        const uint32_t s0 = ptx::smem_addr(tiles + stage * XP_STAGE);
-#pragma unroll
-                        for (int ks = 0; ks < TC_BK / 16; ++ks)
-                            ptx::mma_f16_pair(d, ptx::sdesc_kmajor_sw64(s0 + ks * 32),
-                                              ptx::sdesc_kmajor_sw64(s0 + A_TILE_BYTES + ks * 32),
-                                              IDESC, (kb != kb0 || ks != 0) ? 1u : 0u);
-                        ptx::mma_commit_pair_mc(&bars->empty[stage], (uint16_t)3u);
-                        if (++stage == XP_STAGES) {
-                            stage = 0;
-                            phase ^= 1u;
-                        }
-                    }
-                    if (!ok) break;
-                    ptx::mma_commit_pair_mc(&bars->tfull[buf], (uint16_t)3u);
-                    tph[buf] ^= 1u;
-                }
-            }
-            if (!ok) raise_abort_pair(bars, peer_abort, status);
-            ptx::mma_commit_pair_mc(&bars->drain, (uint16_t)3u);
-        }
-        if (lane == 0) {
-            volatile int never = 0;
-            ptx::mbar_wait_cluster_bounded(&bars->drain, 0u, &never, WAIT_LIMIT_NS);
-        }
-        __syncwarp();
-    } else {
-        // ---------------------------------------------------- epilogue
-        // Warp w reads TMEM lanes 32*(w%4).. (its rows of this CTA's half)
-        // and columns [128 h, 128 h + 128) of the unit's buffer.
-        const int q = warp & 3;
-        const int h = (warp - 2) >> 2;
-        const uint32_t tempty0[2] = {
-            ptx::mapa_shared(ptx::smem_addr(&bars->tempty[0]), 0u),
-            ptx::mapa_shared(ptx::smem_addr(&bars->tempty[1]), 0u)};
-        uint32_t tph[2] = {0u, 0u};
-        int unit = 0;
-        bool ok = true;
-        for (int tile = pair; ok && tile < num_tiles; tile += npairs) {
-            int tm, tn;
-            pair_tile_coords(tile, tiles_m, tiles_n, tm, tn);
-            const int64_t m = (int64_t)tm * XP_BM + (int64_t)rank * PR_HALF + q * 32 + lane;
-            const int col0 = tn * XP_BN + h * 128;
-            for (int kb0 = 0; kb0 < num_kb; kb0 += kbpc, ++unit) {
-                const int buf = unit & 1;
-                const bool got = ptx::mbar_wait_cluster_bounded(&bars->tfull[buf], tph[buf],
-                                                                abort, WAIT_LIMIT_NS);
-                if (!__all_sync(0xffffffffu, got)) {
-                    if (lane == 0) raise_abort_pair(bars, peer_abort, status);
-                    ok = false;
-                    break;
-                }
-                tph[buf] ^= 1u;
-                ptx::tc_fence_after();
-                const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) +
-                                           (uint32_t)(buf * XP_BN + h * 128);
-                int32_t v[128];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t r[32];
-                    ptx::tmem_ld_32cols(lane_base + (uint32_t)(c * 32), r);
-                    ptx::tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[c * 32 + j] = __float2int_rn(__uint_as_float(r[j]));
-                }
-                // The buffer is free for the MMAs two units ahead.
-                ptx::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) ptx::mbar_arrive_cluster(tempty0[buf]);
-                const bool first = kb0 == 0;
-                if (m < M) {
-                    int32_t* zr = Z + m * ldz + col0;
-                    if (vec && col0 + 128 <= N) {
-#pragma unroll
-                        for (int j = 0; j < 128; j += 4) {
-                            int4 o = make_int4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                            if (!first) {
-                                const int4 z = *reinterpret_cast<const int4*>(zr + j);
-                                o.x += z.x;
-                                o.y += z.y;
-                                o.z += z.z;
-                                o.w += z.w;
-                            }
-                            *reinterpret_cast<int4*>(zr + j) = o;
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 128; ++j)
-                            if (col0 + j < N) zr[j] = first ? v[j] : zr[j] + v[j];
-                    }
-                }
-            }
-        }
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::cluster_sync();
-    if (warp == 1) {
-        __syncwarp();
-        ptx::tc_fence_after();
-        ptx::tmem_dealloc_pair(tmem, TMEM_COLS);
-    }
-}
-
 template <int SA, int SB, bool TOUT = false, bool F8 = false>
 afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaStream_t st,
                       int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
@@ -1398,78 +1153,8 @@ afmm_status split_product(const TcPlan* t, float* Z, int64_t ldz, int* status,
                           : launch_tc<2, 1, TOUT>(t, Z, ldz, status, st, m0, m1, n0, n1);
 }
 
-// Clusters of two CTAs that fit at once for the exact pair kernel.
-int exact_pair_clusters() {
-    static int cached[64];
-    static std::once_flag once;
-    std::call_once(once, [] { std::fill(cached, cached + 64, -1); });
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-        cudaGetLastError();
-        return 0;
-    }
-    int& c = cached[dev];
-    if (c >= 0) return c;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2, 1, 1);
-    cfg.blockDim = dim3(TC_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)XP_SMEM;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_exact_pair_kernel, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        n = 0;
-    }
-    c = n;
-    return n;
-}
-
-afmm_status launch_exact_pair(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
-                              int* status, cudaStream_t st) {
-    const int n = (int)t->n;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_exact_pair_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, XP_SMEM));
-    const int tiles = ((n + XP_BM - 1) / XP_BM) * ((n + XP_BN - 1) / XP_BN);
-    const int cap = exact_pair_clusters();
-    if (cap < 1) return AFMM_ERR_UNSUPPORTED;
-    const int clusters = tiles < cap ? tiles : cap;
-    const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
-    CUtensorMap ma, mb;
-    std::memcpy(&ma, t->tmap_a, sizeof ma);
-    std::memcpy(&mb, t->tmap_b2, sizeof mb);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
-    cfg.blockDim = dim3(TC_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)XP_SMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    main_kernel_begin(st);
-    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_exact_pair_kernel, ma, mb,
-                                     static_cast<int32_t*>(Z), ldz, n, n, n, kb_per_chunk,
-                                     vec, status));
-    main_kernel_end(st, 2 * clusters);
-    count_launches(1);
-    return AFMM_OK;
-}
-
 afmm_status launch_exact2(const TcPlan* t, void* Z, int64_t ldz, int kb_per_chunk,
                           int* status, cudaStream_t st) {
-    if (t->pair) {
-        const afmm_status rc = launch_exact_pair(t, Z, ldz, kb_per_chunk, status, st);
-        if (rc != AFMM_ERR_UNSUPPORTED) return rc;
-    }
     DeviceProps dp;
     AFMM_TRY(device_props(&dp));
     const int n = (int)t->n;
@@ -1587,9 +1272,6 @@ void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8) {
         t->kb_per_chunk = tc_exact_chunk_k(amax, bmax) / TC_BK;
         t->a_bytes = (size_t)d.n * t->ld_a * 2;
         t->b_bytes = (size_t)d.n * t->ld_b * 2;
-        // Two-SM kernel from n = 512 (AFMM_TC_PAIR=0 keeps one CTA per tile).
-        t->pair = d.n >= 512;
-        if (const char* e = std::getenv("AFMM_TC_PAIR")) t->pair = t->pair && std::atoi(e) != 0;
         return;
     }
     const int sa = t->sliced_a ? slices : 1, sb = t->sliced_a && !t->both ? 1 : slices;

@@ -64,10 +64,10 @@ def test_no_write_outside_z_and_workspace(form, n):
 @pytest.mark.parametrize("n", [641, 1283])
 @pytest.mark.parametrize("form", ["tc_bf16x3_A", "tc_bf16x3_B", "tc_bf16x2_A",
                                   "tc_exact_A", "tc_exact_B"])
-def test_two_sm_kernels_write_only_z(form, n):
-    """From n = 512 the split and exact forms run on CTA pairs (256 x 256
-    tiles); ragged sizes leave partial pair tiles at the right and bottom
-    edges."""
+def test_large_ragged_tiles_write_only_z(form, n):
+    """From n = 512 the split forms run on CTA pairs (256 x 256 tiles, the
+    last round's tiles in 256 x 128 halves) and the exact form on 256 x 256
+    tiles; ragged sizes leave partial tiles at the right and bottom edges."""
     _guarded_run(form, n)
 
 

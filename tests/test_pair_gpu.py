@@ -1,5 +1,6 @@
 """The two-SM split kernel (tcgen05 cta_group::2, 256 x 256 tiles per CTA
-pair) against the oracle (Sec. 2 loops, FP64).
+pair) and the exact form at sizes with several K chunks, against the
+oracle (Sec. 2 loops, FP64 / int64).
 
 From n = 512 the split form runs on CTA pairs; these sizes put partial pair
 tiles at the edges (n not a multiple of 256) and single-tile problems.  The
@@ -66,11 +67,11 @@ def test_pair_kernel_host_buffers_pipelined(case):
 
 @pytest.mark.parametrize("n", [512, 777, 1283])
 @pytest.mark.parametrize("case", ["A", "B"])
-def test_exact_pair_kernel_is_bit_exact(case, n):
-    """The exact form on CTA pairs: int8 Base values at the extremes and u8
-    Rep-factors up to 255 make K chunks of 16 k-blocks, so a tile takes
-    several chunks through the two TMEM buffers; the result must equal the
-    oracle's integers."""
+def test_exact_form_many_chunks_is_bit_exact(case, n):
+    """The exact form with int8 Base values at the extremes and u8
+    Rep-factors up to 255: K chunks of 16 k-blocks, so every tile adds
+    several chunks into Z in int32; the result must equal the oracle's
+    integers."""
     from _helpers import oracle_rows
     rng = np.random.default_rng(n)
     base = rng.choice(np.array([-127, -126, 0, 1, 126, 127], dtype=np.int8), size=(n, n))
