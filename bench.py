@@ -397,7 +397,7 @@ def traffic_from_profile(kernel_tag, workload):
         return None
     src = {"simt_gemm": "simt_gemm.cu", "tc_gemm": "tc_gemm.cu",
            "tc_gemm_fp8": "tc_gemm.cu", "tc_gemm_real": "tc_gemm.cu",
-           "tc_exact2": "tc_gemm.cu",
+           "tc_exact2": "tc_gemm.cu", "tc_pair_kernel": "tc_gemm.cu",
            "sparse": "sparse.cu"}.get(kernel_tag)
     vals = {}
     with open(path) as f:
@@ -545,7 +545,10 @@ def run_afmm(args):
         peak = bf16_peak
         roof = {"bound": "tensor", "unit": "TFLOP/s",
                 "peak_src": f"{bf16_src}, {peak_src}"}
-        tag = "tc_exact2" if vname == "tc_exact" else "tc_gemm"
+        # The split forms run on CTA pairs from n = 512 (AFMM_TC_PAIR=0: one CTA).
+        pair = (vname in ("tc_bf16x3", "tc_bf16x2") and n >= 512
+                and os.environ.get("AFMM_TC_PAIR", "1") != "0")
+        tag = "tc_exact2" if vname == "tc_exact" else ("tc_pair_kernel" if pair else "tc_gemm")
     else:
         alg = flops
         sm_mhz = SM_MAX_MHZ
