@@ -231,10 +231,10 @@ afmm_status afmm_plan_set_workspace(afmm_plan plan, void* workspace,
  * non-negative integers; no flag needed): a negative one is reported as
  * AFMM_ERR_NEGATIVE_REP, a non-integer one (NaN and infinities included)
  * as AFMM_ERR_NONINTEGER_REP, by afmm_plan_sync (or the next call's
- * status); Z is then unspecified.  Most forms check in the conversion that
- * reads the Rep-factors anyway; the FP32 CUDA-core and sparse forms read
- * them in place and run one check pass first (none for u8 Rep-factors,
- * which cannot be invalid).  Negative Base values are valid. */
+ * status); Z is then unspecified.  Most forms check in the conversion or
+ * compaction that reads the Rep-factors anyway; the FP32 CUDA-core form
+ * reads them in place and runs one check pass first (none for u8
+ * Rep-factors, which cannot be invalid).  Negative Base values are valid. */
 afmm_status afmm_mul_caseA(afmm_plan plan, const void* X, const void* Y,
                            void* Z, void* stream);
 

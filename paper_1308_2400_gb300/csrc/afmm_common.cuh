@@ -175,14 +175,16 @@ afmm_status mlp_adam(int64_t n, float* params, const float* grads, float* m, flo
 
 // Sparse x sparse product (sparse.cu): workspace for density hints d1, d2
 // (< 0: unknown) and the launch sequence (compaction of X and Y, rows past
-// their slot into an overflow region; product).
+// their slot into an overflow region; product).  rep_which: the factor
+// holding Rep-factors (0 X, 1 Y, -1 none), checked by the compaction.
 size_t sparse_ws_bytes(int64_t n, double d1, double d2);
 // Zero the compaction's overflow counters (a fresh or re-bound workspace;
 // after an error).  Each product leaves them at zero for the next call.
 afmm_status sparse_reset(void* ws, cudaStream_t st);
 afmm_status launch_sparse(const void* X, int xdt, int64_t ldx, const void* Y, int ydt,
                           int64_t ldy, float* Z, int64_t ldz, int64_t n, double d1,
-                          double d2, void* ws, int* status, cudaStream_t st);
+                          double d2, void* ws, int* status, cudaStream_t st,
+                          int rep_which);
 
 // K6: error norms, partial sums in `ws` (error_norm_ws_bytes bytes).
 size_t error_norm_ws_bytes(int64_t rows, int64_t cols);

@@ -448,12 +448,12 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
         AFMM_TRY(launch_scan(Y, d.y_dtype, n, d.ldy ? d.ldy : n, y_rep, part,
                              wsp<ScanStats>(p, p->off_sy), status, st));
         p->validated = true;
-    } else if ((x_rep || y_rep) &&
-               (p->variant == AFMM_VARIANT_SIMT_F32 || p->variant == AFMM_VARIANT_SPARSE)) {
+    } else if ((x_rep || y_rep) && p->variant == AFMM_VARIANT_SIMT_F32) {
         // Every call checks the Rep-factors (Sec. 2 types: non-negative
-        // integers).  The other forms check them in the conversion that
-        // reads them; these two read them in place, so a check pass runs
-        // first (no launch for u8 Rep-factors, which are always valid).
+        // integers).  The other forms check them in the conversion or
+        // compaction that reads them; this one reads them in place, so a
+        // check pass runs first (no launch for u8 Rep-factors, which are
+        // always valid).
         AFMM_TRY(launch_rep_check(x_rep ? X : Y, x_rep ? d.x_dtype : d.y_dtype, n,
                                   x_rep ? (d.ldx ? d.ldx : n) : (d.ldy ? d.ldy : n),
                                   wsp<int>(p, p->off_status), st));
@@ -476,7 +476,8 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
             return launch_sparse(X, d.x_dtype, d.ldx ? d.ldx : n, Y, d.y_dtype,
                                  d.ldy ? d.ldy : n, static_cast<float*>(Z),
                                  d.ldz ? d.ldz : n, n, d.d1, d.d2,
-                                 p->ws + p->off_a, wsp<int>(p, p->off_status), st);
+                                 p->ws + p->off_a, wsp<int>(p, p->off_status), st,
+                                 y_rep ? 1 : (x_rep ? 0 : -1));
         default: return AFMM_ERR_UNSUPPORTED;
     }
 }

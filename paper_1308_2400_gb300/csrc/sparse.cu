@@ -43,6 +43,7 @@ struct SpMat {
     const void* M;
     int64_t ld;
     int vec;              // rows 16-byte aligned and n a multiple of 16 bytes
+    int rep;              // the factor holds Rep-factors: check them (Sec. 2 types)
     int R;                // slot size (pairs per row)
     uint2* ent;           // n * R slots, then ovf_cap overflow pairs
     int64_t ovf_cap;
@@ -65,6 +66,20 @@ __device__ __forceinline__ bool nz_elem(const typename Elem<DT>::T* v, int e) {
     return (float)Elem<DT>::get(v, e) != 0.f;
 }
 
+// Rep-factor check bits of one stored element: 1 negative, 2 not an
+// integer (NaN and infinities included).
+template <int DT>
+__device__ __forceinline__ uint32_t rep_check_bits(const typename Elem<DT>::T* v, int e) {
+    if constexpr (DT == AFMM_U8) {
+        return 0u;
+    } else if constexpr (DT == AFMM_I8 || DT == AFMM_I32) {
+        return v[e] < 0 ? 1u : 0u;
+    } else {
+        const double x = Elem<DT>::get(v, e);
+        return (x < 0.0 ? 1u : 0u) | ((!isfinite(x) || trunc(x) != x) ? 2u : 0u);
+    }
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -84,6 +99,7 @@ __device__ __forceinline__ void compact_row(const SpArgs& a, const SpMat& A, int
     int* spl = A.spl + r * (a.C - 1);
     const T* row = static_cast<const T*>(A.M) + r * A.ld;
     int c = 0;
+    uint32_t bad = 0;
     if (A.vec) {
         const uint4* row4 = reinterpret_cast<const uint4*>(row);
         const int64_t units = n / V;
@@ -113,6 +129,10 @@ __device__ __forceinline__ void compact_row(const SpArgs& a, const SpMat& A, int
                 uint32_t nib = 0;
 #pragma unroll
                 for (int t = 0; t < V; ++t) nib |= (uint32_t)nz_elem<DT>(e, t) << t;
+                if (A.rep) {
+#pragma unroll
+                    for (int t = 0; t < V; ++t) bad |= rep_check_bits<DT>(e, t);
+                }
                 const unsigned any = __ballot_sync(0xffffffffu, nib != 0);
                 if (any == 0) continue;
                 const int pc = __popc(nib);
@@ -152,6 +172,7 @@ __device__ __forceinline__ void compact_row(const SpArgs& a, const SpMat& A, int
         for (int64_t j0 = 0; j0 < n; j0 += 32) {
             if (j0 > 0 && j0 % SP_CW == 0 && lane == 0) spl[j0 / SP_CW - 1] = c;
             const int64_t j = j0 + lane;
+            if (A.rep && j < n) bad |= rep_check_bits<DT>(row, (int)j);
             const float v = j < n ? (float)Elem<DT>::get(row, j) : 0.f;
             const unsigned m = __ballot_sync(0xffffffffu, v != 0.f);
             if (v != 0.f) {
@@ -161,6 +182,9 @@ __device__ __forceinline__ void compact_row(const SpArgs& a, const SpMat& A, int
             c += __popc(m);
         }
     }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && lane == 0)
+        atomicCAS(a.status, 0, (int)((bad & 1u) ? AFMM_ERR_NEGATIVE_REP : AFMM_ERR_NONINTEGER_REP));
     int64_t start = r * (int64_t)R;
     if (c > R) {
         // Longer than the slot: the whole row into the overflow region.
@@ -400,7 +424,7 @@ afmm_status sparse_reset(void* ws, cudaStream_t st) {
 
 afmm_status launch_sparse(const void* X, int xdt, int64_t ldx, const void* Y, int ydt,
                           int64_t ldy, float* Z, int64_t ldz, int64_t n, double d1,
-                          double d2, void* ws, int* status, cudaStream_t st) {
+                          double d2, void* ws, int* status, cudaStream_t st, int rep_which) {
     if (n <= 0) return AFMM_OK;
     SpArgs a{};
     sparse_layout(n, d1, d2, static_cast<char*>(ws), &a);
@@ -413,6 +437,8 @@ afmm_status launch_sparse(const void* X, int xdt, int64_t ldx, const void* Y, in
     a.m[1].M = Y;
     a.m[1].ld = ldy;
     a.m[1].vec = rows_vec(Y, ydt, ldy, n);
+    a.m[0].rep = rep_which == 0;
+    a.m[1].rep = rep_which == 1;
     // Compaction: one warp per row of X (grid.y = 0) and of Y (grid.y = 1).
     const dim3 grid((unsigned)((n + SP_ROWS - 1) / SP_ROWS), 2);
     AFMM_TRY(dispatch_dtype(xdt, [&]<int DTX>() -> afmm_status {

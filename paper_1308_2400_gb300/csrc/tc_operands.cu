@@ -147,6 +147,20 @@ widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
     if (bits) atomicCAS(status, 0, bad_status(bits));
 }
 
+// One-byte sources (E4M3, u8, i8): blocks of two stacked 64 x 64 tiles
+// (tile2_transpose_convert_u8), rows 128 * blockIdx.y ...
+template <int DT, int S, bool EXACT>
+__global__ void __launch_bounds__(256)
+widen_transpose2_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
+                        __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim, int vec,
+                        int* status, int rep) {
+    __shared__ float tile[2][64][65];
+    const int bits = tile2_transpose_convert_u8<DT, S, EXACT>(
+        src, n, lds, (int64_t)blockIdx.y * 128, (int64_t)blockIdx.x * 64, dst, ldk, lim,
+        vec != 0, tile, rep != 0);
+    if (bits) atomicCAS(status, 0, bad_status(bits));
+}
+
 template <int S, bool EXACT>
 afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
                               __nv_bfloat16* dst, int64_t ldk, float lim,
@@ -180,8 +194,16 @@ afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
     const dim3 grid((unsigned)g, (unsigned)g), block(256);
     const int vec = rows_aligned16(src, lds, (int64_t)dtype_size(dt));
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
-        widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(
-            src, n, lds, dst, ldk, lim, vec, status, rep ? 1 : 0);
+        if constexpr (sizeof(typename Elem<DT>::T) == 1) {
+            // Rows (of the source) in blocks of 128: the row tiles a block
+            // holds must cover ldk, the destination's padded K extent.
+            const dim3 grid2((unsigned)g, (unsigned)((n + 127) / 128));
+            widen_transpose2_kernel<DT, S, EXACT><<<grid2, block, 0, st>>>(
+                src, n, lds, dst, ldk, lim, vec, status, rep ? 1 : 0);
+        } else {
+            widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(
+                src, n, lds, dst, ldk, lim, vec, status, rep ? 1 : 0);
+        }
         return AFMM_OK;
     });
     AFMM_TRY(rc);

@@ -138,27 +138,20 @@ __device__ __forceinline__ int bad_status(int bits) {
            : bits ? (int)AFMM_ERR_OVERFLOW_RISK : 0;
 }
 
-// Rows r0 .. r0+63 and columns c0 .. c0+63 of the row-major n x n source
-// become rows c (K-major) of the destination: dst[(s * n + c) * ldk + r] =
-// slice s of src[r][c], for S BF16 slices.  S = 1 and EXACT: the value must
-// be exact in BF16 and |v| <= lim, else kBadRange is returned; `rep` adds
-// the Rep-factor checks (rep_bits) of every value in the matrix.
-// Loads: tile_load_f32; the tile goes through shared memory as FP32;
-// stores: four threads write one 128-byte segment of an output row per
-// slice.  256 threads; `tile` is [64][65].
-template <int DT, int S, bool EXACT>
-__device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ src,
-                                                      int64_t n, int64_t lds, int64_t r0,
-                                                      int64_t c0,
-                                                      __nv_bfloat16* __restrict__ dst,
-                                                      int64_t ldk, float lim, bool vec,
-                                                      float (*tile)[65], bool rep = false) {
+// The store half of tile_transpose_convert: tile[r - r0][c - c0] (FP32,
+// filled and synchronised by the caller) becomes rows c (K-major) of the
+// destination, dst[(s * n + c) * ldk + r] = slice s of the value, for S
+// BF16 slices; four threads write one 128-byte segment of an output row per
+// slice.  Returns the check bits of the values this thread converted:
+// kBadRange (EXACT: not exact in BF16 or |v| > lim) and, with `rep`, the
+// Rep-factor checks (rep_bits).  256 threads; `tile` is [64][65].
+template <int S, bool EXACT>
+__device__ __forceinline__ int tile_store_transposed(const float (*tile)[65], int64_t n,
+                                                     int64_t r0, int64_t c0,
+                                                     __nv_bfloat16* __restrict__ dst,
+                                                     int64_t ldk, float lim, bool rep) {
     const int tid = threadIdx.x;
-    bool bad = false;
-    tile_load_f32<DT>(src, n, lds, r0, c0, lim, vec, tile, bad);
-    if (!EXACT) bad = false;
-    int bits = bad ? kBadRange : 0;
-    __syncthreads();
+    int bits = 0;
     const int cc = tid >> 2, qq = tid & 3;
     const int64_t c = c0 + cc, r = r0 + 16 * qq;
     if (c < n && r < ldk) {
@@ -189,6 +182,81 @@ __device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ s
                     make_uint4(w[sl][4], w[sl][5], w[sl][6], w[sl][7]);
         }
     }
+    return bits;
+}
+
+// Rows r0 .. r0+63 and columns c0 .. c0+63 of the row-major n x n source
+// become rows c (K-major) of the destination: dst[(s * n + c) * ldk + r] =
+// slice s of src[r][c], for S BF16 slices.  S = 1 and EXACT: the value must
+// be exact in BF16 and |v| <= lim, else kBadRange is returned; `rep` adds
+// the Rep-factor checks (rep_bits) of every value in the matrix.
+// Loads: tile_load_f32; the tile goes through shared memory as FP32;
+// stores: tile_store_transposed.  256 threads; `tile` is [64][65].
+template <int DT, int S, bool EXACT>
+__device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ src,
+                                                      int64_t n, int64_t lds, int64_t r0,
+                                                      int64_t c0,
+                                                      __nv_bfloat16* __restrict__ dst,
+                                                      int64_t ldk, float lim, bool vec,
+                                                      float (*tile)[65], bool rep = false) {
+    bool bad = false;
+    tile_load_f32<DT>(src, n, lds, r0, c0, lim, vec, tile, bad);
+    __syncthreads();
+    const int bits = tile_store_transposed<S, EXACT>(tile, n, r0, c0, dst, ldk, lim, rep);
+    return bits | ((EXACT && bad) ? kBadRange : 0);
+}
+
+// Two vertically adjacent 64 x 64 tiles (rows r0 .. r0+127) of a source of
+// one-byte elements, both loaded before either is converted: a thread has
+// two 16-byte loads in flight instead of one, which the one-byte transpose
+// needs to keep enough bytes moving.  `vec` as in tile_load_f32; `tile` is
+// [2][64][65].  Returns tile_transpose_convert's check bits of both.
+template <int DT, int S, bool EXACT>
+__device__ __forceinline__ int tile2_transpose_convert_u8(const void* __restrict__ src,
+                                                          int64_t n, int64_t lds, int64_t r0,
+                                                          int64_t c0,
+                                                          __nv_bfloat16* __restrict__ dst,
+                                                          int64_t ldk, float lim, bool vec,
+                                                          float (*tile)[64][65], bool rep) {
+    using T = typename Elem<DT>::T;
+    static_assert(sizeof(T) == 1, "one-byte elements");
+    const int tid = threadIdx.x;
+    const int lc = (tid & 3) * 16, lr = tid >> 2;      // 4 threads x 16 bytes per row
+    const T* s = static_cast<const T*>(src);
+    bool bad = false;
+    if (vec && c0 + 64 <= n) {
+        uint4 q[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = r0 + 64 * h + lr;
+            q[h] = r < n ? *reinterpret_cast<const uint4*>(s + r * lds + c0 + lc)
+                         : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const T* e = reinterpret_cast<const T*>(&q[h]);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) tile[h][lr][lc + t] = value_checked<DT>(e[t], lim, bad);
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = r0 + 64 * h + lr;
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int64_t c = c0 + lc + t;
+                tile[h][lr][lc + t] =
+                    (r < n && c < n) ? value_checked<DT>(s[r * lds + c], lim, bad) : 0.f;
+            }
+        }
+    }
+    __syncthreads();
+    int bits = (EXACT && bad) ? kBadRange : 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (r0 + 64 * h < ldk)
+            bits |= tile_store_transposed<S, EXACT>(tile[h], n, r0 + 64 * h, c0, dst, ldk, lim,
+                                                    rep);
     return bits;
 }
 
