@@ -39,9 +39,12 @@ int64_t launch_counter();
 struct MainTimer {
     cudaEvent_t start = nullptr, stop = nullptr;  // null: timing off
     int ctas = 0;
+    bool started = false;     // start recorded by this call's first main launch
 };
 MainTimer* current_main_timer();   // set by the plan around a call
-// Record around the main kernel launch (no-ops without a current timer).
+// Record around the main kernel launch (no-ops without a current timer); a
+// call with several main launches is timed from the first start to the last
+// end.
 void main_kernel_begin(cudaStream_t st);
 void main_kernel_end(cudaStream_t st, int ctas);
 
