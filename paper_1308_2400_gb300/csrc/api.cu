@@ -438,36 +438,6 @@ afmm_status run_simt_f64slice(afmm_plan_s* p, const void* X, const void* Y,
     return launch_transpose(ZT, 8, n, n, n, Z, ldz, st);
 }
 
-// Case A split form on device buffers in two row blocks, so that the split
-// pass of the second block (HBM-bound) runs beside the product of the first
-// (tensor-bound): the call's stream converts Y and the first block of X,
-// then multiplies the first block; a second stream converts the rest of X
-// once the first block's conversion is done (so it does not slow the
-// conversions the first product waits for); the second product waits for
-// it.  The first block's tiles fill whole rounds of CTA pairs
-// (tc_overlap_rows), so the product loses no round by the cut.
-afmm_status run_split_overlapped(afmm_plan_s* p, const void* X, const void* Y, void* Z,
-                                 int64_t b1, cudaStream_t st) {
-    const afmm_desc& d = p->d;
-    const int64_t n = d.n;
-    int* status = wsp<int>(p, p->off_status);
-    if (!p->s_in) {
-        AFMM_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
-        AFMM_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
-        for (auto& e : p->ev) AFMM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
-    cudaEvent_t ev_x0 = p->ev[0], ev_x1 = p->ev[1];
-    AFMM_TRY(tc_split_prepare_b(&p->tc, d, Y, status, st));
-    AFMM_TRY(tc_split_convert_rows(&p->tc, d, X, 0, b1, status, st));
-    AFMM_CUDA_TRY(cudaEventRecord(ev_x0, st));
-    AFMM_CUDA_TRY(cudaStreamWaitEvent(p->s_in, ev_x0, 0));
-    AFMM_TRY(tc_split_convert_rows(&p->tc, d, X, b1, n, status, p->s_in));
-    AFMM_CUDA_TRY(cudaEventRecord(ev_x1, p->s_in));
-    AFMM_TRY(tc_split_product_rows(&p->tc, d, Z, 0, b1, status, st));
-    AFMM_CUDA_TRY(cudaStreamWaitEvent(st, ev_x1, 0));
-    return tc_split_product_rows(&p->tc, d, Z, b1, n, status, st);
-}
-
 afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
                         cudaStream_t st) {
     const afmm_desc& d = p->d;
@@ -500,12 +470,6 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
         case AFMM_VARIANT_SIMT_F64SLICE: return run_simt_f64slice(p, X, Y, Z, st);
         case AFMM_VARIANT_TC_BF16X3:
         case AFMM_VARIANT_TC_BF16X2:
-            if (d.kase == AFMM_CASE_A && !(d.flags & AFMM_FLAG_FUSED_SPLIT) && !p->tc.z) {
-                DeviceProps dp;
-                AFMM_TRY(device_props(&dp));
-                const int64_t b1 = tc_overlap_rows(&p->tc, dp.sm_count);
-                if (b1 > 0) return run_split_overlapped(p, X, Y, Z, b1, st);
-            }
             return tc_run_split(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_TC_EXACT:
             return tc_run_exact(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);

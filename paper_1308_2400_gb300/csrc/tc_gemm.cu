@@ -1446,35 +1446,6 @@ afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int
                               status, st);
 }
 
-afmm_status tc_split_convert_rows(TcPlan* t, const afmm_desc& d, const void* X, int64_t r0,
-                                  int64_t r1, int* status, cudaStream_t st) {
-    if (!t->maps_ready || t->f8 || d.kase != AFMM_CASE_A) return AFMM_ERR_INVALID_ARG;
-    return tc_widen_rows(t->slices, false, X, d.x_dtype, d.n, d.ldx, t->a, t->ld_a, 0.f, status,
-                         st, r0, r1);
-}
-
-afmm_status tc_split_product_rows(TcPlan* t, const afmm_desc& d, void* Z, int64_t r0,
-                                  int64_t r1, int* status, cudaStream_t st) {
-    if (!t->maps_ready || t->f8 || d.kase != AFMM_CASE_A) return AFMM_ERR_INVALID_ARG;
-    return split_product<false>(t, static_cast<float*>(Z), d.ldz, status, st, (int)r0, (int)r1);
-}
-
-int64_t tc_overlap_rows(const TcPlan* t, int sms) {
-    // Rows of a first block whose pair tiles fill whole rounds of the
-    // pairs, so that splitting the product there costs no round: with
-    // tiles_n pair tiles per 256-row band and P pairs, P / gcd(P, tiles_n)
-    // bands.  0 when the plan does not run on pairs or the first block
-    // would not leave a second one of at least a quarter of the rows.
-    if (!t->pair || t->f8 || t->both || !t->sliced_a) return 0;
-    const int64_t n = t->n;
-    const int64_t bands = (n + PR_BM - 1) / PR_BM, tn = (n + PR_BN - 1) / PR_BN;
-    int64_t g = sms / 2, b = tn;
-    while (b) { const int64_t r = g % b; g = b; b = r; }
-    const int64_t unit = (sms / 2) / (g > 0 ? g : 1);
-    if (unit < 1 || 4 * (bands - unit) < bands || unit >= bands) return 0;
-    return unit * PR_BM;
-}
-
 afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
                           int64_t r0, int64_t r1, int* status, cudaStream_t st) {
     if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;

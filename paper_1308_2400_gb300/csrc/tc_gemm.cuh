@@ -119,16 +119,6 @@ afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int
                                cudaStream_t st);
 afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
                           int64_t r0, int64_t r1, int* status, cudaStream_t st);
-// The Case A split product in two halves for overlapping the split pass
-// with the product on device buffers: tc_split_convert_rows slices rows
-// [r0, r1) of X into the A operand; tc_split_product_rows multiplies rows
-// [r0, r1) (the B operand converted before).  tc_overlap_rows gives the end
-// of a first block whose pair tiles fill whole rounds (0: do not split).
-afmm_status tc_split_convert_rows(TcPlan* t, const afmm_desc& d, const void* X, int64_t r0,
-                                  int64_t r1, int* status, cudaStream_t st);
-afmm_status tc_split_product_rows(TcPlan* t, const afmm_desc& d, void* Z, int64_t r0,
-                                  int64_t r1, int* status, cudaStream_t st);
-int64_t tc_overlap_rows(const TcPlan* t, int sms);
 // Row blocks of Z for pipelining an n x n product: boundaries multiples of
 // the tile extent along Z's rows (128 in Case A, 256 in Case B, whose
 // product is Z^T), chosen so each block's tile count fills whole waves of
