@@ -57,12 +57,6 @@ struct SpArgs {
     int C;                // column chunks of the product
     unsigned long long* ovf_used;   // two counters, zero before a compaction
     int* status;
-    // Rows of Y with their pairs grouped by shared-memory bank (column mod
-    // 32, columns increasing within a bank), at the same places as in
-    // m[1].ent; bo[r * 34 + b] = index, within row r, of bank b's first
-    // pair (bo[r * 34 + 32] = the row's count).  Built when C == 1.
-    uint2* ybank;
-    uint16_t* bo;
 };
 
 // Non-zero test of one stored element, in the precision the product uses
@@ -94,11 +88,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Row r of one factor: the first R pairs into its slot, the count, the
 // chunk split counts; a longer row, whole, into the overflow region.
-// Returns the row's pair count and sets `start` to where its pairs begin;
-// -1 when the overflow region was full (the row was not written).
 template <int DT>
-__device__ __forceinline__ int compact_row(const SpArgs& a, const SpMat& A, int mi, int64_t r,
-                                           int lane, int64_t& start) {
+__device__ __forceinline__ void compact_row(const SpArgs& a, const SpMat& A, int mi, int64_t r,
+                                            int lane) {
     using T = typename Elem<DT>::T;
     constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte piece
     const int64_t n = a.n;
@@ -193,7 +185,7 @@ __device__ __forceinline__ int compact_row(const SpArgs& a, const SpMat& A, int 
     bad = __reduce_or_sync(0xffffffffu, bad);
     if (bad && lane == 0)
         atomicCAS(a.status, 0, (int)((bad & 1u) ? AFMM_ERR_NEGATIVE_REP : AFMM_ERR_NONINTEGER_REP));
-    start = r * (int64_t)R;
+    int64_t start = r * (int64_t)R;
     if (c > R) {
         // Longer than the slot: the whole row into the overflow region.
         // Even counts keep every row start 16-byte aligned.
@@ -202,7 +194,7 @@ __device__ __forceinline__ int compact_row(const SpArgs& a, const SpMat& A, int 
         base = __shfl_sync(0xffffffffu, base, 0);
         if ((int64_t)(base + c) > A.ovf_cap) {
             if (lane == 0) atomicCAS(a.status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
-            return -1;
+            return;
         }
         start = n * (int64_t)R + (int64_t)base;
         uint2* o = A.ent + start;
@@ -222,74 +214,16 @@ __device__ __forceinline__ int compact_row(const SpArgs& a, const SpMat& A, int 
         A.cnt[r] = c;
         A.ptr[r] = start;
     }
-    return c;
-}
-
-// Row r of Y, just compacted by this warp, copied into a.ybank with its
-// pairs grouped by bank (column mod 32), and the bank starts into a.bo.
-// Two passes over the row's pairs in chunks of 32: count per bank (one
-// shared-memory add per bank present in a chunk), then place each pair at
-// its bank's running position; within a bank the pairs keep their column
-// order (chunks in order, ranks by lane).  `hist` is this warp's 32 ints.
-__device__ __forceinline__ void bank_order_row(const SpArgs& a, int64_t r, int c,
-                                               int64_t start, int lane, int* hist) {
-    const SpMat& Y = a.m[1];
-    const uint2* src = Y.ent + start;
-    uint2* dst = a.ybank + start;
-    hist[lane] = 0;
-    __syncwarp();
-    const unsigned lt = lanemask_lt();
-    for (int p0 = 0; p0 < c; p0 += 32) {
-        const bool valid = p0 + lane < c;
-        const uint2 e = valid ? src[p0 + lane] : make_uint2(0u, 0u);
-        const unsigned key = valid ? (e.x & 31u) : 32u + (unsigned)lane;
-        const unsigned grp = __match_any_sync(0xffffffffu, key);
-        if (valid && (grp & lt) == 0) hist[key] += __popc(grp);
-        __syncwarp();
-    }
-    // Exclusive prefix of the counts: lane b holds bank b's start.
-    const int cntb = hist[lane];
-    int incl = cntb;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int excl = incl - cntb;
-    uint16_t* bo = a.bo + r * 34;
-    bo[lane] = (uint16_t)excl;
-    if (lane == 31) bo[32] = (uint16_t)incl;
-    hist[lane] = excl;
-    __syncwarp();
-    for (int p0 = 0; p0 < c; p0 += 32) {
-        const bool valid = p0 + lane < c;
-        const uint2 e = valid ? src[p0 + lane] : make_uint2(0u, 0u);
-        const unsigned key = valid ? (e.x & 31u) : 32u + (unsigned)lane;
-        const unsigned grp = __match_any_sync(0xffffffffu, key);
-        if (valid) dst[hist[key] + __popc(grp & lt)] = e;
-        __syncwarp();
-        if (valid && (grp & lt) == 0) hist[key] += __popc(grp);
-        __syncwarp();
-    }
 }
 
 // blockIdx.y = 0: rows of X, 1: rows of Y; one warp per row.
 template <int DTX, int DTY>
 __global__ void __launch_bounds__(SP_ROWS * 32) sp_compact_kernel(SpArgs a) {
-    __shared__ int hist[SP_ROWS][32];
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * SP_ROWS + (threadIdx.x >> 5);
     if (r >= a.n) return;
-    int64_t start = 0;
-    if (blockIdx.y == 0) {
-        compact_row<DTX>(a, a.m[0], 0, r, lane, start);
-    } else {
-        const int c = compact_row<DTY>(a, a.m[1], 1, r, lane, start);
-        if (a.ybank && c >= 0) {
-            __syncwarp();          // the row's pairs, written by these lanes, are visible
-            bank_order_row(a, r, c, start, lane, hist[threadIdx.x >> 5]);
-        }
-    }
+    if (blockIdx.y == 0) compact_row<DTX>(a, a.m[0], 0, r, lane);
+    else compact_row<DTY>(a, a.m[1], 1, r, lane);
 }
 
 struct SpMul {
@@ -300,8 +234,6 @@ struct SpMul {
     const int* ny;
     const uint2* ey;
     const int* sy;        // Y split counts, C - 1 per row
-    const uint2* eyb;     // Y pairs grouped by bank (C == 1), bank starts in bo
-    const uint16_t* bo;
     int64_t n;
     int C, warps, row_floats;
     float* Z;
@@ -424,93 +356,6 @@ sp_mul_kernel(SpMul a) {
     }
 }
 
-// Z[i, :] for one warp (n <= SP_CW), the Y pairs grouped by bank: lane l
-// applies exactly the terms whose column is l mod 32, i.e. every access to
-// the shared-memory row from lane l falls in bank l -- no bank conflicts and
-// no ordering between lanes.  A lane takes the X entries in k order and,
-// for each, its bank's run of the Y row, so each Z[i,j] still sums its
-// terms in increasing k (the same result as sp_mul_kernel, bit for bit).
-// For SP_G entries at a time the first SP_Q pairs of each of this lane's
-// runs are loaded before any is applied (several loads in flight); longer
-// runs finish in a loop.
-constexpr int SP_Q = 3;
-__global__ void __launch_bounds__(SP_MUL_WARPS * 32, 2)
-sp_mul_bank_kernel(SpMul a) {
-    extern __shared__ __align__(16) float srow[];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.ovf_used[0] = 0;
-        a.ovf_used[1] = 0;
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * a.warps + w;
-    if (i >= a.n || *a.status != 0) return;
-    const int cw = (int)a.n, cw4 = (cw + 3) / 4;
-    float* acc = srow + w * a.row_floats;
-    float4* acc4 = reinterpret_cast<float4*>(acc);
-    for (int j = lane; j < cw4; j += 32) acc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
-    const int64_t xb = a.px[i], xe = xb + a.nx[i];
-    for (int64_t e0 = xb; e0 < xe; e0 += 32) {
-        const int m = xe - e0 < 32 ? (int)(xe - e0) : 32;
-        float xv = 0.f;
-        int64_t yb = 0;
-        int k = 0;
-        if (lane < m) {
-            const uint2 e = a.ex[e0 + lane];
-            xv = __uint_as_float(e.y);
-            k = (int)e.x;
-            yb = a.py[k];
-        }
-        for (int t = 0; t < m; t += SP_G) {
-            float xs[SP_G];
-            int64_t s0[SP_G];
-            int len[SP_G];
-            uint2 p[SP_G][SP_Q];
-#pragma unroll
-            for (int u = 0; u < SP_G; ++u) {
-                const int src = (t + u) & 31;
-                xs[u] = __shfl_sync(0xffffffffu, xv, src);
-                const int ku = __shfl_sync(0xffffffffu, k, src);
-                const int64_t bu = __shfl_sync(0xffffffffu, yb, src);
-                len[u] = 0;
-                s0[u] = 0;
-                if (t + u < m) {
-                    const uint16_t* bo = a.bo + (int64_t)ku * 34;
-                    const int lo = bo[lane], hi = bo[lane + 1];
-                    s0[u] = bu + lo;
-                    len[u] = hi - lo;
-                }
-#pragma unroll
-                for (int q = 0; q < SP_Q; ++q)
-                    p[u][q] = q < len[u] ? __ldg(a.eyb + s0[u] + q) : make_uint2(0u, 0u);
-            }
-#pragma unroll
-            for (int u = 0; u < SP_G; ++u) {
-#pragma unroll
-                for (int q = 0; q < SP_Q; ++q)
-                    if (q < len[u]) {
-                        float* z = acc + p[u][q].x;
-                        *z = fmaf(xs[u], __uint_as_float(p[u][q].y), *z);
-                    }
-                for (int q = SP_Q; q < len[u]; ++q) {
-                    const uint2 y = __ldg(a.eyb + s0[u] + q);
-                    float* z = acc + y.x;
-                    *z = fmaf(xs[u], __uint_as_float(y.y), *z);
-                }
-            }
-        }
-    }
-    __syncwarp();
-    float* zr = a.Z + i * a.ldz;
-    if (a.zvec) {
-        float4* z4 = reinterpret_cast<float4*>(zr);
-        for (int j = lane; j < cw / 4; j += 32) __stcs(z4 + j, acc4[j]);
-        for (int j = (cw & ~3) + lane; j < cw; j += 32) zr[j] = acc[j];
-    } else {
-        for (int j = lane; j < cw; j += 32) zr[j] = acc[j];
-    }
-}
-
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
 int chunks_of(int64_t n) { return (int)((n + SP_CW - 1) / SP_CW); }
@@ -555,15 +400,6 @@ size_t sparse_layout(int64_t n, double d1, double d2, char* base, SpArgs* o) {
         t.ptr = reinterpret_cast<int64_t*>(take((size_t)n * 8));
         t.spl = reinterpret_cast<int*>(take((size_t)n * (C - 1) * 4 + 4));
         if (o) o->m[m] = t;
-        if (m == 1 && C == 1) {
-            // Y's pairs grouped by bank, and the bank starts of each row.
-            uint2* yb = reinterpret_cast<uint2*>(take(((size_t)n * R + ovf + 2) * 8));
-            uint16_t* bo = reinterpret_cast<uint16_t*>(take((size_t)n * 34 * 2));
-            if (o) {
-                o->ybank = yb;
-                o->bo = bo;
-            }
-        }
     }
     return top;
 }
@@ -633,12 +469,8 @@ afmm_status launch_sparse(const void* X, int xdt, int64_t ldx, const void* Y, in
     mp.warps = warps < 1 ? 1 : (warps > SP_MUL_WARPS ? SP_MUL_WARPS : warps);
     mp.row_floats = row_floats;
     const size_t smem = (size_t)mp.warps * row_floats * sizeof(float);
-    mp.eyb = a.ybank;
-    mp.bo = a.bo;
     const int64_t pairs_y = n * (int64_t)a.m[1].R + a.m[1].ovf_cap;
-    auto kern = a.C == 1 ? sp_mul_bank_kernel
-                         : (pairs_y < (int64_t)1 << 31 ? sp_mul_kernel<int>
-                                                       : sp_mul_kernel<int64_t>);
+    auto kern = pairs_y < (int64_t)1 << 31 ? sp_mul_kernel<int> : sp_mul_kernel<int64_t>;
     AFMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     AFMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,

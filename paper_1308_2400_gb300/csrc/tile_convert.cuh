@@ -206,11 +206,61 @@ __device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ s
     return bits | ((EXACT && bad) ? kBadRange : 0);
 }
 
+// Store half for one-byte sources, with a bank-conflict-free read of the
+// tile (row stride 65 floats: element (r, c) sits in bank (r + c) mod 32):
+// thread (column cc, quarter qq) takes rows 8 qq + e and 32 + 8 qq + e
+// (e = 0 .. 7), so the 32 lanes of a warp (8 columns x 4 quarters) read 32
+// different banks; each run of 8 rows becomes one 16-byte store per slice,
+// and the four quarters of a column still fill its 128-byte output row.
+template <int S, bool EXACT>
+__device__ __forceinline__ int tile_store_transposed_il(const float (*tile)[65], int64_t n,
+                                                        int64_t r0, int64_t c0,
+                                                        __nv_bfloat16* __restrict__ dst,
+                                                        int64_t ldk, float lim, bool rep) {
+    const int tid = threadIdx.x;
+    const int cc = tid >> 2, qq = tid & 3;
+    const int64_t c = c0 + cc;
+    int bits = 0;
+    if (c >= n) return 0;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int tr = 32 * half + 8 * qq;             // first tile row of this run
+        const int64_t r = r0 + tr;
+        if (r >= ldk) continue;                        // ldk is a multiple of 8
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = tile[tr + e][cc];
+        uint32_t w[S][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            __nv_bfloat16 o0[S], o1[S];
+            split_bf16<S>(v[e], o0);
+            split_bf16<S>(v[e + 1], o1);
+            if (EXACT && (__bfloat162float(o0[0]) != v[e] ||
+                          __bfloat162float(o1[0]) != v[e + 1] || fabsf(v[e]) > lim ||
+                          fabsf(v[e + 1]) > lim))
+                bits |= kBadRange;
+            if (rep) bits |= rep_bits(v[e]) | rep_bits(v[e + 1]);
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
+        }
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+            *reinterpret_cast<uint4*>(dst + ((int64_t)sl * n + c) * ldk + r) =
+                make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+    }
+    return bits;
+}
+
 // Two vertically adjacent 64 x 64 tiles (rows r0 .. r0+127) of a source of
-// one-byte elements, both loaded before either is converted: a thread has
-// two 16-byte loads in flight instead of one, which the one-byte transpose
-// needs to keep enough bytes moving.  `vec` as in tile_load_f32; `tile` is
-// [2][64][65].  Returns tile_transpose_convert's check bits of both.
+// one-byte elements, both loaded before either is converted (two 16-byte
+// loads in flight per thread).  Load mapping, per tile: warps 2b and 2b+1
+// cover tile rows 16b .. 16b+15; lane l takes the 16 columns q = l / 8 of
+// row 16b + (l mod 8) + 8 * ((q / 2) xor (warp mod 2)), so the 32 lanes of a
+// warp write 32 different banks of the stride-65 tile (the rows and
+// quarters they take differ by 0, 8, 16, 24 in bank).  Store half:
+// tile_store_transposed_il.  `vec` as in tile_load_f32; `tile` is
+// [2][64][65].  Returns the check bits of both tiles.
 template <int DT, int S, bool EXACT>
 __device__ __forceinline__ int tile2_transpose_convert_u8(const void* __restrict__ src,
                                                           int64_t n, int64_t lds, int64_t r0,
@@ -220,21 +270,23 @@ __device__ __forceinline__ int tile2_transpose_convert_u8(const void* __restrict
                                                           float (*tile)[64][65], bool rep) {
     using T = typename Elem<DT>::T;
     static_assert(sizeof(T) == 1, "one-byte elements");
-    const int tid = threadIdx.x;
-    const int lc = (tid & 3) * 16, lr = tid >> 2;      // 4 threads x 16 bytes per row
+    const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int q = l >> 3;
+    const int lr = 16 * (warp >> 1) + (l & 7) + 8 * ((q >> 1) ^ (warp & 1));
+    const int lc = 16 * q;
     const T* s = static_cast<const T*>(src);
     bool bad = false;
     if (vec && c0 + 64 <= n) {
-        uint4 q[2];
+        uint4 v[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int64_t r = r0 + 64 * h + lr;
-            q[h] = r < n ? *reinterpret_cast<const uint4*>(s + r * lds + c0 + lc)
+            v[h] = r < n ? *reinterpret_cast<const uint4*>(s + r * lds + c0 + lc)
                          : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const T* e = reinterpret_cast<const T*>(&q[h]);
+            const T* e = reinterpret_cast<const T*>(&v[h]);
 #pragma unroll
             for (int t = 0; t < 16; ++t) tile[h][lr][lc + t] = value_checked<DT>(e[t], lim, bad);
         }
@@ -255,8 +307,8 @@ __device__ __forceinline__ int tile2_transpose_convert_u8(const void* __restrict
 #pragma unroll
     for (int h = 0; h < 2; ++h)
         if (r0 + 64 * h < ldk)
-            bits |= tile_store_transposed<S, EXACT>(tile[h], n, r0 + 64 * h, c0, dst, ldk, lim,
-                                                    rep);
+            bits |= tile_store_transposed_il<S, EXACT>(tile[h], n, r0 + 64 * h, c0, dst, ldk,
+                                                       lim, rep);
     return bits;
 }
 
