@@ -522,7 +522,8 @@ afmm_status run_pipelined_host(afmm_plan_s* p, const void* X, const void* Y, voi
     AFMM_TRY(stage_buffer(p, 2, span_bytes(n, ldz, d.z_dtype), &dZ));
     int* status = wsp<int>(p, p->off_status);
     int64_t bounds[17];
-    const int nb = tc_pipe_blocks(n, dp.sm_count, bounds, 16, d.kase == AFMM_CASE_B);
+    const int nb = tc_pipe_blocks(n, dp.sm_count, bounds, 16, d.kase == AFMM_CASE_B,
+                                  p->tc.pair && !p->tc.f8);
     cudaEvent_t ev_y = p->ev[0], ev_done = p->ev[1];
     // The staging buffers may still be read by the previous call's copies.
     AFMM_CUDA_TRY(cudaEventRecord(ev_done, st));

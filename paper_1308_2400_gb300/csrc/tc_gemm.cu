@@ -1471,17 +1471,24 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
     return split_product<true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1);
 }
 
-int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb) {
-    const int64_t unit_rows = caseb ? TC_BN : TC_BM;
+int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb,
+                   bool pair) {
+    // Tile extent along Z's rows and tiles per tile row of the kernel that
+    // multiplies the blocks; `sms` becomes the number of CTA pairs when the
+    // two-SM kernel (256 x 256 tiles on pairs of SMs) runs them.
+    const int64_t unit_rows = pair ? PR_BM : (caseb ? TC_BN : TC_BM);
     const int64_t tm = (n + unit_rows - 1) / unit_rows,
-                  tn = caseb ? (n + TC_BM - 1) / TC_BM : (n + TC_BN - 1) / TC_BN;
+                  tn = pair ? (n + PR_BN - 1) / PR_BN
+                            : (caseb ? (n + TC_BM - 1) / TC_BM : (n + TC_BN - 1) / TC_BN);
+    if (pair) sms = std::max(1, sms / 2);
     // First and last blocks of about one wave of tiles: the first product
     // starts after Y and a small piece of X have arrived, and the last
     // block's product and copy-out are short.  Middle blocks fill whole
     // waves where they can.
     const int64_t edge = std::max<int64_t>(1, sms / tn);
     const int64_t mid = tm - 2 * edge;
-    if (mid < 1 || max_blocks < 3) return tc_row_blocks(n, sms, bounds, max_blocks, caseb);
+    if (mid < 1 || max_blocks < 3)
+        return tc_row_blocks(n, pair ? 2 * sms : sms, bounds, max_blocks, caseb, pair);
     int64_t g = sms, b = tn;
     while (b) { const int64_t r = g % b; g = b; b = r; }
     int64_t unit = std::max<int64_t>(1, sms / g);        // tile rows of whole waves
@@ -1500,12 +1507,16 @@ int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool cas
     return k;                                            // number of blocks
 }
 
-int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb) {
+int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb,
+                  bool pair) {
     // Rows of Z are product rows (tiles of TC_BM) in Case A and product
-    // columns (tiles of TC_BN) in Case B.
-    const int64_t unit_rows = caseb ? TC_BN : TC_BM;
+    // columns (tiles of TC_BN) in Case B; pair tiles are 256 x 256 on
+    // sms / 2 pairs.
+    const int64_t unit_rows = pair ? PR_BM : (caseb ? TC_BN : TC_BM);
     const int64_t tm = (n + unit_rows - 1) / unit_rows,
-                  tn = caseb ? (n + TC_BM - 1) / TC_BM : (n + TC_BN - 1) / TC_BN;
+                  tn = pair ? (n + PR_BN - 1) / PR_BN
+                            : (caseb ? (n + TC_BM - 1) / TC_BM : (n + TC_BN - 1) / TC_BN);
+    if (pair) sms = std::max(1, sms / 2);
     // Smallest number of tile rows whose tiles fill whole waves.
     int64_t g = sms, b = tn;
     while (b) { const int64_t r = g % b; g = b; b = r; }

@@ -121,13 +121,15 @@ afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
                           int64_t r0, int64_t r1, int* status, cudaStream_t st);
 // Row blocks of Z for pipelining an n x n product: boundaries multiples of
 // the tile extent along Z's rows (128 in Case A, 256 in Case B, whose
-// product is Z^T), chosen so each block's tile count fills whole waves of
-// `sms` CTAs.
-int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb);
+// product is Z^T; 256 for the two-SM kernel, `pair`), chosen so each
+// block's tile count fills whole waves of `sms` CTAs (sms / 2 pairs).
+int tc_row_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb,
+                  bool pair = false);
 // The schedule of the host-buffer pipeline: first and last blocks of about
 // one wave of tiles, whole-wave blocks between (tc_row_blocks when n is too
 // small for that).  Returns the number of blocks; bounds[0..k] are Z rows.
-int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb);
+int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb,
+                   bool pair = false);
 // Case A, three slices, X FP32 with 16-byte aligned rows: the fused kernel
 // (tc_fused.cu) reads X directly and splits it in shared memory.
 bool tc_fused_usable(const afmm_desc& d, const void* X);
