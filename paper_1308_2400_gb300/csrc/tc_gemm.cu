@@ -1492,6 +1492,21 @@ int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool cas
     int64_t g = sms, b = tn;
     while (b) { const int64_t r = g % b; g = b; b = r; }
     int64_t unit = std::max<int64_t>(1, sms / g);        // tile rows of whole waves
+    if (pair) {
+        // Smaller middle blocks whose tiles come to nearly whole rounds (at
+        // least 95% of their last round busy): a block's rows arrive in a
+        // fraction of its product time, so the products, not the copies,
+        // set the pace.  (At n = 8192: 7 bands, 224 tiles, 2.95 rounds of
+        // 76 pairs, against 19 bands for exactly whole rounds.)
+        for (int64_t k = 2; 4 * k <= mid && k < unit; ++k) {
+            const int64_t tiles = k * tn;
+            const int64_t rounds = (tiles + sms - 1) / sms;
+            if (20 * tiles >= 19 * rounds * sms) {
+                unit = k;
+                break;
+            }
+        }
+    }
     while (mid / unit + (mid % unit ? 1 : 0) > max_blocks - 2) unit *= 2;
     int k = 0;
     bounds[k++] = 0;
