@@ -1446,29 +1446,38 @@ afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int
                               status, st);
 }
 
-afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
-                          int64_t r0, int64_t r1, int* status, cudaStream_t st) {
+afmm_status tc_split_convert_rows(TcPlan* t, const afmm_desc& d, const void* X, int64_t r0,
+                                  int64_t r1, int* status, cudaStream_t st) {
     if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;
     const int64_t n = d.n;
-    const int sl = t->slices;
+    if (t->f8)
+        return tc_f8_rows(d.kase == AFMM_CASE_B, X, d.x_dtype, n, d.ldx, t->a, t->ld_a,
+                          t->amax, status, st, r0, r1);
+    if (d.kase == AFMM_CASE_A)
+        return tc_widen_rows(t->slices, false, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 0.f,
+                             status, st, r0, r1);
+    return tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 256.f, status, st,
+                         r0, r1, true);
+}
+
+afmm_status tc_split_product_rows(TcPlan* t, const afmm_desc& d, void* Z, int64_t r0,
+                                  int64_t r1, int* status, cudaStream_t st) {
+    if (!t->maps_ready) return AFMM_ERR_INVALID_ARG;
     const int m0 = (int)r0, m1 = (int)r1;
     float* Zf = static_cast<float*>(Z);
-    if (t->f8) {
-        AFMM_TRY(tc_f8_rows(d.kase == AFMM_CASE_B, X, d.x_dtype, n, d.ldx, t->a, t->ld_a,
-                            t->amax, status, st, r0, r1));
+    if (t->f8)
         return d.kase == AFMM_CASE_A
                    ? launch_tc<4, 1, false, true>(t, Zf, d.ldz, status, st, m0, m1)
                    : launch_tc<4, 1, true, true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1);
-    }
-    if (d.kase == AFMM_CASE_A)
-        AFMM_TRY(tc_widen_rows(sl, false, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 0.f, status,
-                               st, r0, r1));
-    else
-        AFMM_TRY(tc_widen_rows(1, true, X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 256.f, status,
-                               st, r0, r1, true));
     if (d.kase == AFMM_CASE_A) return split_product<false>(t, Zf, d.ldz, status, st, m0, m1);
     // Case B (Z^T = Y^T X^T): rows [r0, r1) of Z are columns of the product.
     return split_product<true>(t, Zf, d.ldz, status, st, 0, -1, m0, m1);
+}
+
+afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
+                          int64_t r0, int64_t r1, int* status, cudaStream_t st) {
+    AFMM_TRY(tc_split_convert_rows(t, d, X, r0, r1, status, st));
+    return tc_split_product_rows(t, d, Z, r0, r1, status, st);
 }
 
 int tc_pipe_blocks(int64_t n, int sms, int64_t* bounds, int max_blocks, bool caseb,

@@ -119,6 +119,13 @@ afmm_status tc_split_prepare_b(TcPlan* t, const afmm_desc& d, const void* Y, int
                                cudaStream_t st);
 afmm_status tc_split_rows(TcPlan* t, const afmm_desc& d, const void* X, void* Z,
                           int64_t r0, int64_t r1, int* status, cudaStream_t st);
+// tc_split_rows in its two steps: convert rows [r0, r1) of the A operand
+// (X may be a device-mapped pointer to pinned host memory), then multiply
+// them.
+afmm_status tc_split_convert_rows(TcPlan* t, const afmm_desc& d, const void* X, int64_t r0,
+                                  int64_t r1, int* status, cudaStream_t st);
+afmm_status tc_split_product_rows(TcPlan* t, const afmm_desc& d, void* Z, int64_t r0,
+                                  int64_t r1, int* status, cudaStream_t st);
 // Row blocks of Z for pipelining an n x n product: boundaries multiples of
 // the tile extent along Z's rows (128 in Case A, 256 in Case B, whose
 // product is Z^T; 256 for the two-SM kernel, `pair`), chosen so each

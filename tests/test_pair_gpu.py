@@ -92,3 +92,30 @@ def test_exact_form_many_chunks_is_bit_exact(case, n):
     rows = sample_rows(n, 40)
     R = oracle_rows(inst, rows)
     assert np.array_equal(Z.cpu().numpy()[rows].astype(np.int64), R)
+
+
+@pytest.mark.parametrize("variant", [1, 7])
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_pinned_host_buffers_read_in_place(case, variant):
+    """Pinned (page-locked) host X, Y, Z: the conversion kernels read X and
+    Y in place over the host link and Z comes back by copy, row block by
+    row block; the result must match the oracle as on device buffers."""
+    from _helpers import desc_for
+    from paper_1308_2400_gb300 import Plan
+    n = 2304
+    inst = W.make(WORKLOAD[case], n=n, seed=21 + variant)
+    Xs = inst.x_store if inst.x_store is not None else inst.X
+    Ys = inst.y_store if inst.y_store is not None else inst.Y
+    Xh = torch.from_numpy(np.ascontiguousarray(Xs)).pin_memory()
+    Yh = torch.from_numpy(np.ascontiguousarray(Ys)).pin_memory()
+    Zh = torch.full((n, n), float("nan"), dtype=torch.float32).pin_memory()
+    p = Plan(desc_for(inst, variant=variant))
+    for _ in range(2):                       # the second call reuses the plan's buffers
+        Zh.fill_(float("nan"))
+        p(Xh, Yh, Zh)
+        p.sync()
+    p.close()
+    Z = Zh.numpy()
+    from test_fp8_gpu import fp8_elem_bound
+    check_fp32(inst, Z, sample_rows(n, 24),
+               bound_fn=tc_elem_bound if variant == 1 else fp8_elem_bound)
