@@ -499,18 +499,6 @@ afmm_status stage_buffer(afmm_plan_s* p, int idx, size_t bytes, void** out) {
     return AFMM_OK;
 }
 
-// Device address of pinned host memory the kernels may read in place (a
-// cudaHostAlloc'd or registered buffer, mapped into the device's address
-// space), or null for pageable memory, which only copies may read.
-const void* mapped_host_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
-}
-
 // Host X, Y, Z and the split tensor-core form: copy Y in, convert it; then
 // for row blocks of X: copy in (stream s_in), convert and multiply (the
 // call's stream), copy the rows of Z out (stream s_out), so transfers in
@@ -535,37 +523,6 @@ afmm_status run_pipelined_host(afmm_plan_s* p, const void* X, const void* Y, voi
     const int nb = tc_pipe_blocks(n, dp.sm_count, bounds, 16, d.kase == AFMM_CASE_B,
                                   p->tc.pair && !p->tc.f8);
     cudaEvent_t ev_y = p->ev[0], ev_done = p->ev[1];
-    const void* mx = mapped_host_ptr(X);
-    const void* my = mapped_host_ptr(Y);
-    if (mx && my) {
-        // Pinned host X and Y: the conversion kernels read them in place
-        // over the host link (no staging copy, and the split of X runs on
-        // the copy stream instead of the compute stream).  Y first, on the
-        // call's stream; then the row blocks of X, each converted on s_in
-        // while earlier blocks are multiplied; Z's rows go back by copy.
-        AFMM_TRY(tc_split_prepare_b(&p->tc, d, my, status, st));
-        AFMM_CUDA_TRY(cudaEventRecord(ev_y, st));
-        AFMM_CUDA_TRY(cudaStreamWaitEvent(p->s_in, ev_y, 0));
-        for (int b = 0; b < nb; ++b) {
-            const int64_t r0 = bounds[b], r1 = bounds[b + 1];
-            cudaEvent_t e_in = p->ev[2 + 2 * b], e_c = p->ev[3 + 2 * b];
-            AFMM_TRY(tc_split_convert_rows(&p->tc, d, mx, r0, r1, status, p->s_in));
-            AFMM_CUDA_TRY(cudaEventRecord(e_in, p->s_in));
-            AFMM_CUDA_TRY(cudaStreamWaitEvent(st, e_in, 0));
-            AFMM_TRY(tc_split_product_rows(&p->tc, d, dZ, r0, r1, status, st));
-            AFMM_CUDA_TRY(cudaEventRecord(e_c, st));
-            AFMM_CUDA_TRY(cudaStreamWaitEvent(p->s_out, e_c, 0));
-            const size_t zoff = (size_t)r0 * ldz * ez;
-            const size_t zbytes = (size_t)((r1 - r0 - 1) * ldz + n) * ez;
-            AFMM_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(Z) + zoff,
-                                          static_cast<const char*>(dZ) + zoff, zbytes,
-                                          cudaMemcpyDeviceToHost, p->s_out));
-        }
-        AFMM_CUDA_TRY(cudaEventRecord(ev_done, p->s_out));
-        AFMM_CUDA_TRY(cudaStreamWaitEvent(st, ev_done, 0));
-        AFMM_CUDA_TRY(cudaStreamSynchronize(st));
-        return AFMM_OK;
-    }
     AFMM_TRY(stage_buffer(p, 0, span_bytes(n, ldx, d.x_dtype), &dX));
     AFMM_TRY(stage_buffer(p, 1, span_bytes(n, d.ldy, d.y_dtype), &dY));
     // The staging buffers may still be read by the previous call's copies.

@@ -96,10 +96,11 @@ def test_exact_form_many_chunks_is_bit_exact(case, n):
 
 @pytest.mark.parametrize("variant", [1, 7])
 @pytest.mark.parametrize("case", ["A", "B"])
-def test_pinned_host_buffers_read_in_place(case, variant):
-    """Pinned (page-locked) host X, Y, Z: the conversion kernels read X and
-    Y in place over the host link and Z comes back by copy, row block by
-    row block; the result must match the oracle as on device buffers."""
+def test_pinned_host_buffers_pipelined(case, variant):
+    """Pinned (page-locked) host X, Y, Z through the copy pipeline (row
+    blocks of X in, products, row blocks of Z out, on three streams), two
+    calls on one plan; the result must match the oracle as on device
+    buffers."""
     from _helpers import desc_for
     from paper_1308_2400_gb300 import Plan
     n = 2304
