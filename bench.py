@@ -823,7 +823,7 @@ def run_batched(args):
 
     clk = ClockSampler(0)
     clk.start()
-    ms = tune.time_batch(auto, Xs, Ys, Zs, reps=args.steps, warmup=args.warmup)
+    ms = tune.time_batch(auto, Xs, Ys, Zs, reps=args.steps, warmup=args.warmup, rounds=1)
     clocks = clk.stop()
     # accuracy of the timed results on a sample of instances
     errs = []
@@ -854,7 +854,7 @@ def run_batched(args):
             for name, r in policies.items():
                 reps = 3 if name != "all_simt" else 1
                 samples[name].append(tune.time_batch(forced(r), Xs, Ys, Zs, reps=reps,
-                                                     warmup=1))
+                                                     warmup=1, rounds=1))
         times = {name: statistics.median(v) for name, v in samples.items()}
         no_mlp = {k: v for k, v in times.items() if k not in ("learned", "autotune_best")}
         best_no_mlp = min(no_mlp, key=no_mlp.get)

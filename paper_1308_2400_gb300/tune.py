@@ -58,21 +58,24 @@ def device_operands(inst):
     return X, Y, Z
 
 
-def time_batch(descs, Xs, Ys, Zs, reps: int = 5, warmup: int = 2) -> float:
-    """Median milliseconds of one afmm_mul_batched call (CUDA events)."""
+def time_batch(descs, Xs, Ys, Zs, reps: int = 5, warmup: int = 2, rounds: int = 3) -> float:
+    """Milliseconds per afmm_mul_batched call: `reps` calls back to back
+    between two CUDA events (the host's preparation of a call overlaps the
+    GPU work of the one before, as in a loop of calls), median of `rounds`."""
     import torch
     st = torch.cuda.current_stream()
     for _ in range(warmup):
         A.afmm_mul_batched(descs, Xs, Ys, Zs, st)
     torch.cuda.synchronize()
     ts = []
-    for _ in range(reps):
+    for _ in range(max(1, rounds)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        A.afmm_mul_batched(descs, Xs, Ys, Zs, st)
+        for _ in range(max(1, reps)):
+            A.afmm_mul_batched(descs, Xs, Ys, Zs, st)
         e1.record(st)
         e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
+        ts.append(e0.elapsed_time(e1) / max(1, reps))
     A.afmm_batched_sync(descs, st)
     return statistics.median(ts)
 
