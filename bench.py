@@ -388,6 +388,17 @@ def run_reference(args):
     return 0
 
 
+def simt_kernel_tag(d1):
+    """Which CUDA-core FP32 kernel the library picks for a Base density hint
+    d1 (< 0: unknown): the zero-skip kernel below 0.16, else the dense one."""
+    return "simt_gemm" if 0.0 <= d1 < 0.16 else "simt_dense_kernel"
+
+
+def ffma_peak_tflops():
+    """Nominal FP32 FFMA rate at the maximum SM clock."""
+    return SMS * FFMA_PER_SM_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
 def traffic_from_profile(kernel_tag, workload):
     """Bytes per launch from the committed ncu summary, if it still matches
     the kernel source (else None)."""
@@ -395,7 +406,8 @@ def traffic_from_profile(kernel_tag, workload):
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload}.txt")
     if not os.path.exists(path):
         return None
-    src = {"simt_gemm": "simt_gemm.cu", "tc_gemm": "tc_gemm.cu",
+    src = {"simt_gemm": "simt_gemm.cu", "simt_dense_kernel": "simt_dense.cu",
+           "tc_gemm": "tc_gemm.cu",
            "tc_gemm_fp8": "tc_gemm.cu", "tc_gemm_real": "tc_gemm.cu",
            "tc_exact2": "tc_gemm.cu", "tc_pair_kernel": "tc_gemm.cu",
            "sparse": "sparse.cu"}.get(kernel_tag)
@@ -551,11 +563,10 @@ def run_afmm(args):
         tag = "tc_exact2" if vname == "tc_exact" else ("tc_pair_kernel" if pair else "tc_gemm")
     else:
         alg = flops
-        sm_mhz = SM_MAX_MHZ
-        peak = SMS * FFMA_PER_SM_PER_CLK * 2 * sm_mhz * 1e6 / 1e12
+        peak = ffma_peak_tflops()
         roof = {"bound": "alu", "unit": "TFLOP/s",
-                "peak_src": f"FP32 FFMA {SMS} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
-        tag = "simt_gemm"
+                "peak_src": f"FP32 FFMA {SMS} SMs x 128 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"}
+        tag = simt_kernel_tag(prm["d1"])
     if vname != "sparse":
         achieved = alg / (kms * 1e-3) / 1e12
         roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
@@ -570,7 +581,9 @@ def run_afmm(args):
         p2 = Plan(desc(0))
         ms2, kms2, _, _ = timed(p2, max(2, min(args.steps // 4, 100)), 3)
         plain = {"variant": "simt_f32", "value": flops / (ms2 * 1e-3) / 1e12,
-                 "ms_per_step": ms2, "kernel_ms": kms2}
+                 "ms_per_step": ms2, "kernel_ms": kms2,
+                 "kernel": simt_kernel_tag(prm["d1"]),
+                 "kernel_frac_of_ffma_peak": flops / (kms2 * 1e-3) / 1e12 / ffma_peak_tflops()}
         p2.close()
 
     # The split of the real factor done inside the product kernel instead of

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libafmm.so")
 
-SOURCES = ["api.cu", "scan.cu", "convert.cu", "simt_gemm.cu", "norm.cu",
+SOURCES = ["api.cu", "scan.cu", "convert.cu", "simt_gemm.cu", "simt_dense.cu", "norm.cu",
            "tc_gemm.cu", "noalloc.cu", "batched_kernels.cu", "batched.cpp", "mlp.cu",
            "tc_fused.cu", "sparse.cu", "tc_operands.cu", "tc_fp8.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -140,10 +140,20 @@ afmm_status launch_recombine_f64(const int32_t* P, int64_t ldp,
                                  cudaStream_t st);
 
 // K1: CUDA-core GEMMs, C (M x N) = A (M x K) * B (K x N), row-major.
-// FP32 FMA with zero-skip of A over 8-row groups and K-blocked sums.
+// FP32 FMA with zero-skip of A over 4-row groups and K-blocked sums.
 afmm_status launch_simt_f32(const float* A, int64_t lda, const float* B,
                             int64_t ldb, float* C, int64_t ldc, int64_t M,
                             int64_t N, int64_t K, cudaStream_t st);
+// FP32 FMA without zero-skip (simt_dense.cu), for dense Base factors: A
+// given transposed (AT, K x M, ldat a multiple of 4, 16-byte aligned, else
+// AFMM_ERR_INVALID_ARG), sums K-blocked over 128 k.
+afmm_status launch_simt_f32_dense(const float* AT, int64_t ldat, const float* B,
+                                  int64_t ldb, float* C, int64_t ldc, int64_t M,
+                                  int64_t N, int64_t K, cudaStream_t st);
+// dst = src^T as FP32 (n x n, src of afmm_dtype `dtype`, row strides lds
+// and ldd elements).
+afmm_status launch_to_f32_transposed(const void* src, int dtype, int64_t n, int64_t lds,
+                                     float* dst, int64_t ldd, cudaStream_t st);
 // int8 dot products: A int8 rows (lda bytes, multiple of 4), B packed
 // k-word-major int32 words (ldw words), C int32.
 afmm_status launch_simt_dp4a(const int8_t* A, int64_t lda, const int32_t* W,

@@ -32,26 +32,30 @@ def z_torch_dtype(z):
     return {"f32": torch.float32, "f64": torch.float64, "i32": torch.int32}[z]
 
 
-def desc_for(inst, variant=-1, flags=0, hints=True):
+def desc_for(inst, variant=-1, flags=0, hints=True, d1_hint=None):
+    """Descriptor of ``inst``; ``d1_hint`` overrides the X density hint
+    (hints steer kernel choice only, never the result)."""
     from afmm_inputs import density_hints
     from paper_1308_2400_gb300 import make_desc
     d1 = d2 = mp = -1.0
     if hints:
         p = density_hints(inst.X, inst.Y, inst.case)
         d1, d2, mp = p["d1"], p["d2"], p["mu_prime"]
+    if d1_hint is not None:
+        d1 = d1_hint
     return make_desc(inst.n, inst.case, inst.x_dtype, inst.y_dtype,
                      inst.z_dtype, inst.target, variant=variant, flags=flags,
                      d1=d1, d2=d2, mu_prime=mp)
 
 
-def run_gpu(inst, variant=-1, flags=0):
+def run_gpu(inst, variant=-1, flags=0, hints=True, d1_hint=None):
     """Z on the GPU through the C ABI; returns (Z numpy, plan info)."""
     import torch
     from paper_1308_2400_gb300 import Plan
     X, Y = gpu_operands(inst)
     Z = torch.full((inst.n, inst.n), float("nan") if inst.z_dtype != "i32"
                    else -7, dtype=z_torch_dtype(inst.z_dtype), device="cuda")
-    plan = Plan(desc_for(inst, variant, flags))
+    plan = Plan(desc_for(inst, variant, flags, hints, d1_hint))
     plan(X, Y, Z)
     plan.sync()
     info = plan.info

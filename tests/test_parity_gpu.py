@@ -26,21 +26,24 @@ from _helpers import (FP32_REL_FRO, FP64_REL_FRO, U32, U64, abs_product,
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SIMT_BK = 32          # k-tile of the CUDA-core kernel (K-blocked sums)
+SIMT_BK = 32          # k block of the zero-skip CUDA-core kernel
+DENSE_BK = 128        # k block of the dense CUDA-core kernel
 RAGGED = [1, 2, 7, 33, 63, 65, 127, 129, 257, 300]
 
 
 def simt_f32_elem_bound(inst, rows=None):
-    """Worst-case rounding of the K-blocked FP32 sum, to first order.
+    """Worst-case rounding of the K-blocked FP32 sums, to first order.
 
     Each product is formed exactly by the FMA and rounded once when added;
-    a k tile sums at most 32 terms from zero, then <= ceil(n/32) tile sums
-    are added to the running total: error <= (32 + ceil(n/32) + 1) u32
-    sum|x y| for each element, plus the rounding of the real factor to
-    FP32 (u32 each) when it arrives in FP64.
+    a k block sums at most b terms from zero (b = 32 in the zero-skip
+    kernel, 128 in the dense one), then <= ceil(n/b) block sums are added
+    to the running total: error <= (min(n, b) + ceil(n/b)) u32 sum|x y|
+    for each element.  (min(n, 128) + ceil(n/32)) covers both kernels; the
+    rounding of the real factor to FP32 (u32) when it arrives in FP64 and a
+    unit of slack make the +2.
     """
     n = inst.n
-    g = (SIMT_BK + -(-n // SIMT_BK) + 2) * U32
+    g = (min(n, DENSE_BK) + -(-n // SIMT_BK) + 2) * U32
     return g * abs_product(inst, rows) + 1e-30
 
 
@@ -79,8 +82,20 @@ def test_simt_f32_ragged(workload, n):
     check_fp32(inst, Z)
 
 
-def test_simt_f32_sparse_base_skips():
-    """Very sparse Base factor: whole 8-row groups are zero for most k."""
+@pytest.mark.parametrize("n", [1, 65, 129, 300])
+def test_simt_f32_skip_kernel_on_dense_data(n):
+    """A low density hint picks the zero-skip kernel; on dense data it takes
+    its all-k path and must give the same sums (hints never change Z)."""
+    inst = W.make("caseA_n8192_e4m3", n=n, seed=n + 5)
+    Z, _ = run_gpu(inst, variant=0, d1_hint=0.05)
+    check_fp32(inst, Z)
+
+
+@pytest.mark.parametrize("hints", [True, False])
+def test_simt_f32_sparse_base_skips(hints):
+    """Very sparse Base factor: whole 4-row groups are zero for most k.
+    With its density hint (0.03) the zero-skip kernel runs; without hints
+    the dense kernel does."""
     rng = np.random.default_rng(3)
     n = 515
     X = rng.uniform(-1, 1, size=(n, n)).astype(np.float32)
@@ -89,9 +104,32 @@ def test_simt_f32_sparse_base_skips():
     Y = rng.integers(0, 10, size=(n, n)).astype(np.int32)
     inst = W.Instance("A", X, Y, name="sparse", x_dtype="f32", y_dtype="i32",
                       z_dtype="f32", target="fp32")
-    Z, _ = run_gpu(inst, variant=0)
+    Z, _ = run_gpu(inst, variant=0, hints=hints)
     check_fp32(inst, Z)
     assert np.all(Z[64:128] == 0)
+
+
+def test_simt_f32_strided_operands():
+    """Leading dimensions that are not multiples of 4 take the scalar loads
+    and stores of both kernels."""
+    from paper_1308_2400_gb300 import Plan, make_desc
+    n, ld = 203, 207
+    for d1 in (-1.0, 0.05):
+        inst = W.make("caseA_n8192_e4m3", n=n, seed=11)
+        X = torch.zeros((n, ld), dtype=torch.float32)
+        X[:, :n] = torch.from_numpy(inst.X.astype(np.float32))
+        Y = torch.zeros((n, ld), dtype=torch.uint8)
+        Y[:, :n] = torch.from_numpy(inst.Y.astype(np.uint8))
+        Z = torch.full((n, ld), float("nan"))
+        X, Y, Z = X.cuda(), Y.cuda(), Z.cuda()
+        plan = Plan(make_desc(n, "A", "f32", "u8", "f32", "fp32", variant=0,
+                              d1=d1, ldx=ld, ldy=ld, ldz=ld))
+        plan(X, Y, Z)
+        plan.sync()
+        plan.close()
+        Zn = Z.cpu().numpy()
+        check_fp32(inst, Zn[:, :n].copy())
+        assert np.all(np.isnan(Zn[:, n:]))
 
 
 def test_simt_f32_case_b_full_size_sampled():
