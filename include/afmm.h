@@ -283,6 +283,13 @@ typedef struct {
     double timed_ms;           /* their summed duration, milliseconds */
     int32_t main_kernel_ctas;  /* grid size of the last main-kernel launch */
     int32_t reserved_;
+    /* Plain FP32 variant on its zero-skip kernel (Base density hint below
+     * 0.16): the 32-wide k tiles its CTAs multiplied since the workspace
+     * was bound, summed over calls.  A CTA skips a k tile whose 64 x 32 tile
+     * of the first factor or 32 x 256 tile of the second is all zero (the
+     * K0 tile masks, Sec. 2's zero-skip at tile granularity).  Read with a
+     * device synchronisation; -1 for every other variant. */
+    int64_t simt_k_tiles;
 } afmm_counters;
 
 /* Enable (1) or disable (0) event timing of the main kernel; enabling

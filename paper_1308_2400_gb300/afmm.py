@@ -88,7 +88,8 @@ class afmm_info(ctypes.Structure):
 class afmm_counters(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("timed_launches", ctypes.c_int64), ("timed_ms", ctypes.c_double),
-                ("main_kernel_ctas", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("main_kernel_ctas", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("simt_k_tiles", ctypes.c_int64)]
 
 
 AFMM_DISPATCH_FEATURES = 10

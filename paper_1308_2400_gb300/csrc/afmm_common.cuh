@@ -140,10 +140,23 @@ afmm_status launch_recombine_f64(const int32_t* P, int64_t ldp,
                                  cudaStream_t st);
 
 // K1: CUDA-core GEMMs, C (M x N) = A (M x K) * B (K x N), row-major.
-// FP32 FMA with zero-skip of A over 4-row groups and K-blocked sums.
+// FP32 FMA with zero-skip of A over 4-row groups and K-blocked sums.  With
+// the K0 tile masks xm, ym (launch_tile_masks) a CTA loads and multiplies
+// only the 32-wide k tiles whose A and B tiles both hold a non-zero, and
+// adds their number to *ktiles (when given).
 afmm_status launch_simt_f32(const float* A, int64_t lda, const float* B,
                             int64_t ldb, float* C, int64_t ldc, int64_t M,
-                            int64_t N, int64_t K, cudaStream_t st);
+                            int64_t N, int64_t K, cudaStream_t st,
+                            const uint8_t* xm = nullptr, const uint8_t* ym = nullptr,
+                            unsigned long long* ktiles = nullptr);
+// K0 tile masks for launch_simt_f32: one byte per 64 x 32 tile of A
+// ([ceil(M/64)][ceil(K/32)]) and per 32 x 256 tile of B ([ceil(K/32)]
+// [ceil(N/256)]), 1 when the tile holds a non-zero.  simt_mask_bytes gives
+// the bytes of both (B's at *ym_offset, 16-byte aligned).
+size_t simt_mask_bytes(int64_t M, int64_t N, int64_t K, size_t* ym_offset);
+afmm_status launch_tile_masks(const float* A, int64_t lda, const float* B, int64_t ldb,
+                              int64_t M, int64_t N, int64_t K, uint8_t* xm, uint8_t* ym,
+                              cudaStream_t st);
 // FP32 FMA without zero-skip (simt_dense.cu), for dense Base factors: A
 // given transposed (AT, K x M, ldat a multiple of 4, 16-byte aligned, else
 // AFMM_ERR_INVALID_ARG), sums K-blocked over 128 k.

@@ -276,8 +276,9 @@ void plan_layout(afmm_plan_s* p) {
             if (simt_dense(d)) {
                 p->lda = round_up(n, 4);
                 p->off_a = L.take((size_t)n * p->lda * 4);      // X^T
-            } else if (d.x_dtype != AFMM_F32) {
-                p->off_a = L.take(nn * 4);
+            } else {
+                if (d.x_dtype != AFMM_F32) p->off_a = L.take(nn * 4);
+                p->off_c = L.take(simt_mask_bytes(n, n, n, nullptr));   // K0 tile masks
             }
             if (d.y_dtype != AFMM_F32) p->off_b = L.take(nn * 4);
             break;
@@ -378,6 +379,12 @@ T* wsp(afmm_plan_s* p, size_t off) {
     return reinterpret_cast<T*>(p->ws + off);
 }
 
+// The zero-skip kernel's count of multiplied k tiles: a 64-bit word after
+// the status word (zeroed with it when the workspace is bound).
+unsigned long long* simt_ktiles(afmm_plan_s* p) {
+    return reinterpret_cast<unsigned long long*>(p->ws + p->off_status + 8);
+}
+
 afmm_status run_simt_f32(afmm_plan_s* p, const void* X, const void* Y, void* Z,
                          cudaStream_t st) {
     const afmm_desc& d = p->d;
@@ -406,8 +413,13 @@ afmm_status run_simt_f32(afmm_plan_s* p, const void* X, const void* Y, void* Z,
         B = wsp<float>(p, p->off_b);
         ldb = n;
     }
+    // K0 tile masks: k tiles whose A or B tile is all zero are not loaded.
+    size_t ym_off = 0;
+    simt_mask_bytes(n, n, n, &ym_off);
+    uint8_t* xm = wsp<uint8_t>(p, p->off_c);
+    AFMM_TRY(launch_tile_masks(A, lda, B, ldb, n, n, n, xm, xm + ym_off, st));
     return launch_simt_f32(A, lda, B, ldb, static_cast<float*>(Z),
-                           d.ldz ? d.ldz : n, n, n, n, st);
+                           d.ldz ? d.ldz : n, n, n, n, st, xm, xm + ym_off, simt_ktiles(p));
 }
 
 afmm_status run_simt_exact(afmm_plan_s* p, const void* X, const void* Y,
@@ -966,6 +978,12 @@ afmm_status afmm_plan_counters(afmm_plan p, afmm_counters* out) {
     out->timed_ms = p->timed_ms;
     out->main_kernel_ctas = p->last_ctas;
     out->reserved_ = 0;
+    out->simt_k_tiles = -1;
+    if (p->variant == AFMM_VARIANT_SIMT_F32 && !simt_dense(p->d) && p->ws_ready) {
+        unsigned long long v = 0;
+        AFMM_CUDA_TRY(cudaMemcpy(&v, simt_ktiles(p), sizeof(v), cudaMemcpyDeviceToHost));
+        out->simt_k_tiles = (int64_t)v;
+    }
     return AFMM_OK;
 }
 

@@ -20,8 +20,8 @@ import numpy as np
 import pytest
 
 import afmm_inputs as W
-from _helpers import (FP32_REL_FRO, FP64_REL_FRO, U32, U64, abs_product,
-                      oracle_rows, rel_fro, run_gpu, sample_rows, torch_of)
+from _helpers import (FP32_REL_FRO, FP64_REL_FRO, U32, U64, abs_product, desc_for,
+                      gpu_operands, oracle_rows, rel_fro, run_gpu, sample_rows, torch_of)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -878,3 +878,72 @@ def test_degenerate_inputs(variant, kind):
         assert rel_fro(Z, R) <= FP64_REL_FRO
     else:
         assert rel_fro(Z, R) <= FP32_REL_FRO
+
+
+# ------------------------------------------------------- K0 tile masks (K1)
+def _expected_k_tiles(A, B):
+    """k tiles the zero-skip kernel multiplies: per 64 x 256 output tile,
+    the 32-wide k tiles whose 64 x 32 tile of A and 32 x 256 tile of B both
+    hold a non-zero (counted here from the data, in numpy)."""
+    n = A.shape[0]
+    mb, kb, nb = -(-n // 64), -(-n // 32), -(-n // 256)
+    xm = np.zeros((mb, kb), bool)
+    ym = np.zeros((kb, nb), bool)
+    for i in range(mb):
+        for t in range(kb):
+            xm[i, t] = np.any(A[i * 64:(i + 1) * 64, t * 32:(t + 1) * 32] != 0)
+    for t in range(kb):
+        for j in range(nb):
+            ym[t, j] = np.any(B[t * 32:(t + 1) * 32, j * 256:(j + 1) * 256] != 0)
+    return int((xm.astype(np.int64) @ ym.astype(np.int64)).sum())
+
+
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_simt_tile_masks_skip_zero_blocks(case):
+    """Zero bands and blocks in both factors: the zero-skip kernel multiplies
+    exactly the k tiles the masks leave live, and Z matches the oracle."""
+    from paper_1308_2400_gb300 import Plan
+    rng = np.random.default_rng(21 if case == "A" else 22)
+    n = 515
+    real = rng.uniform(-1, 1, size=(n, n)).astype(np.float32)
+    real[rng.random((n, n)) > 0.3] = 0
+    rep = rng.poisson(3.0, size=(n, n)).astype(np.int32)
+    if case == "A":
+        X, Y = real, rep
+    else:
+        X, Y = rep, real
+    X[:, 64:160] = 0                    # k tiles 2..4 of every row block
+    X[128:256, :] = 0                   # row blocks 2 and 3
+    Y[320:352, 0:256] = 0               # k tile 10 of column block 0
+    Y[480:, 256:512] = 0                # k tiles 15, 16 of column block 1
+    inst = W.Instance(case, X, Y, name="blocks" + case, x_dtype="f32" if case == "A" else "i32",
+                      y_dtype="i32" if case == "A" else "f32", z_dtype="f32",
+                      target="fp32")
+    Xg, Yg = torch_of(X), torch_of(Y)
+    Z = torch.full((n, n), float("nan"), device="cuda")
+    plan = Plan(desc_for(inst, variant=0, d1_hint=0.05))
+    plan(Xg, Yg, Z)
+    plan.sync()
+    got = plan.counters()["simt_k_tiles"]
+    plan(Xg, Yg, Z)
+    plan.sync()
+    again = plan.counters()["simt_k_tiles"]
+    plan.close()
+    want = _expected_k_tiles(X.astype(np.float32), Y.astype(np.float32))
+    assert want < -(-n // 64) * -(-n // 256) * -(-n // 32)     # some tiles skipped
+    assert got == want and again == 2 * want
+    Zn = Z.cpu().numpy()
+    check_fp32(inst, Zn)
+    assert np.all(Zn[128:256] == 0)
+
+
+def test_simt_dense_kernel_reports_no_k_tiles():
+    from paper_1308_2400_gb300 import Plan
+    inst = W.make("caseA_n8192_e4m3", n=130, seed=4)
+    plan = Plan(desc_for(inst, variant=0))
+    X, Y = gpu_operands(inst)
+    Z = torch.empty((inst.n, inst.n), device="cuda")
+    plan(X, Y, Z)
+    plan.sync()
+    assert plan.counters()["simt_k_tiles"] == -1
+    plan.close()
