@@ -14,7 +14,8 @@ over ranks; each rank computes its own independent product, no collective).
 
 Beside the main form the line reports, on the same data, the plain FP32
 CUDA-core form (plain_fp32), two BF16 slices (two_slices), the FP8 form
-(fp8_slices), the split done inside the product kernel (fused_split) and a
+(fp8_slices), two FP16 slices (f16_slices), the split done inside the
+product kernel (fused_split) and a
 product of two real matrices, X times itself (real_x_real); --quick leaves
 them out.  --variant 8 makes that real x real product the main one.
 
@@ -558,7 +559,7 @@ def run_afmm(args):
         roof = {"bound": "tensor", "unit": "TFLOP/s",
                 "peak_src": f"{bf16_src}, {peak_src}"}
         # The split forms run on CTA pairs from n = 512 (AFMM_TC_PAIR=0: one CTA).
-        pair = (vname in ("tc_bf16x3", "tc_bf16x2") and n >= 512
+        pair = (vname in ("tc_bf16x3", "tc_bf16x2", "tc_f16x2") and n >= 512
                 and os.environ.get("AFMM_TC_PAIR", "1") != "0")
         tag = "tc_exact2" if vname == "tc_exact" else ("tc_pair_kernel" if pair else "tc_gemm")
     else:
@@ -624,6 +625,23 @@ def run_afmm(args):
               "peak_src": f"2 x bf16 measured (nominal fp8/bf16 ratio), {peak_src}"}
         Z_f8 = Z.cpu().numpy() if ws == 1 else None
         p5.close()
+
+    # The FP16 two-slice form on the same data (Case A): X as two row-scaled
+    # FP16 slices, two MMAs per K step at the BF16 rate; its error below.
+    h16 = None
+    Z_h16 = None
+    if rank == 0 and vname == "tc_bf16x3" and inst.case == "A" and not args.quick:
+        p7 = Plan(desc(10))
+        k7 = max(2, min(args.steps // 4, 100))
+        ms7, kms7, _, _ = timed(p7, k7, 3)
+        tf7 = 2 * flops / (kms7 * 1e-3) / 1e12
+        pk7 = tensor_peak(peaks, ms7 * k7 * 1e-3)
+        h16 = {"variant": "tc_f16x2", "value": flops / (ms7 * 1e-3) / 1e12,
+               "ms_per_step": ms7, "kernel_ms": kms7, "tensor_tflops": tf7,
+               "peak": pk7[0], "frac": tf7 / pk7[0],
+               "peak_src": f"{pk7[1]} (FP16 and BF16 share the rate), {peak_src}"}
+        Z_h16 = Z.cpu().numpy() if ws == 1 else None
+        p7.close()
 
     # A product of two real matrices (no Rep-factor) with the workload's X as
     # both factors: both split into three BF16 slices, six slice products.
@@ -693,6 +711,9 @@ def run_afmm(args):
         if f8 is not None and Z_f8 is not None:
             d8 = float(np.linalg.norm(Z_f8[rows].astype(np.float64) - Zr))
             f8["rel_fro_err_vs_oracle"] = d8 / den if den else 0.0
+        if h16 is not None and Z_h16 is not None:
+            dh = float(np.linalg.norm(Z_h16[rows].astype(np.float64) - Zr))
+            h16["rel_fro_err_vs_oracle"] = dh / den if den else 0.0
         if rr is not None and Z_rr is not None:
             r16 = rows[:16]
             Rr = oracle_classical_rows(inst.X, inst.X, r16)
@@ -705,7 +726,7 @@ def run_afmm(args):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": ("e4m3" if vname == "tc_fp8x4" else "bf16") if tc else
+            "dtype": ({"tc_fp8x4": "e4m3", "tc_f16x2": "f16"}.get(vname, "bf16")) if tc else
                      ("f64" if inst.target == "fp64" else
                                         ("i8" if inst.target == "exact" else "f32")),
             "data": "synthetic",
@@ -714,7 +735,7 @@ def run_afmm(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches) * ws, "clocks": clocks,
             "accuracy": acc, "plain_fp32": plain, "fused_split": fused,
-            "two_slices": two, "fp8_slices": f8, "real_x_real": rr,
+            "two_slices": two, "fp8_slices": f8, "f16_slices": h16, "real_x_real": rr,
         }
         print(json.dumps(line), flush=True)
     plan.close()

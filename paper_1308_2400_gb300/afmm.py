@@ -43,6 +43,7 @@ AFMM_VARIANT_SPARSE = 6
 AFMM_VARIANT_TC_FP8X4 = 7
 AFMM_VARIANT_TC_BF16X3X3 = 8
 AFMM_VARIANT_TC_BF16X3_N128 = 9
+AFMM_VARIANT_TC_F16X2 = 10
 AFMM_FLAG_VALIDATE = 0x1
 AFMM_FLAG_FUSED_SPLIT = 0x2
 
@@ -54,6 +55,7 @@ VARIANT_NAMES = {
     AFMM_VARIANT_SPARSE: "sparse", AFMM_VARIANT_TC_FP8X4: "tc_fp8x4",
     AFMM_VARIANT_TC_BF16X3X3: "tc_bf16x3x3",
     AFMM_VARIANT_TC_BF16X3_N128: "tc_bf16x3_n128",
+    AFMM_VARIANT_TC_F16X2: "tc_f16x2",
 }
 CASE_CODES = {"A": AFMM_CASE_A, "B": AFMM_CASE_B, "REAL": AFMM_CASE_REAL}
 DTYPE_CODES = {"f64": AFMM_F64, "f32": AFMM_F32, "bf16": AFMM_BF16,

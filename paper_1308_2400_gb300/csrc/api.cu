@@ -215,6 +215,8 @@ bool variant_serves(int v, const afmm_desc* d) {
         case AFMM_VARIANT_TC_BF16X2:
         case AFMM_VARIANT_TC_FP8X4:
             return d->target == AFMM_TARGET_FP32 && tc_available();
+        case AFMM_VARIANT_TC_F16X2:
+            return d->target == AFMM_TARGET_FP32 && d->kase == AFMM_CASE_A && tc_available();
         case AFMM_VARIANT_SIMT_F64SLICE:
             return d->target == AFMM_TARGET_FP64;
         case AFMM_VARIANT_SIMT_EXACT:
@@ -328,8 +330,10 @@ void plan_layout(afmm_plan_s* p) {
             p->off_c = L.take(p->tc.z_bytes);
             break;
         }
-        case AFMM_VARIANT_TC_FP8X4: {
-            tc_layout(&p->tc, d, p->slices, true);
+        case AFMM_VARIANT_TC_FP8X4:
+        case AFMM_VARIANT_TC_F16X2: {
+            tc_layout(&p->tc, d, p->slices, p->variant == AFMM_VARIANT_TC_FP8X4,
+                      p->variant == AFMM_VARIANT_TC_F16X2);
             p->off_a = L.take(p->tc.a_bytes);
             p->off_b = L.take(p->tc.b_bytes);
             p->off_c = L.take(p->tc.z_bytes);
@@ -365,7 +369,7 @@ afmm_status ensure_workspace(afmm_plan_s* p, cudaStream_t st) {
         if (p->variant == AFMM_VARIANT_TC_BF16X3 ||
             p->variant == AFMM_VARIANT_TC_BF16X2 ||
             p->variant == AFMM_VARIANT_TC_EXACT || p->variant == AFMM_VARIANT_TC_FP8X4 ||
-            p->variant == AFMM_VARIANT_TC_BF16X3X3)
+            p->variant == AFMM_VARIANT_TC_BF16X3X3 || p->variant == AFMM_VARIANT_TC_F16X2)
             AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a, p->ws + p->off_b,
                                        p->ws + p->off_c, p->ws + p->off_e));
         if (p->variant == AFMM_VARIANT_SPARSE) AFMM_TRY(sparse_reset(p->ws + p->off_a, st));
@@ -513,6 +517,8 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
             return tc_run_exact(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_TC_FP8X4:
             return tc_run_fp8(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
+        case AFMM_VARIANT_TC_F16X2:
+            return tc_run_h16(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_TC_BF16X3X3:
             return tc_run_real(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_SPARSE:
@@ -797,6 +803,8 @@ afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc) {
         p->slices = 2;
     } else if (v == AFMM_VARIANT_TC_FP8X4) {
         p->slices = 4;
+    } else if (v == AFMM_VARIANT_TC_F16X2) {
+        p->slices = 2;
     } else if (v == AFMM_VARIANT_TC_BF16X3X3) {
         p->slices = 3;
     }

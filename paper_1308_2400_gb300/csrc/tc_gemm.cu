@@ -45,6 +45,7 @@
 
 #include "afmm_common.cuh"
 #include "elem.cuh"
+#include "fp16_split.cuh"
 #include "fp8_split.cuh"
 #include "ptx_sm100.cuh"
 #include "tc_gemm.cuh"
@@ -137,7 +138,7 @@ __device__ __forceinline__ void raise_abort(TcBars* b, int* status) {
 // ones, an error that grows with the number of additions; so the hi sum is
 // closed every kbpc k-blocks (kbpc > 0) and handed to the epilogue, which
 // adds the chunks in FP32 registers (round to nearest) while the MMAs wait.
-template <int SA, int SB, bool TOUT = false, bool F8 = false>
+template <int SA, int SB, bool TOUT = false, bool F8 = false, bool H16 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB, float* __restrict__ Z,
@@ -148,6 +149,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     constexpr int BK = F8 ? 64 : TC_BK;
     constexpr int HI = F8 ? 3 : 1;
     static_assert(!F8 || (SA == 4 && SB == 1), "FP8 form: four A slices");
+    static_assert(!H16 || (SA == 2 && SB == 1 && !F8), "FP16 form: two A slices");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
     uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -239,8 +241,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
     } else if (warp == 1) {
         // ---------------------------------------------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t IDESC = F8 ? ptx::idesc_e4m3_f32(TC_BM, TC_BN)
-                                          : ptx::idesc_bf16_f32(TC_BM, TC_BN);
+            constexpr uint32_t IDESC = F8    ? ptx::idesc_e4m3_f32(TC_BM, TC_BN)
+                                       : H16 ? ptx::idesc_f16_f32(TC_BM, TC_BN)
+                                             : ptx::idesc_bf16_f32(TC_BM, TC_BN);
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
@@ -364,15 +367,29 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
             }
             ptx::tc_fence_after();
             const int64_t m = (int64_t)m0 + (int64_t)tm * TC_BM + row;
-            // F8: row m was scaled by 2^sh; 2^-sh as two exact factors.
+            // F8, H16: row m was scaled by 2^sh; 2^-sh as two exact factors.
             float f1 = 1.f, f2 = 1.f;
-            if constexpr (F8) {
-                const int sh = m < M ? f8_row_shift(amax[m]) : 0;
+            if constexpr (F8 || H16) {
+                const int sh = m < M ? (F8 ? f8_row_shift(amax[m]) : h16_row_shift(amax[m])) : 0;
                 const int e1 = max(-sh, -126);
                 f1 = f8_pow2(e1);
                 f2 = f8_pow2(-sh - e1);
             }
-            if constexpr (F8) {
+            if constexpr (H16) {
+                // hi sum plus the lo sum times 2^-8 (one rounding), times
+                // the row's scale (exact).
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    uint32_t r0[16], r1[16];
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
+                    ptx::tmem_ld_16cols(lane_base + (uint32_t)(TC_BN + c * 16), r1);
+                    ptx::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        sum[c * 16 + j] = fmaf(__uint_as_float(r1[j]), 0x1p-8f,
+                                               __uint_as_float(r0[j])) * f1 * f2;
+                }
+            } else if constexpr (F8) {
                 // Last chunk of the hi sum plus the small sum times 2^-12
                 // (one rounding), times the row's scale (exact); 16 columns
                 // per load, so sum[] and the loads fit the registers.
@@ -525,13 +542,15 @@ __device__ __forceinline__ PairUnit pair_unit(int u, int whole, int split, int t
     return w;
 }
 
-template <int SA, bool TOUT>
+template <int SA, bool TOUT, bool H16 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmB64, float* __restrict__ Z, int64_t ldz,
-               int m0, int M, int n0, int N, int K, int vec, int split, int* status) {
+               int m0, int M, int n0, int N, int K, int vec, int split, int* status,
+               const uint32_t* __restrict__ amax) {
     using Cfg = PairCfg<SA>;
+    static_assert(!H16 || SA == 2, "FP16 form: two A slices");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
     uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -642,7 +661,8 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
             bool ok = true;
             for (int u = pair; ok && u < num_units; u += npairs) {
                 const int width = u < whole ? PR_BN : PR_BN / split;
-                const uint32_t IDESC = ptx::idesc_bf16_f32(PR_BM, width);
+                const uint32_t IDESC = H16 ? ptx::idesc_f16_f32(PR_BM, width)
+                                           : ptx::idesc_bf16_f32(PR_BM, width);
                 if (!ptx::mbar_wait_cluster_bounded(&bars->tempty[0], tphase ^ 1u, abort,
                                                     WAIT_LIMIT_NS)) {
                     ok = false;
@@ -713,18 +733,33 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
             ptx::tc_fence_after();
             // A 128-wide part has columns for the h = 0 warps only.
             const bool live = h * 128 < w.width;
+            const int64_t m = (int64_t)m0 + (int64_t)w.tm * PR_BM + (int64_t)rank * PR_HALF + row;
             float sum[128];
             if (live) {
+                // H16: row m was scaled by 2^sh; 2^-sh as two exact factors.
+                float f1 = 1.f, f2 = 1.f;
+                if constexpr (H16) {
+                    const int sh = m < M ? h16_row_shift(amax[m]) : 0;
+                    const int e1 = max(-sh, -126);
+                    f1 = f8_pow2(e1);
+                    f2 = f8_pow2(-sh - e1);
+                }
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    // hi-slice sum + small-slice sum, one rounding.
+                    // hi-slice sum + small-slice sum (H16: times 2^-8), one
+                    // rounding; H16 then the row's scale (exact).
                     uint32_t r0[16], r1[16];
                     ptx::tmem_ld_16cols(lane_base + (uint32_t)(c * 16), r0);
                     ptx::tmem_ld_16cols(lane_base + (uint32_t)(PR_BN + c * 16), r1);
                     ptx::tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        sum[c * 16 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    for (int j = 0; j < 16; ++j) {
+                        if constexpr (H16)
+                            sum[c * 16 + j] = fmaf(__uint_as_float(r1[j]), 0x1p-8f,
+                                                   __uint_as_float(r0[j])) * f1 * f2;
+                        else
+                            sum[c * 16 + j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    }
                 }
             }
             // This warp's TMEM lanes are free again before the stores.
@@ -733,9 +768,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
             if (lane == 0) ptx::mbar_arrive_cluster(tempty0);
             tphase ^= 1u;
             if (!live) continue;
-            const int tm = w.tm, tn = w.tn;
-            const int64_t m = (int64_t)m0 + (int64_t)tm * PR_BM + (int64_t)rank * PR_HALF + row;
-            const int col0 = n0 + tn * PR_BN + w.col + h * 128;
+            const int col0 = n0 + w.tn * PR_BN + w.col + h * 128;
             if (TOUT && m < M) {
                 // Element (m, col0 + j) of Z^T is Z[col0 + j][m]: a warp's
                 // lanes hold consecutive m, one 128-byte segment per store.
@@ -1032,7 +1065,7 @@ tc_exact2_kernel(const __grid_constant__ CUtensorMap tmA,
     }
 }
 
-template <int SA, int SB, bool TOUT = false, bool F8 = false>
+template <int SA, int SB, bool TOUT = false, bool F8 = false, bool H16 = false>
 afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaStream_t st,
                       int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
     using Cfg = TcCfg<SA, SB>;
@@ -1043,7 +1076,7 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
     if (n1 < 0) n1 = n;
     const int tiles = ((m1 - m0 + TC_BM - 1) / TC_BM) * ((n1 - n0 + TC_BN - 1) / TC_BN);
     const int grid = tiles < dp.sm_count ? tiles : dp.sm_count;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, TOUT, F8>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<SA, SB, TOUT, F8, H16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
@@ -1051,7 +1084,7 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
     std::memcpy(&ma, TOUT ? t->tmap_at : t->tmap_a, sizeof ma);
     std::memcpy(&mb, TOUT ? t->tmap_bt : t->tmap_b, sizeof mb);
     main_kernel_begin(st);
-    tc_gemm_kernel<SA, SB, TOUT, F8><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
+    tc_gemm_kernel<SA, SB, TOUT, F8, H16><<<grid, TC_THREADS, Cfg::SMEM, st>>>(
         ma, mb, Z, ldz, m0, m1, n0, n1, n, vec, status, t->amax, t->chunk_kb);
     AFMM_CUDA_TRY(cudaGetLastError());
     main_kernel_end(st, grid);
@@ -1061,7 +1094,7 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
 
 // Clusters of two CTAs (one per SM of a pair) that fit at once, for the
 // pair kernel's persistent grid; 0 when the device cannot co-schedule any.
-template <int SA, bool TOUT>
+template <int SA, bool TOUT, bool H16>
 int pair_clusters(int smem) {
     static int cached[64];
     static std::once_flag once;
@@ -1085,7 +1118,8 @@ int pair_clusters(int smem) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT, H16>, &cfg) !=
+        cudaSuccess) {
         cudaGetLastError();
         n = 0;
     }
@@ -1095,18 +1129,18 @@ int pair_clusters(int smem) {
 
 // The two-SM split product over rows [m0, m1) and columns [n0, n1) of the
 // product (Z^T's when TOUT).
-template <int SA, bool TOUT = false>
+template <int SA, bool TOUT = false, bool H16 = false>
 afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
                            cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
     using Cfg = PairCfg<SA>;
     const int n = (int)t->n;
     if (m1 < 0) m1 = n;
     if (n1 < 0) n1 = n;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT, H16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int tiles = ((m1 - m0 + PR_BM - 1) / PR_BM) * ((n1 - n0 + PR_BN - 1) / PR_BN);
-    const int cap = pair_clusters<SA, TOUT>(Cfg::SMEM);
+    const int cap = pair_clusters<SA, TOUT, H16>(Cfg::SMEM);
     if (cap < 1) return AFMM_ERR_UNSUPPORTED;
     const int clusters = tiles < cap ? tiles : cap;
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
@@ -1131,8 +1165,9 @@ afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     main_kernel_begin(st);
-    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT>, ma, mb, mb64, Z, ldz, m0,
-                                     m1, n0, n1, n, vec, split, status));
+    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT, H16>, ma, mb, mb64, Z,
+                                     ldz, m0, m1, n0, n1, n, vec, split, status,
+                                     (const uint32_t*)t->amax));
     main_kernel_end(st, 2 * clusters);
     count_launches(1);
     return AFMM_OK;
@@ -1143,6 +1178,15 @@ afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
 template <bool TOUT>
 afmm_status split_product(const TcPlan* t, float* Z, int64_t ldz, int* status,
                           cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
+    if (t->h16) {
+        // FP16 two-slice form (Case A).
+        if (t->pair) {
+            const afmm_status rc =
+                launch_tc_pair<2, TOUT, true>(t, Z, ldz, status, st, m0, m1, n0, n1);
+            if (rc != AFMM_ERR_UNSUPPORTED) return rc;
+        }
+        return launch_tc<2, 1, TOUT, false, true>(t, Z, ldz, status, st, m0, m1, n0, n1);
+    }
     if (t->pair) {
         const afmm_status rc =
             t->slices == 3 ? launch_tc_pair<3, TOUT>(t, Z, ldz, status, st, m0, m1, n0, n1)
@@ -1233,12 +1277,13 @@ double dtype_bound(int dt) {
 }
 }  // namespace
 
-void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8) {
+void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8, bool h16) {
     t->n = d.n;
     t->slices = slices;
     t->sliced_a = d.kase != AFMM_CASE_B;
     t->both = d.kase == AFMM_CASE_REAL;
     t->f8 = f8;
+    t->h16 = h16;
     t->ld_a = t->ld_b = (d.n + 7) / 8 * 8;
     if (f8) {
         // E4M3 operands: 16-byte aligned rows of one-byte elements; the
@@ -1288,6 +1333,7 @@ void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8) {
     t->rows_b = d.n;
     t->a_bytes = (size_t)sa * d.n * t->ld_a * 2;
     t->b_bytes = (size_t)sb * d.n * t->ld_b * 2;
+    if (h16) t->s_bytes = (size_t)d.n * sizeof(uint32_t);    // row maxima of X
     const int64_t ldz = d.ldz ? d.ldz : d.n;
     if (t->sliced_a && ldz % 4 != 0) {
         t->ld_z = (d.n + 3) / 4 * 4;
@@ -1416,6 +1462,27 @@ afmm_status tc_run_fp8(TcPlan* t, const afmm_desc& d, const void* X, const void*
     AFMM_TRY(tc_f8_transpose(false, Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, t->amax, status,
                              st));
     return launch_tc<4, 1, true, true>(t, Zf, d.ldz, status, st);
+}
+
+afmm_status tc_run_h16(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
+                       void* Z, int* status, cudaStream_t st) {
+    if (!t->maps_ready || !t->h16 || d.kase != AFMM_CASE_A) return AFMM_ERR_INVALID_ARG;
+    const int64_t n = d.n;
+    float* Zf = static_cast<float*>(Z);
+    // A = two row-scaled FP16 slices of X, B = Rep-factors Y transposed,
+    // FP16, exact up to 2048.
+    AFMM_TRY(tc_h16_rows(X, d.x_dtype, n, d.ldx, t->a, t->ld_a, t->amax, status, st));
+    AFMM_TRY(tc_widen_transpose_h16(Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, 2048.f, status, st,
+                                    true));
+    if (t->z) {
+        float* zt = static_cast<float*>(t->z);
+        AFMM_TRY((split_product<false>(t, zt, t->ld_z, status, st)));
+        AFMM_CUDA_TRY(cudaMemcpy2DAsync(Zf, d.ldz * sizeof(float), zt,
+                                        t->ld_z * sizeof(float), n * sizeof(float), n,
+                                        cudaMemcpyDeviceToDevice, st));
+        return AFMM_OK;
+    }
+    return split_product<false>(t, Zf, d.ldz, status, st);
 }
 
 afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,

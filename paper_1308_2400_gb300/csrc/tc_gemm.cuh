@@ -53,6 +53,9 @@ struct TcPlan {
     bool maps_ready = false;
     // Split form: run the two-SM (cta_group::2) product kernel.
     bool pair = false;
+    // FP16 two-slice form (fp16_split.cuh): FP16 operands, amax[m] sets
+    // the power of two row m of the real factor was scaled by.
+    bool h16 = false;
 };
 
 // TMA descriptor (written to `out`, 128 bytes, 64-byte aligned) of a stack
@@ -76,6 +79,19 @@ afmm_status tc_widen_rows(int slices, bool exact, const void* src, int dt, int64
 afmm_status tc_widen_transpose(int slices, bool exact, const void* src, int dt, int64_t n,
                                int64_t lds, void* dst, int64_t ldk, float lim, int* status,
                                cudaStream_t st, bool rep = false);
+// The same transposition, exact, to FP16 (the FP16 two-slice form's
+// Rep-factor operand; |value| <= lim and exact in FP16).
+afmm_status tc_widen_transpose_h16(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                                   int64_t ldk, float lim, int* status, cudaStream_t st,
+                                   bool rep);
+// FP16 two-slice form (tc_f16.cu): rows [r0, r1) of the real factor
+// (row-major n x n) as two FP16 slices dst[(s * n + r) * ldk + c] (ldk a
+// multiple of 8, zero for n <= c < ldk), row r scaled by 2^h16_row_shift
+// (amax[r]), amax[r] = FP32 bits of the row's largest |value|.  A
+// non-finite value records AFMM_ERR_OVERFLOW_RISK.
+afmm_status tc_h16_rows(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                        int64_t ldk, uint32_t* amax, int* status, cudaStream_t st,
+                        int64_t r0 = 0, int64_t r1 = -1);
 
 // FP8 form conversions (tc_fp8.cu): dst E4M3 [slices][n][ldk], ldk a
 // multiple of 16.  rep: one slice that must equal the source (Rep-factors;
@@ -95,7 +111,8 @@ afmm_status tc_f8_transpose(bool rep, const void* src, int dt, int64_t n, int64_
 bool tc_available();
 // slices = 0 selects the exact-integer form (one BF16 operand each side);
 // f8 the FP8 form (four E4M3 slices).
-void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8 = false);
+// h16 the FP16 two-slice form (Case A, slices = 2).
+void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8 = false, bool h16 = false);
 // Largest K chunk (multiple of 32) with chunk * amax * bmax < 2^24, or 0
 // when even one 32-wide block could overflow.
 int tc_exact_chunk_k(double amax, double bmax);
@@ -109,6 +126,10 @@ afmm_status tc_run_real(TcPlan* t, const afmm_desc& d, const void* X, const void
                         void* Z, int* status, cudaStream_t st);
 // The FP8 form: E4M3 slices and Rep-factors, the tcgen05 product into Z.
 afmm_status tc_run_fp8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
+                       void* Z, int* status, cudaStream_t st);
+// The FP16 two-slice form (Case A): X as two row-scaled FP16 slices, Y as
+// FP16 Rep-factors, the tcgen05 product into Z.
+afmm_status tc_run_h16(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
                        void* Z, int* status, cudaStream_t st);
 // The same product in pieces for transfer pipelining: tc_split_prepare_b
 // converts the B operand (all of the factor that is not split by rows);

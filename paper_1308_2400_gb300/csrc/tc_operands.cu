@@ -1,6 +1,7 @@
 // Operand conversions for the tensor-core products (tc_gemm.cu): exact
-// widening of Rep-factors to BF16 and the hi/mid/lo BF16 split of real
-// values, rows kept (K-major A operand) or transposed (K-major B operand).
+// widening of Rep-factors to BF16 (or FP16, for the FP16 two-slice form)
+// and the hi/mid/lo BF16 split of real values, rows kept (K-major A
+// operand) or transposed (K-major B operand).
 // HBM-bound single passes.
 #include <cuda_bf16.h>
 
@@ -135,13 +136,13 @@ widen_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
 // (tile_transpose_convert: 16-byte loads, FP32 tile in shared memory,
 // 128-byte output row segments).  FP64 real factors are rounded to FP32
 // first (the FP32 target needs no more).
-template <int DT, int S, bool EXACT>
+template <int DT, int S, bool EXACT, bool H16 = false>
 __global__ void __launch_bounds__(256)
 widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                        __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim,
                        int vec, int* status, int rep) {
     __shared__ float tile[64][65];
-    const int bits = tile_transpose_convert<DT, S, EXACT>(
+    const int bits = tile_transpose_convert<DT, S, EXACT, H16>(
         src, n, lds, (int64_t)blockIdx.y * 64, (int64_t)blockIdx.x * 64, dst, ldk, lim,
         vec != 0, tile, rep != 0);
     if (bits) atomicCAS(status, 0, bad_status(bits));
@@ -149,13 +150,13 @@ widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
 
 // One-byte sources (E4M3, u8, i8): blocks of two stacked 64 x 64 tiles
 // (tile2_transpose_convert_u8), rows 128 * blockIdx.y ...
-template <int DT, int S, bool EXACT>
+template <int DT, int S, bool EXACT, bool H16 = false>
 __global__ void __launch_bounds__(256)
 widen_transpose2_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                         __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim, int vec,
                         int* status, int rep) {
     __shared__ float tile[2][64][65];
-    const int bits = tile2_transpose_convert_u8<DT, S, EXACT>(
+    const int bits = tile2_transpose_convert_u8<DT, S, EXACT, H16>(
         src, n, lds, (int64_t)blockIdx.y * 128, (int64_t)blockIdx.x * 64, dst, ldk, lim,
         vec != 0, tile, rep != 0);
     if (bits) atomicCAS(status, 0, bad_status(bits));
@@ -185,7 +186,7 @@ afmm_status launch_widen_rows(const void* src, int dt, int64_t n, int64_t lds,
     return AFMM_OK;
 }
 
-template <int S, bool EXACT>
+template <int S, bool EXACT, bool H16 = false>
 afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
                                    int64_t lds, __nv_bfloat16* dst, int64_t ldk,
                                    float lim, int* status, cudaStream_t st, bool rep) {
@@ -198,10 +199,10 @@ afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
             // Rows (of the source) in blocks of 128: the row tiles a block
             // holds must cover ldk, the destination's padded K extent.
             const dim3 grid2((unsigned)g, (unsigned)((n + 127) / 128));
-            widen_transpose2_kernel<DT, S, EXACT><<<grid2, block, 0, st>>>(
+            widen_transpose2_kernel<DT, S, EXACT, H16><<<grid2, block, 0, st>>>(
                 src, n, lds, dst, ldk, lim, vec, status, rep ? 1 : 0);
         } else {
-            widen_transpose_kernel<DT, S, EXACT><<<grid, block, 0, st>>>(
+            widen_transpose_kernel<DT, S, EXACT, H16><<<grid, block, 0, st>>>(
                 src, n, lds, dst, ldk, lim, vec, status, rep ? 1 : 0);
         }
         return AFMM_OK;
@@ -226,6 +227,14 @@ afmm_status tc_widen_rows(int slices, bool exact, const void* src, int dt, int64
     if (!exact && slices == 2)
         return launch_widen_rows<2, false>(src, dt, n, lds, d, ldk, lim, status, st, r0, r1, rep);
     return AFMM_ERR_INVALID_ARG;
+}
+
+afmm_status tc_widen_transpose_h16(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                                   int64_t ldk, float lim, int* status, cudaStream_t st,
+                                   bool rep) {
+    return launch_widen_transpose<1, true, true>(src, dt, n, lds,
+                                                 static_cast<__nv_bfloat16*>(dst), ldk, lim,
+                                                 status, st, rep);
 }
 
 afmm_status tc_widen_transpose(int slices, bool exact, const void* src, int dt, int64_t n,

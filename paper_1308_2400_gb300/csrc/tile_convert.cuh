@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 #include "bf16_split.cuh"
@@ -138,14 +139,42 @@ __device__ __forceinline__ int bad_status(int bits) {
            : bits ? (int)AFMM_ERR_OVERFLOW_RISK : 0;
 }
 
+// Two values as S BF16 slices (or, H16, one FP16 value each, S = 1) packed
+// into w[sl]; the check bits as in tile_store_transposed.
+template <int S, bool EXACT, bool H16>
+__device__ __forceinline__ int convert_pair(float v0, float v1, float lim, bool rep,
+                                            uint32_t (&w)[S]) {
+    int bits = 0;
+    if constexpr (H16) {
+        static_assert(S == 1 && EXACT, "FP16 output: exact values, one slice");
+        const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
+        if (__half2float(h0) != v0 || __half2float(h1) != v1 || fabsf(v0) > lim ||
+            fabsf(v1) > lim)
+            bits |= kBadRange;
+        w[0] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+    } else {
+        __nv_bfloat16 o0[S], o1[S];
+        split_bf16<S>(v0, o0);
+        split_bf16<S>(v1, o1);
+        if (EXACT && (__bfloat162float(o0[0]) != v0 || __bfloat162float(o1[0]) != v1 ||
+                      fabsf(v0) > lim || fabsf(v1) > lim))
+            bits |= kBadRange;
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) w[sl] = pack2(o0[sl], o1[sl]);
+    }
+    if (rep) bits |= rep_bits(v0) | rep_bits(v1);
+    return bits;
+}
+
 // The store half of tile_transpose_convert: tile[r - r0][c - c0] (FP32,
 // filled and synchronised by the caller) becomes rows c (K-major) of the
 // destination, dst[(s * n + c) * ldk + r] = slice s of the value, for S
 // BF16 slices; four threads write one 128-byte segment of an output row per
 // slice.  Returns the check bits of the values this thread converted:
 // kBadRange (EXACT: not exact in BF16 or |v| > lim) and, with `rep`, the
-// Rep-factor checks (rep_bits).  256 threads; `tile` is [64][65].
-template <int S, bool EXACT>
+// Rep-factor checks (rep_bits).  H16: FP16 instead of BF16 (S = 1, EXACT).
+// 256 threads; `tile` is [64][65].
+template <int S, bool EXACT, bool H16 = false>
 __device__ __forceinline__ int tile_store_transposed(const float (*tile)[65], int64_t n,
                                                      int64_t r0, int64_t c0,
                                                      __nv_bfloat16* __restrict__ dst,
@@ -162,16 +191,10 @@ __device__ __forceinline__ int tile_store_transposed(const float (*tile)[65], in
         uint32_t w[S][8];
 #pragma unroll
         for (int e = 0; e < 16; e += 2) {
-            __nv_bfloat16 o0[S], o1[S];
-            split_bf16<S>(v[e], o0);
-            split_bf16<S>(v[e + 1], o1);
-            if (EXACT && (__bfloat162float(o0[0]) != v[e] ||
-                          __bfloat162float(o1[0]) != v[e + 1] || fabsf(v[e]) > lim ||
-                          fabsf(v[e + 1]) > lim))
-                bits |= kBadRange;
-            if (rep) bits |= rep_bits(v[e]) | rep_bits(v[e + 1]);
+            uint32_t q[S];
+            bits |= convert_pair<S, EXACT, H16>(v[e], v[e + 1], lim, rep, q);
 #pragma unroll
-            for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
+            for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = q[sl];
         }
 #pragma unroll
         for (int sl = 0; sl < S; ++sl) {
@@ -192,7 +215,7 @@ __device__ __forceinline__ int tile_store_transposed(const float (*tile)[65], in
 // the Rep-factor checks (rep_bits) of every value in the matrix.
 // Loads: tile_load_f32; the tile goes through shared memory as FP32;
 // stores: tile_store_transposed.  256 threads; `tile` is [64][65].
-template <int DT, int S, bool EXACT>
+template <int DT, int S, bool EXACT, bool H16 = false>
 __device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ src,
                                                       int64_t n, int64_t lds, int64_t r0,
                                                       int64_t c0,
@@ -202,7 +225,7 @@ __device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ s
     bool bad = false;
     tile_load_f32<DT>(src, n, lds, r0, c0, lim, vec, tile, bad);
     __syncthreads();
-    const int bits = tile_store_transposed<S, EXACT>(tile, n, r0, c0, dst, ldk, lim, rep);
+    const int bits = tile_store_transposed<S, EXACT, H16>(tile, n, r0, c0, dst, ldk, lim, rep);
     return bits | ((EXACT && bad) ? kBadRange : 0);
 }
 
@@ -212,7 +235,7 @@ __device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ s
 // (e = 0 .. 7), so the 32 lanes of a warp (8 columns x 4 quarters) read 32
 // different banks; each run of 8 rows becomes one 16-byte store per slice,
 // and the four quarters of a column still fill its 128-byte output row.
-template <int S, bool EXACT>
+template <int S, bool EXACT, bool H16 = false>
 __device__ __forceinline__ int tile_store_transposed_il(const float (*tile)[65], int64_t n,
                                                         int64_t r0, int64_t c0,
                                                         __nv_bfloat16* __restrict__ dst,
@@ -233,16 +256,10 @@ __device__ __forceinline__ int tile_store_transposed_il(const float (*tile)[65],
         uint32_t w[S][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            __nv_bfloat16 o0[S], o1[S];
-            split_bf16<S>(v[e], o0);
-            split_bf16<S>(v[e + 1], o1);
-            if (EXACT && (__bfloat162float(o0[0]) != v[e] ||
-                          __bfloat162float(o1[0]) != v[e + 1] || fabsf(v[e]) > lim ||
-                          fabsf(v[e + 1]) > lim))
-                bits |= kBadRange;
-            if (rep) bits |= rep_bits(v[e]) | rep_bits(v[e + 1]);
+            uint32_t q[S];
+            bits |= convert_pair<S, EXACT, H16>(v[e], v[e + 1], lim, rep, q);
 #pragma unroll
-            for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = pack2(o0[sl], o1[sl]);
+            for (int sl = 0; sl < S; ++sl) w[sl][e / 2] = q[sl];
         }
 #pragma unroll
         for (int sl = 0; sl < S; ++sl)
@@ -261,7 +278,7 @@ __device__ __forceinline__ int tile_store_transposed_il(const float (*tile)[65],
 // quarters they take differ by 0, 8, 16, 24 in bank).  Store half:
 // tile_store_transposed_il.  `vec` as in tile_load_f32; `tile` is
 // [2][64][65].  Returns the check bits of both tiles.
-template <int DT, int S, bool EXACT>
+template <int DT, int S, bool EXACT, bool H16 = false>
 __device__ __forceinline__ int tile2_transpose_convert_u8(const void* __restrict__ src,
                                                           int64_t n, int64_t lds, int64_t r0,
                                                           int64_t c0,
@@ -307,8 +324,8 @@ __device__ __forceinline__ int tile2_transpose_convert_u8(const void* __restrict
 #pragma unroll
     for (int h = 0; h < 2; ++h)
         if (r0 + 64 * h < ldk)
-            bits |= tile_store_transposed_il<S, EXACT>(tile[h], n, r0 + 64 * h, c0, dst, ldk,
-                                                       lim, rep);
+            bits |= tile_store_transposed_il<S, EXACT, H16>(tile[h], n, r0 + 64 * h, c0, dst,
+                                                            ldk, lim, rep);
     return bits;
 }
 

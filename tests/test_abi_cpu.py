@@ -36,6 +36,21 @@ def test_binding_exposes_same_names():
         assert hasattr(P.afmm, name), name
 
 
+def test_binding_constants_match_header():
+    """Every AFMM_VARIANT_, AFMM_FLAG_ and AFMM_ERR_ value the header
+    defines has the same value in the Python binding."""
+    import paper_1308_2400_gb300 as P
+    src = open(os.path.join(ROOT, "include", "afmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    found = re.findall(r"\b(AFMM_(?:VARIANT|FLAG|ERR)_[A-Z0-9_]+)\s*=\s*(-?(?:0x)?[0-9A-Fa-f]+)u?",
+                       src)
+    assert len(found) >= 20
+    for name, val in found:
+        if name.endswith("COUNT_"):
+            continue
+        assert getattr(P.afmm, name) == int(val, 0), name
+
+
 def test_status_strings():
     import paper_1308_2400_gb300 as P
     assert P.afmm_status_string(0) == "AFMM_OK"
@@ -105,7 +120,8 @@ def test_real_by_real_descriptors():
     assert P.afmm_get_info(h)["variant"] == A.AFMM_VARIANT_SIMT_F32
     P.afmm_plan_destroy(h)
     for kase, v in (("REAL", A.AFMM_VARIANT_TC_FP8X4), ("REAL", A.AFMM_VARIANT_TC_BF16X3),
-                    ("A", A.AFMM_VARIANT_TC_BF16X3X3)):
+                    ("A", A.AFMM_VARIANT_TC_BF16X3X3), ("B", A.AFMM_VARIANT_TC_F16X2),
+                    ("REAL", A.AFMM_VARIANT_TC_F16X2)):
         with pytest.raises(P.AfmmError) as e:
             P.afmm_plan_create(P.make_desc(64, kase, "f32", "i32", "f32", "fp32",
                                            variant=v))

@@ -947,3 +947,75 @@ def test_simt_dense_kernel_reports_no_k_tiles():
     plan.sync()
     assert plan.counters()["simt_k_tiles"] == -1
     plan.close()
+
+
+# ------------------------------------------------------ FP16 two-slice form
+F16X2 = 10                      # AFMM_VARIANT_TC_F16X2
+F16_RAGGED = [1, 7, 33, 127, 129, 255, 257, 300, 513, 600]
+
+
+@pytest.mark.parametrize("n", F16_RAGGED)
+def test_tc_f16x2_ragged(n):
+    """Two FP16 slices, one-CTA kernel below n = 512, CTA pairs from it."""
+    inst = W.make("caseA_n8192_e4m3", n=n, seed=n + 7)
+    Z, info = run_gpu(inst, variant=F16X2)
+    assert info["variant"] == F16X2 and info["slices"] == 2
+    check_fp32(inst, Z, bound_fn=tc_elem_bound)
+
+
+def test_tc_f16x2_full_size_sampled():
+    inst = W.make("caseA_n8192_e4m3")
+    Z, _ = run_gpu(inst, variant=F16X2)
+    err = check_fp32(inst, Z, sample_rows(inst.n, 12), bound_fn=tc_elem_bound)
+    assert err < 5e-7
+
+
+def test_tc_f16x2_row_scales():
+    """Rows 2^-120 .. 2^100 apart, a zero row and a row of FP32 subnormals:
+    each row's own power of two keeps its slices in FP16's range."""
+    rng = np.random.default_rng(17)
+    n = 300
+    X = rng.uniform(-1, 1, size=(n, n))
+    X[rng.random((n, n)) > 0.7] = 0
+    X *= np.exp2(np.linspace(-120, 100, n)).reshape(n, 1)
+    X[5] = 0
+    X[6] = rng.uniform(-1, 1, n) * 1e-40
+    X = X.astype(np.float32)
+    Y = rng.integers(0, 17, size=(n, n)).astype(np.int32)
+    inst = W.Instance("A", X, Y, name="scales", x_dtype="f32", y_dtype="i32",
+                      z_dtype="f32", target="fp32")
+    Z, _ = run_gpu(inst, variant=F16X2)
+    check_fp32(inst, Z, bound_fn=tc_elem_bound)
+    assert np.all(Z[5] == 0)
+
+
+def test_tc_f16x2_rep_factor_limit():
+    """Rep-factors up to 2048 are exact in FP16; 2049 is refused."""
+    from paper_1308_2400_gb300 import AfmmError, Plan
+    from paper_1308_2400_gb300.afmm import AFMM_ERR_OVERFLOW_RISK
+    rng = np.random.default_rng(5)
+    n = 130
+    X = rng.uniform(-1, 1, size=(n, n)).astype(np.float32)
+    Y = rng.integers(0, 2049, size=(n, n)).astype(np.int32)
+    Y[3, 4] = 2048
+    inst = W.Instance("A", X, Y, name="big_rep", x_dtype="f32", y_dtype="i32",
+                      z_dtype="f32", target="fp32")
+    Z, _ = run_gpu(inst, variant=F16X2)
+    check_fp32(inst, Z, bound_fn=tc_elem_bound)
+    Y[7, 9] = 2049
+    Xg, Yg = torch_of(X), torch_of(Y)
+    Zg = torch.empty((n, n), device="cuda")
+    plan = Plan(desc_for(inst, variant=F16X2))
+    plan(Xg, Yg, Zg)
+    with pytest.raises(AfmmError) as e:
+        plan.sync()
+    assert e.value.status == AFMM_ERR_OVERFLOW_RISK
+    plan.close()
+
+
+def test_tc_f16x2_case_b_refused():
+    from paper_1308_2400_gb300 import AfmmError, Plan, make_desc
+    from paper_1308_2400_gb300.afmm import AFMM_ERR_UNSUPPORTED
+    with pytest.raises(AfmmError) as e:
+        Plan(make_desc(256, "B", "i32", "f32", "f32", "fp32", variant=F16X2))
+    assert e.value.status == AFMM_ERR_UNSUPPORTED
