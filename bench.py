@@ -626,11 +626,12 @@ def run_afmm(args):
         Z_f8 = Z.cpu().numpy() if ws == 1 else None
         p5.close()
 
-    # The FP16 two-slice form on the same data (Case A): X as two row-scaled
-    # FP16 slices, two MMAs per K step at the BF16 rate; its error below.
+    # The FP16 two-slice form on the same data: the real factor as two
+    # row-scaled FP16 slices (Case B: Y's columns), two MMAs per K step at
+    # the BF16 rate; its error below.
     h16 = None
     Z_h16 = None
-    if rank == 0 and vname == "tc_bf16x3" and inst.case == "A" and not args.quick:
+    if rank == 0 and vname == "tc_bf16x3" and not args.quick:
         p7 = Plan(desc(10))
         k7 = max(2, min(args.steps // 4, 100))
         ms7, kms7, _, _ = timed(p7, k7, 3)

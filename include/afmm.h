@@ -144,8 +144,9 @@ typedef enum {
      * multiple of 128, more staged bytes per flop.  A route of
      * afmm_mul_batched only (a plan refuses it with AFMM_ERR_UNSUPPORTED). */
     AFMM_VARIANT_TC_BF16X3_N128 = 9,
-    /* Tensor cores, Case A, two FP16 slices of the real factor: each row
-     * of X scaled by a power of two so that its largest |value| lies in
+    /* Tensor cores, two FP16 slices of the real factor: each row of X
+     * (Case A; each column of Y in Case B) scaled by a power of two so that
+     * its largest |value| lies in
      * [2^14, 2^15), then split as hi + lo 2^-8, hi the value rounded to 8
      * significant bits and lo the remainder times 2^8 rounded to FP16
      * (split half precision; Ootomo and Yokota, IJHPCA 36, 2022).  The
@@ -155,9 +156,8 @@ typedef enum {
      * where AFMM_VARIANT_TC_BF16X3 takes three, at the same tensor rate;
      * its representation error, below 2^-20 of each value, keeps the FP32
      * target.  A Rep-factor above 2048 (or not exact in FP16) or a
-     * non-finite X records AFMM_ERR_OVERFLOW_RISK (reported by
-     * afmm_plan_sync).  Case B plans refuse it (AFMM_ERR_UNSUPPORTED);
-     * never chosen automatically. */
+     * non-finite real factor records AFMM_ERR_OVERFLOW_RISK (reported by
+     * afmm_plan_sync).  Never chosen automatically. */
     AFMM_VARIANT_TC_F16X2 = 10,
     AFMM_VARIANT_COUNT_ = 11
 } afmm_variant;

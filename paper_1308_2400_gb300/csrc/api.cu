@@ -216,7 +216,7 @@ bool variant_serves(int v, const afmm_desc* d) {
         case AFMM_VARIANT_TC_FP8X4:
             return d->target == AFMM_TARGET_FP32 && tc_available();
         case AFMM_VARIANT_TC_F16X2:
-            return d->target == AFMM_TARGET_FP32 && d->kase == AFMM_CASE_A && tc_available();
+            return d->target == AFMM_TARGET_FP32 && tc_available();
         case AFMM_VARIANT_SIMT_F64SLICE:
             return d->target == AFMM_TARGET_FP64;
         case AFMM_VARIANT_SIMT_EXACT:

@@ -1466,9 +1466,16 @@ afmm_status tc_run_fp8(TcPlan* t, const afmm_desc& d, const void* X, const void*
 
 afmm_status tc_run_h16(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
                        void* Z, int* status, cudaStream_t st) {
-    if (!t->maps_ready || !t->h16 || d.kase != AFMM_CASE_A) return AFMM_ERR_INVALID_ARG;
+    if (!t->maps_ready || !t->h16) return AFMM_ERR_INVALID_ARG;
     const int64_t n = d.n;
     float* Zf = static_cast<float*>(Z);
+    if (d.kase == AFMM_CASE_B) {
+        // As Z^T = Y^T X^T: A = two column-scaled FP16 slices of Y^T (the
+        // b buffer), B = the Rep-factors X as FP16 rows.
+        AFMM_TRY(tc_h16_rep_rows(X, d.x_dtype, n, d.ldx, t->a, t->ld_a, 2048.f, status, st));
+        AFMM_TRY(tc_h16_transpose(Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, t->amax, status, st));
+        return split_product<true>(t, Zf, d.ldz, status, st);
+    }
     // A = two row-scaled FP16 slices of X, B = Rep-factors Y transposed,
     // FP16, exact up to 2048.
     AFMM_TRY(tc_h16_rows(X, d.x_dtype, n, d.ldx, t->a, t->ld_a, t->amax, status, st));

@@ -92,6 +92,13 @@ afmm_status tc_widen_transpose_h16(const void* src, int dt, int64_t n, int64_t l
 afmm_status tc_h16_rows(const void* src, int dt, int64_t n, int64_t lds, void* dst,
                         int64_t ldk, uint32_t* amax, int* status, cudaStream_t st,
                         int64_t r0 = 0, int64_t r1 = -1);
+// Case B: the columns of the real factor as the K-major rows of two FP16
+// slices, column c scaled by 2^h16_row_shift(amax[c]) (amax written here).
+afmm_status tc_h16_transpose(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                             int64_t ldk, uint32_t* amax, int* status, cudaStream_t st);
+// Case B: the Rep-factors' rows kept as exact FP16 (|value| <= lim).
+afmm_status tc_h16_rep_rows(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                            int64_t ldk, float lim, int* status, cudaStream_t st);
 
 // FP8 form conversions (tc_fp8.cu): dst E4M3 [slices][n][ldk], ldk a
 // multiple of 16.  rep: one slice that must equal the source (Rep-factors;

@@ -120,8 +120,7 @@ def test_real_by_real_descriptors():
     assert P.afmm_get_info(h)["variant"] == A.AFMM_VARIANT_SIMT_F32
     P.afmm_plan_destroy(h)
     for kase, v in (("REAL", A.AFMM_VARIANT_TC_FP8X4), ("REAL", A.AFMM_VARIANT_TC_BF16X3),
-                    ("A", A.AFMM_VARIANT_TC_BF16X3X3), ("B", A.AFMM_VARIANT_TC_F16X2),
-                    ("REAL", A.AFMM_VARIANT_TC_F16X2)):
+                    ("A", A.AFMM_VARIANT_TC_BF16X3X3), ("REAL", A.AFMM_VARIANT_TC_F16X2)):
         with pytest.raises(P.AfmmError) as e:
             P.afmm_plan_create(P.make_desc(64, kase, "f32", "i32", "f32", "fp32",
                                            variant=v))

@@ -1013,9 +1013,34 @@ def test_tc_f16x2_rep_factor_limit():
     plan.close()
 
 
-def test_tc_f16x2_case_b_refused():
-    from paper_1308_2400_gb300 import AfmmError, Plan, make_desc
-    from paper_1308_2400_gb300.afmm import AFMM_ERR_UNSUPPORTED
-    with pytest.raises(AfmmError) as e:
-        Plan(make_desc(256, "B", "i32", "f32", "f32", "fp32", variant=F16X2))
-    assert e.value.status == AFMM_ERR_UNSUPPORTED
+@pytest.mark.parametrize("n", [1, 33, 129, 300, 513, 600])
+def test_tc_f16x2_case_b_ragged(n):
+    """Case B as Z^T = Y^T X^T: Y's columns scaled and split, X's
+    Rep-factors as FP16 rows; both kernels."""
+    inst = W.make("caseB_n4096_f32", n=n, seed=n + 11)
+    Z, info = run_gpu(inst, variant=F16X2)
+    assert info["variant"] == F16X2
+    check_fp32(inst, Z, bound_fn=tc_elem_bound)
+
+
+def test_tc_f16x2_case_b_full_size_sampled():
+    inst = W.make("caseB_n4096_f32")
+    Z, _ = run_gpu(inst, variant=F16X2)
+    err = check_fp32(inst, Z, sample_rows(inst.n, 16), bound_fn=tc_elem_bound)
+    assert err < 5e-7
+
+
+def test_tc_f16x2_case_b_column_scales():
+    """Columns of Y 2^-100 .. 2^100 apart and an all-zero column."""
+    rng = np.random.default_rng(19)
+    n = 260
+    X = rng.integers(0, 16, size=(n, n)).astype(np.int32)
+    X[rng.random((n, n)) > 0.5] = 0
+    Y = rng.standard_normal((n, n)) * np.exp2(np.linspace(-100, 100, n)).reshape(1, n)
+    Y[:, 7] = 0
+    Y = Y.astype(np.float32)
+    inst = W.Instance("B", X, Y, name="colscales", x_dtype="i32", y_dtype="f32",
+                      z_dtype="f32", target="fp32")
+    Z, _ = run_gpu(inst, variant=F16X2)
+    check_fp32(inst, Z, bound_fn=tc_elem_bound)
+    assert np.all(Z[:, 7] == 0)
