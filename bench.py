@@ -411,6 +411,7 @@ def traffic_from_profile(kernel_tag, workload):
            "tc_gemm": "tc_gemm.cu",
            "tc_gemm_fp8": "tc_gemm.cu", "tc_gemm_real": "tc_gemm.cu",
            "tc_exact2": "tc_gemm.cu", "tc_pair_kernel": "tc_gemm.cu",
+           "tc_pair_kernel_x8": "tc_gemm.cu",
            "sparse": "sparse.cu"}.get(kernel_tag)
     vals = {}
     with open(path) as f:
@@ -546,13 +547,14 @@ def run_afmm(args):
         roof = {"bound": "tensor", "unit": "TFLOP/s",
                 "peak_src": f"{bf16_src}, {peak_src}"}
         tag = "tc_gemm_real"
-    elif vname == "tc_fp8x4":
-        # E4M3 MMAs: the measured BF16 rate times the nominal FP8/BF16 ratio.
+    elif vname in ("tc_fp8x4", "tc_exact_f8"):
+        # E4M3 MMAs: the measured BF16 rate times the nominal FP8/BF16 ratio
+        # (four slices of the real factor, or two digits of the integers).
         alg = slices * flops
         peak = 2.0 * bf16_peak
         roof = {"bound": "tensor", "unit": "TFLOP/s",
                 "peak_src": f"2 x {bf16_src} (nominal fp8/bf16 ratio), {peak_src}"}
-        tag = "tc_gemm_fp8"
+        tag = "tc_gemm_fp8" if vname == "tc_fp8x4" else "tc_pair_kernel_x8"
     elif tc:
         alg = (1 if vname == "tc_exact" else slices) * flops
         peak = bf16_peak
@@ -727,7 +729,8 @@ def run_afmm(args):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": ({"tc_fp8x4": "e4m3", "tc_f16x2": "f16"}.get(vname, "bf16")) if tc else
+            "dtype": ({"tc_fp8x4": "e4m3", "tc_f16x2": "f16",
+                       "tc_exact_f8": "e4m3"}.get(vname, "bf16")) if tc else
                      ("f64" if inst.target == "fp64" else
                                         ("i8" if inst.target == "exact" else "f32")),
             "data": "synthetic",

@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "libafmm.so")
 
 SOURCES = ["api.cu", "scan.cu", "convert.cu", "simt_gemm.cu", "simt_dense.cu", "norm.cu",
            "tc_gemm.cu", "noalloc.cu", "batched_kernels.cu", "batched.cpp", "mlp.cu",
-           "tc_fused.cu", "sparse.cu", "tc_operands.cu", "tc_fp8.cu", "tc_f16.cu"]
+           "tc_fused.cu", "sparse.cu", "tc_operands.cu", "tc_fp8.cu", "tc_f16.cu", "tc_x8.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC",
                 "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

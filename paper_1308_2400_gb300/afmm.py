@@ -44,6 +44,7 @@ AFMM_VARIANT_TC_FP8X4 = 7
 AFMM_VARIANT_TC_BF16X3X3 = 8
 AFMM_VARIANT_TC_BF16X3_N128 = 9
 AFMM_VARIANT_TC_F16X2 = 10
+AFMM_VARIANT_TC_EXACT_F8 = 11
 AFMM_FLAG_VALIDATE = 0x1
 AFMM_FLAG_FUSED_SPLIT = 0x2
 
@@ -56,6 +57,7 @@ VARIANT_NAMES = {
     AFMM_VARIANT_TC_BF16X3X3: "tc_bf16x3x3",
     AFMM_VARIANT_TC_BF16X3_N128: "tc_bf16x3_n128",
     AFMM_VARIANT_TC_F16X2: "tc_f16x2",
+    AFMM_VARIANT_TC_EXACT_F8: "tc_exact_f8",
 }
 CASE_CODES = {"A": AFMM_CASE_A, "B": AFMM_CASE_B, "REAL": AFMM_CASE_REAL}
 DTYPE_CODES = {"f64": AFMM_F64, "f32": AFMM_F32, "bf16": AFMM_BF16,

@@ -223,6 +223,9 @@ bool variant_serves(int v, const afmm_desc* d) {
             return d->target == AFMM_TARGET_EXACT;
         case AFMM_VARIANT_TC_EXACT:
             return d->target == AFMM_TARGET_EXACT && tc_available();
+        case AFMM_VARIANT_TC_EXACT_F8:
+            return d->target == AFMM_TARGET_EXACT && d->kase == AFMM_CASE_A && d->n >= 512 &&
+                   tc_available();
         case AFMM_VARIANT_SPARSE:
             return d->target == AFMM_TARGET_FP32;
         default:
@@ -234,9 +237,16 @@ int auto_variant(const afmm_desc* d) {
     if (d->kase == AFMM_CASE_REAL)
         return (tc_available() && d->n >= 128) ? AFMM_VARIANT_TC_BF16X3X3
                                                : AFMM_VARIANT_SIMT_F32;
-    if (d->target == AFMM_TARGET_EXACT)
+    if (d->target == AFMM_TARGET_EXACT) {
+        // E4M3 digits when the magnitude hints fit them (twice the BF16
+        // rate and a quarter fewer staged bytes per MMA).
+        if (tc_available() && d->kase == AFMM_CASE_A && d->n >= 512 && d->n < 65536 &&
+            d->rep_max >= 0.0 && d->rep_max <= 16.0 && d->base_max >= 0.0 &&
+            d->base_max <= 255.0)
+            return AFMM_VARIANT_TC_EXACT_F8;
         return (tc_available() && d->n >= 128) ? AFMM_VARIANT_TC_EXACT
                                                : AFMM_VARIANT_SIMT_EXACT;
+    }
     if (d->target == AFMM_TARGET_FP64) return AFMM_VARIANT_SIMT_F64SLICE;
     // FP32 target.  Quadratic regime of Sec. 2.2 (on average at most a few
     // non-zero terms per element of Z): both factors compacted.
@@ -331,9 +341,11 @@ void plan_layout(afmm_plan_s* p) {
             break;
         }
         case AFMM_VARIANT_TC_FP8X4:
-        case AFMM_VARIANT_TC_F16X2: {
+        case AFMM_VARIANT_TC_F16X2:
+        case AFMM_VARIANT_TC_EXACT_F8: {
             tc_layout(&p->tc, d, p->slices, p->variant == AFMM_VARIANT_TC_FP8X4,
-                      p->variant == AFMM_VARIANT_TC_F16X2);
+                      p->variant == AFMM_VARIANT_TC_F16X2,
+                      p->variant == AFMM_VARIANT_TC_EXACT_F8);
             p->off_a = L.take(p->tc.a_bytes);
             p->off_b = L.take(p->tc.b_bytes);
             p->off_c = L.take(p->tc.z_bytes);
@@ -369,7 +381,8 @@ afmm_status ensure_workspace(afmm_plan_s* p, cudaStream_t st) {
         if (p->variant == AFMM_VARIANT_TC_BF16X3 ||
             p->variant == AFMM_VARIANT_TC_BF16X2 ||
             p->variant == AFMM_VARIANT_TC_EXACT || p->variant == AFMM_VARIANT_TC_FP8X4 ||
-            p->variant == AFMM_VARIANT_TC_BF16X3X3 || p->variant == AFMM_VARIANT_TC_F16X2)
+            p->variant == AFMM_VARIANT_TC_BF16X3X3 || p->variant == AFMM_VARIANT_TC_F16X2 ||
+            p->variant == AFMM_VARIANT_TC_EXACT_F8)
             AFMM_TRY(tc_bind_workspace(&p->tc, p->ws + p->off_a, p->ws + p->off_b,
                                        p->ws + p->off_c, p->ws + p->off_e));
         if (p->variant == AFMM_VARIANT_SPARSE) AFMM_TRY(sparse_reset(p->ws + p->off_a, st));
@@ -519,6 +532,8 @@ afmm_status run_variant(afmm_plan_s* p, const void* X, const void* Y, void* Z,
             return tc_run_fp8(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_TC_F16X2:
             return tc_run_h16(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
+        case AFMM_VARIANT_TC_EXACT_F8:
+            return tc_run_exact_x8(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_TC_BF16X3X3:
             return tc_run_real(&p->tc, d, X, Y, Z, wsp<int>(p, p->off_status), st);
         case AFMM_VARIANT_SPARSE:
@@ -804,6 +819,14 @@ afmm_status afmm_plan_create(afmm_plan* out, const afmm_desc* desc) {
     } else if (v == AFMM_VARIANT_TC_FP8X4) {
         p->slices = 4;
     } else if (v == AFMM_VARIANT_TC_F16X2) {
+        p->slices = 2;
+    } else if (v == AFMM_VARIANT_TC_EXACT_F8) {
+        // Digit and Rep-factor magnitudes at most 16: FP32 sums of n products
+        // stay exact integers below 2^24.
+        if ((double)desc->n * 16.0 * 16.0 >= 16777216.0) {
+            delete p;
+            return AFMM_ERR_OVERFLOW_RISK;
+        }
         p->slices = 2;
     } else if (v == AFMM_VARIANT_TC_BF16X3X3) {
         p->slices = 3;

@@ -542,7 +542,13 @@ __device__ __forceinline__ PairUnit pair_unit(int u, int whole, int split, int t
     return w;
 }
 
-template <int SA, bool TOUT, bool H16 = false>
+// Modes of the pair kernel: the split-BF16 form, the FP16 two-slice form,
+// and the exact form on E4M3 digits (A = two digit slices h, l of integer
+// values x = 16 h + l, B = E4M3 Rep-factors; every partial sum is an exact
+// integer below 2^24, and the epilogue writes 16 acc_h + acc_l as int32).
+constexpr int PM_SPLIT = 0, PM_H16 = 1, PM_X8 = 2;
+
+template <int SA, bool TOUT, int MODE = PM_SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB,
@@ -550,7 +556,10 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                int m0, int M, int n0, int N, int K, int vec, int split, int* status,
                const uint32_t* __restrict__ amax) {
     using Cfg = PairCfg<SA>;
-    static_assert(!H16 || SA == 2, "FP16 form: two A slices");
+    constexpr bool H16 = MODE == PM_H16, X8 = MODE == PM_X8;
+    static_assert((!H16 && !X8) || SA == 2, "FP16 and digit forms: two A slices");
+    // Elements per 64-byte row of a K block.
+    constexpr int BKE = X8 ? 64 : TC_BK;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
     uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -562,7 +571,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
     const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
     const int tiles_m = (M - m0 + PR_BM - 1) / PR_BM, tiles_n = (N - n0 + PR_BN - 1) / PR_BN;
     const int num_tiles = tiles_m * tiles_n;
-    const int num_kb = (K + TC_BK - 1) / TC_BK;
+    const int num_kb = (K + BKE - 1) / BKE;
     // The tiles of the last, partial round are split when split > 1.
     const int rem = split > 1 ? num_tiles % npairs : 0;
     const int whole = num_tiles - rem;
@@ -624,9 +633,9 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                     uint8_t* st = tiles + stage * Cfg::STAGE_BYTES;
 #pragma unroll
                     for (int s = 0; s < SA; ++s)
-                        ptx::tma_load_3d_pair(st + s * A_TILE_BYTES, &tmA, full0, kb * TC_BK,
+                        ptx::tma_load_3d_pair(st + s * A_TILE_BYTES, &tmA, full0, kb * BKE,
                                               arow, s);
-                    ptx::tma_load_3d_pair(st + SA * A_TILE_BYTES, mb, full0, kb * TC_BK, brow,
+                    ptx::tma_load_3d_pair(st + SA * A_TILE_BYTES, mb, full0, kb * BKE, brow,
                                           0);
                     issued_phase[stage] = (int)phase;
                     if (++stage == Cfg::STAGES) {
@@ -661,8 +670,9 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
             bool ok = true;
             for (int u = pair; ok && u < num_units; u += npairs) {
                 const int width = u < whole ? PR_BN : PR_BN / split;
-                const uint32_t IDESC = H16 ? ptx::idesc_f16_f32(PR_BM, width)
-                                           : ptx::idesc_bf16_f32(PR_BM, width);
+                const uint32_t IDESC = X8    ? ptx::idesc_e4m3_f32(PR_BM, width)
+                                       : H16 ? ptx::idesc_f16_f32(PR_BM, width)
+                                             : ptx::idesc_bf16_f32(PR_BM, width);
                 if (!ptx::mbar_wait_cluster_bounded(&bars->tempty[0], tphase ^ 1u, abort,
                                                     WAIT_LIMIT_NS)) {
                     ok = false;
@@ -686,10 +696,16 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                             // Issued from the smallest slice: the first MMA
                             // into each accumulator overwrites it.
                             const bool first = kb == 0 && ks == 0 && (p == 0 || p == SA - 1);
-                            ptx::mma_f16_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
-                                              ptx::sdesc_kmajor_sw64(a_addr),
-                                              ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                              first ? 0u : 1u);
+                            if constexpr (X8)
+                                ptx::mma_f8_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
+                                                 ptx::sdesc_kmajor_sw64(a_addr),
+                                                 ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                                 first ? 0u : 1u);
+                            else
+                                ptx::mma_f16_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
+                                                  ptx::sdesc_kmajor_sw64(a_addr),
+                                                  ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                                  first ? 0u : 1u);
                         }
                     }
                     ptx::mma_commit_pair_mc(&bars->empty[stage], (uint16_t)3u);
@@ -754,7 +770,11 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                     ptx::tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        if constexpr (H16)
+                        if constexpr (X8)    // int32 bits, stored as they are
+                            sum[c * 16 + j] = __int_as_float(
+                                16 * __float2int_rn(__uint_as_float(r0[j])) +
+                                __float2int_rn(__uint_as_float(r1[j])));
+                        else if constexpr (H16)
                             sum[c * 16 + j] = fmaf(__uint_as_float(r1[j]), 0x1p-8f,
                                                    __uint_as_float(r0[j])) * f1 * f2;
                         else
@@ -1094,7 +1114,7 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
 
 // Clusters of two CTAs (one per SM of a pair) that fit at once, for the
 // pair kernel's persistent grid; 0 when the device cannot co-schedule any.
-template <int SA, bool TOUT, bool H16>
+template <int SA, bool TOUT, int MODE>
 int pair_clusters(int smem) {
     static int cached[64];
     static std::once_flag once;
@@ -1118,7 +1138,7 @@ int pair_clusters(int smem) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT, H16>, &cfg) !=
+    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT, MODE>, &cfg) !=
         cudaSuccess) {
         cudaGetLastError();
         n = 0;
@@ -1129,18 +1149,18 @@ int pair_clusters(int smem) {
 
 // The two-SM split product over rows [m0, m1) and columns [n0, n1) of the
 // product (Z^T's when TOUT).
-template <int SA, bool TOUT = false, bool H16 = false>
+template <int SA, bool TOUT = false, int MODE = PM_SPLIT>
 afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
                            cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
     using Cfg = PairCfg<SA>;
     const int n = (int)t->n;
     if (m1 < 0) m1 = n;
     if (n1 < 0) n1 = n;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT, H16>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int tiles = ((m1 - m0 + PR_BM - 1) / PR_BM) * ((n1 - n0 + PR_BN - 1) / PR_BN);
-    const int cap = pair_clusters<SA, TOUT, H16>(Cfg::SMEM);
+    const int cap = pair_clusters<SA, TOUT, MODE>(Cfg::SMEM);
     if (cap < 1) return AFMM_ERR_UNSUPPORTED;
     const int clusters = tiles < cap ? tiles : cap;
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
@@ -1165,7 +1185,7 @@ afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     main_kernel_begin(st);
-    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT, H16>, ma, mb, mb64, Z,
+    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT, MODE>, ma, mb, mb64, Z,
                                      ldz, m0, m1, n0, n1, n, vec, split, status,
                                      (const uint32_t*)t->amax));
     main_kernel_end(st, 2 * clusters);
@@ -1182,7 +1202,7 @@ afmm_status split_product(const TcPlan* t, float* Z, int64_t ldz, int* status,
         // FP16 two-slice form (Case A).
         if (t->pair) {
             const afmm_status rc =
-                launch_tc_pair<2, TOUT, true>(t, Z, ldz, status, st, m0, m1, n0, n1);
+                launch_tc_pair<2, TOUT, PM_H16>(t, Z, ldz, status, st, m0, m1, n0, n1);
             if (rc != AFMM_ERR_UNSUPPORTED) return rc;
         }
         return launch_tc<2, 1, TOUT, false, true>(t, Z, ldz, status, st, m0, m1, n0, n1);
@@ -1277,13 +1297,24 @@ double dtype_bound(int dt) {
 }
 }  // namespace
 
-void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8, bool h16) {
+void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8, bool h16, bool x8) {
     t->n = d.n;
     t->slices = slices;
     t->sliced_a = d.kase != AFMM_CASE_B;
     t->both = d.kase == AFMM_CASE_REAL;
     t->f8 = f8;
     t->h16 = h16;
+    t->x8 = x8;
+    if (x8) {
+        // One byte per element: 16-byte aligned rows; two digit slices of
+        // X, one Rep-factor operand; the two-SM kernel.
+        t->ld_a = t->ld_b = (d.n + 15) / 16 * 16;
+        t->rows_a = t->rows_b = d.n;
+        t->a_bytes = (size_t)2 * d.n * t->ld_a;
+        t->b_bytes = (size_t)d.n * t->ld_b;
+        t->pair = true;
+        return;
+    }
     t->ld_a = t->ld_b = (d.n + 7) / 8 * 8;
     if (f8) {
         // E4M3 operands: 16-byte aligned rows of one-byte elements; the
@@ -1350,7 +1381,7 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z, void* s) {
     if (t->n <= 0) return AFMM_OK;
     const int sl = t->slices > 0 ? t->slices : 1;
     const int sa = t->sliced_a ? sl : 1, sb = t->sliced_a && !t->both ? 1 : sl;
-    const int es = t->f8 ? 1 : 2;
+    const int es = (t->f8 || t->x8) ? 1 : 2;
     AFMM_TRY(tc_encode_map(t->tmap_a, a, t->n, t->n, t->ld_a, sa, TC_BM, es));
     AFMM_TRY(tc_encode_map(t->tmap_b, b, t->n, t->n, t->ld_b, sb, TC_BN, es));
     // B side with 128-row boxes: each CTA of a pair loads half of a B tile.
@@ -1490,6 +1521,16 @@ afmm_status tc_run_h16(TcPlan* t, const afmm_desc& d, const void* X, const void*
         return AFMM_OK;
     }
     return split_product<false>(t, Zf, d.ldz, status, st);
+}
+
+afmm_status tc_run_exact_x8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
+                            void* Z, int* status, cudaStream_t st) {
+    if (!t->maps_ready || !t->x8 || d.kase != AFMM_CASE_A) return AFMM_ERR_INVALID_ARG;
+    const int64_t n = d.n;
+    AFMM_TRY(tc_x8_digit_rows(X, d.x_dtype, n, d.ldx, t->a, t->ld_a, status, st));
+    AFMM_TRY(tc_x8_rep_transpose(Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, status, st));
+    // The kernel writes int32 bit patterns through its float pointer.
+    return launch_tc_pair<2, false, PM_X8>(t, static_cast<float*>(Z), d.ldz, status, st);
 }
 
 afmm_status tc_run_exact(TcPlan* t, const afmm_desc& d, const void* X,

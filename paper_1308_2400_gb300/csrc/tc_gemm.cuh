@@ -56,6 +56,9 @@ struct TcPlan {
     // FP16 two-slice form (fp16_split.cuh): FP16 operands, amax[m] sets
     // the power of two row m of the real factor was scaled by.
     bool h16 = false;
+    // Exact form on E4M3 digits (Case A, two-SM kernel): A = two digit
+    // slices of X, B = Rep-factors, one byte each; Z int32.
+    bool x8 = false;
 };
 
 // TMA descriptor (written to `out`, 128 bytes, 64-byte aligned) of a stack
@@ -96,6 +99,18 @@ afmm_status tc_h16_rows(const void* src, int dt, int64_t n, int64_t lds, void* d
 // slices, column c scaled by 2^h16_row_shift(amax[c]) (amax written here).
 afmm_status tc_h16_transpose(const void* src, int dt, int64_t n, int64_t lds, void* dst,
                              int64_t ldk, uint32_t* amax, int* status, cudaStream_t st);
+// Exact form on E4M3 digits (tc_x8.cu): the rows of X (integers, |x| <=
+// 255) as two digit slices dst[(s * n + r) * ldk + c], h = floor(x / 16)
+// and l = x - 16 h; the Rep-factors of Y (0 .. 16) transposed to K-major
+// E4M3.  ldk a multiple of 16; range errors record AFMM_ERR_OVERFLOW_RISK.
+afmm_status tc_x8_digit_rows(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                             int64_t ldk, int* status, cudaStream_t st);
+afmm_status tc_x8_rep_transpose(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                                int64_t ldk, int* status, cudaStream_t st);
+// The exact form on E4M3 digits (Case A, n >= 512): conversions and the
+// two-SM product into Z (int32).
+afmm_status tc_run_exact_x8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
+                            void* Z, int* status, cudaStream_t st);
 // Case B: the Rep-factors' rows kept as exact FP16 (|value| <= lim).
 afmm_status tc_h16_rep_rows(const void* src, int dt, int64_t n, int64_t lds, void* dst,
                             int64_t ldk, float lim, int* status, cudaStream_t st);
@@ -118,8 +133,10 @@ afmm_status tc_f8_transpose(bool rep, const void* src, int dt, int64_t n, int64_
 bool tc_available();
 // slices = 0 selects the exact-integer form (one BF16 operand each side);
 // f8 the FP8 form (four E4M3 slices).
-// h16 the FP16 two-slice form (Case A, slices = 2).
-void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8 = false, bool h16 = false);
+// h16 the FP16 two-slice form (slices = 2); x8 the exact form on E4M3
+// digits (Case A, slices = 2).
+void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8 = false, bool h16 = false,
+               bool x8 = false);
 // Largest K chunk (multiple of 32) with chunk * amax * bmax < 2^24, or 0
 // when even one 32-wide block could overflow.
 int tc_exact_chunk_k(double amax, double bmax);

@@ -423,7 +423,7 @@ def test_tc_exact_full_size_sampled_with_hints():
     inst = W.make("caseA_n16384_i8")
     X, Y = torch_of(inst.X), torch_of(inst.Y)
     Z = T.empty((inst.n, inst.n), dtype=T.int32, device="cuda")
-    p = Plan(make_desc(inst.n, "A", "i8", "i8", "i32", "exact",
+    p = Plan(make_desc(inst.n, "A", "i8", "i8", "i32", "exact", variant=5,
                        rep_max=15, base_max=127))
     assert p.info["variant"] == 5 and p.info["k_split"] == 2
     p(X, Y, Z)
@@ -447,6 +447,81 @@ def test_tc_exact_hint_violation_is_reported():
     with pytest.raises(AfmmError) as e:
         p.sync()
     assert e.value.status == 4          # AFMM_ERR_OVERFLOW_RISK
+
+
+# ------------------------------------------------- exact, TC, E4M3 digits
+X8 = 11                        # AFMM_VARIANT_TC_EXACT_F8
+
+
+@pytest.mark.parametrize("n", [512, 513, 600, 1000, 1537])
+def test_tc_exact_f8_ragged(n):
+    """Two E4M3 digits of X, CTA pairs, int32 epilogue: bit-exact."""
+    inst = exact_case("A", n, seed=n + 3)
+    Z, info = run_gpu(inst, variant=X8)
+    assert info["variant"] == X8
+    assert np.array_equal(Z.astype(np.int64), oracle_rows(inst))
+
+
+def test_tc_exact_f8_worst_case_digits():
+    """Base values at +-255 and at digit boundaries (-1, -16, 15, 16),
+    Rep-factors at 16: the largest digit sums the form allows."""
+    n = 1024
+    X = np.full((n, n), -255, dtype=np.int32)
+    X[1::2] = 255
+    X[::3, ::5] = -1
+    X[::7, ::2] = -16
+    X[::5, 1::3] = 15
+    X[::11, ::7] = 16
+    Y = np.full((n, n), 16, dtype=np.int32)
+    Y[::4] = 0
+    inst = W.Instance("A", X, Y, name="worst_digits", x_dtype="i32", y_dtype="i32",
+                      z_dtype="i32", target="exact")
+    Z, _ = run_gpu(inst, variant=X8)
+    assert np.array_equal(Z.astype(np.int64), oracle_rows(inst))
+
+
+def test_tc_exact_f8_full_size_sampled_auto():
+    """n = 16384 with the workload's magnitudes as hints: the planner takes
+    the E4M3 digit form."""
+    import torch as T
+    from paper_1308_2400_gb300 import Plan, make_desc
+    inst = W.make("caseA_n16384_i8")
+    X, Y = torch_of(inst.X), torch_of(inst.Y)
+    Z = T.empty((inst.n, inst.n), dtype=T.int32, device="cuda")
+    p = Plan(make_desc(inst.n, "A", "i8", "i8", "i32", "exact", rep_max=15, base_max=127))
+    assert p.info["variant"] == X8
+    p(X, Y, Z)
+    p.sync()
+    p.close()
+    rows = sample_rows(inst.n, 6)
+    assert np.array_equal(Z.cpu().numpy()[rows].astype(np.int64), oracle_rows(inst, rows))
+
+
+@pytest.mark.parametrize("where,value,code", [("X", 256, 4), ("Y", 17, 4), ("Y", -1, 3)])
+def test_tc_exact_f8_range_errors(where, value, code):
+    """A Base value past 255 or a Rep-factor past 16 is AFMM_ERR_OVERFLOW_RISK,
+    a negative Rep-factor AFMM_ERR_NEGATIVE_REP."""
+    import torch as T
+    from paper_1308_2400_gb300 import AfmmError, Plan, make_desc
+    n = 600
+    X = T.ones((n, n), dtype=T.int32, device="cuda")
+    Y = T.ones((n, n), dtype=T.int32, device="cuda")
+    (X if where == "X" else Y)[3, 4] = value
+    Z = T.empty((n, n), dtype=T.int32, device="cuda")
+    p = Plan(make_desc(n, "A", "i32", "i32", "i32", "exact", variant=X8))
+    p(X, Y, Z)
+    with pytest.raises(AfmmError) as e:
+        p.sync()
+    assert e.value.status == code
+    p.close()
+
+
+def test_tc_exact_f8_refuses_small_and_case_b():
+    from paper_1308_2400_gb300 import AfmmError, Plan, make_desc
+    for n, case in ((256, "A"), (1024, "B")):
+        with pytest.raises(AfmmError) as e:
+            Plan(make_desc(n, case, "i8", "i8", "i32", "exact", variant=X8))
+        assert e.value.status == 2      # AFMM_ERR_UNSUPPORTED
 
 
 # ------------------------------------------------------------------ exact
