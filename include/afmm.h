@@ -159,8 +159,9 @@ typedef enum {
      * non-finite real factor records AFMM_ERR_OVERFLOW_RISK (reported by
      * afmm_plan_sync).  Never chosen automatically. */
     AFMM_VARIANT_TC_F16X2 = 10,
-    /* Exact target, Case A, n >= 512, on E4M3 digits: each integer Base
-     * value x of X (|x| <= 255) as x = 16 h + l with h = floor(x / 16) and
+    /* Exact target, n >= 512, on E4M3 digits: each integer Base value x
+     * (of X in Case A, of Y in Case B; |x| <= 255) as x = 16 h + l with
+     * h = floor(x / 16) and
      * l in [0, 15], the Rep-factors (0 .. 16) and both digits exact in
      * E4M3; two kind::f8f6f4 MMAs per K step (twice the BF16 rate) on CTA
      * pairs, the h and l products in two FP32 accumulators whose sums stay
@@ -168,7 +169,7 @@ typedef enum {
      * in int32.  A value outside those ranges records
      * AFMM_ERR_OVERFLOW_RISK (a negative or non-integer Rep-factor
      * AFMM_ERR_NEGATIVE_REP / _NONINTEGER_REP), reported by
-     * afmm_plan_sync.  Chosen automatically for exact Case A plans whose
+     * afmm_plan_sync.  Chosen automatically for exact plans whose
      * magnitude hints (rep_max <= 16, base_max <= 255) allow it. */
     AFMM_VARIANT_TC_EXACT_F8 = 11,
     AFMM_VARIANT_COUNT_ = 12

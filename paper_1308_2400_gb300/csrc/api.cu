@@ -224,8 +224,7 @@ bool variant_serves(int v, const afmm_desc* d) {
         case AFMM_VARIANT_TC_EXACT:
             return d->target == AFMM_TARGET_EXACT && tc_available();
         case AFMM_VARIANT_TC_EXACT_F8:
-            return d->target == AFMM_TARGET_EXACT && d->kase == AFMM_CASE_A && d->n >= 512 &&
-                   tc_available();
+            return d->target == AFMM_TARGET_EXACT && d->n >= 512 && tc_available();
         case AFMM_VARIANT_SPARSE:
             return d->target == AFMM_TARGET_FP32;
         default:
@@ -240,7 +239,7 @@ int auto_variant(const afmm_desc* d) {
     if (d->target == AFMM_TARGET_EXACT) {
         // E4M3 digits when the magnitude hints fit them (twice the BF16
         // rate and a quarter fewer staged bytes per MMA).
-        if (tc_available() && d->kase == AFMM_CASE_A && d->n >= 512 && d->n < 65536 &&
+        if (tc_available() && d->n >= 512 && d->n < 65536 &&
             d->rep_max >= 0.0 && d->rep_max <= 16.0 && d->base_max >= 0.0 &&
             d->base_max <= 255.0)
             return AFMM_VARIANT_TC_EXACT_F8;

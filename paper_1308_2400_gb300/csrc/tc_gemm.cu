@@ -1307,11 +1307,12 @@ void tc_layout(TcPlan* t, const afmm_desc& d, int slices, bool f8, bool h16, boo
     t->x8 = x8;
     if (x8) {
         // One byte per element: 16-byte aligned rows; two digit slices of
-        // X, one Rep-factor operand; the two-SM kernel.
+        // the integer Base factor (the a buffer in Case A, b in Case B),
+        // one Rep-factor operand; the two-SM kernel.
         t->ld_a = t->ld_b = (d.n + 15) / 16 * 16;
         t->rows_a = t->rows_b = d.n;
-        t->a_bytes = (size_t)2 * d.n * t->ld_a;
-        t->b_bytes = (size_t)d.n * t->ld_b;
+        t->a_bytes = (size_t)(t->sliced_a ? 2 : 1) * d.n * t->ld_a;
+        t->b_bytes = (size_t)(t->sliced_a ? 1 : 2) * d.n * t->ld_b;
         t->pair = true;
         return;
     }
@@ -1525,8 +1526,15 @@ afmm_status tc_run_h16(TcPlan* t, const afmm_desc& d, const void* X, const void*
 
 afmm_status tc_run_exact_x8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
                             void* Z, int* status, cudaStream_t st) {
-    if (!t->maps_ready || !t->x8 || d.kase != AFMM_CASE_A) return AFMM_ERR_INVALID_ARG;
+    if (!t->maps_ready || !t->x8) return AFMM_ERR_INVALID_ARG;
     const int64_t n = d.n;
+    if (d.kase == AFMM_CASE_B) {
+        // A = two digit slices of Y^T (the b buffer), B = X's Rep-factors;
+        // tiles of Z^T, stored transposed.
+        AFMM_TRY(tc_x8_rep_rows(X, d.x_dtype, n, d.ldx, t->a, t->ld_a, status, st));
+        AFMM_TRY(tc_x8_digit_transpose(Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, status, st));
+        return launch_tc_pair<2, true, PM_X8>(t, static_cast<float*>(Z), d.ldz, status, st);
+    }
     AFMM_TRY(tc_x8_digit_rows(X, d.x_dtype, n, d.ldx, t->a, t->ld_a, status, st));
     AFMM_TRY(tc_x8_rep_transpose(Y, d.y_dtype, n, d.ldy, t->b, t->ld_b, status, st));
     // The kernel writes int32 bit patterns through its float pointer.

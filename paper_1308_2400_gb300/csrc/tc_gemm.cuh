@@ -107,8 +107,14 @@ afmm_status tc_x8_digit_rows(const void* src, int dt, int64_t n, int64_t lds, vo
                              int64_t ldk, int* status, cudaStream_t st);
 afmm_status tc_x8_rep_transpose(const void* src, int dt, int64_t n, int64_t lds, void* dst,
                                 int64_t ldk, int* status, cudaStream_t st);
-// The exact form on E4M3 digits (Case A, n >= 512): conversions and the
-// two-SM product into Z (int32).
+// Case B: the columns of Y (integer Base values) as two transposed digit
+// slices; the Rep-factors of X kept as E4M3 rows.
+afmm_status tc_x8_digit_transpose(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                                  int64_t ldk, int* status, cudaStream_t st);
+afmm_status tc_x8_rep_rows(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                           int64_t ldk, int* status, cudaStream_t st);
+// The exact form on E4M3 digits (n >= 512): conversions and the two-SM
+// product into Z (int32); Case B as Z^T = Y^T X^T.
 afmm_status tc_run_exact_x8(TcPlan* t, const afmm_desc& d, const void* X, const void* Y,
                             void* Z, int* status, cudaStream_t st);
 // Case B: the Rep-factors' rows kept as exact FP16 (|value| <= lim).

@@ -1,7 +1,8 @@
-// Conversions of the exact form on E4M3 digits (Case A): the integer Base
-// values x of X (|x| <= 255) as two digit slices, h = floor(x / 16) in
-// [-16, 15] and l = x - 16 h in [0, 15], and the Rep-factors of Y (0 .. 16)
-// transposed to K-major; every digit and Rep-factor is an integer of
+// Conversions of the exact form on E4M3 digits: the integer Base values x
+// (|x| <= 255; X's rows in Case A, Y's columns in Case B) as two digit slices, h = floor(x / 16) in
+// [-16, 15] and l = x - 16 h in [0, 15], and the Rep-factors (0 .. 16) as
+// the K-major E4M3 operand (Y transposed in Case A, X's rows in Case B);
+// every digit and Rep-factor is an integer of
 // magnitude at most 16, exact in E4M3, so the tensor pipe's products are
 // exact and, with n 16 16 < 2^24, so are its FP32 sums.  Values outside
 // those ranges (or not integers) record AFMM_ERR_OVERFLOW_RISK; a negative
@@ -99,7 +100,106 @@ x8_rep_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
     if (bits) atomicCAS(status, 0, bad_status(bits));
 }
 
+// Case B: the integer Base values of Y transposed into two digit slices,
+// dst[(s * n + c) * ldk + r] from Y[r][c]; and the Rep-factors of X kept
+// as E4M3 rows dst[r * ldk + c].  Same ranges and checks as above.
+template <int DT>
+__global__ void __launch_bounds__(X8_THREADS)
+x8_digit_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
+                          uint8_t* __restrict__ dst, int64_t ldk, int vec, int* status) {
+    __shared__ float tile[64][65];
+    const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
+    bool unused = false;
+    tile_load_f32<DT>(src, n, lds, r0, c0, 3.0e38f, vec != 0, tile, unused);
+    __syncthreads();
+    const int cc = threadIdx.x >> 2, qq = threadIdx.x & 3;
+    const int64_t c = c0 + cc, r = r0 + 16 * qq;
+    if (c >= n || r >= ldk) return;
+    bool bad = false;
+    uint32_t wh[4], wl[4];
+#pragma unroll
+    for (int e = 0; e < 16; e += 2) {
+        float h[2], l[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float x = tile[16 * qq + e + u][cc];
+            bad |= !(truncf(x) == x) || fabsf(x) > kX8BaseMax;
+            h[u] = floorf(x * 0.0625f);
+            l[u] = x - 16.f * h[u];
+        }
+        const uint32_t qh = e4m3x2_rn(h[0], h[1]), ql = e4m3x2_rn(l[0], l[1]);
+        const int word = e >> 2, half = (e >> 1) & 1;
+        wh[word] = half ? (wh[word] | (qh << 16)) : qh;
+        wl[word] = half ? (wl[word] | (ql << 16)) : ql;
+    }
+    *reinterpret_cast<uint4*>(dst + c * ldk + r) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4*>(dst + (n + c) * ldk + r) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    if (bad) atomicCAS(status, 0, (int)AFMM_ERR_OVERFLOW_RISK);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(X8_THREADS)
+x8_rep_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
+                   uint8_t* __restrict__ dst, int64_t ldk, int* status) {
+    const int64_t c = ((int64_t)blockIdx.x * X8_THREADS + threadIdx.x) * 16;
+    if (c >= ldk) return;
+    int bits = 0;
+    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
+        uint32_t w[4];
+#pragma unroll
+        for (int t = 0; t < 16; t += 2) {
+            const float y0 = c + t < n ? (float)Elem<DT>::get(src, r * lds + c + t) : 0.f;
+            const float y1 = c + t + 1 < n ? (float)Elem<DT>::get(src, r * lds + c + t + 1) : 0.f;
+            bits |= rep_bits(y0) | rep_bits(y1);
+            if (y0 > kX8RepMax || y1 > kX8RepMax) bits |= kBadRange;
+            const uint32_t q = e4m3x2_rn(y0, y1);
+            const int word = t >> 2, half = (t >> 1) & 1;
+            w[word] = half ? (w[word] | (q << 16)) : q;
+        }
+        *reinterpret_cast<uint4*>(dst + r * ldk + c) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (bits) atomicCAS(status, 0, bad_status(bits));
+}
+
 }  // namespace
+
+afmm_status tc_x8_digit_transpose(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                                  int64_t ldk, int* status, cudaStream_t st) {
+    if (n <= 0) return AFMM_OK;
+    if (ldk % 16 != 0 || (reinterpret_cast<uintptr_t>(dst) & 15u) != 0)
+        return AFMM_ERR_INVALID_ARG;
+    const int64_t g = (n + 63) / 64;
+    if (g > 65535) return AFMM_ERR_UNSUPPORTED;
+    const int vec = rows_aligned16(src, lds, (int64_t)dtype_size(dt));
+    auto* d = static_cast<uint8_t*>(dst);
+    afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
+        x8_digit_transpose_kernel<DT><<<dim3((unsigned)g, (unsigned)g), X8_THREADS, 0, st>>>(
+            src, n, lds, d, ldk, vec, status);
+        return AFMM_OK;
+    });
+    AFMM_TRY(rc);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
+}
+
+afmm_status tc_x8_rep_rows(const void* src, int dt, int64_t n, int64_t lds, void* dst,
+                           int64_t ldk, int* status, cudaStream_t st) {
+    if (n <= 0) return AFMM_OK;
+    if (ldk % 16 != 0 || (reinterpret_cast<uintptr_t>(dst) & 15u) != 0)
+        return AFMM_ERR_INVALID_ARG;
+    const dim3 grid((unsigned)((ldk / 16 + X8_THREADS - 1) / X8_THREADS),
+                    (unsigned)(n < 65535 ? n : 65535));
+    auto* d = static_cast<uint8_t*>(dst);
+    afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
+        x8_rep_rows_kernel<DT><<<grid, X8_THREADS, 0, st>>>(src, n, lds, d, ldk, status);
+        return AFMM_OK;
+    });
+    AFMM_TRY(rc);
+    AFMM_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFMM_OK;
+}
 
 afmm_status tc_x8_digit_rows(const void* src, int dt, int64_t n, int64_t lds, void* dst,
                              int64_t ldk, int* status, cudaStream_t st) {
