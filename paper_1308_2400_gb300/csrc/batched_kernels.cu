@@ -79,9 +79,11 @@ __device__ __forceinline__ int find_job(const int* prefix, int n, int b) {
 // 3 BF16 rows; Case B (KIND 1) widens a row of the Rep-factors X to BF16
 // (values must be exact, |v| <= 256, else the instance's flag is set and
 // its Z becomes NaN).  Eight columns per thread and step (vector loads when
-// the rows are aligned), one 16-byte store per slice.
+// the rows are aligned), one 16-byte store per slice; the row's threads are
+// t0, t0 + 1, .. (nt of them).
 template <int DT, int KIND>
-__device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags, int* status) {
+__device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags, int* status,
+                                           int t0, int nt) {
     using T = typename Elem<DT>::T;
     const int64_t n = g.n, ldk = g.ldk;
     const int64_t va = sizeof(T) * 8 < 16 ? sizeof(T) * 8 : 16;
@@ -90,7 +92,7 @@ __device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags
     const T* x = static_cast<const T*>(g.X) + r * g.ldx;
     bool bad = false;
     int bits = 0;
-    for (int64_t c = 8 * threadIdx.x; c < ldk; c += 8 * 128) {
+    for (int64_t c = 8 * (int64_t)t0; c < ldk; c += 8 * (int64_t)nt) {
         float v[8];
         // FP32 rows that start off a 16-byte boundary: aligned loads and a shift.
         constexpr bool kF32 = DT == AFMM_F32;
@@ -146,19 +148,25 @@ __device__ __forceinline__ void g_row_body(const GInst& g, int64_t r, int* flags
     }
 }
 
-// Block b converts row b - row_prefix[j] of the A operand of instance
-// j = row_job[b].
-__global__ void __launch_bounds__(128)
+// Warp w of block b converts row q = 8 b + w (of all instances' A rows in
+// order): row q - row_prefix[j] of instance j = row_job[q].  A warp per row
+// keeps eight rows' loads in flight per block (instances' rows are short:
+// n <= 2048).
+constexpr int G_ROWS_PER_BLOCK = 8;
+__global__ void __launch_bounds__(32 * G_ROWS_PER_BLOCK)
 g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix,
               const int* __restrict__ row_job, int rows_total, int* __restrict__ flags,
               int* __restrict__ status) {
-    const int j = row_job[blockIdx.x];
+    const int q = blockIdx.x * G_ROWS_PER_BLOCK + (threadIdx.x >> 5);
+    if (q >= rows_total) return;
+    const int lane = threadIdx.x & 31;
+    const int j = row_job[q];
     const GInst& g = inst[j];
-    const int64_t r = blockIdx.x - row_prefix[j];
+    const int64_t r = q - row_prefix[j];
     if (g.kind == 0) {
-        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 0>(g, r, flags, status)))
+        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 0>(g, r, flags, status, lane, 32)))
     } else {
-        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 1>(g, r, flags, status)))
+        G_DTYPE_SWITCH(g.x_dtype, (g_row_body<DT, 1>(g, r, flags, status, lane, 32)))
     }
 }
 
@@ -458,8 +466,9 @@ afmm_status launch_batch_convert(const GInst* inst, const int* row_prefix,
                                  int tt_total, int* flags, int* status, cudaStream_t st) {
     if (ninst <= 0) return AFMM_OK;
     AFMM_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (ninst + 1), st));
-    g_rows_kernel<<<rows_total, 128, 0, st>>>(inst, row_prefix, row_job, rows_total, flags,
-                                              status);
+    g_rows_kernel<<<(rows_total + G_ROWS_PER_BLOCK - 1) / G_ROWS_PER_BLOCK,
+                    32 * G_ROWS_PER_BLOCK, 0, st>>>(inst, row_prefix, row_job, rows_total,
+                                                    flags, status);
     AFMM_CUDA_TRY(cudaGetLastError());
     g_transpose_kernel<<<tt_total, 256, 0, st>>>(inst, tt_prefix, tt_job, flags, status);
     AFMM_CUDA_TRY(cudaGetLastError());
