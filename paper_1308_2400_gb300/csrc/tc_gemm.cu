@@ -490,9 +490,12 @@ constexpr int PR_B_BYTES = PR_HALF * TC_BK * 2;    // 8 KiB
 constexpr int PR_GROUP_M = 5;                      // tile raster band (tile rows)
 constexpr int PR_EPI_WARPS = 2 * (TC_EPI_THREADS / 32);   // tempty arrivals
 
-template <int SA>
+// A stage holds SUB consecutive 64-byte K blocks, each laid out as its SA
+// A tiles then its B tile (SUB = 2 halves the stage hand-overs per MMA).
+template <int SA, int SUB = 1>
 struct PairCfg {
-    static constexpr int STAGE_BYTES = SA * A_TILE_BYTES + PR_B_BYTES;
+    static constexpr int SUB_BYTES = SA * A_TILE_BYTES + PR_B_BYTES;
+    static constexpr int STAGE_BYTES = SUB * SUB_BYTES;
     static constexpr int STAGES_FIT = (SMEM_OPTIN - 1024 - BARS_BYTES) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT > MAX_STAGES ? MAX_STAGES : STAGES_FIT;
     static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + BARS_BYTES;
@@ -548,14 +551,14 @@ __device__ __forceinline__ PairUnit pair_unit(int u, int whole, int split, int t
 // integer below 2^24, and the epilogue writes 16 acc_h + acc_l as int32).
 constexpr int PM_SPLIT = 0, PM_H16 = 1, PM_X8 = 2;
 
-template <int SA, bool TOUT, int MODE = PM_SPLIT>
+template <int SA, bool TOUT, int MODE = PM_SPLIT, int SUB = 1>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmB64, float* __restrict__ Z, int64_t ldz,
                int m0, int M, int n0, int N, int K, int vec, int split, int* status,
                const uint32_t* __restrict__ amax) {
-    using Cfg = PairCfg<SA>;
+    using Cfg = PairCfg<SA, SUB>;
     constexpr bool H16 = MODE == PM_H16, X8 = MODE == PM_X8;
     static_assert((!H16 && !X8) || SA == 2, "FP16 and digit forms: two A slices");
     // Elements per 64-byte row of a K block.
@@ -620,23 +623,31 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                 const int brow = n0 + w.tn * PR_BN + w.col + (int)rank * bhalf;
                 const CUtensorMap* mb = w.width == PR_BN ? &tmB : &tmB64;
                 const uint32_t bytes = SA * A_TILE_BYTES + (uint32_t)bhalf * TC_BK * 2;
-                for (int kb = 0; kb < num_kb; ++kb) {
+                for (int kb0 = 0; kb0 < num_kb; kb0 += SUB) {
                     if (!ptx::mbar_wait_cluster_bounded(&bars->empty[stage], phase ^ 1u, abort,
                                                         WAIT_LIMIT_NS)) {
                         ok = false;
                         break;
                     }
+                    // K blocks of this stage (the last stage may hold fewer).
+                    const int nsub = num_kb - kb0 < SUB ? num_kb - kb0 : SUB;
                     // The even CTA's barrier counts both CTAs' bytes.
-                    if (leader) ptx::mbar_arrive_expect_tx(&bars->full[stage], 2 * bytes);
+                    if (leader)
+                        ptx::mbar_arrive_expect_tx(&bars->full[stage], 2 * bytes * (uint32_t)nsub);
                     const uint32_t full0 =
                         ptx::mapa_shared(ptx::smem_addr(&bars->full[stage]), 0u);
-                    uint8_t* st = tiles + stage * Cfg::STAGE_BYTES;
 #pragma unroll
-                    for (int s = 0; s < SA; ++s)
-                        ptx::tma_load_3d_pair(st + s * A_TILE_BYTES, &tmA, full0, kb * BKE,
-                                              arow, s);
-                    ptx::tma_load_3d_pair(st + SA * A_TILE_BYTES, mb, full0, kb * BKE, brow,
-                                          0);
+                    for (int q = 0; q < SUB; ++q) {
+                        if (q >= nsub) break;
+                        const int kb = kb0 + q;
+                        uint8_t* st = tiles + stage * Cfg::STAGE_BYTES + q * Cfg::SUB_BYTES;
+#pragma unroll
+                        for (int s = 0; s < SA; ++s)
+                            ptx::tma_load_3d_pair(st + s * A_TILE_BYTES, &tmA, full0, kb * BKE,
+                                                  arow, s);
+                        ptx::tma_load_3d_pair(st + SA * A_TILE_BYTES, mb, full0, kb * BKE, brow,
+                                              0);
+                    }
                     issued_phase[stage] = (int)phase;
                     if (++stage == Cfg::STAGES) {
                         stage = 0;
@@ -679,33 +690,40 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                     break;
                 }
                 ptx::tc_fence_after();
-                for (int kb = 0; kb < num_kb; ++kb) {
+                for (int kb0 = 0; kb0 < num_kb; kb0 += SUB) {
                     if (!ptx::mbar_wait_cluster_bounded(&bars->full[stage], phase, abort,
                                                         WAIT_LIMIT_NS)) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES);
+                    const int nsub = num_kb - kb0 < SUB ? num_kb - kb0 : SUB;
 #pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {     // two 32-byte MMA steps
+                    for (int q = 0; q < SUB; ++q) {
+                        if (q >= nsub) break;
+                        const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES) +
+                                            (uint32_t)(q * Cfg::SUB_BYTES);
 #pragma unroll
-                        for (int p = SA - 1; p >= 0; --p) {
-                            const uint32_t a_addr = s0 + p * A_TILE_BYTES + ks * 32;
-                            const uint32_t b_addr = s0 + SA * A_TILE_BYTES + ks * 32;
-                            // Issued from the smallest slice: the first MMA
-                            // into each accumulator overwrites it.
-                            const bool first = kb == 0 && ks == 0 && (p == 0 || p == SA - 1);
-                            if constexpr (X8)
-                                ptx::mma_f8_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
-                                                 ptx::sdesc_kmajor_sw64(a_addr),
-                                                 ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                                 first ? 0u : 1u);
-                            else
-                                ptx::mma_f16_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
-                                                  ptx::sdesc_kmajor_sw64(a_addr),
-                                                  ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                                  first ? 0u : 1u);
+                        for (int ks = 0; ks < 2; ++ks) {     // two 32-byte MMA steps
+#pragma unroll
+                            for (int p = SA - 1; p >= 0; --p) {
+                                const uint32_t a_addr = s0 + p * A_TILE_BYTES + ks * 32;
+                                const uint32_t b_addr = s0 + SA * A_TILE_BYTES + ks * 32;
+                                // Issued from the smallest slice: the first MMA
+                                // into each accumulator overwrites it.
+                                const bool first =
+                                    kb0 + q == 0 && ks == 0 && (p == 0 || p == SA - 1);
+                                if constexpr (X8)
+                                    ptx::mma_f8_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
+                                                     ptx::sdesc_kmajor_sw64(a_addr),
+                                                     ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                                     first ? 0u : 1u);
+                                else
+                                    ptx::mma_f16_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
+                                                      ptx::sdesc_kmajor_sw64(a_addr),
+                                                      ptx::sdesc_kmajor_sw64(b_addr), IDESC,
+                                                      first ? 0u : 1u);
+                            }
                         }
                     }
                     ptx::mma_commit_pair_mc(&bars->empty[stage], (uint16_t)3u);
@@ -1114,7 +1132,7 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
 
 // Clusters of two CTAs (one per SM of a pair) that fit at once, for the
 // pair kernel's persistent grid; 0 when the device cannot co-schedule any.
-template <int SA, bool TOUT, int MODE>
+template <int SA, bool TOUT, int MODE, int SUB>
 int pair_clusters(int smem) {
     static int cached[64];
     static std::once_flag once;
@@ -1138,7 +1156,7 @@ int pair_clusters(int smem) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT, MODE>, &cfg) !=
+    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT, MODE, SUB>, &cfg) !=
         cudaSuccess) {
         cudaGetLastError();
         n = 0;
@@ -1149,18 +1167,18 @@ int pair_clusters(int smem) {
 
 // The two-SM split product over rows [m0, m1) and columns [n0, n1) of the
 // product (Z^T's when TOUT).
-template <int SA, bool TOUT = false, int MODE = PM_SPLIT>
-afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
-                           cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
-    using Cfg = PairCfg<SA>;
+template <int SA, bool TOUT, int MODE, int SUB>
+afmm_status launch_tc_pair_sub(const TcPlan* t, float* Z, int64_t ldz, int* status,
+                               cudaStream_t st, int m0, int m1, int n0, int n1) {
+    using Cfg = PairCfg<SA, SUB>;
     const int n = (int)t->n;
     if (m1 < 0) m1 = n;
     if (n1 < 0) n1 = n;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT, MODE>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT, MODE, SUB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int tiles = ((m1 - m0 + PR_BM - 1) / PR_BM) * ((n1 - n0 + PR_BN - 1) / PR_BN);
-    const int cap = pair_clusters<SA, TOUT, MODE>(Cfg::SMEM);
+    const int cap = pair_clusters<SA, TOUT, MODE, SUB>(Cfg::SMEM);
     if (cap < 1) return AFMM_ERR_UNSUPPORTED;
     const int clusters = tiles < cap ? tiles : cap;
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
@@ -1185,12 +1203,33 @@ afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     main_kernel_begin(st);
-    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT, MODE>, ma, mb, mb64, Z,
+    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT, MODE, SUB>, ma, mb, mb64, Z,
                                      ldz, m0, m1, n0, n1, n, vec, split, status,
                                      (const uint32_t*)t->amax));
     main_kernel_end(st, 2 * clusters);
     count_launches(1);
     return AFMM_OK;
+}
+
+// K blocks per pair-kernel stage: 2, or AFMM_TC_KSUB=1 in the environment
+// (read once).  Measured at n = 8192 / 16384, two blocks per stage against
+// one: split BF16 kernel 1.54 against 1.55 ms, FP16 two slices 1.07
+// against 1.11 ms, E4M3 digits 4.26 against 4.39 ms; three blocks (the
+// two-slice forms, three 72 KiB stages) 1-2% slower than two.
+inline int pair_sub() {
+    static const int v = [] {
+        const char* e = std::getenv("AFMM_TC_KSUB");
+        return e && std::atoi(e) == 1 ? 1 : 2;
+    }();
+    return v;
+}
+
+template <int SA, bool TOUT = false, int MODE = PM_SPLIT>
+afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
+                           cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
+    if (pair_sub() == 2)
+        return launch_tc_pair_sub<SA, TOUT, MODE, 2>(t, Z, ldz, status, st, m0, m1, n0, n1);
+    return launch_tc_pair_sub<SA, TOUT, MODE, 1>(t, Z, ldz, status, st, m0, m1, n0, n1);
 }
 
 // The split product with S = t->slices BF16 slices: the two-SM kernel when
