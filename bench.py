@@ -569,7 +569,8 @@ def run_afmm(args):
         peak = ffma_peak_tflops()
         roof = {"bound": "alu", "unit": "TFLOP/s",
                 "peak_src": f"FP32 FFMA {SMS} SMs x 128 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"}
-        tag = simt_kernel_tag(prm["d1"])
+        # The FP64-target and exact CUDA-core forms run int8 dot products.
+        tag = (simt_kernel_tag(prm["d1"]) if vname == "simt_f32" else "simt_dp4a")
     if vname != "sparse":
         achieved = alg / (kms * 1e-3) / 1e12
         roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
