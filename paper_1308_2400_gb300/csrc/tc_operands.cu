@@ -148,17 +148,21 @@ widen_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
     if (bits) atomicCAS(status, 0, bad_status(bits));
 }
 
-// One-byte sources (E4M3, u8, i8): blocks of two stacked 64 x 64 tiles
-// (tile2_transpose_convert_u8), rows 128 * blockIdx.y ...
+// One-byte sources (E4M3, u8, i8): blocks of 256 rows x 64 columns, the
+// tile kept as bytes (tile_bytes_transpose_convert), rows 256 * blockIdx.y
+// ...
+constexpr int U8_TILE_ROWS = 256;
+
 template <int DT, int S, bool EXACT, bool H16 = false>
 __global__ void __launch_bounds__(256)
 widen_transpose2_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
                         __nv_bfloat16* __restrict__ dst, int64_t ldk, float lim, int vec,
                         int* status, int rep) {
-    __shared__ float tile[2][64][65];
-    const int bits = tile2_transpose_convert_u8<DT, S, EXACT, H16>(
-        src, n, lds, (int64_t)blockIdx.y * 128, (int64_t)blockIdx.x * 64, dst, ldk, lim,
-        vec != 0, tile, rep != 0);
+    __shared__ alignas(16) uint8_t tile[U8_TILE_ROWS][64];
+    __shared__ uint32_t lut[256];
+    const int bits = tile_bytes_transpose_convert<DT, S, EXACT, H16, U8_TILE_ROWS>(
+        src, n, lds, (int64_t)blockIdx.y * U8_TILE_ROWS, (int64_t)blockIdx.x * 64, dst, ldk,
+        lim, vec != 0, tile, rep != 0, lut);
     if (bits) atomicCAS(status, 0, bad_status(bits));
 }
 
@@ -196,9 +200,11 @@ afmm_status launch_widen_transpose(const void* src, int dt, int64_t n,
     const int vec = rows_aligned16(src, lds, (int64_t)dtype_size(dt));
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
         if constexpr (sizeof(typename Elem<DT>::T) == 1) {
-            // Rows (of the source) in blocks of 128: the row tiles a block
-            // holds must cover ldk, the destination's padded K extent.
-            const dim3 grid2((unsigned)g, (unsigned)((n + 127) / 128));
+            // Rows (of the source) in blocks of 256: the row tiles a block
+            // holds must cover ldk, the destination's padded K extent (n
+            // rounded up to 8, so within the last block).
+            const dim3 grid2((unsigned)g,
+                             (unsigned)((n + U8_TILE_ROWS - 1) / U8_TILE_ROWS));
             widen_transpose2_kernel<DT, S, EXACT, H16><<<grid2, block, 0, st>>>(
                 src, n, lds, dst, ldk, lim, vec, status, rep ? 1 : 0);
         } else {

@@ -229,30 +229,124 @@ __device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ s
     return bits | ((EXACT && bad) ? kBadRange : 0);
 }
 
-// Store half for one-byte sources, with a bank-conflict-free read of the
-// tile (row stride 65 floats: element (r, c) sits in bank (r + c) mod 32):
-// thread (column cc, quarter qq) takes rows 8 qq + e and 32 + 8 qq + e
-// (e = 0 .. 7), so the 32 lanes of a warp (8 columns x 4 quarters) read 32
-// different banks; each run of 8 rows becomes one 16-byte store per slice,
-// and the four quarters of a column still fill its 128-byte output row.
-template <int S, bool EXACT, bool H16 = false>
-__device__ __forceinline__ int tile_store_transposed_il(const float (*tile)[65], int64_t n,
-                                                        int64_t r0, int64_t c0,
-                                                        __nv_bfloat16* __restrict__ dst,
-                                                        int64_t ldk, float lim, bool rep) {
+// Rows r0 .. r0+RB-1 and columns c0 .. c0+63 of a source of one-byte
+// elements become rows c (K-major) of the destination, dst[(s * n + c) *
+// ldk + r] = slice s of src[r][c], with the checks of tile_store_transposed.
+// The tile stays in shared memory as the raw bytes, 64 per row, its four
+// 16-byte pieces stored at piece p ^ ((row / 8) mod 4):
+//   - loads: thread t copies piece t mod 4 of rows t / 4 + 64 i (16-byte
+//     cp.async copies, all RB / 64 in flight); the 8 lanes of a store
+//     phase write two 64-byte rows, 32 different banks;
+//   - stores: thread (column cc = t / 4, quarter qq = t mod 4) reads the
+//     bytes of rows 64 h + 32 half + 8 qq + e (e = 0 .. 7) of its column,
+//     whose pieces sit at (cc / 16) ^ qq: the four quarters of a warp read
+//     four different 16-byte slots of rows of one parity, 8 banks, no
+//     conflict; each run of 8 rows is one 16-byte store per slice, and the
+//     quarters fill a column's 128-byte output row.
+// Rows past n are zero (they pad K up to ldk); rows at or past ldk are not
+// stored.  `vec`: 16-byte aligned rows (element loads otherwise, and for a
+// tile cut by the last column).  `tile` is [RB][64], 16-byte aligned.
+// S = 1 and EXACT (Rep-factors): a byte has 256 possible values, so the
+// block first converts each once into lut[code] = the 16-bit result |
+// check bits << 16, and each element is then one table read.
+template <int DT, int S, bool EXACT, bool H16, int RB>
+__device__ __forceinline__ int tile_bytes_transpose_convert(const void* __restrict__ src,
+                                                            int64_t n, int64_t lds, int64_t r0,
+                                                            int64_t c0,
+                                                            __nv_bfloat16* __restrict__ dst,
+                                                            int64_t ldk, float lim, bool vec,
+                                                            uint8_t (*tile)[64], bool rep,
+                                                            uint32_t* lut) {
+    using T = typename Elem<DT>::T;
+    static_assert(sizeof(T) == 1, "one-byte elements");
+    static_assert(RB % 64 == 0, "whole 64-row passes");
+    constexpr int P = RB / 64;
+    constexpr bool LUT = S == 1 && EXACT;
     const int tid = threadIdx.x;
+    const uint8_t* s = static_cast<const uint8_t*>(src);
+    if constexpr (LUT) {
+        // 256 threads, one code each.
+        const uint8_t code = (uint8_t)tid;
+        T x;
+        __builtin_memcpy(&x, &code, 1);
+        bool bad = false;
+        const float v = value_checked<DT>(x, lim, bad);
+        uint32_t q[1];
+        int b = convert_pair<1, true, H16>(v, 0.f, lim, rep, q);
+        if (bad) b |= kBadRange;
+        lut[tid] = (q[0] & 0xFFFFu) | ((uint32_t)b << 16);
+    }
+    {
+        const int lr = tid >> 2, piece = tid & 3;
+        if (vec && c0 + 64 <= n) {
+            // Asynchronous 16-byte copies straight into the tile (no
+            // registers held while they are in flight); rows past n are
+            // zero-filled (source size 0, the address stays in row r0).
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const int row = 64 * i + lr;
+                const int64_t r = r0 + row;
+                const uint8_t* g = s + (r < n ? r : r0) * lds + c0 + 16 * piece;
+                const uint32_t d = (uint32_t)__cvta_generic_to_shared(
+                    &tile[row][16 * (piece ^ ((row >> 3) & 3))]);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(g),
+                             "r"(r < n ? 16 : 0)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        } else {
+            // Unaligned rows or the last, cut column tile: element loads.
+#pragma unroll 1
+            for (int i = 0; i < P; ++i) {
+                const int row = 64 * i + lr;
+                const int64_t r = r0 + row;
+                uint8_t* d = &tile[row][16 * (piece ^ ((row >> 3) & 3))];
+                for (int t = 0; t < 16; ++t) {
+                    const int64_t c = c0 + 16 * piece + t;
+                    d[t] = (r < n && c < n) ? s[r * lds + c] : (uint8_t)0;
+                }
+            }
+        }
+    }
+    __syncthreads();
     const int cc = tid >> 2, qq = tid & 3;
     const int64_t c = c0 + cc;
-    int bits = 0;
     if (c >= n) return 0;
+    const int slot = 16 * ((cc >> 4) ^ qq) + (cc & 15);
+    if constexpr (LUT) {
+        uint32_t acc = 0;
+#pragma unroll 2
+        for (int h = 0; h < 2 * P; ++h) {
+            const int tr = 32 * h + 8 * qq;
+            const int64_t r = r0 + tr;
+            if (r >= ldk) continue;
+            uint32_t w[4];
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int tr = 32 * half + 8 * qq;             // first tile row of this run
+            for (int e = 0; e < 8; e += 2) {
+                const uint32_t a = lut[tile[tr + e][slot]], b = lut[tile[tr + e + 1][slot]];
+                acc |= a | b;
+                w[e / 2] = __byte_perm(a, b, 0x5410);   // a's low half, then b's
+            }
+            *reinterpret_cast<uint4*>(dst + c * ldk + r) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        return (int)(acc >> 16);
+    }
+    int bits = 0;
+    bool bad = false;
+#pragma unroll 2
+    for (int h = 0; h < 2 * P; ++h) {
+        const int tr = 32 * h + 8 * qq;                // first tile row of this run
         const int64_t r = r0 + tr;
         if (r >= ldk) continue;                        // ldk is a multiple of 8
         float v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = tile[tr + e][cc];
+        for (int e = 0; e < 8; ++e) {
+            T x;
+            const uint8_t byte = tile[tr + e][slot];
+            __builtin_memcpy(&x, &byte, 1);
+            v[e] = value_checked<DT>(x, lim, bad);
+        }
         uint32_t w[S][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
@@ -266,67 +360,7 @@ __device__ __forceinline__ int tile_store_transposed_il(const float (*tile)[65],
             *reinterpret_cast<uint4*>(dst + ((int64_t)sl * n + c) * ldk + r) =
                 make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
     }
-    return bits;
-}
-
-// Two vertically adjacent 64 x 64 tiles (rows r0 .. r0+127) of a source of
-// one-byte elements, both loaded before either is converted (two 16-byte
-// loads in flight per thread).  Load mapping, per tile: warps 2b and 2b+1
-// cover tile rows 16b .. 16b+15; lane l takes the 16 columns q = l / 8 of
-// row 16b + (l mod 8) + 8 * ((q / 2) xor (warp mod 2)), so the 32 lanes of a
-// warp write 32 different banks of the stride-65 tile (the rows and
-// quarters they take differ by 0, 8, 16, 24 in bank).  Store half:
-// tile_store_transposed_il.  `vec` as in tile_load_f32; `tile` is
-// [2][64][65].  Returns the check bits of both tiles.
-template <int DT, int S, bool EXACT, bool H16 = false>
-__device__ __forceinline__ int tile2_transpose_convert_u8(const void* __restrict__ src,
-                                                          int64_t n, int64_t lds, int64_t r0,
-                                                          int64_t c0,
-                                                          __nv_bfloat16* __restrict__ dst,
-                                                          int64_t ldk, float lim, bool vec,
-                                                          float (*tile)[64][65], bool rep) {
-    using T = typename Elem<DT>::T;
-    static_assert(sizeof(T) == 1, "one-byte elements");
-    const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int q = l >> 3;
-    const int lr = 16 * (warp >> 1) + (l & 7) + 8 * ((q >> 1) ^ (warp & 1));
-    const int lc = 16 * q;
-    const T* s = static_cast<const T*>(src);
-    bool bad = false;
-    if (vec && c0 + 64 <= n) {
-        uint4 v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t r = r0 + 64 * h + lr;
-            v[h] = r < n ? *reinterpret_cast<const uint4*>(s + r * lds + c0 + lc)
-                         : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const T* e = reinterpret_cast<const T*>(&v[h]);
-#pragma unroll
-            for (int t = 0; t < 16; ++t) tile[h][lr][lc + t] = value_checked<DT>(e[t], lim, bad);
-        }
-    } else {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t r = r0 + 64 * h + lr;
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int64_t c = c0 + lc + t;
-                tile[h][lr][lc + t] =
-                    (r < n && c < n) ? value_checked<DT>(s[r * lds + c], lim, bad) : 0.f;
-            }
-        }
-    }
-    __syncthreads();
-    int bits = (EXACT && bad) ? kBadRange : 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-        if (r0 + 64 * h < ldk)
-            bits |= tile_store_transposed_il<S, EXACT, H16>(tile[h], n, r0 + 64 * h, c0, dst,
-                                                            ldk, lim, rep);
-    return bits;
+    return bits | ((EXACT && bad) ? kBadRange : 0);
 }
 
 // Whether rows of a dtype-dt source start 16-byte aligned.

@@ -157,6 +157,48 @@ def test_tc_bf16x3_ragged(workload, n):
     check_fp32(inst, Z, bound_fn=tc_elem_bound)
 
 
+def _padded(arr, ld, dtype):
+    """arr (n x n) in an n x ld buffer of torch dtype `dtype` (padding 0)."""
+    n = arr.shape[0]
+    buf = np.zeros((n, ld), dtype=np.float64)
+    buf[:, :n] = arr
+    if dtype == "e4m3":
+        return torch.from_numpy(buf.astype(np.float32)).to(torch.float8_e4m3fn) \
+            .view(torch.uint8).cuda()
+    tdt = {"u8": torch.uint8, "i32": torch.int32, "f32": torch.float32,
+           "bf16": torch.bfloat16}[dtype]
+    return torch.from_numpy(buf.astype(np.float64)).to(tdt).cuda()
+
+
+@pytest.mark.parametrize("n,yd,pad", [(512, "e4m3", 0), (520, "i32", 0), (600, "u8", 3),
+                                      (777, "f32", 5), (1000, "bf16", 1), (1537, "e4m3", 16)])
+@pytest.mark.parametrize("variant", [1, 10])
+def test_tc_pair_case_a_storage_types_and_padding(variant, n, yd, pad):
+    """Case A on the two-SM kernel (split BF16 and FP16 forms): ragged n,
+    every Rep-factor storage type through the transposition, padded rows
+    of X, Y (the per-element load paths) and Z (padding left alone)."""
+    from paper_1308_2400_gb300 import Plan, make_desc
+    rng = np.random.default_rng(n + pad)
+    X = rng.uniform(-1, 1, size=(n, n))
+    X[rng.random((n, n)) > 0.7] = 0
+    X = X.astype(np.float32)
+    Y = np.minimum(rng.poisson(3.0, size=(n, n)), 16).astype(np.int64)
+    Y[:, -1] = 16                       # the last, partial tile column
+    ld = n + pad
+    Xt = _padded(X, ld, "f32")
+    Yt = _padded(Y, ld, yd)
+    Zb = torch.full((n, ld), 7.0, dtype=torch.float32, device="cuda")
+    p = Plan(make_desc(n, "A", "f32", yd, "f32", "fp32", variant=variant,
+                       ldx=ld, ldy=ld, ldz=ld))
+    p(Xt, Yt, Zb)
+    p.sync()
+    Z = Zb.cpu().numpy()
+    inst = W.Instance("A", X, Y, name=f"mn_{yd}", x_dtype="f32", y_dtype=yd,
+                      z_dtype="f32", target="fp32")
+    check_fp32(inst, Z[:, :n], bound_fn=tc_elem_bound)
+    assert np.all(Z[:, n:] == 7.0)
+
+
 @pytest.mark.parametrize("n", [32, 200, 256, 1000])
 def test_tc_fused_split_kernel(n):
     """Case A with the split done inside the product kernel
