@@ -100,6 +100,36 @@ x8_rep_transpose_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
     if (bits) atomicCAS(status, 0, bad_status(bits));
 }
 
+// The same for one-byte Rep-factors (int8, uint8, E4M3): blocks of 256
+// rows x 64 columns kept as bytes in shared memory, each of the 256 codes
+// converted and checked once per block (tile_bytes_load and
+// tile_bytes_store_lut); 8-byte stores of eight rows.
+constexpr int X8_TILE_ROWS = 256;
+
+template <int DT>
+__global__ void __launch_bounds__(X8_THREADS)
+x8_rep_transpose_u8_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
+                           uint8_t* __restrict__ dst, int64_t ldk, int vec, int* status) {
+    using T = typename Elem<DT>::T;
+    static_assert(sizeof(T) == 1, "one-byte elements");
+    __shared__ alignas(16) uint8_t tile[X8_TILE_ROWS][64];
+    __shared__ uint32_t lut[256];
+    {
+        const uint8_t code = (uint8_t)threadIdx.x;
+        T x;
+        __builtin_memcpy(&x, &code, 1);
+        const float y = (float)Elem<DT>::get(&x, 0);
+        const int b = rep_bits(y) | (y > kX8RepMax ? kBadRange : 0);
+        lut[threadIdx.x] = (uint32_t)(e4m3x2_rn(y, 0.f) & 0xFFu) | ((uint32_t)b << 16);
+    }
+    const int64_t r0 = (int64_t)blockIdx.y * X8_TILE_ROWS, c0 = (int64_t)blockIdx.x * 64;
+    tile_bytes_load<X8_TILE_ROWS>(static_cast<const uint8_t*>(src), n, lds, r0, c0, vec != 0,
+                                  tile);
+    __syncthreads();
+    const uint32_t acc = tile_bytes_store_lut<X8_TILE_ROWS, 1>(tile, lut, n, r0, c0, dst, ldk);
+    if (acc >> 16) atomicCAS(status, 0, bad_status((int)(acc >> 16)));
+}
+
 // Case B: the integer Base values of Y transposed into two digit slices,
 // dst[(s * n + c) * ldk + r] from Y[r][c]; and the Rep-factors of X kept
 // as E4M3 rows dst[r * ldk + c].  Same ranges and checks as above.
@@ -233,8 +263,15 @@ afmm_status tc_x8_rep_transpose(const void* src, int dt, int64_t n, int64_t lds,
     const int vec = rows_aligned16(src, lds, (int64_t)dtype_size(dt));
     auto* d = static_cast<uint8_t*>(dst);
     afmm_status rc = dispatch_dtype(dt, [&]<int DT>() -> afmm_status {
-        x8_rep_transpose_kernel<DT><<<dim3((unsigned)g, (unsigned)g), X8_THREADS, 0, st>>>(
-            src, n, lds, d, ldk, vec, status);
+        if constexpr (sizeof(typename Elem<DT>::T) == 1) {
+            // Row blocks of 256 cover ldk (n rounded up to 16).
+            const dim3 grid((unsigned)g, (unsigned)((n + X8_TILE_ROWS - 1) / X8_TILE_ROWS));
+            x8_rep_transpose_u8_kernel<DT><<<grid, X8_THREADS, 0, st>>>(src, n, lds, d, ldk,
+                                                                         vec, status);
+        } else {
+            x8_rep_transpose_kernel<DT><<<dim3((unsigned)g, (unsigned)g), X8_THREADS, 0, st>>>(
+                src, n, lds, d, ldk, vec, status);
+        }
         return AFMM_OK;
     });
     AFMM_TRY(rc);

@@ -229,26 +229,116 @@ __device__ __forceinline__ int tile_transpose_convert(const void* __restrict__ s
     return bits | ((EXACT && bad) ? kBadRange : 0);
 }
 
+// One-byte sources transposed through shared memory as raw bytes.  A block
+// of 256 threads takes rows r0 .. r0+RB-1 and columns c0 .. c0+63 of the
+// row-major source into tile[RB][64] (16-byte aligned), each row's four
+// 16-byte pieces stored at piece p ^ ((row / 8) mod 4):
+//   - loads (tile_bytes_load): thread t copies piece t mod 4 of rows t / 4 +
+//     64 i (16-byte cp.async copies, all RB / 64 in flight); the 8 lanes of
+//     a store phase write two 64-byte rows, 32 different banks.  Rows past n
+//     are zero (they pad K up to ldk); `vec`: 16-byte aligned rows (element
+//     loads otherwise, and for a tile cut by the last column);
+//   - stores: thread (column cc = t / 4, quarter qq = t mod 4) reads the
+//     bytes of rows 32 h + 8 qq + e (e = 0 .. 7) of its column, whose pieces
+//     sit at (cc / 16) ^ qq: the four quarters of a warp read four different
+//     16-byte slots of rows of one parity, 8 banks, no conflict.  Each run
+//     of 8 rows is one store, and the quarters fill a column's output row.
+//     Rows at or past ldk (a multiple of 8) are not stored.
+template <int RB>
+__device__ __forceinline__ void tile_bytes_load(const uint8_t* __restrict__ s, int64_t n,
+                                                int64_t lds, int64_t r0, int64_t c0, bool vec,
+                                                uint8_t (*tile)[64]) {
+    static_assert(RB % 64 == 0, "whole 64-row passes");
+    constexpr int P = RB / 64;
+    const int lr = threadIdx.x >> 2, piece = threadIdx.x & 3;
+    if (vec && c0 + 64 <= n) {
+        // Asynchronous 16-byte copies straight into the tile (no registers
+        // held while they are in flight); rows past n are zero-filled
+        // (source size 0, the address stays in row r0).
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int row = 64 * i + lr;
+            const int64_t r = r0 + row;
+            const uint8_t* g = s + (r < n ? r : r0) * lds + c0 + 16 * piece;
+            const uint32_t d =
+                (uint32_t)__cvta_generic_to_shared(&tile[row][16 * (piece ^ ((row >> 3) & 3))]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(g),
+                         "r"(r < n ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    } else {
+        // Unaligned rows or the last, cut column tile: element loads.
+#pragma unroll 1
+        for (int i = 0; i < P; ++i) {
+            const int row = 64 * i + lr;
+            const int64_t r = r0 + row;
+            uint8_t* d = &tile[row][16 * (piece ^ ((row >> 3) & 3))];
+            for (int t = 0; t < 16; ++t) {
+                const int64_t c = c0 + 16 * piece + t;
+                d[t] = (r < n && c < n) ? s[r * lds + c] : (uint8_t)0;
+            }
+        }
+    }
+}
+
+// The byte of tile row `row` in this thread's column (slot from
+// tile_bytes_slot).
+__device__ __forceinline__ int tile_bytes_slot(int cc, int qq) {
+    return 16 * ((cc >> 4) ^ qq) + (cc & 15);
+}
+
+// Store half through a table: a byte has 256 possible values, each
+// converted once per block into lut[code] = the OB-byte result (low bits)
+// | check bits << 16.  Output row c = c0 + cc gets dst[c * ldk + r] for
+// OB-byte elements (OB = 2: 16-byte stores of 8 values; OB = 1: 8-byte
+// stores).  Returns the OR of the table entries used (check bits << 16).
+template <int RB, int OB>
+__device__ __forceinline__ uint32_t tile_bytes_store_lut(const uint8_t (*tile)[64],
+                                                         const uint32_t* lut, int64_t n,
+                                                         int64_t r0, int64_t c0,
+                                                         void* __restrict__ dst, int64_t ldk) {
+    static_assert(OB == 1 || OB == 2, "one- or two-byte results");
+    const int cc = threadIdx.x >> 2, qq = threadIdx.x & 3;
+    const int64_t c = c0 + cc;
+    if (c >= n) return 0;
+    const int slot = tile_bytes_slot(cc, qq);
+    uint32_t acc = 0;
+#pragma unroll 2
+    for (int h = 0; h < RB / 32; ++h) {
+        const int tr = 32 * h + 8 * qq;
+        const int64_t r = r0 + tr;
+        if (r >= ldk) continue;
+        uint32_t e[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            e[u] = lut[tile[tr + u][slot]];
+            acc |= e[u];
+        }
+        if constexpr (OB == 2) {
+            *reinterpret_cast<uint4*>(static_cast<uint16_t*>(dst) + c * ldk + r) =
+                make_uint4(__byte_perm(e[0], e[1], 0x5410), __byte_perm(e[2], e[3], 0x5410),
+                           __byte_perm(e[4], e[5], 0x5410), __byte_perm(e[6], e[7], 0x5410));
+        } else {
+            // Low bytes of e[0..3] and e[4..7]: pairs, then pairs of pairs.
+            const uint32_t lo = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
+                                            __byte_perm(e[2], e[3], 0x0040), 0x5410);
+            const uint32_t hi = __byte_perm(__byte_perm(e[4], e[5], 0x0040),
+                                            __byte_perm(e[6], e[7], 0x0040), 0x5410);
+            *reinterpret_cast<uint2*>(static_cast<uint8_t*>(dst) + c * ldk + r) =
+                make_uint2(lo, hi);
+        }
+    }
+    return acc;
+}
+
 // Rows r0 .. r0+RB-1 and columns c0 .. c0+63 of a source of one-byte
 // elements become rows c (K-major) of the destination, dst[(s * n + c) *
-// ldk + r] = slice s of src[r][c], with the checks of tile_store_transposed.
-// The tile stays in shared memory as the raw bytes, 64 per row, its four
-// 16-byte pieces stored at piece p ^ ((row / 8) mod 4):
-//   - loads: thread t copies piece t mod 4 of rows t / 4 + 64 i (16-byte
-//     cp.async copies, all RB / 64 in flight); the 8 lanes of a store
-//     phase write two 64-byte rows, 32 different banks;
-//   - stores: thread (column cc = t / 4, quarter qq = t mod 4) reads the
-//     bytes of rows 64 h + 32 half + 8 qq + e (e = 0 .. 7) of its column,
-//     whose pieces sit at (cc / 16) ^ qq: the four quarters of a warp read
-//     four different 16-byte slots of rows of one parity, 8 banks, no
-//     conflict; each run of 8 rows is one 16-byte store per slice, and the
-//     quarters fill a column's 128-byte output row.
-// Rows past n are zero (they pad K up to ldk); rows at or past ldk are not
-// stored.  `vec`: 16-byte aligned rows (element loads otherwise, and for a
-// tile cut by the last column).  `tile` is [RB][64], 16-byte aligned.
-// S = 1 and EXACT (Rep-factors): a byte has 256 possible values, so the
-// block first converts each once into lut[code] = the 16-bit result |
-// check bits << 16, and each element is then one table read.
+// ldk + r] = slice s of src[r][c], with the checks of tile_store_transposed
+// (tile_bytes_load, then the stores described there).  S = 1 and EXACT
+// (Rep-factors): through the table of tile_bytes_store_lut, built here
+// into `lut` (256 entries).
 template <int DT, int S, bool EXACT, bool H16, int RB>
 __device__ __forceinline__ int tile_bytes_transpose_convert(const void* __restrict__ src,
                                                             int64_t n, int64_t lds, int64_t r0,
@@ -259,11 +349,8 @@ __device__ __forceinline__ int tile_bytes_transpose_convert(const void* __restri
                                                             uint32_t* lut) {
     using T = typename Elem<DT>::T;
     static_assert(sizeof(T) == 1, "one-byte elements");
-    static_assert(RB % 64 == 0, "whole 64-row passes");
-    constexpr int P = RB / 64;
     constexpr bool LUT = S == 1 && EXACT;
     const int tid = threadIdx.x;
-    const uint8_t* s = static_cast<const uint8_t*>(src);
     if constexpr (LUT) {
         // 256 threads, one code each.
         const uint8_t code = (uint8_t)tid;
@@ -276,66 +363,18 @@ __device__ __forceinline__ int tile_bytes_transpose_convert(const void* __restri
         if (bad) b |= kBadRange;
         lut[tid] = (q[0] & 0xFFFFu) | ((uint32_t)b << 16);
     }
-    {
-        const int lr = tid >> 2, piece = tid & 3;
-        if (vec && c0 + 64 <= n) {
-            // Asynchronous 16-byte copies straight into the tile (no
-            // registers held while they are in flight); rows past n are
-            // zero-filled (source size 0, the address stays in row r0).
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-                const int row = 64 * i + lr;
-                const int64_t r = r0 + row;
-                const uint8_t* g = s + (r < n ? r : r0) * lds + c0 + 16 * piece;
-                const uint32_t d = (uint32_t)__cvta_generic_to_shared(
-                    &tile[row][16 * (piece ^ ((row >> 3) & 3))]);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(g),
-                             "r"(r < n ? 16 : 0)
-                             : "memory");
-            }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        } else {
-            // Unaligned rows or the last, cut column tile: element loads.
-#pragma unroll 1
-            for (int i = 0; i < P; ++i) {
-                const int row = 64 * i + lr;
-                const int64_t r = r0 + row;
-                uint8_t* d = &tile[row][16 * (piece ^ ((row >> 3) & 3))];
-                for (int t = 0; t < 16; ++t) {
-                    const int64_t c = c0 + 16 * piece + t;
-                    d[t] = (r < n && c < n) ? s[r * lds + c] : (uint8_t)0;
-                }
-            }
-        }
-    }
+    tile_bytes_load<RB>(static_cast<const uint8_t*>(src), n, lds, r0, c0, vec, tile);
     __syncthreads();
+    if constexpr (LUT)
+        return (int)(tile_bytes_store_lut<RB, 2>(tile, lut, n, r0, c0, dst, ldk) >> 16);
     const int cc = tid >> 2, qq = tid & 3;
     const int64_t c = c0 + cc;
     if (c >= n) return 0;
-    const int slot = 16 * ((cc >> 4) ^ qq) + (cc & 15);
-    if constexpr (LUT) {
-        uint32_t acc = 0;
-#pragma unroll 2
-        for (int h = 0; h < 2 * P; ++h) {
-            const int tr = 32 * h + 8 * qq;
-            const int64_t r = r0 + tr;
-            if (r >= ldk) continue;
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                const uint32_t a = lut[tile[tr + e][slot]], b = lut[tile[tr + e + 1][slot]];
-                acc |= a | b;
-                w[e / 2] = __byte_perm(a, b, 0x5410);   // a's low half, then b's
-            }
-            *reinterpret_cast<uint4*>(dst + c * ldk + r) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        return (int)(acc >> 16);
-    }
+    const int slot = tile_bytes_slot(cc, qq);
     int bits = 0;
     bool bad = false;
 #pragma unroll 2
-    for (int h = 0; h < 2 * P; ++h) {
+    for (int h = 0; h < RB / 32; ++h) {
         const int tr = 32 * h + 8 * qq;                // first tile row of this run
         const int64_t r = r0 + tr;
         if (r >= ldk) continue;                        // ldk is a multiple of 8
