@@ -187,6 +187,20 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
     return d;
 }
 
+// The same for a tile stored with a 128-byte swizzle: rows of 128 bytes,
+// 8-row groups 1024 bytes apart, swizzle mode 2 (SWIZZLE_128B).  A K step
+// inside a row advances the start address by its byte offset (the tile
+// base stays 1024-byte aligned, so the base offset field stays 0).
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;                 // leading byte offset (unused)
+    d |= (uint64_t)(1024u >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1u << 46;                 // version
+    d |= (uint64_t)2u << 61;                 // SWIZZLE_128B
+    return d;
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both
 // operands K-major, shape M x N.
 //   bits 4-5 D format (1 = F32)   bits 7-9 A format (1 = BF16)

@@ -486,15 +486,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
 // (barriers initialised) and before releasing TMEM.
 constexpr int PR_BM = 256, PR_BN = 256;           // pair tile
 constexpr int PR_HALF = 128;                       // rows of A and of B per CTA
-constexpr int PR_B_BYTES = PR_HALF * TC_BK * 2;    // 8 KiB
 constexpr int PR_GROUP_M = 5;                      // tile raster band (tile rows)
 constexpr int PR_EPI_WARPS = 2 * (TC_EPI_THREADS / 32);   // tempty arrivals
 
-// A stage holds SUB consecutive 64-byte K blocks, each laid out as its SA
-// A tiles then its B tile (SUB = 2 halves the stage hand-overs per MMA).
-template <int SA, int SUB = 1>
+// A stage holds SUB consecutive K blocks of RB-byte operand rows (64: a
+// 64-byte swizzle, 128: a 128-byte swizzle), each laid out as its SA A
+// tiles (128 rows) then its B tile (128 rows).  SUB = 2 halves the stage
+// hand-overs per MMA; 128-byte rows move the same stage in half as many
+// TMA row requests as two 64-byte blocks.
+template <int SA, int SUB = 1, int RB = 64>
 struct PairCfg {
-    static constexpr int SUB_BYTES = SA * A_TILE_BYTES + PR_B_BYTES;
+    static constexpr int A_BYTES = PR_HALF * RB;     // one A slice tile
+    static constexpr int B_BYTES = PR_HALF * RB;     // this CTA's half of B
+    static constexpr int SUB_BYTES = SA * A_BYTES + B_BYTES;
     static constexpr int STAGE_BYTES = SUB * SUB_BYTES;
     static constexpr int STAGES_FIT = (SMEM_OPTIN - 1024 - BARS_BYTES) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT > MAX_STAGES ? MAX_STAGES : STAGES_FIT;
@@ -551,18 +555,20 @@ __device__ __forceinline__ PairUnit pair_unit(int u, int whole, int split, int t
 // integer below 2^24, and the epilogue writes 16 acc_h + acc_l as int32).
 constexpr int PM_SPLIT = 0, PM_H16 = 1, PM_X8 = 2;
 
-template <int SA, bool TOUT, int MODE = PM_SPLIT, int SUB = 1>
+template <int SA, bool TOUT, int MODE = PM_SPLIT, int SUB = 1, int RB = 64>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmB64, float* __restrict__ Z, int64_t ldz,
                int m0, int M, int n0, int N, int K, int vec, int split, int* status,
                const uint32_t* __restrict__ amax) {
-    using Cfg = PairCfg<SA, SUB>;
+    using Cfg = PairCfg<SA, SUB, RB>;
     constexpr bool H16 = MODE == PM_H16, X8 = MODE == PM_X8;
     static_assert((!H16 && !X8) || SA == 2, "FP16 and digit forms: two A slices");
-    // Elements per 64-byte row of a K block.
-    constexpr int BKE = X8 ? 64 : TC_BK;
+    static_assert(RB == 64 || RB == 128, "64- or 128-byte operand rows");
+    // Elements per RB-byte row of a K block; 32-byte MMA K steps per row.
+    constexpr int BKE = X8 ? RB : RB / 2;
+    constexpr int KSTEPS = RB / 32;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
     uint8_t* tiles = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -622,7 +628,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                 const int bhalf = w.width / 2;
                 const int brow = n0 + w.tn * PR_BN + w.col + (int)rank * bhalf;
                 const CUtensorMap* mb = w.width == PR_BN ? &tmB : &tmB64;
-                const uint32_t bytes = SA * A_TILE_BYTES + (uint32_t)bhalf * TC_BK * 2;
+                const uint32_t bytes = SA * Cfg::A_BYTES + (uint32_t)bhalf * RB;
                 for (int kb0 = 0; kb0 < num_kb; kb0 += SUB) {
                     if (!ptx::mbar_wait_cluster_bounded(&bars->empty[stage], phase ^ 1u, abort,
                                                         WAIT_LIMIT_NS)) {
@@ -643,9 +649,9 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         uint8_t* st = tiles + stage * Cfg::STAGE_BYTES + q * Cfg::SUB_BYTES;
 #pragma unroll
                         for (int s = 0; s < SA; ++s)
-                            ptx::tma_load_3d_pair(st + s * A_TILE_BYTES, &tmA, full0, kb * BKE,
+                            ptx::tma_load_3d_pair(st + s * Cfg::A_BYTES, &tmA, full0, kb * BKE,
                                                   arow, s);
-                        ptx::tma_load_3d_pair(st + SA * A_TILE_BYTES, mb, full0, kb * BKE, brow,
+                        ptx::tma_load_3d_pair(st + SA * Cfg::A_BYTES, mb, full0, kb * BKE, brow,
                                               0);
                     }
                     issued_phase[stage] = (int)phase;
@@ -704,25 +710,27 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         const uint32_t s0 = ptx::smem_addr(tiles + stage * Cfg::STAGE_BYTES) +
                                             (uint32_t)(q * Cfg::SUB_BYTES);
 #pragma unroll
-                        for (int ks = 0; ks < 2; ++ks) {     // two 32-byte MMA steps
+                        for (int ks = 0; ks < KSTEPS; ++ks) {     // 32-byte MMA steps
 #pragma unroll
                             for (int p = SA - 1; p >= 0; --p) {
-                                const uint32_t a_addr = s0 + p * A_TILE_BYTES + ks * 32;
-                                const uint32_t b_addr = s0 + SA * A_TILE_BYTES + ks * 32;
+                                const uint32_t a_addr = s0 + p * Cfg::A_BYTES + ks * 32;
+                                const uint32_t b_addr = s0 + SA * Cfg::A_BYTES + ks * 32;
+                                const uint64_t a_desc = RB == 128
+                                                            ? ptx::sdesc_kmajor_sw128(a_addr)
+                                                            : ptx::sdesc_kmajor_sw64(a_addr);
+                                const uint64_t b_desc = RB == 128
+                                                            ? ptx::sdesc_kmajor_sw128(b_addr)
+                                                            : ptx::sdesc_kmajor_sw64(b_addr);
                                 // Issued from the smallest slice: the first MMA
                                 // into each accumulator overwrites it.
                                 const bool first =
                                     kb0 + q == 0 && ks == 0 && (p == 0 || p == SA - 1);
                                 if constexpr (X8)
                                     ptx::mma_f8_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
-                                                     ptx::sdesc_kmajor_sw64(a_addr),
-                                                     ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                                     first ? 0u : 1u);
+                                                     a_desc, b_desc, IDESC, first ? 0u : 1u);
                                 else
                                     ptx::mma_f16_pair(tmem + (p == 0 ? 0u : (uint32_t)PR_BN),
-                                                      ptx::sdesc_kmajor_sw64(a_addr),
-                                                      ptx::sdesc_kmajor_sw64(b_addr), IDESC,
-                                                      first ? 0u : 1u);
+                                                      a_desc, b_desc, IDESC, first ? 0u : 1u);
                             }
                         }
                     }
@@ -859,20 +867,22 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
 }  // namespace
 
 // 3-D map over a stack of `slices` matrices of `rows` x `cols` (K) es-byte
-// elements with leading dimension `ld`; box = 64 bytes (K) x box_rows x 1.
+// elements with leading dimension `ld`; box = row_bytes (64 or 128, with a
+// swizzle of that width) of K x box_rows x 1.
 afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
-                       int64_t ld, int slices, int box_rows, int es) {
+                       int64_t ld, int slices, int box_rows, int es, int row_bytes) {
     auto fn = get_encode_fn();
-    if (!fn || (es != 1 && es != 2)) return AFMM_ERR_CUDA;
+    if (!fn || (es != 1 && es != 2) || (row_bytes != 64 && row_bytes != 128))
+        return AFMM_ERR_CUDA;
     cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)slices};
     cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(ld * es * rows)};
-    cuuint32_t box[3] = {(cuuint32_t)(64 / es), (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(row_bytes / es), (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(reinterpret_cast<CUtensorMap*>(out),
                     es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
                     3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? AFMM_OK : AFMM_ERR_CUDA;
 }
 
@@ -1132,7 +1142,7 @@ afmm_status launch_tc(const TcPlan* t, float* Z, int64_t ldz, int* status, cudaS
 
 // Clusters of two CTAs (one per SM of a pair) that fit at once, for the
 // pair kernel's persistent grid; 0 when the device cannot co-schedule any.
-template <int SA, bool TOUT, int MODE, int SUB>
+template <int SA, bool TOUT, int MODE, int SUB, int RB>
 int pair_clusters(int smem) {
     static int cached[64];
     static std::once_flag once;
@@ -1156,7 +1166,7 @@ int pair_clusters(int smem) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT, MODE, SUB>, &cfg) !=
+    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<SA, TOUT, MODE, SUB, RB>, &cfg) !=
         cudaSuccess) {
         cudaGetLastError();
         n = 0;
@@ -1167,25 +1177,31 @@ int pair_clusters(int smem) {
 
 // The two-SM split product over rows [m0, m1) and columns [n0, n1) of the
 // product (Z^T's when TOUT).
-template <int SA, bool TOUT, int MODE, int SUB>
+template <int SA, bool TOUT, int MODE, int SUB, int RB>
 afmm_status launch_tc_pair_sub(const TcPlan* t, float* Z, int64_t ldz, int* status,
                                cudaStream_t st, int m0, int m1, int n0, int n1) {
-    using Cfg = PairCfg<SA, SUB>;
+    using Cfg = PairCfg<SA, SUB, RB>;
     const int n = (int)t->n;
     if (m1 < 0) m1 = n;
     if (n1 < 0) n1 = n;
-    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT, MODE, SUB>,
+    AFMM_CUDA_TRY(cudaFuncSetAttribute(tc_pair_kernel<SA, TOUT, MODE, SUB, RB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::SMEM));
     const int tiles = ((m1 - m0 + PR_BM - 1) / PR_BM) * ((n1 - n0 + PR_BN - 1) / PR_BN);
-    const int cap = pair_clusters<SA, TOUT, MODE, SUB>(Cfg::SMEM);
+    const int cap = pair_clusters<SA, TOUT, MODE, SUB, RB>(Cfg::SMEM);
     if (cap < 1) return AFMM_ERR_UNSUPPORTED;
     const int clusters = tiles < cap ? tiles : cap;
     const int vec = (ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0);
     CUtensorMap ma, mb, mb64;
-    std::memcpy(&ma, TOUT ? t->tmap_at : t->tmap_a, sizeof ma);
-    std::memcpy(&mb, TOUT ? t->tmap_bt2 : t->tmap_b2, sizeof mb);
-    std::memcpy(&mb64, TOUT ? t->tmap_bt3 : t->tmap_b3, sizeof mb64);
+    if constexpr (RB == 128) {
+        std::memcpy(&ma, TOUT ? t->tmap_atw : t->tmap_aw, sizeof ma);
+        std::memcpy(&mb, TOUT ? t->tmap_bt2w : t->tmap_b2w, sizeof mb);
+        std::memcpy(&mb64, TOUT ? t->tmap_bt3w : t->tmap_b3w, sizeof mb64);
+    } else {
+        std::memcpy(&ma, TOUT ? t->tmap_at : t->tmap_a, sizeof ma);
+        std::memcpy(&mb, TOUT ? t->tmap_bt2 : t->tmap_b2, sizeof mb);
+        std::memcpy(&mb64, TOUT ? t->tmap_bt3 : t->tmap_b3, sizeof mb64);
+    }
     // A last round with at most half as many tiles as pairs is run as
     // 256 x 128 halves.
     const int rem = tiles % clusters;
@@ -1203,7 +1219,7 @@ afmm_status launch_tc_pair_sub(const TcPlan* t, float* Z, int64_t ldz, int* stat
     cfg.attrs = at;
     cfg.numAttrs = 1;
     main_kernel_begin(st);
-    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT, MODE, SUB>, ma, mb, mb64, Z,
+    AFMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_pair_kernel<SA, TOUT, MODE, SUB, RB>, ma, mb, mb64, Z,
                                      ldz, m0, m1, n0, n1, n, vec, split, status,
                                      (const uint32_t*)t->amax));
     main_kernel_end(st, 2 * clusters);
@@ -1211,13 +1227,17 @@ afmm_status launch_tc_pair_sub(const TcPlan* t, float* Z, int64_t ldz, int* stat
     return AFMM_OK;
 }
 
-// K blocks per pair-kernel stage: 2, or AFMM_TC_KSUB=1 in the environment
-// (read once).  Measured at n = 8192 / 16384, two blocks per stage against
-// one: split BF16 kernel 1.54 against 1.55 ms, FP16 two slices 1.07
-// against 1.11 ms, E4M3 digits 4.26 against 4.39 ms; three blocks (the
-// two-slice forms, three 72 KiB stages) 1-2% slower than two.
-inline int pair_sub() {
+// Pair-kernel stage layout (read once from the environment): one K block
+// of 128-byte operand rows per stage (default), or with AFMM_TC_ROW=64
+// 64-byte rows, two K blocks per stage (AFMM_TC_KSUB=1: one).  Measured at
+// n = 8192 / 16384 with 64-byte rows, two blocks per stage against one:
+// split BF16 kernel 1.54 against 1.55 ms, FP16 two slices 1.07 against
+// 1.11 ms, E4M3 digits 4.26 against 4.39 ms; three blocks (the two-slice
+// forms, three 72 KiB stages) 1-2% slower than two.
+inline int pair_layout() {
     static const int v = [] {
+        const char* r = std::getenv("AFMM_TC_ROW");
+        if (!(r && std::atoi(r) == 64)) return 128;
         const char* e = std::getenv("AFMM_TC_KSUB");
         return e && std::atoi(e) == 1 ? 1 : 2;
     }();
@@ -1227,9 +1247,17 @@ inline int pair_sub() {
 template <int SA, bool TOUT = false, int MODE = PM_SPLIT>
 afmm_status launch_tc_pair(const TcPlan* t, float* Z, int64_t ldz, int* status,
                            cudaStream_t st, int m0 = 0, int m1 = -1, int n0 = 0, int n1 = -1) {
-    if (pair_sub() == 2)
-        return launch_tc_pair_sub<SA, TOUT, MODE, 2>(t, Z, ldz, status, st, m0, m1, n0, n1);
-    return launch_tc_pair_sub<SA, TOUT, MODE, 1>(t, Z, ldz, status, st, m0, m1, n0, n1);
+    switch (pair_layout()) {
+        case 128:
+            return launch_tc_pair_sub<SA, TOUT, MODE, 1, 128>(t, Z, ldz, status, st, m0, m1,
+                                                              n0, n1);
+        case 2:
+            return launch_tc_pair_sub<SA, TOUT, MODE, 2, 64>(t, Z, ldz, status, st, m0, m1, n0,
+                                                             n1);
+        default:
+            return launch_tc_pair_sub<SA, TOUT, MODE, 1, 64>(t, Z, ldz, status, st, m0, m1, n0,
+                                                             n1);
+    }
 }
 
 // The split product with S = t->slices BF16 slices: the two-SM kernel when
@@ -1427,12 +1455,25 @@ afmm_status tc_bind_workspace(TcPlan* t, void* a, void* b, void* z, void* s) {
     // B side with 128-row boxes: each CTA of a pair loads half of a B tile.
     AFMM_TRY(tc_encode_map(t->tmap_b2, b, t->n, t->n, t->ld_b, sb, PR_HALF, es));
     AFMM_TRY(tc_encode_map(t->tmap_b3, b, t->n, t->n, t->ld_b, sb, PR_HALF / 2, es));
-    if (!t->sliced_a && t->slices > 0) {
+    const bool caseb = !t->sliced_a && t->slices > 0;
+    if (caseb) {
         // Case B as Z^T = Y^T X^T: the sliced Y^T rows are the A side.
         AFMM_TRY(tc_encode_map(t->tmap_at, b, t->n, t->n, t->ld_b, sb, TC_BM, es));
         AFMM_TRY(tc_encode_map(t->tmap_bt, a, t->n, t->n, t->ld_a, sa, TC_BN, es));
         AFMM_TRY(tc_encode_map(t->tmap_bt2, a, t->n, t->n, t->ld_a, sa, PR_HALF, es));
         AFMM_TRY(tc_encode_map(t->tmap_bt3, a, t->n, t->n, t->ld_a, sa, PR_HALF / 2, es));
+    }
+    if (t->pair) {
+        // The same maps with 128-byte rows for the pair kernel.
+        AFMM_TRY(tc_encode_map(t->tmap_aw, a, t->n, t->n, t->ld_a, sa, PR_HALF, es, 128));
+        AFMM_TRY(tc_encode_map(t->tmap_b2w, b, t->n, t->n, t->ld_b, sb, PR_HALF, es, 128));
+        AFMM_TRY(tc_encode_map(t->tmap_b3w, b, t->n, t->n, t->ld_b, sb, PR_HALF / 2, es, 128));
+        if (caseb) {
+            AFMM_TRY(tc_encode_map(t->tmap_atw, b, t->n, t->n, t->ld_b, sb, PR_HALF, es, 128));
+            AFMM_TRY(tc_encode_map(t->tmap_bt2w, a, t->n, t->n, t->ld_a, sa, PR_HALF, es, 128));
+            AFMM_TRY(
+                tc_encode_map(t->tmap_bt3w, a, t->n, t->n, t->ld_a, sa, PR_HALF / 2, es, 128));
+        }
     }
     t->maps_ready = true;
     return AFMM_OK;

@@ -50,6 +50,14 @@ struct TcPlan {
     alignas(64) unsigned char tmap_bt2[128];
     alignas(64) unsigned char tmap_b3[128];
     alignas(64) unsigned char tmap_bt3[128];
+    // The pair kernel's maps with 128-byte operand rows (128-byte swizzle):
+    // A (128-row boxes), the two B halves, and Case B's transposed roles.
+    alignas(64) unsigned char tmap_aw[128];
+    alignas(64) unsigned char tmap_atw[128];
+    alignas(64) unsigned char tmap_b2w[128];
+    alignas(64) unsigned char tmap_bt2w[128];
+    alignas(64) unsigned char tmap_b3w[128];
+    alignas(64) unsigned char tmap_bt3w[128];
     bool maps_ready = false;
     // Split form: run the two-SM (cta_group::2) product kernel.
     bool pair = false;
@@ -63,10 +71,11 @@ struct TcPlan {
 
 // TMA descriptor (written to `out`, 128 bytes, 64-byte aligned) of a stack
 // of `slices` matrices of es-byte elements (2: BF16, 1: E4M3), `rows` x
-// `cols` with leading dimension `ld` elements; boxes of 64 bytes of
-// columns x box_rows rows x 1 slice, 64-byte swizzle.
+// `cols` with leading dimension `ld` elements; boxes of row_bytes (64 or
+// 128) of columns x box_rows rows x 1 slice, swizzle of the same width.
 afmm_status tc_encode_map(void* out, void* base, int64_t cols, int64_t rows,
-                          int64_t ld, int slices, int box_rows, int es = 2);
+                          int64_t ld, int slices, int box_rows, int es = 2,
+                          int row_bytes = 64);
 
 // Operand conversions (tc_operands.cu): dst BF16 [slices][n][ldk].  Rows
 // kept (K-major A) or transposed (K-major B, dst row = source column).
