@@ -22,8 +22,28 @@ namespace {
 constexpr int X8_THREADS = 256;
 constexpr float kX8BaseMax = 255.f, kX8RepMax = 16.f;
 
+// Four byte-sized indices (each 0 .. 15) looked up in a 16-entry byte table
+// held in four words (byte k of word j is entry 4 j + k) with two byte
+// permutes: the indices' low three bits select within the table's halves,
+// bit 3 picks the half.  The tables, as template arguments: the E4M3 codes
+// of 0 .. 15 (E4M3_INT), and those of the high digit of a two's-complement
+// byte, whose high nibble k stands for k (k < 8) or k - 16 (E4M3_HI_I8).
+template <uint32_t T0, uint32_t T1, uint32_t T2, uint32_t T3>
+__device__ __forceinline__ uint32_t lut16_bytes(uint32_t b) {
+    const uint32_t packed = b | (b >> 4);                       // nibbles i0 i1 | i2 i3
+    const uint32_t sel = __byte_perm(packed, 0u, 0x0020u) & 0x7777u;
+    const uint32_t lo = __byte_perm(T0, T1, sel);
+    const uint32_t hi = __byte_perm(T2, T3, sel);
+    const uint32_t m = ((b >> 3) & 0x01010101u) * 0xFFu;       // indices 8 .. 15
+    return (lo & ~m) | (hi & m);
+}
+#define E4M3_INT 0x44403800u, 0x4E4C4A48u, 0x53525150u, 0x57565554u
+#define E4M3_HI_I8 0x44403800u, 0x4E4C4A48u, 0xCACCCED0u, 0xB8C0C4C8u
+
 // Rows of X as the two digit slices dst[(s * n + r) * ldk + c] (zero for
-// n <= c < ldk; ldk a multiple of 16), sixteen columns per thread.
+// n <= c < ldk; ldk a multiple of 16), sixteen columns per thread.  int8
+// and uint8 values are always integers within |x| <= 255: their digits are
+// the nibbles (the high one read as signed for int8), coded by table.
 template <int DT>
 __global__ void __launch_bounds__(X8_THREADS)
 x8_digit_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
@@ -34,6 +54,29 @@ x8_digit_rows_kernel(const void* __restrict__ src, int64_t n, int64_t lds,
     bool bad = false;
     for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
         const T* row = static_cast<const T*>(src) + r * lds;
+        if constexpr (DT == AFMM_I8 || DT == AFMM_U8) {
+            if (vec && c + 16 <= n) {
+                // Rows are 8-byte aligned here: two 8-byte loads.
+                const uint2 a = *reinterpret_cast<const uint2*>(row + c);
+                const uint2 b = *reinterpret_cast<const uint2*>(row + c + 8);
+                const uint32_t w[4] = {a.x, a.y, b.x, b.y};
+                uint32_t wh[4], wl[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    wl[k] = lut16_bytes<E4M3_INT>(w[k] & 0x0F0F0F0Fu);
+                    const uint32_t hn = (w[k] >> 4) & 0x0F0F0F0Fu;
+                    if constexpr (DT == AFMM_I8)
+                        wh[k] = lut16_bytes<E4M3_HI_I8>(hn);
+                    else
+                        wh[k] = lut16_bytes<E4M3_INT>(hn);
+                }
+                *reinterpret_cast<uint4*>(dst + r * ldk + c) =
+                    make_uint4(wh[0], wh[1], wh[2], wh[3]);
+                *reinterpret_cast<uint4*>(dst + (n + r) * ldk + c) =
+                    make_uint4(wl[0], wl[1], wl[2], wl[3]);
+                continue;
+            }
+        }
         float v[16];
         if (vec && c + 16 <= n) {
 #pragma unroll
