@@ -506,6 +506,34 @@ def test_tc_exact_f8_ragged(case, n):
     assert np.array_equal(Z.astype(np.int64), oracle_rows(inst))
 
 
+@pytest.mark.parametrize("xd,n,pad", [("u8", 512, 0), ("i8", 520, 0), ("u8", 600, 8),
+                                      ("i8", 777, 0), ("u8", 513, 3)])
+def test_tc_exact_f8_one_byte_base_values_every_code(xd, n, pad):
+    """int8 and uint8 Base values: their digits are the two nibbles, coded
+    by table when rows are 8-byte aligned (n + pad a multiple of 8) and by
+    the per-element path otherwise; every byte value appears in every
+    column position of the first 256 rows; uint8 Rep-factors.  Bit-exact."""
+    from paper_1308_2400_gb300 import Plan, make_desc
+    rng = np.random.default_rng(n + pad)
+    lo = 0 if xd == "u8" else -128
+    X = rng.integers(lo, lo + 256, size=(n, n))
+    r = np.arange(256).reshape(-1, 1)
+    X[:256] = (r + np.arange(n).reshape(1, -1)) % 256 + lo
+    Y = rng.integers(0, 17, size=(n, n))
+    ld = n + pad
+    npdt = np.uint8 if xd == "u8" else np.int8
+    Xb = np.zeros((n, ld), dtype=npdt)
+    Xb[:, :n] = X
+    Z = torch.full((n, n), -7, dtype=torch.int32, device="cuda")
+    p = Plan(make_desc(n, "A", xd, "u8", "i32", "exact", variant=X8, ldx=ld))
+    p(torch_of(Xb), torch_of(Y.astype(np.uint8)), Z)
+    p.sync()
+    p.close()
+    inst = W.Instance("A", X, Y, name=f"bytes_{xd}", x_dtype=xd, y_dtype="u8",
+                      z_dtype="i32", target="exact")
+    assert np.array_equal(Z.cpu().numpy().astype(np.int64), oracle_rows(inst))
+
+
 def test_tc_exact_f8_worst_case_digits():
     """Base values at +-255 and at digit boundaries (-1, -16, 15, 16),
     Rep-factors at 16: the largest digit sums the form allows."""
