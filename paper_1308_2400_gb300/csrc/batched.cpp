@@ -136,8 +136,9 @@ afmm_status build_state(BatchState* b, int count, const afmm_desc* descs, int de
         opbytes += ((size_t)sa * n * ldk * 2 + 255) / 256 * 256;
         opbytes += ((size_t)(4 - sa) * n * ldk * 2 + 255) / 256 * 256;
         row_prefix[j + 1] = row_prefix[j] + (int)n;
-        const int64_t tpr = (n + 63) / 64;
-        tt_prefix[j + 1] = tt_prefix[j] + (int)(tpr * tpr);
+        const bool byte_tiles = descs[b->tc_ids[j]].kase == AFMM_CASE_A &&
+                                dtype_size(descs[b->tc_ids[j]].y_dtype) == 1;
+        tt_prefix[j + 1] = tt_prefix[j] + (int)g_transpose_blocks(n, byte_tiles);
     }
     // widening jobs for CUDA-core instances with non-FP32 operands
     std::vector<int> wprefix(1, 0);

@@ -12,6 +12,17 @@ namespace afmm {
 // Tile shape of the grouped tensor-core kernel.
 constexpr int GB_BM = 128, GB_BN = 256, GB_BK = 32;
 
+// Rows per block of the B-operand transposition for Case A instances whose
+// Rep-factors are one-byte elements (byte tiles; every other instance is
+// transposed in 64 x 64 tiles).  Columns per block: 64.
+constexpr int GB_U8_ROWS = 128;
+
+// Blocks of the B-operand transposition of an instance of size n.
+inline int64_t g_transpose_blocks(int64_t n, bool byte_tiles) {
+    const int64_t cols = (n + 63) / 64;
+    return byte_tiles ? (n + GB_U8_ROWS - 1) / GB_U8_ROWS * cols : cols * cols;
+}
+
 // Device record of one tensor-core instance.
 struct GInst {
     const void* X;

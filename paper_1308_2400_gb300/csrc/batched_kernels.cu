@@ -170,29 +170,59 @@ g_rows_kernel(const GInst* __restrict__ inst, const int* __restrict__ row_prefix
     }
 }
 
-// Block b converts one 64 x 64 tile of the B operand (Y transposed to
-// K-major) of instance j = tt_job[b]: Case A widens the Rep-factors Y
-// (exact non-negative integers, |v| <= 256); Case B splits the real Y into
-// 3 slices.
+// The byte-tile path of g_transpose_kernel, kept out of line so that its
+// registers are allocated apart from the FP32-tile paths.
+__device__ __noinline__ int g_transpose_bytes(const GInst& g, int64_t r0, int64_t c0,
+                                              uint8_t (*bt)[64], uint32_t* lut) {
+    auto* B = static_cast<__nv_bfloat16*>(g.B);
+    const bool vec = rows_aligned16(g.Y, g.ldy, 1);
+    switch (g.y_dtype) {
+        case AFMM_E4M3:
+            return tile_bytes_transpose_convert<AFMM_E4M3, 1, true, false, GB_U8_ROWS>(
+                g.Y, g.n, g.ldy, r0, c0, B, g.ldk, 256.f, vec, bt, true, lut);
+        case AFMM_I8:
+            return tile_bytes_transpose_convert<AFMM_I8, 1, true, false, GB_U8_ROWS>(
+                g.Y, g.n, g.ldy, r0, c0, B, g.ldk, 256.f, vec, bt, true, lut);
+        default:
+            return tile_bytes_transpose_convert<AFMM_U8, 1, true, false, GB_U8_ROWS>(
+                g.Y, g.n, g.ldy, r0, c0, B, g.ldk, 256.f, vec, bt, true, lut);
+    }
+}
+
+// Block b converts one tile of the B operand (Y transposed to K-major) of
+// instance j = tt_job[b]: Case A widens the Rep-factors Y (exact
+// non-negative integers, |v| <= 256), one-byte ones in GB_U8_ROWS x 64 byte
+// tiles through a per-block table of the 256 codes
+// (tile_bytes_transpose_convert), others in 64 x 64 FP32 tiles; Case B
+// splits the real Y into 3 slices (64 x 64 FP32 tiles).
 __global__ void __launch_bounds__(256, 6)
 g_transpose_kernel(const GInst* __restrict__ inst, const int* __restrict__ tt_prefix,
                    const int* __restrict__ tt_job, int* __restrict__ flags,
                    int* __restrict__ status) {
-    __shared__ float tile[64][65];
+    // The FP32 tile; a byte tile and its code table reuse its first 9 KiB.
+    __shared__ alignas(16) float tile[64][65];
+    static_assert(GB_U8_ROWS * 64 + 256 * 4 <= 64 * 65 * 4, "byte tile fits");
     const int j = tt_job[blockIdx.x];
     const GInst& g = inst[j];
     const int64_t n = g.n;
     const int64_t tpr = (n + 63) / 64;
     const int64_t t = blockIdx.x - tt_prefix[j];
-    const int64_t r0 = (t / tpr) * 64, c0 = (t % tpr) * 64;
     auto* B = static_cast<__nv_bfloat16*>(g.B);
     int bits = 0;
-    if (g.kind == 0) {
+    const bool byte_rep =
+        g.y_dtype == AFMM_E4M3 || g.y_dtype == AFMM_I8 || g.y_dtype == AFMM_U8;
+    if (g.kind == 0 && byte_rep) {
+        const int64_t r0 = (t / tpr) * GB_U8_ROWS, c0 = (t % tpr) * 64;
+        bits = g_transpose_bytes(g, r0, c0, reinterpret_cast<uint8_t(*)[64]>(&tile[0][0]),
+                                 reinterpret_cast<uint32_t*>(&tile[0][0]) + GB_U8_ROWS * 64 / 4);
+    } else if (g.kind == 0) {
+        const int64_t r0 = (t / tpr) * 64, c0 = (t % tpr) * 64;
         G_DTYPE_SWITCH(g.y_dtype, (bits = tile_transpose_convert<DT, 1, true>(
                                        g.Y, n, g.ldy, r0, c0, B, g.ldk, 256.f,
                                        rows_aligned16(g.Y, g.ldy, sizeof(typename Elem<DT>::T)),
                                        tile, true)))
     } else {
+        const int64_t r0 = (t / tpr) * 64, c0 = (t % tpr) * 64;
         G_DTYPE_SWITCH(g.y_dtype, (tile_transpose_convert<DT, 3, false>(
                                        g.Y, n, g.ldy, r0, c0, B, g.ldk, 0.f,
                                        rows_aligned16(g.Y, g.ldy, sizeof(typename Elem<DT>::T)),
